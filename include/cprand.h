@@ -1,0 +1,207 @@
+/*
+ * cprand.h -- C ABI of the GB300 (sm_103a) CPRAND / CPRAND-MIX library.
+ *
+ * Randomized CP tensor decomposition after Battaglino, Ballard and Kolda, "A Practical
+ * Randomized CP Tensor Decomposition" (SIAM J. Matrix Anal. Appl., 2018; arXiv 1701.06600).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - A dense order-N tensor is stored column-major: entry (i_1, ..., i_N) (0-based) lives at
+ *    offset sum_n i_n * st_n with st_n = prod_{m<n} I_m, i.e. i_1 varies fastest.  This is the
+ *    order the mode-n unfolding of Sec. 2.1 assumes.  Offsets are 64-bit.
+ *  - Modes are 0-based in this API (mode n here is mode n+1 in the paper).
+ *  - Factor matrices A^(n) are I_n x R, row-major (the R entries of a row are contiguous), FP64.
+ *    lambda holds the R component weights of the normalized model (Sec. 2.1, eq. cpform+lambda).
+ *  - Every pointer inside cpr_tensor / cpr_ktensor and every buffer argument named *_dev or ws is
+ *    DEVICE memory owned by the caller.  The library allocates no device memory: scratch space is
+ *    the caller's workspace `ws` of at least cpr_workspace_size(...) bytes (256-byte aligned).
+ *  - All device work is enqueued on the caller's `stream` (a cudaStream_t passed as void*; NULL
+ *    means the legacy default stream).  Step entry points return right after enqueueing.  The
+ *    whole-algorithm entry points (cpr_cprand, cpr_cprand_mix, cpr_cprand_batched) synchronize
+ *    the stream once at the end to fill cpr_result.
+ *  - Return value: CPR_OK (0) or a CPR_E* status.  Arguments are checked on the host before any
+ *    work is enqueued; a failed check enqueues nothing.  Device-detected conditions (a
+ *    non-positive-definite Gram matrix, a non-finite fit) are reported through cpr_result.status.
+ *    Nothing on the device traps.
+ *  - Random quantities are Philox4x32-10 draws keyed by the 64-bit seed; counter words are
+ *    (item, (stream << 8) | (block << 4) | mode, iteration or column group, batch index), with
+ *    stream 0 = least-squares samples, 1 = fit entries, 2 = initial factors, 3 = mixing signs.
+ *    An index in [0, I) is floor(w * I / 2^32); a uniform value is (w >> 8) * 2^-24; a sign is
+ *    +1 when the low bit of w is 0.
+ */
+#ifndef CPRAND_H
+#define CPRAND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CPR_API __attribute__((visibility("default")))
+#else
+#define CPR_API
+#endif
+
+#define CPR_MAX_ORDER 8
+#define CPR_MAX_RANK 64
+
+typedef enum { CPR_F64 = 0, CPR_F32 = 1, CPR_BF16 = 2 } cpr_dtype;
+
+enum {
+  CPR_OK = 0,
+  CPR_EINVAL = 1,      /* bad argument: order, rank, S < R, dims, dtype, null pointer, ... */
+  CPR_EWORKSPACE = 2,  /* ws_bytes smaller than cpr_workspace_size() or ws misaligned */
+  CPR_ESINGULAR = 3,   /* sampled Gram matrix Z_S^T Z_S not positive definite */
+  CPR_ENONFINITE = 4,  /* a NaN or Inf reached the fit estimate */
+  CPR_ETIMEOUT = 5,    /* a bounded device-side wait expired */
+  CPR_ECUDA = 6        /* a CUDA runtime call failed */
+};
+
+/* Methods for cpr_workspace_size. */
+enum {
+  CPR_METHOD_CPRAND = 0,
+  CPR_METHOD_CPRAND_MIX = 1,
+  CPR_METHOD_UPDATE = 2,   /* cpr_sampled_update */
+  CPR_METHOD_FIT = 3,      /* cpr_fit_estimate */
+  CPR_METHOD_NORM = 4      /* cpr_tensor_norm */
+};
+
+typedef struct {
+  const void* data;              /* device, column-major */
+  int32_t dtype;                 /* cpr_dtype */
+  int32_t order;                 /* N, 2 .. CPR_MAX_ORDER */
+  int64_t dims[CPR_MAX_ORDER];   /* I_1 .. I_N, each >= 1 and < 2^31 */
+} cpr_tensor;
+
+typedef struct {
+  int32_t order;
+  int32_t rank;                  /* R, 1 .. CPR_MAX_RANK */
+  int64_t dims[CPR_MAX_ORDER];
+  double* lambda;                /* device, R */
+  double* factors[CPR_MAX_ORDER];/* device, factor n is I_n x R row-major */
+} cpr_ktensor;
+
+typedef struct {
+  int32_t max_iters;     /* outer-iteration cap (Sec. 4.2: 200) */
+  int32_t fixed_iters;   /* > 0: run exactly this many outer iterations, no other rule */
+  double fit_tol;        /* stop when |F_t - F_{t-1}| <= fit_tol, from the 2nd iteration (1e-4) */
+  double noise_eta;      /* >= 0: stop when F_t >= 1 - 1.2 eta (Sec. 4.2); < 0: rule off */
+  int32_t stall_iters;   /* > 0: stop when the best fit has not improved for this many iters */
+  int32_t init_from_out; /* 1: the initial factors of modes 2..N are read from out->factors
+                            (mixed basis for cpr_cprand_mix); 0: Philox U[0,1) */
+  int64_t fit_samples;   /* P_hat, entries of the sampled fit (Sec. 3.4: 2^14) */
+  uint64_t seed;         /* Philox key */
+  uint32_t batch_index;  /* counter word 3 (decomposition index inside a batch) */
+  uint32_t first_iter;   /* counter word 2 of the first outer iteration (resume) */
+  double* fit_trace_dev; /* device, >= max(max_iters, fixed_iters) doubles, or NULL */
+} cpr_opts;
+
+typedef struct {
+  int32_t iters;         /* outer iterations run */
+  int32_t status;        /* CPR_OK or a device-detected CPR_E* */
+  double fit_est;        /* last sampled fit estimate */
+  double norm_x;         /* ||X|| (Frobenius) */
+  int64_t kernel_launches; /* kernels this call put on the GPU */
+} cpr_result;
+
+/* Fill *opts with the paper's defaults (Sec. 4.2): max_iters 200, fit_tol 1e-4, noise rule off,
+ * no stall rule, P_hat = 2^14, seed 0, random initial factors. */
+CPR_API void cpr_default_opts(cpr_opts* opts);
+
+/* Text for a status code; never NULL. */
+CPR_API const char* cpr_status_string(int status);
+
+/* S = 10 R ln R rounded to nearest (Sec. 3.2; Sec. 4.2 prints S = 80 for R = 5, 108 for R = 6). */
+CPR_API int64_t cpr_sample_size(int R);
+
+/* Bytes of workspace the given method needs for tensor X, rank R and S samples; 0 on a bad
+ * argument.  For CPR_METHOD_FIT, S is ignored and opts->fit_samples sizes the fit set. */
+CPR_API size_t cpr_workspace_size(int method, const cpr_tensor* X, int R, int64_t S, const cpr_opts* opts);
+
+/* ---------------------------------------------------------------------------------------------
+ * Whole algorithms
+ * ------------------------------------------------------------------------------------------- */
+
+/* CPRAND (Alg. 3): randomized ALS.  Each outer iteration updates modes 1..N in turn; the mode-n
+ * update draws S fresh multi-indices, builds the sampled Khatri-Rao rows Z_S (Alg. 2), gathers
+ * the matching mode-n fibers X_S, solves min ||Z_S A^T - X_S^T|| through the R x R normal
+ * equations (FP64 Gram and Cholesky; the contraction X_S Z_S accumulates in FP32, or FP64 for an
+ * FP64 tensor) and normalizes the columns into lambda.  After each outer iteration the sampled
+ * fit of Sec. 3.4 (fixed P_hat entries) drives the stopping rules of Sec. 4.2 on the device.
+ * Output: out->lambda and out->factors (normalized columns).  out->order/rank/dims must match X
+ * and R.  S >= R. */
+CPR_API int cpr_cprand(const cpr_tensor* X, int R, int64_t S, const cpr_opts* opts, cpr_ktensor* out,
+               cpr_result* result, void* ws, size_t ws_bytes, void* stream);
+
+/* CPRAND-MIX in its real-transform form (Alg. 5, "CPRAND-PREMIX"): mix every mode with F_n D_n
+ * (D_n Philox signs, F_n the orthonormal DCT-II), run CPRAND on the mixed tensor (held in the
+ * workspace; X itself is not modified), then unmix A^(n) = D_n F_n^T A^^(n).  The stopping test
+ * runs on the mixed tensor, whose norm equals ||X||. */
+CPR_API int cpr_cprand_mix(const cpr_tensor* X, int R, int64_t S, const cpr_opts* opts, cpr_ktensor* out,
+                   cpr_result* result, void* ws, size_t ws_bytes, void* stream);
+
+/* Many independent decompositions at once (the paper's multiple random starts, Sec. 4.2): B
+ * problems of any shapes and ranks (all of the same order and dtype) advance together, every
+ * kernel launch serving all of them; each stops on its own rule.  opts[b].batch_index should be
+ * b.  mix != 0 runs CPRAND-MIX for every problem.  Workspace from cpr_batched_workspace_size. */
+CPR_API size_t cpr_batched_workspace_size(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss,
+                                  const cpr_opts* opts, int mix);
+CPR_API int cpr_cprand_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss,
+                       const cpr_opts* opts, int mix, cpr_ktensor* outs, cpr_result* results,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Steps of the hot path (each is also a parity-test hook)
+ * ------------------------------------------------------------------------------------------- */
+
+/* Sampled multi-indices of one mode update (Alg. 3, "define sampling operator"): for samples
+ * j < S, idx_dev[j*N + m] = i_m^(j) for m != mode (idx_dev[j*N + mode] = 0), drawn from Philox
+ * stream 0 with counter (j, mode, t, b); off_dev[j] = sum_{m != mode} i_m st_m, the storage
+ * offset of the first entry of the sampled fiber (Sec. 2.1 index map).  Either output may be
+ * NULL.  idx_dev: S*N uint32; off_dev: S int64. */
+CPR_API int cpr_sample_indices(const cpr_tensor* X, int mode, int64_t S, uint64_t seed, uint32_t b,
+                       uint32_t t, uint32_t* idx_dev, int64_t* off_dev, void* stream);
+
+/* Fiber gather X_S = (S X_(n)^T)^T (Sec. 3.2): xs_dev[i + I_n * j] = X[off_dev[j] + i * st_mode]
+ * for i < I_n, j < S, a bit copy in X's dtype (I_n x S, column-major). */
+CPR_API int cpr_gather_fibers(const cpr_tensor* X, int mode, int64_t S, const int64_t* off_dev,
+                      void* xs_dev, void* stream);
+
+/* One mode-n update of Alg. 3: sample (seed, b, t), SKR, gather, contract, FP64 Gram +
+ * Cholesky solve, normalize.  Reads K->factors[m] for m != mode (FP64; rounded to FP32 for the
+ * contraction unless X is FP64), writes K->factors[mode] and K->lambda.  result may be NULL;
+ * when given, this call synchronizes the stream and reports a singular Gram in result->status. */
+CPR_API int cpr_sampled_update(const cpr_tensor* X, cpr_ktensor* K, int mode, int64_t S, uint64_t seed,
+                       uint32_t b, uint32_t t, cpr_result* result, void* ws, size_t ws_bytes,
+                       void* stream);
+
+/* Sampled fit estimate (Sec. 3.4): F^ = 1 - sqrt(P * mean_i e_i^2) / ||X|| over P_hat entries
+ * drawn from Philox stream 1 (seed, b), e_i = x_i - sum_r lambda_r prod_n A^(n)(i_n, r).  norm_x
+ * < 0 computes ||X|| first.  Writes the estimate to *fit_host (synchronizes the stream). */
+CPR_API int cpr_fit_estimate(const cpr_tensor* X, const cpr_ktensor* K, int64_t P_hat, uint64_t seed,
+                     uint32_t b, double norm_x, double* fit_host, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* Mixing preprocess (Alg. 5, mixing step): out_dev = X x_1 F_1 D_1 ... x_N F_N D_N, mode 1
+ * first, in X's dtype and layout (FP32 accumulation; FP64 for an FP64 tensor).  out_dev must
+ * not overlap X.  ws from cpr_workspace_size(CPR_METHOD_CPRAND_MIX, ...) is enough. */
+CPR_API int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, uint32_t b, void* ws,
+                   size_t ws_bytes, void* stream);
+
+/* Unmixing (Alg. 5, last step): out->factors[n] = D_n F_n^T Khat->factors[n] (FP64), lambda
+ * copied.  Khat and out may not share factor buffers. */
+CPR_API int cpr_unmix_factors(const cpr_ktensor* Khat, cpr_ktensor* out, uint64_t seed, uint32_t b,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* ||X||_F (FP64 accumulation) written to *norm_host (synchronizes the stream). */
+CPR_API int cpr_tensor_norm(const cpr_tensor* X, double* norm_host, void* ws, size_t ws_bytes,
+                    void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPRAND_H */

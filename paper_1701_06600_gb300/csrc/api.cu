@@ -1,0 +1,660 @@
+// C-ABI entry points of libcprand (declared in include/cprand.h): argument checks, workspace
+// layout, and the order of kernel launches.  No device memory is allocated here; every buffer is
+// carved out of the caller's workspace.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace cpr;
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Carves typed sub-buffers out of the workspace; with a null base it only measures.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <class T> T* take(size_t count) {
+    off = align256(off);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+int elem_size(int dtype) { return dtype == CPR_F64 ? 8 : (dtype == CPR_F32 ? 4 : 2); }
+
+int check_tensor(const cpr_tensor* X, bool need_data) {
+  if (!X) return CPR_EINVAL;
+  if (X->order < 2 || X->order > CPR_MAX_ORDER) return CPR_EINVAL;
+  if (X->dtype < CPR_F64 || X->dtype > CPR_BF16) return CPR_EINVAL;
+  if (need_data && !X->data) return CPR_EINVAL;
+  double P = 1.0;
+  for (int n = 0; n < X->order; ++n) {
+    if (X->dims[n] < 1 || X->dims[n] >= (int64_t(1) << 31)) return CPR_EINVAL;
+    P *= (double)X->dims[n];
+  }
+  if (P > 4.0e18) return CPR_EINVAL;
+  return CPR_OK;
+}
+
+int64_t prod_dims(const cpr_tensor* X) {
+  int64_t P = 1;
+  for (int n = 0; n < X->order; ++n) P *= X->dims[n];
+  return P;
+}
+
+int check_rank_samples(int R, int64_t S) {
+  if (R < 1 || R > CPR_MAX_RANK) return CPR_EINVAL;
+  if (S < R || S > INT32_MAX) return CPR_EINVAL;
+  return CPR_OK;
+}
+
+int check_ktensor(const cpr_ktensor* K, const cpr_tensor* X, int R) {
+  if (!K || K->order != X->order || K->rank != R || !K->lambda) return CPR_EINVAL;
+  for (int n = 0; n < X->order; ++n)
+    if (K->dims[n] != X->dims[n] || !K->factors[n]) return CPR_EINVAL;
+  return CPR_OK;
+}
+
+int check_ws(void* ws, size_t ws_bytes, size_t need) {
+  if (need > 0 && !ws) return CPR_EWORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CPR_EWORKSPACE;
+  if (ws_bytes < need) return CPR_EWORKSPACE;
+  return CPR_OK;
+}
+
+#define CPR_CUDA(call)                 \
+  do {                                 \
+    cudaError_t e_ = (call);           \
+    if (e_ != cudaSuccess) return CPR_ECUDA; \
+  } while (0)
+
+// Mixing buffers of one problem.
+struct MixBufs {
+  float* W32[kMaxOrder] = {};
+  double* W64[kMaxOrder] = {};
+  double* F64[kMaxOrder] = {};
+  double* sg[kMaxOrder] = {};
+  void* xhat = nullptr;   // mixed tensor
+};
+
+// A batch of problems laid out in the workspace.
+struct Plan {
+  int B = 0, mix = 0, dtype = 0;
+  GridInfo g{};
+  std::vector<Prob> probs;
+  std::vector<MixBufs> mixb;
+  Prob* d_probs = nullptr;
+  State* d_states = nullptr;
+  int* d_counter = nullptr;
+  double* d_normpart = nullptr;
+  void* d_tmp = nullptr;     // shared ping-pong buffer of the mixing passes
+  int normblk = 0;
+  size_t bytes = 0;
+};
+
+struct ProbSpec {
+  const cpr_tensor* X;
+  int R;
+  int64_t S;
+  int64_t P_hat;
+  const cpr_opts* opts;
+  double* const* user_A64;   // non-null: factors live in caller buffers (step entry points)
+  double* user_lambda;
+};
+
+// Pick the sample split of the contraction so one mode update of the whole batch fills the GPU
+// with a few blocks per SM.
+void choose_split(int B, int64_t imax_mean, int S, int* spl, int* nsplit) {
+  const int64_t target = std::max<int64_t>(1, (4 * 152) / std::max(1, B));
+  const int64_t ntile = std::max<int64_t>(1, (imax_mean + kContractRows - 1) / kContractRows);
+  int64_t ns = (target + ntile - 1) / ntile;
+  ns = std::max<int64_t>(1, std::min<int64_t>(ns, (S + 7) / 8));
+  int64_t sp = (S + ns - 1) / ns;
+  sp = std::min<int64_t>(sp, 64);   // keeps the split's offsets + Z rows under 48 KB of shared memory
+  ns = (S + sp - 1) / sp;
+  *spl = (int)sp;
+  *nsplit = (int)ns;
+}
+
+// Lays out (ws == nullptr: measures) the buffers of B problems.  mix: also the mixing buffers.
+Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws) {
+  Plan pl;
+  pl.B = B;
+  pl.mix = mix;
+  pl.dtype = specs[0].X->dtype;
+  Carver cv(ws);
+  pl.d_probs = cv.take<Prob>(B);
+  pl.d_states = cv.take<State>(B);
+  pl.d_counter = cv.take<int>(4);
+  int64_t maxP = 0;
+  for (int b = 0; b < B; ++b) maxP = std::max(maxP, prod_dims(specs[b].X));
+  pl.normblk = sumsq_blocks(maxP);
+  pl.d_normpart = cv.take<double>(pl.normblk);
+  if (mix) pl.d_tmp = cv.take<unsigned char>((size_t)maxP * elem_size(pl.dtype));
+  GridInfo& g = pl.g;
+  memset(&g, 0, sizeof(g));
+  g.B = B;
+  g.dtype = pl.dtype;
+  g.any_f64 = pl.dtype == CPR_F64;
+  g.max_P = maxP;
+  pl.probs.resize(B);
+  pl.mixb.resize(B);
+  const bool f64 = pl.dtype == CPR_F64;
+  for (int b = 0; b < B; ++b) {
+    const ProbSpec& sp = specs[b];
+    const cpr_tensor* X = sp.X;
+    Prob& p = pl.probs[b];
+    memset(&p, 0, sizeof(p));
+    p.N = X->order;
+    p.R = sp.R;
+    p.S = (int)sp.S;
+    p.dtype = X->dtype;
+    int64_t st = 1, imax = 0, isum = 0;
+    for (int n = 0; n < p.N; ++n) {
+      p.dims[n] = X->dims[n];
+      p.st[n] = st;
+      st *= X->dims[n];
+      imax = std::max(imax, X->dims[n]);
+      isum += X->dims[n];
+    }
+    p.P = st;
+    p.X = X->data;
+    p.imax = (int)imax;
+    const int R = p.R, N = p.N, S = p.S;
+    for (int n = 0; n < N; ++n) {
+      p.A32[n] = cv.take<float>((size_t)p.dims[n] * R);
+      p.A64[n] = sp.user_A64 ? sp.user_A64[n] : cv.take<double>((size_t)p.dims[n] * R);
+    }
+    p.lambda = sp.user_lambda ? sp.user_lambda : cv.take<double>(R);
+    if (S > 0) {
+      choose_split(B, isum / N, S, &p.spl, &p.nsplit);
+      p.ng = (S + kGramChunk - 1) / kGramChunk;
+      p.idx = cv.take<uint32_t>((size_t)S * N);
+      p.off = cv.take<int64_t>(S);
+      if (f64) p.Z64 = cv.take<double>((size_t)S * R);
+      else p.Z32 = cv.take<float>((size_t)S * R);
+      p.Gpart = cv.take<double>((size_t)p.ng * R * R);
+      p.L = cv.take<double>((size_t)R * R);
+      p.Mpart = cv.take<unsigned char>((size_t)p.nsplit * imax * R * (f64 ? 8 : 4));
+      p.Npart = cv.take<double>((size_t)((imax + kSolveRows - 1) / kSolveRows) * R);
+    }
+    p.P_hat = (int)sp.P_hat;
+    if (p.P_hat > 0) {
+      p.nfb = (p.P_hat + kFitThreads - 1) / kFitThreads;
+      p.fit_idx = cv.take<uint32_t>((size_t)p.P_hat * N);
+      p.fit_x = cv.take<double>(p.P_hat);
+      p.fit_part = cv.take<double>(p.nfb);
+    }
+    const cpr_opts* o = sp.opts;
+    if (o) {
+      p.max_iters = o->max_iters;
+      p.fixed_iters = o->fixed_iters;
+      p.stall_iters = o->stall_iters;
+      p.tol = o->fit_tol;
+      p.eta = o->noise_eta;
+      p.seed = o->seed;
+      p.b = o->batch_index;
+      p.t0 = o->first_iter;
+      p.trace = o->fit_trace_dev;
+    }
+    p.state = pl.d_states + b;   // pointer arithmetic on a null base only measures
+    if (mix) {
+      MixBufs& mb = pl.mixb[b];
+      for (int n = 0; n < N; ++n) {
+        const size_t I = (size_t)p.dims[n];
+        if (f64) mb.W64[n] = cv.take<double>(I * I);
+        else mb.W32[n] = cv.take<float>(I * I);
+        mb.F64[n] = cv.take<double>(I * I);
+        mb.sg[n] = cv.take<double>(I);
+      }
+      mb.xhat = cv.take<unsigned char>((size_t)p.P * elem_size(pl.dtype));
+      p.X = mb.xhat;
+    }
+    // grid maxima
+    g.max_S = std::max(g.max_S, S);
+    g.max_ng = std::max(g.max_ng, p.ng);
+    g.max_spl = std::max(g.max_spl, p.spl);
+    g.max_nfb = std::max(g.max_nfb, p.nfb);
+    g.max_R = std::max(g.max_R, R);
+    g.max_Phat = std::max(g.max_Phat, p.P_hat);
+    for (int n = 0; n < N; ++n) {
+      g.max_I[n] = std::max<int>(g.max_I[n], (int)p.dims[n]);
+      const int ntile = (int)((p.dims[n] + kContractRows - 1) / kContractRows);
+      g.max_tiles_x_split[n] = std::max(g.max_tiles_x_split[n], ntile * std::max(1, p.nsplit));
+    }
+  }
+  pl.bytes = align256(cv.off);
+  return pl;
+}
+
+cpr_opts defaults() {
+  cpr_opts o;
+  cpr_default_opts(&o);
+  return o;
+}
+
+// Enqueue the mode loop and the fit/stop test of one outer iteration for the whole batch.
+int enqueue_iteration(const Plan& pl, int maxN, int use_cond, unsigned long long cond, cudaStream_t s,
+                      int64_t* launches) {
+  for (int n = 0; n < maxN; ++n) {
+    CPR_CUDA(launch_sample_skr_gram(pl.d_probs, pl.g, n, s));
+    CPR_CUDA(launch_gather_contract(pl.d_probs, pl.g, n, s));
+    CPR_CUDA(launch_gram_chol(pl.d_probs, pl.g, n, s));
+    CPR_CUDA(launch_solve_rows(pl.d_probs, pl.g, n, s));
+    CPR_CUDA(launch_normalize(pl.d_probs, pl.g, n, s));
+    *launches += 5;
+  }
+  CPR_CUDA(launch_fit_partial(pl.d_probs, pl.g, s));
+  CPR_CUDA(launch_fit_finish(pl.d_probs, pl.g, pl.d_counter, cond, use_cond, s));
+  *launches += 2;
+  return CPR_OK;
+}
+
+int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, const cpr_opts* opts, int mix,
+                cpr_ktensor* outs, cpr_result* results, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (B < 1 || !Xs || !Rs || !Ss || !outs) return CPR_EINVAL;
+  std::vector<cpr_opts> op(B);
+  std::vector<ProbSpec> specs(B);
+  int maxN = 0;
+  for (int b = 0; b < B; ++b) {
+    if (int st = check_tensor(&Xs[b], true)) return st;
+    if (Xs[b].dtype != Xs[0].dtype) return CPR_EINVAL;
+    if (int st = check_rank_samples(Rs[b], Ss[b])) return st;
+    if (int st = check_ktensor(&outs[b], &Xs[b], Rs[b])) return st;
+    op[b] = opts ? opts[b] : defaults();
+    if (!opts) op[b].batch_index = (uint32_t)b;
+    if (op[b].fit_samples < 1 || op[b].fit_samples > INT32_MAX) return CPR_EINVAL;
+    if (op[b].max_iters < 1 && op[b].fixed_iters < 1) return CPR_EINVAL;
+    specs[b] = ProbSpec{&Xs[b], Rs[b], Ss[b], op[b].fit_samples, &op[b], nullptr, nullptr};
+    maxN = std::max(maxN, (int)Xs[b].order);
+  }
+  const Plan measure = make_plan(B, specs.data(), mix, nullptr);
+  if (int st = check_ws(ws, ws_bytes, measure.bytes)) return st;
+  Plan pl = make_plan(B, specs.data(), mix, ws);
+  int64_t launches = 0;
+  CPR_CUDA(cudaMemcpyAsync(pl.d_probs, pl.probs.data(), sizeof(Prob) * B, cudaMemcpyHostToDevice, s));
+  CPR_CUDA(cudaMemsetAsync(pl.d_counter, 0, 4 * sizeof(int), s));
+  CPR_CUDA(launch_init_state(pl.d_probs, B, s));
+  ++launches;
+  for (int b = 0; b < B; ++b) {
+    const Prob& p = pl.probs[b];
+    // ||X|| on the caller's tensor (equal to the mixed tensor's norm, Alg. 5)
+    CPR_CUDA(launch_sumsq(Xs[b].data, p.dtype, p.P, pl.d_normpart, pl.normblk, s));
+    CPR_CUDA(launch_sumsq_finish(pl.d_normpart, pl.normblk, nullptr, pl.d_states + b, 1, s));
+    launches += 2;
+    if (mix) {
+      const MixBufs& mb = pl.mixb[b];
+      for (int n = 0; n < p.N; ++n) {
+        CPR_CUDA(launch_build_mix_ops((int)p.dims[n], p.seed, p.b, n, mb.W32[n], mb.W64[n], mb.F64[n], mb.sg[n], s));
+        ++launches;
+      }
+      // mode passes alternate between the mixed-tensor buffer and the shared temporary so that
+      // the last pass lands in xhat
+      const void* src = Xs[b].data;
+      void* bufs[2] = {mb.xhat, pl.d_tmp};
+      int cur = (p.N % 2 == 1) ? 0 : 1;
+      for (int n = 0; n < p.N; ++n) {
+        CPR_CUDA(launch_mix_mode(src, bufs[cur], p.dtype, p.N, p.dims, n, mb.W32[n], mb.W64[n], s));
+        ++launches;
+        src = bufs[cur];
+        cur ^= 1;
+      }
+    }
+    if (op[b].init_from_out) {
+      for (int n = 1; n < p.N; ++n)
+        CPR_CUDA(cudaMemcpyAsync(p.A64[n], outs[b].factors[n], sizeof(double) * p.dims[n] * p.R,
+                                 cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  // initial factors: every problem of the batch is either random or caller-given
+  {
+    bool any_from = false, any_rand = false;
+    for (int b = 0; b < B; ++b) (op[b].init_from_out ? any_from : any_rand) = true;
+    if (any_from && any_rand) return CPR_EINVAL;
+    CPR_CUDA(launch_init_factors(pl.d_probs, pl.g, any_from ? 1 : 0, s));
+    ++launches;
+    if (any_from) {  // lambda = 1 for caller-given starts
+      std::vector<double> ones(CPR_MAX_RANK, 1.0);
+      for (int b = 0; b < B; ++b)
+        CPR_CUDA(cudaMemcpyAsync(pl.probs[b].lambda, ones.data(), sizeof(double) * pl.probs[b].R,
+                                 cudaMemcpyHostToDevice, s));
+    }
+  }
+  CPR_CUDA(launch_fit_setup(pl.d_probs, pl.g, s));
+  ++launches;
+  // outer iterations; every problem stops on its own rule, the loop ends when all have
+  int cap = 0;
+  for (int b = 0; b < B; ++b) cap = std::max(cap, op[b].fixed_iters > 0 ? op[b].fixed_iters : op[b].max_iters);
+  std::vector<State> hs(B);
+  int ran = 0, chunk = 4;
+  while (ran < cap) {
+    const int todo = std::min(chunk, cap - ran);
+    for (int c = 0; c < todo; ++c)
+      if (int st = enqueue_iteration(pl, maxN, 0, 0ull, s, &launches)) return st;
+    ran += todo;
+    CPR_CUDA(cudaMemcpyAsync(hs.data(), pl.d_states, sizeof(State) * B, cudaMemcpyDeviceToHost, s));
+    CPR_CUDA(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int b = 0; b < B; ++b) all = all && hs[b].done;
+    if (all) break;
+    chunk = std::min(chunk * 2, 16);
+  }
+  // outputs (unmixed for CPRAND-MIX)
+  for (int b = 0; b < B; ++b) {
+    const Prob& p = pl.probs[b];
+    for (int n = 0; n < p.N; ++n) {
+      if (mix) {
+        CPR_CUDA(launch_unmix(p.A64[n], outs[b].factors[n], pl.mixb[b].F64[n], pl.mixb[b].sg[n], (int)p.dims[n], p.R, s));
+        ++launches;
+      } else {
+        CPR_CUDA(cudaMemcpyAsync(outs[b].factors[n], p.A64[n], sizeof(double) * p.dims[n] * p.R,
+                                 cudaMemcpyDeviceToDevice, s));
+      }
+    }
+    CPR_CUDA(cudaMemcpyAsync(outs[b].lambda, p.lambda, sizeof(double) * p.R, cudaMemcpyDeviceToDevice, s));
+  }
+  CPR_CUDA(cudaMemcpyAsync(hs.data(), pl.d_states, sizeof(State) * B, cudaMemcpyDeviceToHost, s));
+  CPR_CUDA(cudaStreamSynchronize(s));
+  if (results) {
+    for (int b = 0; b < B; ++b) {
+      results[b].iters = hs[b].iter;
+      results[b].status = hs[b].status;
+      results[b].fit_est = hs[b].last_fit;
+      results[b].norm_x = hs[b].norm_x;
+      results[b].kernel_launches = launches;
+    }
+  }
+  return CPR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cpr_default_opts(cpr_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->max_iters = 200;
+  o->fixed_iters = 0;
+  o->fit_tol = 1e-4;
+  o->noise_eta = -1.0;
+  o->stall_iters = 0;
+  o->init_from_out = 0;
+  o->fit_samples = 16384;
+  o->seed = 0;
+  o->batch_index = 0;
+  o->first_iter = 0;
+  o->fit_trace_dev = nullptr;
+}
+
+const char* cpr_status_string(int status) {
+  switch (status) {
+    case CPR_OK: return "ok";
+    case CPR_EINVAL: return "invalid argument";
+    case CPR_EWORKSPACE: return "workspace too small or misaligned";
+    case CPR_ESINGULAR: return "sampled Gram matrix is not positive definite";
+    case CPR_ENONFINITE: return "non-finite value in the fit estimate";
+    case CPR_ETIMEOUT: return "bounded device wait expired";
+    case CPR_ECUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+int64_t cpr_sample_size(int R) {
+  if (R < 1) return 0;
+  return (int64_t)floor(10.0 * R * log((double)R) + 0.5);
+}
+
+size_t cpr_workspace_size(int method, const cpr_tensor* X, int R, int64_t S, const cpr_opts* opts) {
+  if (check_tensor(X, false)) return 0;
+  cpr_opts o = opts ? *opts : defaults();
+  switch (method) {
+    case CPR_METHOD_CPRAND:
+    case CPR_METHOD_CPRAND_MIX: {
+      if (check_rank_samples(R, S)) return 0;
+      ProbSpec sp{X, R, S, o.fit_samples, &o, nullptr, nullptr};
+      return make_plan(1, &sp, method == CPR_METHOD_CPRAND_MIX, nullptr).bytes;
+    }
+    case CPR_METHOD_UPDATE: {
+      if (check_rank_samples(R, S)) return 0;
+      static double* dummy[CPR_MAX_ORDER] = {};
+      ProbSpec sp{X, R, S, 0, &o, dummy, (double*)nullptr};
+      // caller-owned factors and lambda take no workspace
+      Plan pl = make_plan(1, &sp, 0, nullptr);
+      return pl.bytes;
+    }
+    case CPR_METHOD_FIT: {
+      if (R < 1 || R > CPR_MAX_RANK || o.fit_samples < 1 || o.fit_samples > INT32_MAX) return 0;
+      static double* dummy[CPR_MAX_ORDER] = {};
+      ProbSpec sp{X, R, 0, o.fit_samples, &o, dummy, nullptr};
+      return make_plan(1, &sp, 0, nullptr).bytes;
+    }
+    case CPR_METHOD_NORM:
+      return align256(sizeof(double) * (sumsq_blocks(prod_dims(X)) + 1)) + 256;
+    default:
+      return 0;
+  }
+}
+
+int cpr_cprand(const cpr_tensor* X, int R, int64_t S, const cpr_opts* opts, cpr_ktensor* out, cpr_result* result,
+               void* ws, size_t ws_bytes, void* stream) {
+  if (!X) return CPR_EINVAL;
+  return run_batched(1, X, &R, &S, opts, 0, out, result, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int cpr_cprand_mix(const cpr_tensor* X, int R, int64_t S, const cpr_opts* opts, cpr_ktensor* out,
+                   cpr_result* result, void* ws, size_t ws_bytes, void* stream) {
+  if (!X) return CPR_EINVAL;
+  return run_batched(1, X, &R, &S, opts, 1, out, result, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+size_t cpr_batched_workspace_size(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss,
+                                  const cpr_opts* opts, int mix) {
+  if (B < 1 || !Xs || !Rs || !Ss) return 0;
+  std::vector<cpr_opts> op(B);
+  std::vector<ProbSpec> specs(B);
+  for (int b = 0; b < B; ++b) {
+    if (check_tensor(&Xs[b], false) || check_rank_samples(Rs[b], Ss[b])) return 0;
+    if (Xs[b].dtype != Xs[0].dtype) return 0;
+    op[b] = opts ? opts[b] : defaults();
+    specs[b] = ProbSpec{&Xs[b], Rs[b], Ss[b], op[b].fit_samples, &op[b], nullptr, nullptr};
+  }
+  return make_plan(B, specs.data(), mix, nullptr).bytes;
+}
+
+int cpr_cprand_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, const cpr_opts* opts, int mix,
+                       cpr_ktensor* outs, cpr_result* results, void* ws, size_t ws_bytes, void* stream) {
+  return run_batched(B, Xs, Rs, Ss, opts, mix ? 1 : 0, outs, results, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int cpr_sample_indices(const cpr_tensor* X, int mode, int64_t S, uint64_t seed, uint32_t b, uint32_t t,
+                       uint32_t* idx_dev, int64_t* off_dev, void* stream) {
+  if (int st = check_tensor(X, false)) return st;
+  if (mode < 0 || mode >= X->order || S < 0 || S > INT32_MAX) return CPR_EINVAL;
+  if (S > 0 && !idx_dev && !off_dev) return CPR_EINVAL;
+  CPR_CUDA(launch_sample_only(X->data, X->order, X->dims, mode, S, seed, b, t, idx_dev, off_dev,
+                              (cudaStream_t)stream));
+  return CPR_OK;
+}
+
+int cpr_gather_fibers(const cpr_tensor* X, int mode, int64_t S, const int64_t* off_dev, void* xs_dev, void* stream) {
+  if (int st = check_tensor(X, true)) return st;
+  if (mode < 0 || mode >= X->order || S < 0 || S > INT32_MAX) return CPR_EINVAL;
+  if (S > 0 && (!off_dev || !xs_dev)) return CPR_EINVAL;
+  int64_t st = 1;
+  for (int m = 0; m < mode; ++m) st *= X->dims[m];
+  CPR_CUDA(launch_gather_only(X->data, X->dtype, X->dims[mode], st, S, off_dev, xs_dev, (cudaStream_t)stream));
+  return CPR_OK;
+}
+
+int cpr_sampled_update(const cpr_tensor* X, cpr_ktensor* K, int mode, int64_t S, uint64_t seed, uint32_t b,
+                       uint32_t t, cpr_result* result, void* ws, size_t ws_bytes, void* stream) {
+  if (int st = check_tensor(X, true)) return st;
+  if (!K) return CPR_EINVAL;
+  const int R = K->rank;
+  if (int st = check_rank_samples(R, S)) return st;
+  if (int st = check_ktensor(K, X, R)) return st;
+  if (mode < 0 || mode >= X->order) return CPR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cpr_opts o = defaults();
+  o.seed = seed;
+  o.batch_index = b;
+  o.first_iter = t;
+  o.fixed_iters = 1;
+  ProbSpec sp{X, R, S, 0, &o, K->factors, K->lambda};
+  const Plan measure = make_plan(1, &sp, 0, nullptr);
+  if (int st = check_ws(ws, ws_bytes, measure.bytes)) return st;
+  Plan pl = make_plan(1, &sp, 0, ws);
+  CPR_CUDA(cudaMemcpyAsync(pl.d_probs, pl.probs.data(), sizeof(Prob), cudaMemcpyHostToDevice, s));
+  CPR_CUDA(launch_init_state(pl.d_probs, 1, s));
+  CPR_CUDA(launch_init_factors(pl.d_probs, pl.g, 1, s));
+  CPR_CUDA(launch_sample_skr_gram(pl.d_probs, pl.g, mode, s));
+  CPR_CUDA(launch_gather_contract(pl.d_probs, pl.g, mode, s));
+  CPR_CUDA(launch_gram_chol(pl.d_probs, pl.g, mode, s));
+  CPR_CUDA(launch_solve_rows(pl.d_probs, pl.g, mode, s));
+  CPR_CUDA(launch_normalize(pl.d_probs, pl.g, mode, s));
+  if (result) {
+    State h;
+    CPR_CUDA(cudaMemcpyAsync(&h, pl.d_states, sizeof(State), cudaMemcpyDeviceToHost, s));
+    CPR_CUDA(cudaStreamSynchronize(s));
+    result->iters = 0;
+    result->status = h.status;
+    result->fit_est = NAN;
+    result->norm_x = NAN;
+    result->kernel_launches = 7;
+  }
+  return CPR_OK;
+}
+
+int cpr_fit_estimate(const cpr_tensor* X, const cpr_ktensor* K, int64_t P_hat, uint64_t seed, uint32_t b,
+                     double norm_x, double* fit_host, void* ws, size_t ws_bytes, void* stream) {
+  if (int st = check_tensor(X, true)) return st;
+  if (!K || !fit_host) return CPR_EINVAL;
+  const int R = K->rank;
+  if (R < 1 || R > CPR_MAX_RANK) return CPR_EINVAL;
+  if (int st = check_ktensor(K, X, R)) return st;
+  if (P_hat < 1 || P_hat > INT32_MAX) return CPR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cpr_opts o = defaults();
+  o.seed = seed;
+  o.batch_index = b;
+  o.fixed_iters = 1;
+  o.fit_samples = P_hat;
+  ProbSpec sp{X, R, 0, P_hat, &o, K->factors, K->lambda};
+  const Plan measure = make_plan(1, &sp, 0, nullptr);
+  if (int st = check_ws(ws, ws_bytes, measure.bytes)) return st;
+  Plan pl = make_plan(1, &sp, 0, ws);
+  CPR_CUDA(cudaMemcpyAsync(pl.d_probs, pl.probs.data(), sizeof(Prob), cudaMemcpyHostToDevice, s));
+  CPR_CUDA(launch_init_state(pl.d_probs, 1, s));
+  if (norm_x < 0) {
+    CPR_CUDA(launch_sumsq(X->data, X->dtype, pl.probs[0].P, pl.d_normpart, pl.normblk, s));
+    CPR_CUDA(launch_sumsq_finish(pl.d_normpart, pl.normblk, nullptr, pl.d_states, 1, s));
+  } else {
+    CPR_CUDA(cudaMemcpyAsync(&pl.d_states[0].norm_x, &norm_x, sizeof(double), cudaMemcpyHostToDevice, s));
+  }
+  CPR_CUDA(launch_init_factors(pl.d_probs, pl.g, 1, s));
+  CPR_CUDA(launch_fit_setup(pl.d_probs, pl.g, s));
+  CPR_CUDA(launch_fit_partial(pl.d_probs, pl.g, s));
+  CPR_CUDA(launch_fit_finish(pl.d_probs, pl.g, pl.d_counter, 0ull, 0, s));
+  State h;
+  CPR_CUDA(cudaMemcpyAsync(&h, pl.d_states, sizeof(State), cudaMemcpyDeviceToHost, s));
+  CPR_CUDA(cudaStreamSynchronize(s));
+  *fit_host = h.last_fit;
+  return CPR_OK;
+}
+
+int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, uint32_t b, void* ws, size_t ws_bytes,
+                   void* stream) {
+  if (int st = check_tensor(X, true)) return st;
+  if (!out_dev || out_dev == X->data) return CPR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = X->order, dt = X->dtype;
+  const int64_t P = prod_dims(X);
+  Carver cv(nullptr);
+  auto lay = [&](Carver& c, float** W32, double** W64, double** F64, double** sg, void** tmp) {
+    for (int n = 0; n < N; ++n) {
+      const size_t I = (size_t)X->dims[n];
+      W32[n] = dt == CPR_F64 ? nullptr : c.take<float>(I * I);
+      W64[n] = dt == CPR_F64 ? c.take<double>(I * I) : nullptr;
+      F64[n] = c.take<double>(I * I);
+      sg[n] = c.take<double>(I);
+    }
+    *tmp = c.take<unsigned char>((size_t)P * elem_size(dt));
+  };
+  float* W32[kMaxOrder];
+  double *W64[kMaxOrder], *F64[kMaxOrder], *sg[kMaxOrder];
+  void* tmp;
+  lay(cv, W32, W64, F64, sg, &tmp);
+  if (int st = check_ws(ws, ws_bytes, align256(cv.off))) return st;
+  Carver cw(ws);
+  lay(cw, W32, W64, F64, sg, &tmp);
+  for (int n = 0; n < N; ++n)
+    CPR_CUDA(launch_build_mix_ops((int)X->dims[n], seed, b, n, W32[n], W64[n], F64[n], sg[n], s));
+  const void* src = X->data;
+  void* bufs[2] = {out_dev, tmp};
+  int cur = (N % 2 == 1) ? 0 : 1;
+  for (int n = 0; n < N; ++n) {
+    CPR_CUDA(launch_mix_mode(src, bufs[cur], dt, N, X->dims, n, W32[n], W64[n], s));
+    src = bufs[cur];
+    cur ^= 1;
+  }
+  return CPR_OK;
+}
+
+int cpr_unmix_factors(const cpr_ktensor* Khat, cpr_ktensor* out, uint64_t seed, uint32_t b, void* ws,
+                      size_t ws_bytes, void* stream) {
+  if (!Khat || !out || Khat->order != out->order || Khat->rank != out->rank) return CPR_EINVAL;
+  if (Khat->order < 2 || Khat->order > CPR_MAX_ORDER || Khat->rank < 1 || Khat->rank > CPR_MAX_RANK)
+    return CPR_EINVAL;
+  const int N = Khat->order, R = Khat->rank;
+  for (int n = 0; n < N; ++n) {
+    if (Khat->dims[n] != out->dims[n] || Khat->dims[n] < 1 || Khat->dims[n] >= (int64_t(1) << 31)) return CPR_EINVAL;
+    if (!Khat->factors[n] || !out->factors[n] || Khat->factors[n] == out->factors[n]) return CPR_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Carver cv(nullptr);
+  for (int n = 0; n < N; ++n) {
+    cv.take<double>((size_t)Khat->dims[n] * Khat->dims[n]);
+    cv.take<double>((size_t)Khat->dims[n]);
+  }
+  if (int st = check_ws(ws, ws_bytes, align256(cv.off))) return st;
+  Carver cw(ws);
+  for (int n = 0; n < N; ++n) {
+    const int I = (int)Khat->dims[n];
+    double* F64 = cw.take<double>((size_t)I * I);
+    double* sg = cw.take<double>((size_t)I);
+    CPR_CUDA(launch_build_mix_ops(I, seed, b, n, nullptr, nullptr, F64, sg, s));
+    CPR_CUDA(launch_unmix(Khat->factors[n], out->factors[n], F64, sg, I, R, s));
+  }
+  if (Khat->lambda && out->lambda && Khat->lambda != out->lambda)
+    CPR_CUDA(cudaMemcpyAsync(out->lambda, Khat->lambda, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
+  return CPR_OK;
+}
+
+int cpr_tensor_norm(const cpr_tensor* X, double* norm_host, void* ws, size_t ws_bytes, void* stream) {
+  if (int st = check_tensor(X, true)) return st;
+  if (!norm_host) return CPR_EINVAL;
+  const int64_t P = prod_dims(X);
+  const int nblk = sumsq_blocks(P);
+  const size_t need = cpr_workspace_size(CPR_METHOD_NORM, X, 1, 1, nullptr);
+  if (int st = check_ws(ws, ws_bytes, need)) return st;
+  Carver cw(ws);
+  double* part = cw.take<double>(nblk);
+  double* out = cw.take<double>(1);
+  cudaStream_t s = (cudaStream_t)stream;
+  CPR_CUDA(launch_sumsq(X->data, X->dtype, P, part, nblk, s));
+  CPR_CUDA(launch_sumsq_finish(part, nblk, out, nullptr, 0, s));
+  CPR_CUDA(cudaMemcpyAsync(norm_host, out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CPR_CUDA(cudaStreamSynchronize(s));
+  return CPR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+// Internal declarations shared by the CUDA translation units of libcprand.
+//
+// Device-side design (GB300, sm_103a):
+//  * Every kernel serves a BATCH of independent problems (blockIdx.y = problem).  A single
+//    decomposition is a batch of one, so the batched multi-start path and the single path are the
+//    same kernels.
+//  * Everything a kernel needs about a problem is in a Prob descriptor in device memory, and every
+//    per-iteration quantity (the outer-iteration counter t, the stop flag) is read from the
+//    problem's State in device memory.  Kernel arguments therefore never change between outer
+//    iterations, which is what lets one iteration be captured once in a CUDA graph and replayed
+//    under a device-evaluated while-condition.
+//  * A problem whose stopping rule fired (State::done) makes every later kernel return at once.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/cprand.h"
+
+namespace cpr {
+
+constexpr int kMaxOrder = CPR_MAX_ORDER;
+constexpr int kMaxRank = CPR_MAX_RANK;
+
+// Tiling constants (block shapes sized so small problems still spread over the 152 SMs).
+constexpr int kGramChunk = 16;     // samples per block in the sample/SKR/Gram kernel
+constexpr int kContractRows = 64;  // fiber rows per block in the gather/contract kernel
+constexpr int kSolveRows = 32;     // factor rows per block in the solve kernel
+constexpr int kNormRows = 128;     // factor rows per block in the normalize kernel
+constexpr int kFitThreads = 256;   // fit entries per block in the fit kernel
+
+struct State {
+  int32_t iter;      // outer iterations completed in this run
+  int32_t done;      // stopping rule fired (or an error occurred)
+  int32_t status;    // CPR_OK or a device-detected CPR_E*
+  int32_t stall;     // iterations since the best fit last improved
+  double best;       // best sampled fit so far
+  double last_fit;   // sampled fit of the last completed iteration
+  double norm_x;     // ||X||
+  double pad;
+};
+
+struct Prob {
+  int32_t N, R, S, dtype;
+  int64_t dims[kMaxOrder];
+  int64_t st[kMaxOrder];   // column-major strides: st[n] = prod_{m<n} dims[m]
+  int64_t P;               // prod dims
+  const void* X;           // tensor being decomposed (the mixed tensor for CPRAND-MIX)
+
+  float* A32[kMaxOrder];   // FP32 working copy of each factor (I_n x R row-major)
+  double* A64[kMaxOrder];  // FP64 factors (I_n x R row-major)
+  double* lambda;          // R
+
+  // scratch of one mode update
+  uint32_t* idx;           // S x N sampled multi-indices
+  int64_t* off;            // S fiber base offsets
+  float* Z32;              // S x R sampled Khatri-Rao rows (FP32 copy for the contraction)
+  double* Z64;             // S x R, FP64 tensors only
+  double* Gpart;           // ng x R x R partial Grams (upper triangle used)
+  double* L;               // R x R Cholesky factor (lower)
+  void* Mpart;             // nsplit x Imax x R partial X_S Z_S (float, or double for FP64)
+  double* Npart;           // nrb_max x R partial column sums of squares
+  int32_t ng;              // Gram chunks = ceil(S / kGramChunk)
+  int32_t spl, nsplit;     // samples per contraction split, number of splits
+  int32_t imax;            // max dims (row stride of Mpart)
+
+  // sampled fit (Sec. 3.4)
+  int32_t P_hat, nfb;
+  uint32_t* fit_idx;       // P_hat x N
+  double* fit_x;           // P_hat tensor values
+  double* fit_part;        // nfb partial sums of e^2
+  double* trace;           // may be null
+
+  // stopping rules (Sec. 4.2)
+  int32_t max_iters, fixed_iters, stall_iters, pad0;
+  double tol, eta;
+
+  // random streams
+  uint64_t seed;
+  uint32_t b, t0;
+
+  State* state;
+};
+
+// ------------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 multiplies with key bumps.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int rnd = 0; rnd < 10; ++rnd) {
+    if (rnd) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4& w, int q) {
+  return q == 0 ? w.x : (q == 1 ? w.y : (q == 2 ? w.z : w.w));
+}
+
+// index in [0, extent): high word of the 64-bit product
+__device__ __forceinline__ uint32_t scale_index(uint32_t w, uint32_t extent) {
+  return __umulhi(w, extent);
+}
+
+__device__ __forceinline__ uint32_t counter_word1(uint32_t stream, uint32_t block, uint32_t mode) {
+  return (stream << 8) | (block << 4) | mode;
+}
+
+constexpr uint32_t kStreamSamples = 0, kStreamFit = 1, kStreamInit = 2, kStreamSigns = 3;
+
+template <typename T> __device__ __forceinline__ double load_as_double(const T* p, int64_t i);
+template <> __device__ __forceinline__ double load_as_double<double>(const double* p, int64_t i) { return p[i]; }
+template <> __device__ __forceinline__ double load_as_double<float>(const float* p, int64_t i) { return (double)p[i]; }
+template <> __device__ __forceinline__ double load_as_double<__nv_bfloat16>(const __nv_bfloat16* p, int64_t i) {
+  return (double)__bfloat162float(p[i]);
+}
+
+__device__ __forceinline__ bool is_done(const Prob& p) {
+  return *((volatile int32_t*)&p.state->done) != 0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Launch wrappers (defined in the .cu files).  `probs` is the device descriptor array, B the batch
+// size, bmax_* the per-batch maxima used to size grids.
+// ------------------------------------------------------------------------------------------------
+struct GridInfo {
+  int B;
+  int max_S;        // max S over problems
+  int max_ng;       // max Gram chunks
+  int max_spl;      // max samples per contraction split
+  int max_nfb;      // max fit blocks
+  int max_I[kMaxOrder];  // max dims[n] over problems
+  int max_tiles_x_split[kMaxOrder];  // max over problems of ceil(I_n/kContractRows)*nsplit
+  int max_R;
+  int max_Phat;
+  int any_f64;      // tensors are FP64
+  int dtype;
+  int64_t max_P;
+};
+
+cudaError_t launch_init_state(const Prob* probs, int B, cudaStream_t s);
+cudaError_t launch_init_factors(const Prob* probs, const GridInfo& g, int from_a64, cudaStream_t s);
+cudaError_t launch_sample_skr_gram(const Prob* probs, const GridInfo& g, int n, cudaStream_t s);
+cudaError_t launch_gather_contract(const Prob* probs, const GridInfo& g, int n, cudaStream_t s);
+cudaError_t launch_gram_chol(const Prob* probs, const GridInfo& g, int n, cudaStream_t s);
+cudaError_t launch_solve_rows(const Prob* probs, const GridInfo& g, int n, cudaStream_t s);
+cudaError_t launch_normalize(const Prob* probs, const GridInfo& g, int n, cudaStream_t s);
+cudaError_t launch_fit_setup(const Prob* probs, const GridInfo& g, cudaStream_t s);
+cudaError_t launch_fit_partial(const Prob* probs, const GridInfo& g, cudaStream_t s);
+cudaError_t launch_fit_finish(const Prob* probs, const GridInfo& g, int* counter,
+                              unsigned long long cond_handle, int use_cond, cudaStream_t s);
+cudaError_t launch_sumsq(const void* X, int dtype, int64_t P, double* part, int nblk, cudaStream_t s);
+cudaError_t launch_sumsq_finish(const double* part, int nblk, double* out_norm, State* st,
+                                int nstates, cudaStream_t s);
+int sumsq_blocks(int64_t P);
+
+// step hooks
+cudaError_t launch_sample_only(const void* X, int N, const int64_t* dims, int n, int64_t S,
+                               uint64_t seed, uint32_t b, uint32_t t, uint32_t* idx, int64_t* off,
+                               cudaStream_t s);
+cudaError_t launch_gather_only(const void* X, int dtype, int64_t I, int64_t st, int64_t S,
+                               const int64_t* off, void* out, cudaStream_t s);
+
+// mixing (Alg. 5)
+cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, float* W32, double* W64,
+                                 double* F64, double* signs, cudaStream_t s);
+cudaError_t launch_mix_mode(const void* X, void* Y, int dtype, int N, const int64_t* dims, int n,
+                            const float* W32, const double* W64, cudaStream_t s);
+cudaError_t launch_unmix(const double* Ahat, double* A, const double* F64, const double* signs,
+                         int I, int R, cudaStream_t s);
+
+}  // namespace cpr

@@ -1,0 +1,179 @@
+// Mixing preprocess and unmixing of CPRAND-MIX in its real-transform form (Alg. 5).
+//
+// Mode-n operator W_n = F_n D_n: D_n = diag of Philox signs (stream 3), F_n = orthonormal DCT-II,
+//   F_n[i][k] = c_i cos(pi (2k+1) i / (2 I_n)), c_0 = sqrt(1/I_n), c_i = sqrt(2/I_n).
+// The cosine argument is reduced exactly in integers ((2k+1) i mod 4 I_n) before cospi.
+//
+// Mode-n product Y = X x_n W_n on the column-major tensor, viewed as [L][I_n][Rr] with
+// L = prod_{m<n} I_m (contiguous) and Rr = prod_{m>n} I_m:
+//   mode 1 (L = 1):  Y[:, r] = W X[:, r]          -> rows of the GEMM are the Rr fibers (k contiguous)
+//   mode n > 1:      Y_r[l][i] = sum_k X_r[l][k] W[i][k]  (batched over r, l contiguous)
+// Both are one register-tiled SIMT GEMM (128 x 64 output tile, 8 x 4 per thread, FP32
+// accumulation; FP64 for FP64 tensors).  Unmixing A = D_n F_n^T A^ runs in FP64.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace cpr {
+
+__global__ void k_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, float* W32, double* W64,
+                                double* F64, double* signs) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)I * I) return;
+  const int i = (int)(e / I), k = (int)(e % I);
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const uint4 w = philox10(make_uint4((uint32_t)k, counter_word1(kStreamSigns, 0, n), 0u, b), k0, k1);
+  const double d = (w.x & 1u) ? -1.0 : 1.0;
+  const int64_t q = ((int64_t)(2 * k + 1) * i) % (4 * (int64_t)I);
+  const double c = (i == 0) ? sqrt(1.0 / I) : sqrt(2.0 / I);
+  const double f = c * cospi((double)q / (2.0 * I));
+  if (F64) F64[e] = f;
+  if (W64) W64[e] = f * d;
+  if (W32) W32[e] = (float)(f * d);
+  if (signs && i == 0) signs[k] = d;
+}
+
+cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, float* W32, double* W64, double* F64,
+                                 double* signs, cudaStream_t s) {
+  const int64_t total = (int64_t)I * I;
+  k_build_mix_ops<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(I, seed, b, n, W32, W64, F64, signs);
+  return cudaGetLastError();
+}
+
+template <typename T> struct Conv;
+template <> struct Conv<double> {
+  static __device__ __forceinline__ double in(double v) { return v; }
+  static __device__ __forceinline__ double out(double v) { return v; }
+};
+template <> struct Conv<float> {
+  static __device__ __forceinline__ float in(float v) { return v; }
+  static __device__ __forceinline__ float out(float v) { return v; }
+};
+template <> struct Conv<__nv_bfloat16> {
+  static __device__ __forceinline__ float in(__nv_bfloat16 v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ __nv_bfloat16 out(float v) { return __float2bfloat16(v); }
+};
+
+template <typename T, typename ACC, bool KC>
+__global__ void __launch_bounds__(256) k_mix_mode(const T* __restrict__ X, T* __restrict__ Y,
+                                                  const ACC* __restrict__ W, int64_t Mdim, int I, int64_t L,
+                                                  int64_t nbatch) {
+  constexpr int BM = 128, BC = 64, BK = 16;
+  __shared__ ACC As[BK][BM + 4];
+  __shared__ ACC Ws[BK][BC + 4];
+  const int tid = threadIdx.x, tm = tid & 15, tc = tid >> 4;
+  const int64_t m0 = (int64_t)blockIdx.x * BM;
+  const int c0 = blockIdx.y * BC;
+  for (int64_t bz = blockIdx.z; bz < nbatch; bz += gridDim.z) {
+    const int64_t base = KC ? 0 : bz * L * I;
+    ACC acc[8][4];
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[x][y] = ACC(0);
+    for (int k0 = 0; k0 < I; k0 += BK) {
+      if (KC) {
+        const int kk = tid & 15;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int mm = (tid >> 4) + 16 * q;
+          const int64_t m = m0 + mm;
+          const int k = k0 + kk;
+          As[kk][mm] = (m < Mdim && k < I) ? (ACC)Conv<T>::in(X[m * I + k]) : ACC(0);
+        }
+      } else {
+        const int mm = tid & 127;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int kk = (tid >> 7) + 2 * q;
+          const int64_t m = m0 + mm;
+          const int k = k0 + kk;
+          As[kk][mm] = (m < Mdim && k < I) ? (ACC)Conv<T>::in(X[base + m + (int64_t)k * L]) : ACC(0);
+        }
+      }
+      {
+        const int kk = tid & 15;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int cc = (tid >> 4) + 16 * q;
+          const int c = c0 + cc, k = k0 + kk;
+          Ws[kk][cc] = (c < I && k < I) ? W[(int64_t)c * I + k] : ACC(0);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        ACC a[8], w[4];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) a[x] = As[kk][tm * 8 + x];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) w[y] = Ws[kk][tc * 4 + y];
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], w[y], acc[x][y]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      const int64_t m = m0 + tm * 8 + x;
+      if (m >= Mdim) continue;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int c = c0 + tc * 4 + y;
+        if (c >= I) continue;
+        if (KC) Y[m * I + c] = Conv<T>::out(acc[x][y]);
+        else Y[base + m + (int64_t)c * L] = Conv<T>::out(acc[x][y]);
+      }
+    }
+  }
+}
+
+template <typename T, typename ACC>
+static cudaError_t mix_dispatch(const void* X, void* Y, const ACC* W, int N, const int64_t* dims, int n,
+                                cudaStream_t s) {
+  int64_t L = 1, Rr = 1;
+  for (int m = 0; m < n; ++m) L *= dims[m];
+  for (int m = n + 1; m < N; ++m) Rr *= dims[m];
+  const int I = (int)dims[n];
+  const int cblocks = (I + 63) / 64;
+  if (n == 0) {
+    const int64_t Mdim = Rr;
+    const dim3 grid((unsigned)((Mdim + 127) / 128), cblocks, 1);
+    k_mix_mode<T, ACC, true><<<grid, 256, 0, s>>>((const T*)X, (T*)Y, W, Mdim, I, 1, 1);
+  } else {
+    const int64_t nz = Rr < 65535 ? Rr : 65535;
+    const dim3 grid((unsigned)((L + 127) / 128), cblocks, (unsigned)nz);
+    k_mix_mode<T, ACC, false><<<grid, 256, 0, s>>>((const T*)X, (T*)Y, W, L, I, L, Rr);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mix_mode(const void* X, void* Y, int dtype, int N, const int64_t* dims, int n, const float* W32,
+                            const double* W64, cudaStream_t s) {
+  switch (dtype) {
+    case CPR_F64: return mix_dispatch<double, double>(X, Y, W64, N, dims, n, s);
+    case CPR_F32: return mix_dispatch<float, float>(X, Y, W32, N, dims, n, s);
+    default: return mix_dispatch<__nv_bfloat16, float>(X, Y, W32, N, dims, n, s);
+  }
+}
+
+__global__ void k_unmix(const double* __restrict__ Ahat, double* __restrict__ A, const double* __restrict__ F64,
+                        const double* __restrict__ signs, int I, int R) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)I * R) return;
+  const int i = (int)(e / R), r = (int)(e % R);
+  double acc = 0.0;
+  for (int k = 0; k < I; ++k) acc = fma(F64[(int64_t)k * I + i], Ahat[(int64_t)k * R + r], acc);
+  A[e] = signs[i] * acc;
+}
+
+cudaError_t launch_unmix(const double* Ahat, double* A, const double* F64, const double* signs, int I, int R,
+                         cudaStream_t s) {
+  const int64_t total = (int64_t)I * R;
+  k_unmix<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(Ahat, A, F64, signs, I, R);
+  return cudaGetLastError();
+}
+
+}  // namespace cpr

@@ -1,0 +1,254 @@
+"""GPU parity: every step of the hot path, through the C ABI, against the CPU oracle.
+
+Bars: sampled indices and gathered fibers bit-exact; updated factors within 1e-4 relative
+Frobenius for FP32/BF16 tensors (FP32 contraction) and 1e-10 for FP64 tensors; whole runs reach
+the oracle's final fit within 1e-3.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cp, mixing, streams
+from synth import make_problem, to_oracle_array
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def cb():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1701_06600_gb300 import binding
+    return binding
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def rand_tensor(dims, dtype, seed=0):
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    return torch.randn(int(np.prod(dims)), generator=g, dtype=torch.float64).to(dtype).to(DEV)
+
+
+# ------------------------------------------------------------------------------------------------
+# a1: sampler (bit-exact)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,n,S,t,b", [
+    ((400, 400, 400), 0, 230, 0, 0), ((400, 400, 400), 2, 230, 7, 0), ((100, 100, 100, 100), 1, 450, 3, 2),
+    ((7, 1, 13, 5, 3, 2), 3, 1000, 1, 1), ((64, 512, 300), 1, 1109, 199, 63), ((50, 50, 50), 1, 80, 49, 0),
+    ((1500, 1500, 1500), 1, 2000, 11, 0), ((3, 4, 5, 6, 7, 8, 9, 10), 7, 4096, 2, 5), ((9, 9), 0, 0, 0, 0)])
+def test_sampler_bit_exact(cb, dims, n, S, t, b):
+    seed = 2001
+    idx, off = cb.cpr_sample_indices(dims, n, S, seed, b, t)
+    torch.cuda.synchronize()
+    ref = streams.ls_sample_indices(seed, b, t, n, S, dims)
+    np.testing.assert_array_equal(idx.cpu().numpy().astype(np.int64), ref)
+    if S:
+        ref_off = np.ravel_multi_index(tuple(ref[:, m] for m in range(len(dims))), dims, order="F")
+        np.testing.assert_array_equal(off.cpu().numpy(), ref_off)
+
+
+# ------------------------------------------------------------------------------------------------
+# a2: fiber gather (bit-exact)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float64])
+@pytest.mark.parametrize("dims", [(37, 29, 41), (1, 30, 20), (11, 7, 5, 9, 3)])
+def test_gather_bit_exact(cb, dtype, dims):
+    X = rand_tensor(dims, dtype, 1)
+    T = to_oracle_array(X, dims)
+    for n in range(len(dims)):
+        idx, off = cb.cpr_sample_indices(dims, n, 77, 9, 0, n)
+        Xs = cb.cpr_gather_fibers(X, dims, n, off)
+        torch.cuda.synchronize()
+        ref = cp.gather_fibers(T, idx.cpu().numpy().astype(np.int64), n)
+        got = Xs.float().cpu().double().numpy() if dtype == torch.bfloat16 else Xs.cpu().double().numpy()
+        np.testing.assert_array_equal(got, ref)
+
+
+# ------------------------------------------------------------------------------------------------
+# a1-a6: one mode update of Alg. 3
+# ------------------------------------------------------------------------------------------------
+UPDATE_CASES = [
+    # dims, R, S, dtype, tol
+    ((37, 29, 41), 4, 60, torch.float32, 1e-4),
+    ((70, 130, 65), 7, 100, torch.bfloat16, 1e-4),
+    ((50, 50, 50), 5, 80, torch.float64, 1e-10),
+    ((9, 8, 7, 6, 5, 4), 3, 40, torch.float32, 1e-4),
+    ((80, 70, 90), 64, 64, torch.float32, 1e-4),       # R = CPR_MAX_RANK, S = R
+    ((1, 30, 20), 1, 5, torch.float32, 1e-4),          # I_1 = 1, R = 1
+    ((400, 400, 400), 10, 230, torch.float32, 1e-4),   # full size of the 400^3 workload
+]
+
+
+@pytest.mark.parametrize("dims,R,S,dtype,tol", UPDATE_CASES)
+def test_sampled_update_matches_oracle(cb, dims, R, S, dtype, tol):
+    prob = make_problem(dims, min(R, min(dims)), C=0.5, eta=0.01, seed=3, dtype=dtype, device=DEV)
+    T = to_oracle_array(prob.X, dims)
+    rng = np.random.default_rng(4)
+    if dtype == torch.float64:
+        f0 = [rng.random((d, R)) for d in dims]
+    else:
+        f0 = [rng.random((d, R)).astype(np.float32).astype(np.float64) for d in dims]
+    for n in range(len(dims)):
+        facs = [torch.tensor(f, device=DEV) for f in f0]
+        lam = torch.empty(R, dtype=torch.float64, device=DEV)
+        st = cb.cpr_sampled_update(prob.X, dims, lam, facs, n, S, seed=77, b=1, t=5 + n)
+        assert st == cb.OK
+        idx = streams.ls_sample_indices(77, 1, 5 + n, n, S, dims)
+        A_ref, lam_ref = cp.cprand_update(T, f0, n, idx)
+        assert rel(facs[n].cpu().numpy(), A_ref) < tol, n
+        assert rel(lam.cpu().numpy(), lam_ref) < tol, n
+
+
+def test_singular_gram_is_reported(cb):
+    dims = (20, 15, 12)
+    X = rand_tensor(dims, torch.float32, 2)
+    rng = np.random.default_rng(5)
+    f0 = [rng.random((d, 3)).astype(np.float32).astype(np.float64) for d in dims]
+    f0[1][:, 2] = 0.0       # a zero column makes Z_S^T Z_S singular
+    facs = [torch.tensor(f, device=DEV) for f in f0]
+    lam = torch.empty(3, dtype=torch.float64, device=DEV)
+    assert cb.cpr_sampled_update(X, dims, lam, facs, 0, 30, seed=1) == cb.ESINGULAR
+
+
+# ------------------------------------------------------------------------------------------------
+# a7: sampled fit, ||X||
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 1e-6), (torch.float64, 1e-12), (torch.bfloat16, 1e-6)])
+def test_fit_estimate_and_norm(cb, dtype, tol):
+    dims = (33, 40, 27)
+    prob = make_problem(dims, 4, C=0.3, eta=0.05, seed=6, dtype=dtype, device=DEV)
+    T = to_oracle_array(prob.X, dims)
+    rng = np.random.default_rng(7)
+    lam0 = rng.uniform(0.2, 0.8, 4)
+    fac = [f + 0.01 * rng.standard_normal(f.shape) for f in prob.factors]
+    if dtype != torch.float64:
+        fac = [f.astype(np.float32).astype(np.float64) for f in fac]
+    nrm = cb.cpr_tensor_norm(prob.X, dims)
+    assert abs(nrm - np.linalg.norm(T)) < (1e-13 if dtype == torch.float64 else 1e-6) * np.linalg.norm(T)
+    fit = cb.cpr_fit_estimate(prob.X, dims, torch.tensor(lam0, device=DEV), [torch.tensor(f, device=DEV) for f in fac],
+                              16384, seed=13, b=2)
+    idx = streams.fit_sample_indices(13, 2, 16384, dims)
+    x = T[tuple(idx[:, m] for m in range(3))]
+    ref = cp.sampled_fit(x, lam0, fac, idx, np.linalg.norm(T), T.size)
+    assert abs(fit - ref) < tol
+
+
+# ------------------------------------------------------------------------------------------------
+# a0, a9: mixing and unmixing
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dims,dtype,tol", [((37, 29, 41), torch.float32, 1e-5), ((130, 64, 65), torch.float32, 1e-5),
+                                            ((20, 17, 9, 11), torch.float64, 1e-12),
+                                            ((70, 33, 50), torch.bfloat16, 1e-2)])
+def test_mix_tensor_matches_oracle(cb, dims, dtype, tol):
+    X = rand_tensor(dims, dtype, 8)
+    T = to_oracle_array(X, dims)
+    Y = cb.cpr_mix_tensor(X, dims, seed=31, b=3)
+    ref = mixing.mix_tensor(T, mixing.mixing_operators(31, 3, dims))
+    got = to_oracle_array(Y, dims)
+    assert rel(got, ref) < tol
+    assert abs(np.linalg.norm(got) - np.linalg.norm(T)) < 10 * tol * np.linalg.norm(T)
+
+
+def test_unmix_matches_oracle(cb):
+    dims = (45, 64, 17)
+    rng = np.random.default_rng(9)
+    fh = [rng.standard_normal((d, 6)) for d in dims]
+    lam = torch.tensor(rng.random(6), device=DEV)
+    out_lam, out_f = cb.cpr_unmix_factors(lam, [torch.tensor(f, device=DEV) for f in fh], seed=4, b=1)
+    ref = mixing.unmix_factors(fh, mixing.mixing_operators(4, 1, dims))
+    for A, Ar in zip(out_f, ref):
+        assert rel(A.cpu().numpy(), Ar) < 1e-12
+    np.testing.assert_array_equal(out_lam.cpu().numpy(), lam.cpu().numpy())
+
+
+# ------------------------------------------------------------------------------------------------
+# a0-a9: whole runs against the oracle
+# ------------------------------------------------------------------------------------------------
+def test_cprand_fp64_run_follows_oracle_exactly(cb):
+    # plain CPRAND, FP64 50^3, rank-5 N(0,1) factors, 1% noise, R=5, S=80, 50 fixed iterations
+    dims = (50, 50, 50)
+    prob = make_problem(dims, 5, eta=0.01, seed=1000, dtype=torch.float64, device=DEV, gaussian_factors=True)
+    T = to_oracle_array(prob.X, dims)
+    trace = torch.zeros(50, dtype=torch.float64, device=DEV)
+    opts = cb.cpr_default_opts(fixed_iters=50, seed=2000, fit_trace_dev=trace.data_ptr())
+    out = cb.cpr_cprand(prob.X, dims, 5, 80, opts=opts)
+    ref = cp.cprand(T, 5, 80, seed=2000, rule=cp.StopRule(fixed_iters=50))
+    assert out["iters"] == 50 and out["status"] == cb.OK
+    np.testing.assert_allclose(trace.cpu().numpy(), ref["fits"], rtol=0, atol=1e-9)
+    for A, Ar in zip(out["factors"], ref["factors"]):
+        assert rel(A.cpu().numpy(), Ar) < 1e-7
+
+
+def test_cprand_fp64_stopping_rules_match_oracle(cb):
+    dims = (40, 30, 35)
+    prob = make_problem(dims, 4, C=0.5, eta=0.01, seed=17, dtype=torch.float64, device=DEV)
+    T = to_oracle_array(prob.X, dims)
+    for kw, rule in [({"noise_eta": 0.01}, cp.StopRule(eta=0.01)),
+                     ({"stall_iters": 3, "fit_tol": -1.0}, cp.StopRule(tol=-1.0, stall_iters=3)),
+                     ({}, cp.StopRule())]:
+        opts = cb.cpr_default_opts(seed=5, **kw)
+        out = cb.cpr_cprand(prob.X, dims, 4, 60, opts=opts)
+        ref = cp.cprand(T, 4, 60, seed=5, rule=rule)
+        assert out["iters"] == ref["iters"], (kw, out["iters"], ref["iters"])
+        assert abs(out["fit_est"] - ref["fits"][-1]) < 1e-9
+
+
+@pytest.mark.parametrize("mix", [False, True])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_whole_run_reaches_oracle_fit(cb, mix, dtype):
+    dims = (60, 50, 40)
+    prob = make_problem(dims, 5, C=0.9, eta=0.01, seed=23, dtype=dtype, device=DEV)
+    T = to_oracle_array(prob.X, dims)
+    S = cp.sample_size(5)
+    opts = cb.cpr_default_opts(seed=41, noise_eta=0.01)
+    fn = cb.cpr_cprand_mix if mix else cb.cpr_cprand
+    out = fn(prob.X, dims, 5, S, opts=opts)
+    rule = cp.StopRule(eta=0.01)
+    ref = mixing.cprand_mix(T, 5, S, seed=41, rule=rule) if mix else cp.cprand(T, 5, S, seed=41, rule=rule)
+    f_gpu = cp.exact_fit(T, out["lam"].cpu().numpy(), [A.cpu().numpy() for A in out["factors"]])
+    f_ref = cp.exact_fit(T, ref["lam"], ref["factors"])
+    assert out["status"] == cb.OK
+    assert abs(f_gpu - f_ref) < 1e-3, (f_gpu, f_ref)
+
+
+def test_full_size_mix_run_tracks_oracle(cb):
+    # the 400^3 FP32 workload (R=10, S=230, congruence 0.9), three outer iterations
+    dims = (400, 400, 400)
+    prob = make_problem(dims, 10, C=0.9, eta=0.01, seed=1001, dtype=torch.float32, device=DEV)
+    T = to_oracle_array(prob.X, dims)
+    trace = torch.zeros(3, dtype=torch.float64, device=DEV)
+    opts = cb.cpr_default_opts(fixed_iters=3, seed=2001, fit_trace_dev=trace.data_ptr())
+    out = cb.cpr_cprand_mix(prob.X, dims, 10, 230, opts=opts)
+    ref = mixing.cprand_mix(T, 10, 230, seed=2001, rule=cp.StopRule(fixed_iters=3))
+    np.testing.assert_allclose(trace.cpu().numpy(), ref["fits"], rtol=0, atol=1e-4)
+    for A, Ar in zip(out["factors"], ref["factors"]):
+        assert rel(A.cpu().numpy(), Ar) < 1e-3
+
+
+# ------------------------------------------------------------------------------------------------
+# a10: batching
+# ------------------------------------------------------------------------------------------------
+def test_batched_matches_single_runs_and_oracle(cb):
+    specs = [((64, 80, 100), 4, 0.0), ((120, 64, 90), 7, 0.5), ((200, 150, 64), 12, 0.9), ((70, 70, 70), 32, 0.3)]
+    Xs, dims_l, Rs, Ss, probs = [], [], [], [], []
+    for q, (d, R, C) in enumerate(specs):
+        p = make_problem(d, R, C=C, eta=0.01, seed=4000 + q, dtype=torch.float32, device=DEV)
+        probs.append(p)
+        Xs.append(p.X)
+        dims_l.append(d)
+        Rs.append(R)
+        Ss.append(max(R, cp.sample_size(R)))
+    opts = [cb.cpr_default_opts(seed=99, batch_index=q, noise_eta=0.01) for q in range(len(specs))]
+    outs, _ = cb.cpr_cprand_batched(Xs, dims_l, Rs, Ss, opts, mix=True)
+    for q in range(len(specs)):
+        T = to_oracle_array(Xs[q], dims_l[q])
+        ref = mixing.cprand_mix(T, Rs[q], Ss[q], seed=99, b=q, rule=cp.StopRule(eta=0.01))
+        f_gpu = cp.exact_fit(T, outs[q]["lam"].cpu().numpy(), [A.cpu().numpy() for A in outs[q]["factors"]])
+        f_ref = cp.exact_fit(T, ref["lam"], ref["factors"])
+        assert abs(f_gpu - f_ref) < 1e-3, (q, f_gpu, f_ref)
+        single = cb.cpr_cprand_mix(Xs[q], dims_l[q], Rs[q], Ss[q], opts=opts[q])
+        f_single = cp.exact_fit(T, single["lam"].cpu().numpy(), [A.cpu().numpy() for A in single["factors"]])
+        assert abs(f_gpu - f_single) < 1e-3
