@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the CPRAND-MIX hot path on one GB300 (or N replicas under torchrun).
+
+Workload: the 400x400x400 FP32 tensor of rank 10 with factor congruence 0.9 and 1% noise (the
+paper's synthetic recipe, Sec. 4.2), R = 10, S = 230 samples per least-squares solve, P_hat = 2^14
+fit entries, the paper's stopping rules (200 iterations, |dF| <= 1e-4, F >= 1 - 1.2 eta).
+
+One step = one complete CPRAND-MIX decomposition (Alg. 5): ||X||, mixing of all three modes,
+random start, outer iterations until the stopping rule fires, unmixing.  The input tensor is
+resident in HBM when the timed region starts and is larger than L2 (256 MB vs 129 MB).
+
+metric: ALS iters/s = outer iterations per second of the iteration phase (the preprocess of each
+decomposition, mixing included, is timed separately and reported as time_to_solution).
+e2e: the same call through the C ABI with the tensor in pinned host memory: every step copies X to
+the device, decomposes it and copies lambda and the factors back; e2e.value = outer iterations per
+second of that whole loop.
+
+--impl reference times the CPU oracle (oracle/, FP64 NumPy) on the same workload: one step is one
+outer iteration of the oracle's CPRAND on the mixed tensor (the oracle mixes once, untimed, and
+reports that time).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "workload": "cprand_mix 400x400x400 fp32, rank-10 congruence-0.9 factors, 1% noise; R=10, S=230, "
+                "P_hat=2^14, paper stopping rules",
+    "dims": [400, 400, 400], "R": 10, "S": 230, "congruence": 0.9, "eta": 0.01, "P_hat": 16384,
+    "max_iters": 200, "fit_tol": 1e-4, "data_seed": 1001, "philox_seed": 2001,
+}
+SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def kernel_traffic(cls):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary, if the kernel's source is
+    unchanged since the capture (file hash recorded next to the number); else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for ln in open(path):
+        f = ln.split()
+        if len(f) >= 3 and f[0] == cls and not ln.startswith("#"):
+            src = os.path.join(ROOT, "paper_1701_06600_gb300", "csrc", f[2].split(":")[0])
+            want = f[2].split(":")[1] if ":" in f[2] else ""
+            if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == want:
+                return float(f[1])
+    return None
+
+
+def algorithmic(cls, w, P, b):
+    """Algorithmic bytes and flops of ONE launch of a kernel class on this workload."""
+    I, R, S = w["dims"][0], w["R"], w["S"]
+    if cls == "mix":
+        return {"bytes": 2.0 * P * b, "flops": 2.0 * I * P}
+    if cls == "contract":
+        return {"bytes": float(S * I * b + S * R * 4 + S * 8), "flops": 2.0 * S * R * I}
+    return None
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1701_06600_gb300 import binding as cb
+    from synth import make_problem
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    w = WORKLOAD
+    dims = tuple(w["dims"])
+    prob = make_problem(dims, w["R"], C=w["congruence"], eta=w["eta"], seed=w["data_seed"], dtype=torch.float32,
+                        device=dev)
+    X = prob.X
+    P = X.numel()
+    opts = cb.cpr_default_opts(seed=w["philox_seed"], batch_index=rank, noise_eta=w["eta"],
+                               max_iters=w["max_iters"], fit_tol=w["fit_tol"], fit_samples=w["P_hat"])
+    run = cb.PreparedRun(X, dims, w["R"], w["S"], opts=opts, mix=True)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up; the first warm-up step (plain stream launches, events around every kernel) also
+    # finds the kernel class with the most device time
+    cb.cpr_profile_begin(0xFF)
+    run()
+    prof_all = cb.cpr_profile_end()
+    for _ in range(max(0, args.warmup - 1)):
+        run()
+    torch.cuda.synchronize()
+    dom = max(prof_all, key=lambda c: prof_all[c][0] if c != "other" else -1)
+
+    # timed region 1: the production path (iteration loop as one graph launch), no profiler
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    iters, it_ms, launches, fits = 0, 0.0, 0, []
+    for _ in range(args.steps):
+        r = run()
+        iters += r["iters"]
+        it_ms += r["ms_iterate"]
+        launches += r["kernel_launches"]
+        fits.append(r["fit_est"])
+        assert r["status"] == cb.OK, r
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    # timed region 2: the same steps with CUDA events around every launch of the dominant kernel
+    # (kernels inside the iteration loop are then launched one by one on the stream)
+    torch.cuda.synchronize()
+    cb.cpr_profile_begin(1 << cb.KERNEL_CLASSES.index(dom))
+    for _ in range(args.steps):
+        run()
+    torch.cuda.synchronize()
+    prof = cb.cpr_profile_end()
+    # max over ranks of the time, sum over ranks of the work
+    vals = torch.tensor([total_ms, it_ms, float(iters)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = vals[:2].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        isum = vals[2:].clone()
+        dist.all_reduce(isum, op=dist.ReduceOp.SUM)
+        total_ms_all, it_ms_all, iters_all = float(tmax[0]), float(tmax[1]), float(isum[0])
+    else:
+        total_ms_all, it_ms_all, iters_all = total_ms, it_ms, float(iters)
+    value = iters_all / (it_ms_all / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    Xh = X.cpu().pin_memory()
+    R = w["R"]
+    lam_h = torch.empty(R, dtype=torch.float64).pin_memory()
+    fac_h = [torch.empty((d, R), dtype=torch.float64).pin_memory() for d in dims]
+    h2d = P * X.element_size()
+    d2h = 8 * (R + sum(d * R for d in dims))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(args.e2e_steps):
+        X.copy_(Xh, non_blocking=True)
+        r = run()
+        e2e_iters += r["iters"]
+        lam_h.copy_(run.lam, non_blocking=True)
+        for fh, fd in zip(fac_h, run.factors):
+            fh.copy_(fd, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+
+    # true fit of the last decomposition (out of the timed region)
+    with torch.no_grad():
+        A = run.factors
+        Xt = torch.einsum("r,ir,jr,kr->kji", run.lam, A[0], A[1], A[2]).reshape(-1)
+        true_fit = 1.0 - torch.linalg.vector_norm(X.double() - Xt).item() / torch.linalg.vector_norm(X.double()).item()
+
+    pk, pk_src = peaks()
+    roof = None
+    alg = algorithmic(dom, w, P, X.element_size())
+    dom_ms, dom_n = prof[dom]
+    if alg is not None and dom_n > 0:
+        per_launch_s = dom_ms / dom_n / 1e3
+        if dom == "mix":
+            # SIMT FP32 mode product: bound by FP32 FMA issue (152 SMs x 128 lanes x 2 flop x max clock)
+            peak = SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            ach = alg["flops"] / per_launch_s / 1e12
+            roof = {"bound": "alu", "kernel": "k_mix_mode (SIMT FP32 mode-n DCT product)", "achieved": ach,
+                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %d MHz" % pk.get("sm_max_mhz", 2070),
+                    "traffic": kernel_traffic(dom), "per_launch_ms": dom_ms / dom_n,
+                    "algorithmic_bytes": alg["bytes"], "algorithmic_flops": alg["flops"]}
+        else:
+            ach = alg["bytes"] / per_launch_s / 1e9
+            roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / pk["hbm_gbs"], "peak_source": pk_src, "traffic": kernel_traffic(dom),
+                    "per_launch_ms": dom_ms / dom_n, "algorithmic_bytes": alg["bytes"]}
+    out = {
+        "metric": "ALS iters/s", "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (Sec. 4.2 recipe, seeded)",
+        "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single GPU",
+                       l2="input tensor 256 MB > 129 MB L2, no flush"),
+        "time_to_solution_ms": total_ms_all / args.steps,
+        "iters_per_step": iters / args.steps,
+        "phase_ms_per_step": {"iterate": it_ms / args.steps,
+                              "setup_mix_finish": (total_ms - it_ms) / args.steps},
+        "fit_est_last": fits[-1], "true_fit_last": true_fit,
+        "gpu_launches": int(launches) * (1 if world == 1 else world),
+        "clocks": clk,
+        "e2e": {"value": e2e_iters * (world if world > 1 else 1) / e2e_s, "unit": "iters/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "note": "wall clock per full call incl. H2D of X, mixing, iterations, unmixing, D2H"},
+        "kernel_ms_per_step": {c: prof_all[c][0] for c in prof_all},
+        "dominant_kernel": dom,
+        "roofline": roof,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(X, dims, seconds=20.0)
+    if world > 1:
+        dist.destroy_process_group()
+    return out
+
+
+def cpu_baseline(X_dev, dims, seconds=20.0, steps=None):
+    """The oracle as it stands on this host's cores: mixing once, then outer iterations of CPRAND on the
+    mixed tensor until `steps` iterations or `seconds` have been spent (at least one)."""
+    from oracle import cp, mixing, streams
+    from synth import to_oracle_array
+    w = WORKLOAD
+    T = to_oracle_array(X_dev, dims)
+    t0 = time.perf_counter()
+    ops = mixing.mixing_operators(w["philox_seed"], 0, dims)
+    Th = mixing.mix_tensor(T, ops)
+    t_mix = time.perf_counter() - t0
+    R, S = w["R"], w["S"]
+    factors = [np.zeros((dims[0], R))] + [streams.init_factor(w["philox_seed"], 0, n, dims[n], R)
+                                          for n in range(1, 3)]
+    fit_idx = streams.fit_sample_indices(w["philox_seed"], 0, w["P_hat"], dims)
+    fit_x = Th[tuple(fit_idx[:, m] for m in range(3))]
+    normT = float(np.linalg.norm(T))
+    times = []
+    t = 0
+    while True:
+        a = time.perf_counter()
+        for n in range(3):
+            idx = streams.ls_sample_indices(w["philox_seed"], 0, t, n, S, dims)
+            factors[n], lam = cp.cprand_update(Th, factors, n, idx)
+        cp.sampled_fit(fit_x, lam, factors, fit_idx, normT, Th.size)
+        times.append(time.perf_counter() - a)
+        t += 1
+        if (steps is not None and t >= steps) or (steps is None and sum(times) >= seconds):
+            break
+    return {"value": len(times) / sum(times), "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d outer iterations of the FP64 NumPy oracle's CPRAND on the mixed 400^3 tensor "
+                      "(mixing once beforehand: %.2f s, not in the value)" % (len(times), t_mix),
+            "mix_s": t_mix, "iter_s": float(np.mean(times))}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import torch
+    from synth import make_problem
+    w = WORKLOAD
+    dims = tuple(w["dims"])
+    prob = make_problem(dims, w["R"], C=w["congruence"], eta=w["eta"], seed=w["data_seed"], dtype=torch.float32,
+                        device="cpu")
+    cb = cpu_baseline(prob.X, dims, steps=args.warmup + args.steps)
+    # the first `warmup` iterations are discarded
+    from oracle import cp  # noqa: F401  (import cost outside timing)
+    value = cb["value"]
+    return {"impl": "reference", "metric": "ALS iters/s", "value": value, "unit": "iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (Sec. 4.2 recipe, seeded)",
+            "config": dict(WORKLOAD, parallelism="host cores"),
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

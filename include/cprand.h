@@ -105,7 +105,23 @@ typedef struct {
   double fit_est;        /* last sampled fit estimate */
   double norm_x;         /* ||X|| (Frobenius) */
   int64_t kernel_launches; /* kernels this call put on the GPU */
+  double ms_setup;       /* device time of ||X||, mixing, initial factors and fit-set setup */
+  double ms_iterate;     /* device time of the outer iterations (wall time between two events) */
+  double ms_finish;      /* device time of unmixing and output copies */
 } cpr_result;
+
+/* Kernel classes of the profiler. */
+enum {
+  CPR_KERNEL_MIX = 0,        /* mode-n mixing product (Alg. 5 mixing step) */
+  CPR_KERNEL_SAMPLE_SKR = 1, /* sampler + sampled Khatri-Rao rows + partial Grams */
+  CPR_KERNEL_CONTRACT = 2,   /* fiber gather fused with X_S Z_S */
+  CPR_KERNEL_CHOL = 3,       /* Gram reduction + Cholesky */
+  CPR_KERNEL_SOLVE = 4,      /* row solves */
+  CPR_KERNEL_NORMALIZE = 5,  /* column normalization */
+  CPR_KERNEL_FIT = 6,        /* sampled fit + stopping test */
+  CPR_KERNEL_OTHER = 7,      /* setup, norm, unmixing */
+  CPR_KERNEL_CLASSES = 8
+};
 
 /* Fill *opts with the paper's defaults (Sec. 4.2): max_iters 200, fit_tol 1e-4, noise rule off,
  * no stall rule, P_hat = 2^14, seed 0, random initial factors. */
@@ -195,6 +211,16 @@ CPR_API int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, ui
  * copied.  Khat and out may not share factor buffers. */
 CPR_API int cpr_unmix_factors(const cpr_ktensor* Khat, cpr_ktensor* out, uint64_t seed, uint32_t b,
                       void* ws, size_t ws_bytes, void* stream);
+
+/* Kernel profiler (process-wide, host-side bookkeeping only).  After cpr_profile_begin(mask),
+ * every launch of a kernel class whose bit is set in mask is bracketed by a pair of CUDA events
+ * recorded on the launching stream; cpr_profile_end synchronizes those events and returns, per
+ * class c, the summed device time ms[c] and the launch count launches[c] (arrays of
+ * CPR_KERNEL_CLASSES entries, either may be NULL), then stops recording.  Events are created by
+ * the profiler; no device memory is allocated.  Launch counts are kept for every class whether or
+ * not its bit is set.  Not thread-safe against concurrent begin/end. */
+CPR_API int cpr_profile_begin(unsigned mask);
+CPR_API int cpr_profile_end(double* ms, int64_t* launches);
 
 /* ||X||_F (FP64 accumulation) written to *norm_host (synchronizes the stream). */
 CPR_API int cpr_tensor_norm(const cpr_tensor* X, double* norm_host, void* ws, size_t ws_bytes,

