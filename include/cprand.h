@@ -222,6 +222,22 @@ CPR_API int cpr_unmix_factors(const cpr_ktensor* Khat, cpr_ktensor* out, uint64_
 CPR_API int cpr_profile_begin(unsigned mask);
 CPR_API int cpr_profile_end(double* ms, int64_t* launches);
 
+/* Sampled fit estimate for callers that cannot allocate device memory when they need it (a plugin
+ * restricted to memory its host application owns, a process whose device memory belongs to another
+ * allocator, a latency-critical path).  The paper has no counterpart: this is the computation of
+ * cpr_fit_estimate (same Philox fit entries; the model is evaluated in FP64 from the FP64 factors)
+ * with its scratch in one fixed array of device memory declared by the library (about 42 KB per
+ * device, held until the process exits) instead of a caller workspace.  It allocates nothing.
+ * P_hat must be in [1, CPR_NOALLOC_MAX_FIT_SAMPLES]; a larger P_hat is rejected with CPR_EINVAL
+ * before anything is enqueued.  norm_x < 0 computes ||X|| in the same array.  Every call on a
+ * device shares the array (each call clears what must start at zero): calls whose work overlaps on
+ * the GPU race and must be ordered by the caller.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first call
+ * outside any stream capture.  Writes the estimate to *fit_host (synchronizes the stream). */
+#define CPR_NOALLOC_MAX_FIT_SAMPLES (1 << 20)
+CPR_API int cpr_fit_estimate_noalloc(const cpr_tensor* X, const cpr_ktensor* K, int64_t P_hat, uint64_t seed,
+                                     uint32_t b, double norm_x, double* fit_host, void* stream);
+
 /* ||X||_F (FP64 accumulation) written to *norm_host (synchronizes the stream). */
 CPR_API int cpr_tensor_norm(const cpr_tensor* X, double* norm_host, void* ws, size_t ws_bytes,
                     void* stream);

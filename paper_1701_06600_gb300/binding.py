@@ -92,6 +92,9 @@ _SIGS = {
                                          ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "cpr_tensor_norm": (ctypes.c_int, [ctypes.POINTER(CprTensor), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
                                        ctypes.c_size_t, ctypes.c_void_p]),
+    "cpr_fit_estimate_noalloc": (ctypes.c_int, [ctypes.POINTER(CprTensor), ctypes.POINTER(CprKtensor), ctypes.c_int64,
+                                                ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
+                                                ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "cpr_profile_begin": (ctypes.c_int, [ctypes.c_uint]),
     "cpr_profile_end": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }
@@ -357,6 +360,18 @@ def cpr_fit_estimate(X, dims, lam, factors, P_hat, seed, b=0, norm_x=-1.0, strea
                                 float(norm_x), ctypes.byref(fit), ctypes.c_void_p(ws.data_ptr()),
                                 ctypes.c_size_t(ws.numel()), _stream(stream))
     _check(st, "cpr_fit_estimate")
+    return fit.value
+
+
+def cpr_fit_estimate_noalloc(X, dims, lam, factors, P_hat, seed, b=0, norm_x=-1.0, stream=None):
+    """The sampled fit without a workspace: the library's fixed device scratch array is used instead, so
+    nothing is allocated for this call (see include/cprand.h for the sharing rules)."""
+    d = tensor_desc(X, dims)
+    k = ktensor_desc(lam, factors)
+    fit = ctypes.c_double()
+    st = lib().cpr_fit_estimate_noalloc(ctypes.byref(d), ctypes.byref(k), int(P_hat), ctypes.c_uint64(seed), int(b),
+                                        float(norm_x), ctypes.byref(fit), _stream(stream))
+    _check(st, "cpr_fit_estimate_noalloc")
     return fit.value
 
 
