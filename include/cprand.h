@@ -97,6 +97,15 @@ typedef struct {
   uint32_t batch_index;  /* counter word 3 (decomposition index inside a batch) */
   uint32_t first_iter;   /* counter word 2 of the first outer iteration (resume) */
   double* fit_trace_dev; /* device, >= max(max_iters, fixed_iters) doubles, or NULL */
+  int32_t loop_path;     /* how the outer iterations are launched: 0 automatic (a thread-block
+                            cluster per problem when every problem of the call fits one, else the
+                            captured graph); 1 clusters (CPR_EINVAL if a problem does not fit);
+                            2 captured graph; 3 plain stream launches.  Read from the first
+                            problem's options in a batched call. */
+  int32_t layout;        /* 0: before iterating, also store every mode-n unfolding X_(n) as its own
+                            column-major copy (N-1 extra copies of the tensor in the workspace) so
+                            that every sampled fiber is read contiguously; 1: gather every mode
+                            from the single tensor (fibers of modes 2..N are strided) */
 } cpr_opts;
 
 typedef struct {
@@ -120,7 +129,8 @@ enum {
   CPR_KERNEL_NORMALIZE = 5,  /* column normalization */
   CPR_KERNEL_FIT = 6,        /* sampled fit + stopping test */
   CPR_KERNEL_OTHER = 7,      /* setup, norm, unmixing */
-  CPR_KERNEL_CLASSES = 8
+  CPR_KERNEL_LOOP = 8,       /* whole iteration loop in one thread-block cluster per problem */
+  CPR_KERNEL_CLASSES = 9
 };
 
 /* Fill *opts with the paper's defaults (Sec. 4.2): max_iters 200, fit_tol 1e-4, noise rule off,

@@ -36,7 +36,9 @@ class CprOpts(ctypes.Structure):
                 ("noise_eta", ctypes.c_double), ("stall_iters", ctypes.c_int32),
                 ("init_from_out", ctypes.c_int32), ("fit_samples", ctypes.c_int64), ("seed", ctypes.c_uint64),
                 ("batch_index", ctypes.c_uint32), ("first_iter", ctypes.c_uint32),
-                ("fit_trace_dev", ctypes.c_void_p)]
+                ("fit_trace_dev", ctypes.c_void_p), ("loop_path", ctypes.c_int32), ("layout", ctypes.c_int32)]
+
+LOOP_AUTO, LOOP_CLUSTER, LOOP_GRAPH, LOOP_STREAM = range(4)
 
 
 class CprResult(ctypes.Structure):
@@ -99,7 +101,7 @@ _SIGS = {
     "cpr_profile_end": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }
 
-KERNEL_CLASSES = ["mix", "sample_skr", "contract", "chol", "solve", "normalize", "fit", "other"]
+KERNEL_CLASSES = ["mix", "sample_skr", "contract", "chol", "solve", "normalize", "fit", "other", "loop"]
 
 
 def lib():

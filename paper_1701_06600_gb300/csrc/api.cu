@@ -307,6 +307,11 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws) {
       mb.xhat = cv.take<unsigned char>((size_t)p.P * elem_size(pl.dtype));
       p.X = mb.xhat;
     }
+    // the copies each mode-n gather reads
+    p.use_rep = (S > 0 && o && o->layout == 0) ? 1 : 0;
+    p.Xrep[0] = p.X;
+    for (int n = 1; n < N; ++n)
+      p.Xrep[n] = p.use_rep ? (const void*)cv.take<unsigned char>((size_t)p.P * elem_size(pl.dtype)) : p.X;
     // grid maxima
     g.max_S = std::max(g.max_S, S);
     g.max_spl = std::max(g.max_spl, p.spl);
@@ -466,6 +471,9 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
         cur ^= 1;
       }
     }
+    if (p.use_rep)
+      for (int n = 1; n < p.N; ++n)
+        CPR_LAUNCH(CPR_KERNEL_OTHER, launch_unfold_copy(p.X, const_cast<void*>(p.Xrep[n]), p.dtype, p.N, p.dims, n, s));
     if (from_out) {
       for (int n = 1; n < p.N; ++n)
         CPR_CUDA(cudaMemcpyAsync(p.A64[n], outs[b].factors[n], sizeof(double) * p.dims[n] * p.R,
@@ -488,8 +496,32 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
   // lives inside the loop (events need plain stream launches)
   const unsigned loop_classes = (1u << CPR_KERNEL_SAMPLE_SKR) | (1u << CPR_KERNEL_CONTRACT) | (1u << CPR_KERNEL_CHOL) |
                                 (1u << CPR_KERNEL_SOLVE) | (1u << CPR_KERNEL_NORMALIZE) | (1u << CPR_KERNEL_FIT);
-  const bool use_graph = !(prof().on && (prof().mask & loop_classes));
-  if (use_graph) {
+  const int path = op[0].loop_path;
+  if (path < 0 || path > 3) return CPR_EINVAL;
+  const bool stream_only = path == 3 || (prof().on && (prof().mask & loop_classes));
+  // small problems: the whole loop in thread-block clusters (one cluster per problem at a time)
+  int C = 16, csmem = -1, ncl = 0;
+  if (!stream_only && path != 2) {
+    int maxR = 0;
+    for (int b = 0; b < B; ++b) maxR = std::max(maxR, pl.probs[b].R);
+    for (int c : {16, 8}) {
+      C = c;
+      csmem = cluster_smem_bytes(pl.probs.data(), B, C);
+      if (csmem < 0) continue;
+      ncl = cluster_capacity(pl.dtype, C, csmem, maxR);
+      if (ncl > 0) break;
+    }
+    if (path == 1 && ncl <= 0) return CPR_EINVAL;
+    if (ncl > 0) {
+      ncl = std::min(ncl, B);
+      CPR_CUDA(cudaMemsetAsync(pl.d_counter + 1, 0, sizeof(int), s));
+      CPR_LAUNCH(CPR_KERNEL_LOOP, launch_cluster_run(pl.d_probs, B, pl.d_counter + 1, pl.dtype, C, csmem, ncl, maxR, s));
+    }
+  }
+  const bool use_graph = !stream_only && ncl <= 0;
+  if (ncl > 0) {
+    // the cluster kernel ran the whole loop
+  } else if (use_graph) {
     if (int st = run_iterations_graph(pl, maxN, cap, s, &body_kernels)) return st;
   } else {
     // profiling: plain stream launches (events around single kernels), stop flag polled per chunk
@@ -562,6 +594,8 @@ void cpr_default_opts(cpr_opts* o) {
   o->batch_index = 0;
   o->first_iter = 0;
   o->fit_trace_dev = nullptr;
+  o->loop_path = 0;
+  o->layout = 0;
 }
 
 const char* cpr_status_string(int status) {
@@ -594,6 +628,7 @@ size_t cpr_workspace_size(int method, const cpr_tensor* X, int R, int64_t S, con
     }
     case CPR_METHOD_UPDATE: {
       if (check_rank_samples(R, S)) return 0;
+      o.layout = 1;
       static double* dummy[CPR_MAX_ORDER] = {};
       ProbSpec sp{X, R, S, 0, &o, dummy, (double*)nullptr};
       // caller-owned factors and lambda take no workspace
@@ -678,6 +713,7 @@ int cpr_sampled_update(const cpr_tensor* X, cpr_ktensor* K, int mode, int64_t S,
   o.batch_index = b;
   o.first_iter = t;
   o.fixed_iters = 1;
+  o.layout = 1;
   ProbSpec sp{X, R, S, 0, &o, K->factors, K->lambda};
   const Plan measure = make_plan(1, &sp, 0, nullptr);
   if (int st = check_ws(ws, ws_bytes, measure.bytes)) return st;

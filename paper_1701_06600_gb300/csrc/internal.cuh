@@ -48,6 +48,10 @@ struct Prob {
   int64_t st[kMaxOrder];   // column-major strides: st[n] = prod_{m<n} dims[m]
   int64_t P;               // prod dims
   const void* X;           // tensor being decomposed (the mixed tensor for CPRAND-MIX)
+  const void* Xrep[kMaxOrder];  // mode-n gathers read Xrep[n]: X itself (mode 1, or no copies) or
+                                // X_(n) stored column-major (every sampled fiber contiguous)
+  int32_t use_rep;         // Xrep[n] for n >= 1 are the column-major unfoldings
+  int32_t pad_rep;
 
   float* A32[kMaxOrder];   // FP32 working copy of each factor (I_n x R row-major), unnormalized
   double* A64[kMaxOrder];  // FP64 factors (I_n x R row-major), unnormalized during a run
@@ -170,6 +174,11 @@ cudaError_t launch_fit(const Prob* probs, const GridInfo& g, cudaStream_t s);
 cudaError_t launch_loop_cond(const Prob* probs, int B, int* loop_iter, int cap, unsigned long long cond_handle,
                              cudaStream_t s);
 cudaError_t prepare_kernel_attributes();
+// the whole iteration loop in thread-block clusters (small problems)
+int cluster_smem_bytes(const Prob* probs_host, int B, int C);
+int cluster_capacity(int dtype, int C, int smem, int maxR);
+cudaError_t launch_cluster_run(const Prob* probs, int B, int* queue, int dtype, int C, int smem, int nclusters,
+                               int maxR, cudaStream_t s);
 cudaError_t launch_sumsq(const void* X, int dtype, int64_t P, double* part, int nblk, cudaStream_t s);
 cudaError_t launch_sumsq_finish(const double* part, int nblk, double* out_norm, State* st,
                                 int nstates, cudaStream_t s);
@@ -181,6 +190,23 @@ cudaError_t launch_sample_only(const void* X, int N, const int64_t* dims, int n,
                                cudaStream_t s);
 cudaError_t launch_gather_only(const void* X, int dtype, int64_t I, int64_t st, int64_t S,
                                const int64_t* off, void* out, cudaStream_t s);
+
+// mode-n unfolding X_(n) stored column-major (a batched transpose)
+cudaError_t launch_unfold_copy(const void* X, void* Y, int dtype, int N, const int64_t* dims, int n, cudaStream_t s);
+
+// Storage offset of the first entry of the mode-n fiber with multi-index idx (mode-n slot ignored),
+// and the stride between its entries, in the copy a mode-n gather reads.
+__device__ __forceinline__ int64_t fiber_offset(const Prob& p, int n, const uint32_t* idx_by_mode, int64_t* stride) {
+  int64_t off = 0;
+  const int64_t In = p.dims[n];
+  for (int m = 0; m < p.N; ++m) {
+    if (m == n) continue;
+    const int64_t w = (p.use_rep && m < n) ? p.st[m] * In : p.st[m];
+    off += (int64_t)idx_by_mode[m] * w;
+  }
+  *stride = p.use_rep ? 1 : p.st[n];
+  return off;
+}
 
 // mixing (Alg. 5)
 cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, double* table, float* W32,

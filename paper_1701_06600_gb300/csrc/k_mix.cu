@@ -167,6 +167,49 @@ cudaError_t launch_mix_mode(const void* X, void* Y, int dtype, int N, const int6
   }
 }
 
+// Mode-n unfolding X_(n) stored column-major: with X viewed as [L][I_n][Rr] (L = prod_{m<n} I_m
+// fastest), Y[i + I_n (l + L r)] = X[l + L (i + I_n r)].  Column j = l + L r of X_(n) is the mode-n
+// fiber with unfolding index j (the index map of Sec. 2.1), contiguous in Y.  32 x 32 tiles through
+// shared memory: coalesced reads along l, coalesced writes along i.
+template <typename T>
+__global__ void __launch_bounds__(256) k_unfold_copy(const T* __restrict__ X, T* __restrict__ Y, int64_t L, int64_t I,
+                                                     int64_t Rr) {
+  __shared__ T tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  const int64_t l0 = (int64_t)blockIdx.x * 32, i0 = (int64_t)blockIdx.y * 32;
+  for (int64_t r = blockIdx.z; r < Rr; r += gridDim.z) {
+    const T* Xr = X + r * L * I;
+    T* Yr = Y + r * L * I;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = i0 + ty + 8 * k, l = l0 + tx;
+      if (l < L && i < I) tile[ty + 8 * k][tx] = Xr[l + L * i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t l = l0 + ty + 8 * k, i = i0 + tx;
+      if (l < L && i < I) Yr[i + I * l] = tile[tx][ty + 8 * k];
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_unfold_copy(const void* X, void* Y, int dtype, int N, const int64_t* dims, int n, cudaStream_t s) {
+  int64_t L = 1, Rr = 1;
+  for (int m = 0; m < n; ++m) L *= dims[m];
+  for (int m = n + 1; m < N; ++m) Rr *= dims[m];
+  const int64_t I = dims[n];
+  const dim3 grid((unsigned)((L + 31) / 32), (unsigned)((I + 31) / 32), (unsigned)(Rr < 65535 ? Rr : 65535));
+  switch (dtype) {
+    case CPR_F64: k_unfold_copy<double><<<grid, 256, 0, s>>>((const double*)X, (double*)Y, L, I, Rr); break;
+    case CPR_F32: k_unfold_copy<float><<<grid, 256, 0, s>>>((const float*)X, (float*)Y, L, I, Rr); break;
+    default:
+      k_unfold_copy<unsigned short><<<grid, 256, 0, s>>>((const unsigned short*)X, (unsigned short*)Y, L, I, Rr);
+  }
+  return cudaGetLastError();
+}
+
 // A = D F^T A^ in FP64: a block computes 32 rows i of A (all R columns); F and A^ are staged through
 // shared memory in 32-row chunks of k so every global load is coalesced and many are in flight.
 constexpr int kUnmixRows = 32;

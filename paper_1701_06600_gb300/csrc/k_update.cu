@@ -161,19 +161,18 @@ __global__ void __launch_bounds__(kP1Rows) k_sample_contract(const Prob* probs, 
     const uint4 w0 = philox10(make_uint4(j, counter_word1(kStreamSamples, 0, n), t, p.b), k0, k1);
     uint4 w1 = make_uint4(0u, 0u, 0u, 0u);
     if (N - 1 > 4) w1 = philox10(make_uint4(j, counter_word1(kStreamSamples, 1, n), t, p.b), k0, k1);
-    int64_t off = 0;
     int k = 0;
     for (int m = 0; m < N; ++m) {
       uint32_t im = 0;
       if (m != n) {
         const uint32_t w = k < 4 ? word_of(w0, k) : word_of(w1, k - 4);
         im = scale_index(w, (uint32_t)p.dims[m]);
-        off += (int64_t)im * p.st[m];
         ++k;
       }
       ids[tid * kMaxOrder + m] = im;
     }
-    offs[tid] = off;
+    int64_t stride;
+    offs[tid] = fiber_offset(p, n, ids + tid * kMaxOrder, &stride);
   }
   __syncthreads();
   for (int e = tid; e < cnt * R; e += blockDim.x) {
@@ -191,8 +190,8 @@ __global__ void __launch_bounds__(kP1Rows) k_sample_contract(const Prob* probs, 
   __syncthreads();
   const int64_t i = (int64_t)tile * kP1Rows + tid;
   if (i < I) {
-    const T* __restrict__ X = reinterpret_cast<const T*>(p.X);
-    const int64_t sti = i * p.st[n];
+    const T* __restrict__ X = reinterpret_cast<const T*>(p.Xrep[n]);
+    const int64_t sti = i * (p.use_rep ? 1 : p.st[n]);
     ACC acc[MAXR];
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) acc[r] = ACC(0);

@@ -298,3 +298,61 @@ def test_batched_matches_single_runs_and_oracle(cb):
         single = cb.cpr_cprand_mix(Xs[q], dims_l[q], Rs[q], Ss[q], opts=opts[q])
         f_single = cp.exact_fit(T, single["lam"].cpu().numpy(), [A.cpu().numpy() for A in single["factors"]])
         assert abs(f_gpu - f_single) < 1e-3
+
+
+# ------------------------------------------------------------------------------------------------
+# the three ways of running the iteration loop give the same run
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype,mix", [(torch.float64, False), (torch.float32, True), (torch.bfloat16, True)])
+def test_loop_paths_agree(cb, dtype, mix):
+    dims = (45, 38, 52)
+    prob = make_problem(dims, 4, C=0.5, eta=0.01, seed=31, dtype=dtype, device=DEV)
+    T = to_oracle_array(prob.X, dims)
+    fn = cb.cpr_cprand_mix if mix else cb.cpr_cprand
+    runs = {}
+    for path in (cb.LOOP_CLUSTER, cb.LOOP_GRAPH, cb.LOOP_STREAM):
+        trace = torch.zeros(12, dtype=torch.float64, device=DEV)
+        opts = cb.cpr_default_opts(seed=8, fixed_iters=12, fit_trace_dev=trace.data_ptr(), loop_path=path)
+        out = fn(prob.X, dims, 4, 60, opts=opts)
+        assert out["iters"] == 12 and out["status"] == cb.OK
+        runs[path] = (trace.cpu().numpy(), [A.cpu().numpy() for A in out["factors"]], out["lam"].cpu().numpy())
+    if mix:
+        # the oracle's CPRAND on the mixed tensor the GPU stored (BF16 storage rounds it), unmixed
+        # with the oracle's own operators
+        Th = to_oracle_array(cb.cpr_mix_tensor(prob.X, dims, seed=8), dims)
+        ops = mixing.mixing_operators(8, 0, dims)
+        ref = cp.cprand(Th, 4, 60, seed=8, rule=cp.StopRule(fixed_iters=12))
+        ref["factors"] = mixing.unmix_factors(ref["factors"], ops)
+    else:
+        ref = cp.cprand(T, 4, 60, seed=8, rule=cp.StopRule(fixed_iters=12))
+    tol = 1e-9 if dtype == torch.float64 else 1e-4
+    for path, (trace, facs, lam) in runs.items():
+        np.testing.assert_allclose(trace, ref["fits"], rtol=0, atol=tol)
+        for A, Ar in zip(facs, ref["factors"]):
+            assert rel(A, Ar) < (1e-7 if dtype == torch.float64 else 1e-3), path
+
+
+def test_cluster_path_rejects_problems_that_do_not_fit(cb):
+    dims = (3000, 20, 20)      # 3000 x 64 FP32 partial rows per CTA exceed the cluster's shared memory
+    X = rand_tensor(dims, torch.float32, 4)
+    opts = cb.cpr_default_opts(seed=1, fixed_iters=1, loop_path=cb.LOOP_CLUSTER)
+    with pytest.raises(cb.CprError):
+        cb.cpr_cprand(X, dims, 64, 100, opts=opts)
+
+
+@pytest.mark.parametrize("path", ["cluster", "graph"])
+@pytest.mark.parametrize("dims", [(41, 37, 29), (13, 11, 9, 7)])
+def test_unfolding_copies_give_identical_runs(cb, path, dims):
+    # gathering each mode from its column-major unfolding reads the same values in the same order
+    prob = make_problem(dims, 3, C=0.5, eta=0.01, seed=77, dtype=torch.float32, device=DEV)
+    lp = cb.LOOP_CLUSTER if path == "cluster" else cb.LOOP_GRAPH
+    traces = []
+    for layout in (0, 1):
+        trace = torch.zeros(6, dtype=torch.float64, device=DEV)
+        opts = cb.cpr_default_opts(seed=3, fixed_iters=6, fit_trace_dev=trace.data_ptr(), loop_path=lp,
+                                   layout=layout)
+        out = cb.cpr_cprand_mix(prob.X, dims, 3, 40, opts=opts)
+        traces.append((trace.cpu().numpy(), [A.cpu().numpy() for A in out["factors"]]))
+    np.testing.assert_array_equal(traces[0][0], traces[1][0])
+    for A, B in zip(traces[0][1], traces[1][1]):
+        np.testing.assert_array_equal(A, B)
