@@ -261,10 +261,12 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws) {
     p.X = X->data;
     p.imax = (int)imax;
     const int R = p.R, N = p.N, S = p.S;
+    const int Rp = (R + 3) / 4 * 4;
     for (int n = 0; n < N; ++n) {
       p.A32[n] = cv.take<float>((size_t)p.dims[n] * R);
       p.A64[n] = sp.user_A64 ? sp.user_A64[n] : cv.take<double>((size_t)p.dims[n] * R);
       p.scale[n] = cv.take<double>(R);
+      p.Apad[n] = (S > 0) ? (void*)cv.take<unsigned char>((size_t)p.dims[n] * Rp * (f64 ? 8 : 4)) : nullptr;
     }
     p.lambda = sp.user_lambda ? sp.user_lambda : cv.take<double>(R);
     if (S > 0) {

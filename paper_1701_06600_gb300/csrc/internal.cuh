@@ -58,6 +58,8 @@ struct Prob {
   double* scale[kMaxOrder];// per mode, R inverse column norms (1 where the norm is 0): the
                            // normalized factor is A * scale, applied lazily by its consumers
   double* lambda;          // R: column norms of the mode updated last
+  void* Apad[kMaxOrder];   // cluster loop: factor rows padded to Rp = 4 ceil(R/4) elements (FP32,
+                           // FP64 for FP64 tensors) for 16-byte vector reads by the fit
 
   // scratch of one mode update
   double* Gpart;           // nsplit x R x R partial Grams (upper triangle used)

@@ -28,7 +28,7 @@ namespace cpr {
 constexpr int kCT = 512;   // threads per CTA of the cluster kernel
 
 struct ClusterSmem {       // offsets (bytes) into the dynamic shared memory
-  int sc, lam, wr, dinv, Mp, Gp, G, Li, colp, Zd, Zf, ids, offs, V, fitp, bytes;
+  int sc, lam, wr, dinv, Mp, Gp, G, Li, T, U, Gf, Lif, colp, Zd, Zf, ids, offs, V, fitp, bytes;
   int F[kMaxOrder];        // this CTA's rows of each factor
   int rpc[kMaxOrder];      // rows of factor m per CTA (CTA c owns rows [c rpc, (c+1) rpc))
 };
@@ -55,12 +55,16 @@ __host__ __device__ inline ClusterSmem cluster_smem_layout(int N, int R, const i
   const int spc = (S + C - 1) / C;
   L.sc = o;   o = align_up(o + N * R * 8, 16);
   L.lam = o;  o = align_up(o + R * 8, 16);
-  L.wr = o;   o = align_up(o + R * 8, 16);
+  L.wr = o;   o = align_up(o + (R + 3) / 4 * 4 * 8, 16);
   L.dinv = o; o = align_up(o + R * 8, 16);
   L.Mp = o;   o = align_up(o + maxI * R * acc_bytes, 16);
   L.Gp = o;   o = align_up(o + R * R * 8, 16);
   L.G = o;    o = align_up(o + R * R * 8, 16);
   L.Li = o;   o = align_up(o + R * R * 8, 16);
+  L.T = o;    o = align_up(o + R * R * 8, 16);
+  L.U = o;    o = align_up(o + R * R * 8, 16);
+  L.Gf = o;   o = align_up(o + R * R * 4, 16);
+  L.Lif = o;  o = align_up(o + R * R * 4, 16);
   L.colp = o; o = align_up(o + R * 8, 16);
   L.Zd = o;   o = align_up(o + spc * R * 8, 16);
   L.Zf = o;   o = align_up(o + spc * R * acc_bytes, 16);
@@ -175,6 +179,145 @@ __device__ void cholesky_smem(double* G, double* dinv, int R, int* s_bad) {
   }
 }
 
+// Block-wide max of a non-negative value (every thread gets the result).
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t = fmax(t, red[q]);
+  __syncthreads();
+  return t;
+}
+
+// X = G^-1 (R x R, FP64) in shared memory, identical in every CTA (no data-dependent thread
+// counts, fixed operation order).  Small R: Cholesky and triangular inverse in FP32 (a short
+// latency chain on the FP32 pipe), X0 = L^-T L^-1, then FP64 Newton-Schulz steps
+// X <- X + X (I - G X), each squaring the residual ||I - G X||; the FP32 start is used only when
+// that residual is below 1/4.  Otherwise (and for larger R) the Cholesky and the inverse are FP64.
+// Returns through *s_bad a non-positive FP64 pivot (Gram matrix singular).
+__device__ void gram_inverse(const double* G, double* X, double* Tm, double* Um, float* Gf, float* Lif,
+                             double* dinv, double* Lw, int R, int ns_steps, int* s_bad, double* red) {
+  const int tid = threadIdx.x;
+  bool fast = R <= 16;
+  if (fast) {
+    for (int e = tid; e < R * R; e += blockDim.x) Gf[e] = (float)G[e];
+    __syncthreads();
+    __shared__ int fbad;
+    if (tid < 32) {                      // FP32 Cholesky, lane i owns row i
+      const int lane = tid;
+      float md = lane < R ? Gf[lane * R + lane] : 0.f;
+      for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+      int bad = 0;
+      for (int k = 0; k < R; ++k) {
+        const float d = Gf[k * R + k];
+        if (!(d > 1e-6f * md) || !isfinite(d)) bad = 1;
+        const float y = rsqrtf(fmaxf(d, 1e-30f));
+        __syncwarp();
+        if (lane == 0) Gf[k * R + k] = d * y;
+        if (lane > k && lane < R) Gf[lane * R + k] *= y;
+        __syncwarp();
+        if (lane > k && lane < R) {
+          const float lik = Gf[lane * R + k];
+          for (int c = k + 1; c <= lane; ++c) Gf[lane * R + c] = fmaf(-lik, Gf[c * R + k], Gf[lane * R + c]);
+        }
+        __syncwarp();
+      }
+      if (lane == 0) fbad = bad;
+    }
+    __syncthreads();
+    fast = fbad == 0;
+  }
+  if (fast) {
+    if (tid < R) {                       // L^-1 in FP32, column tid
+      const int c = tid;
+      for (int r = 0; r < c; ++r) Lif[r * R + c] = 0.f;
+      Lif[c * R + c] = 1.f / Gf[c * R + c];
+      for (int r = c + 1; r < R; ++r) {
+        float acc = 0.f;
+        for (int l = c; l < r; ++l) acc = fmaf(Gf[r * R + l], Lif[l * R + c], acc);
+        Lif[r * R + c] = -acc / Gf[r * R + r];
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < R * R; e += blockDim.x) {   // X0 = L^-T L^-1
+      const int r = e / R, c = e - r * R;
+      float acc = 0.f;
+      for (int l = max(r, c); l < R; ++l) acc = fmaf(Lif[l * R + r], Lif[l * R + c], acc);
+      X[e] = (double)acc;
+    }
+    __syncthreads();
+    for (int it = 0; it < ns_steps; ++it) {
+      double emax = 0.0;
+      for (int e = tid; e < R * R; e += blockDim.x) {   // E = I - G X
+        const int r = e / R, c = e - r * R;
+        double a0 = 0.0, a1 = 0.0;
+        int l = 0;
+        for (; l + 1 < R; l += 2) {
+          a0 = fma(G[r * R + l], X[l * R + c], a0);
+          a1 = fma(G[r * R + l + 1], X[(l + 1) * R + c], a1);
+        }
+        if (l < R) a0 = fma(G[r * R + l], X[l * R + c], a0);
+        const double ev = (r == c ? 1.0 : 0.0) - (a0 + a1);
+        Tm[e] = ev;
+        emax = fmax(emax, fabs(ev));
+      }
+      emax = block_max(emax, red);
+      if (it == 0 && !(emax < 0.25)) {
+        fast = false;
+        break;
+      }
+      for (int e = tid; e < R * R; e += blockDim.x) {   // X + X E
+        const int r = e / R, c = e - r * R;
+        double a0 = 0.0, a1 = 0.0;
+        int l = 0;
+        for (; l + 1 < R; l += 2) {
+          a0 = fma(X[r * R + l], Tm[l * R + c], a0);
+          a1 = fma(X[r * R + l + 1], Tm[(l + 1) * R + c], a1);
+        }
+        if (l < R) a0 = fma(X[r * R + l], Tm[l * R + c], a0);
+        Um[e] = X[e] + (a0 + a1);
+      }
+      __syncthreads();
+      for (int e = tid; e < R * R; e += blockDim.x) X[e] = Um[e];
+      __syncthreads();
+    }
+    if (fast) return;
+  }
+  // FP64 path: Cholesky into Lw (a copy of G), triangular inverse, X = L^-T L^-1
+  for (int e = tid; e < R * R; e += blockDim.x) Lw[e] = G[e];
+  __syncthreads();
+  cholesky_smem(Lw, dinv, R, s_bad);
+  if (tid < R) {
+    const int c = tid;
+    for (int r = 0; r < c; ++r) Tm[r * R + c] = 0.0;
+    Tm[c * R + c] = dinv[c];
+    for (int r = c + 1; r < R; ++r) {
+      double s0 = 0.0, s1 = 0.0;
+      int l = c;
+      for (; l + 1 < r; l += 2) {
+        s0 = fma(Lw[r * R + l], Tm[l * R + c], s0);
+        s1 = fma(Lw[r * R + l + 1], Tm[(l + 1) * R + c], s1);
+      }
+      if (l < r) s0 = fma(Lw[r * R + l], Tm[l * R + c], s0);
+      Tm[r * R + c] = -(s0 + s1) * dinv[r];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < R * R; e += blockDim.x) {
+    const int r = e / R, c = e - r * R;
+    double a0 = 0.0, a1 = 0.0;
+    int l = max(r, c);
+    for (; l + 1 < R; l += 2) {
+      a0 = fma(Tm[l * R + r], Tm[l * R + c], a0);
+      a1 = fma(Tm[(l + 1) * R + r], Tm[(l + 1) * R + c], a1);
+    }
+    if (l < R) a0 = fma(Tm[l * R + r], Tm[l * R + c], a0);
+    X[e] = a0 + a1;
+  }
+  __syncthreads();
+}
+
 template <typename T, typename ACC, int MAXR, int C>
 __device__ void cluster_mode_update(const Prob& p, int n, uint32_t t, unsigned char* sm, const ClusterSmem& Lo,
                                     cg::cluster_group& cl, int* s_bad) {
@@ -284,22 +427,14 @@ __device__ void cluster_mode_update(const Prob& p, int n, uint32_t t, unsigned c
     G[c * R + r] = g;
   }
   __syncthreads();
-  cholesky_smem(G, dinv, R, s_bad);
-  // column c of L^-1 by thread c (forward substitution against the unit vector e_c)
-  if (tid < R) {
-    const int c = tid;
-    for (int r = 0; r < c; ++r) Li[r * R + c] = 0.0;
-    Li[c * R + c] = dinv[c];
-    for (int r = c + 1; r < R; ++r) {
-      double s0 = 0.0, s1 = 0.0;
-      int l = c;
-      for (; l + 1 < r; l += 2) {
-        s0 = fma(G[r * R + l], Li[l * R + c], s0);
-        s1 = fma(G[r * R + l + 1], Li[(l + 1) * R + c], s1);
-      }
-      if (l < r) s0 = fma(G[r * R + l], Li[l * R + c], s0);
-      Li[r * R + c] = -(s0 + s1) * dinv[r];
-    }
+  {
+    __shared__ double red[kCT / 32];
+    double* Tm = reinterpret_cast<double*>(sm + Lo.T);
+    double* Um = reinterpret_cast<double*>(sm + Lo.U);
+    float* Gf = reinterpret_cast<float*>(sm + Lo.Gf);
+    float* Lif = reinterpret_cast<float*>(sm + Lo.Lif);
+    // Li receives X = G^-1; U doubles as the FP64 Cholesky workspace of the fallback
+    gram_inverse(G, Li, Tm, Um, Gf, Lif, dinv, Um, R, sizeof(ACC) == 8 ? 2 : 1, s_bad, red);
   }
   // ---- this CTA's rows: partial M rows summed through DSMEM (fixed order)
   const int rpc = Lo.rpc[n];
@@ -313,35 +448,25 @@ __device__ void cluster_mode_update(const Prob& p, int n, uint32_t t, unsigned c
     V1[e] = (double)a;
   }
   __syncthreads();
-  // y = L^-1 m, then a = L^-T y, every (row, column) in parallel (FP64)
+  // a = m X for every (row, column) in parallel (FP64; X = G^-1 is symmetric)
   for (int e = tid; e < nrows * R; e += kCT) {
     const int li = e / R, r = e - li * R;
     const double* m = V1 + li * R;
     double s0 = 0.0, s1 = 0.0;
     int l = 0;
-    for (; l + 1 <= r; l += 2) {
-      s0 = fma(Li[r * R + l], m[l], s0);
-      s1 = fma(Li[r * R + l + 1], m[l + 1], s1);
-    }
-    if (l <= r) s0 = fma(Li[r * R + l], m[l], s0);
-    V2[e] = s0 + s1;
-  }
-  __syncthreads();
-  for (int e = tid; e < nrows * R; e += kCT) {
-    const int li = e / R, r = e - li * R;
-    const double* y = V2 + li * R;
-    double s0 = 0.0, s1 = 0.0;
-    int l = r;
     for (; l + 1 < R; l += 2) {
-      s0 = fma(Li[l * R + r], y[l], s0);
-      s1 = fma(Li[(l + 1) * R + r], y[l + 1], s1);
+      s0 = fma(m[l], Li[l * R + r], s0);
+      s1 = fma(m[l + 1], Li[(l + 1) * R + r], s1);
     }
-    if (l < R) s0 = fma(Li[l * R + r], y[l], s0);
+    if (l < R) s0 = fma(m[l], Li[l * R + r], s0);
     const double a = s0 + s1;
-    V1[e] = a;
+    V2[e] = a;
     Fn[e] = (ACC)a;                               // this CTA's slice of the new factor
     p.A64[n][(int64_t)i0 * R + e] = a;            // FP64 result (read only after the run)
+    reinterpret_cast<ACC*>(p.Apad[n])[(int64_t)(i0 + li) * ((R + 3) / 4 * 4) + r] = (ACC)a;   // for the fit
   }
+  __syncthreads();
+  for (int e = tid; e < nrows * R; e += kCT) V1[e] = V2[e];
   __syncthreads();
   {
     // column sums of squares of this CTA's rows: 8-row chunks in parallel, then a fixed-order sum
@@ -360,6 +485,7 @@ __device__ void cluster_mode_update(const Prob& p, int n, uint32_t t, unsigned c
       colp[r] = sq;
     }
   }
+  if (n == N - 1) asm volatile("fence.acq_rel.cluster;" ::: "memory");   // padded rows read by the fit
   cl.sync();  // new factor slices and column partials of every CTA complete
   // ---- lambda and lazy scales of mode n in every CTA
   for (int r = tid; r < R; r += kCT) {
@@ -405,13 +531,21 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_run(const Prob* probs, int B
     double* fitp = reinterpret_cast<double*>(sm + Lo.fitp);
     State* st = p.state;
     // this CTA's rows of every factor (the starting point)
+    const int Rp = (R + 3) / 4 * 4;
     for (int m = 0; m < N; ++m) {
       ACC* F = reinterpret_cast<ACC*>(sm + Lo.F[m]);
+      ACC* Ap = reinterpret_cast<ACC*>(p.Apad[m]);
       const int i0 = rank * Lo.rpc[m];
       const int nr = max(0, min((int)p.dims[m], i0 + Lo.rpc[m]) - i0);
-      for (int e = tid; e < nr * R; e += kCT) {
-        if constexpr (sizeof(ACC) == 8) F[e] = p.A64[m][(int64_t)i0 * R + e];
-        else F[e] = p.A32[m][(int64_t)i0 * R + e];
+      for (int e = tid; e < nr * Rp; e += kCT) {
+        const int li = e / Rp, r = e - li * Rp;
+        ACC v = ACC(0);
+        if (r < R) {
+          if constexpr (sizeof(ACC) == 8) v = p.A64[m][(int64_t)(i0 + li) * R + r];
+          else v = p.A32[m][(int64_t)(i0 + li) * R + r];
+          F[li * R + r] = v;
+        }
+        Ap[(int64_t)(i0 + li) * Rp + r] = v;
       }
     }
     for (int e = tid; e < N * R; e += kCT) sc[e] = p.scale[e / R][e % R];
@@ -442,42 +576,42 @@ __global__ void __launch_bounds__(kCT, 1) k_cluster_run(const Prob* probs, int B
         break;
       }
       // ---- sampled fit (Sec. 3.4) on this CTA's share of the fixed entries
-      for (int r = tid; r < R; r += kCT) {
-        double w = lam[r];
-        for (int m = 0; m < N; ++m) w *= sc[m * R + r];
+      for (int r = tid; r < Rp; r += kCT) {
+        double w = 0.0;
+        if (r < R) {
+          w = lam[r];
+          for (int m = 0; m < N; ++m) w *= sc[m * R + r];
+        }
         wr[r] = w;
       }
       __syncthreads();
       const int fpc = (p.P_hat + C - 1) / C;
       const int f0 = rank * fpc, f1 = min(p.P_hat, f0 + fpc);
       double e2 = 0.0;
+      constexpr int VW = 16 / sizeof(ACC);          // elements per 16-byte vector
+      const int nv = Rp / VW;
       for (int j = f0 + tid; j < f1; j += kCT) {
         const uint32_t* id = p.fit_idx + (int64_t)j * N;
-        const ACC* rows[kMaxOrder];
+        const uint4* rows[kMaxOrder];
 #pragma unroll
         for (int m = 0; m < kMaxOrder; ++m)
-          rows[m] = (m < N) ? factor_row<ACC, C>(cl, sm, Lo, m, __ldg(&id[m]), R) : nullptr;
+          rows[m] = (m < N) ? reinterpret_cast<const uint4*>(reinterpret_cast<const ACC*>(p.Apad[m]) +
+                                                             (int64_t)__ldg(&id[m]) * Rp)
+                            : nullptr;
         ACC acc = ACC(0);
-        int r = 0;
-        for (; r + 4 <= R; r += 4) {   // four columns per round: 4N independent loads in flight
-          ACC w0 = (ACC)wr[r], w1 = (ACC)wr[r + 1], w2 = (ACC)wr[r + 2], w3 = (ACC)wr[r + 3];
-#pragma unroll
-          for (int m = 0; m < kMaxOrder; ++m) {
-            if (m < N) {
-              w0 *= rows[m][r];
-              w1 *= rows[m][r + 1];
-              w2 *= rows[m][r + 2];
-              w3 *= rows[m][r + 3];
-            }
-          }
-          acc += (w0 + w1) + (w2 + w3);
-        }
-        for (; r < R; ++r) {
-          ACC w = (ACC)wr[r];
+        for (int v = 0; v < nv; ++v) {
+          uint4 q[kMaxOrder];
 #pragma unroll
           for (int m = 0; m < kMaxOrder; ++m)
-            if (m < N) w *= rows[m][r];
-          acc += w;
+            if (m < N) q[m] = __ldcg(&rows[m][v]);
+#pragma unroll
+          for (int u = 0; u < VW; ++u) {
+            ACC w = (ACC)wr[v * VW + u];
+#pragma unroll
+            for (int m = 0; m < kMaxOrder; ++m)
+              if (m < N) w *= reinterpret_cast<const ACC*>(&q[m])[u];
+            acc += w;
+          }
         }
         const double e = p.fit_x[j] - (double)acc;
         e2 = fma(e, e, e2);
