@@ -46,7 +46,7 @@ FP32_LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -81,7 +81,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -134,13 +134,23 @@ def kernel_traffic(cls):
     return None
 
 
-def algorithmic(cls, w, P, b):
-    """Algorithmic bytes and flops of ONE launch of a kernel class on this workload."""
-    I, R, S = w["dims"][0], w["R"], w["S"]
+def algorithmic(cls, w, P, b, iters_per_launch=None):
+    """Algorithmic bytes and flops of ONE launch of a kernel class on this workload.
+
+    mix: one mode-n product, reads and writes the tensor once (2 P b bytes), 2 I_n P flops.
+    loop: the whole iteration loop of one decomposition; per outer iteration and mode the sampled
+    fibers (S I_n b bytes), plus the fit entries' values once (P_hat 8 bytes); flops 2 S R I_n per
+    mode."""
+    dims, R, S, Ph = w["dims"], w["R"], w["S"], w["P_hat"]
+    N = len(dims)
     if cls == "mix":
-        return {"bytes": 2.0 * P * b, "flops": 2.0 * I * P}
-    if cls == "contract":
-        return {"bytes": float(S * I * b + S * R * 4 + S * 8), "flops": 2.0 * S * R * I}
+        return {"bytes": 2.0 * P * b, "flops": 2.0 * dims[0] * P}
+    if cls == "loop" and iters_per_launch:
+        # DRAM-relevant bytes: the sampled fibers (the factor rows and the fit entries' rows are
+        # L2-resident); the fit values are read once per decomposition
+        per_iter = sum(S * I * b for I in dims)
+        return {"bytes": float(per_iter * iters_per_launch + Ph * 8),
+                "flops": float(iters_per_launch * sum(2 * S * R * I for I in dims))}
     return None
 
 
@@ -171,15 +181,16 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
-    # warm-up; the first warm-up step (plain stream launches, events around every kernel) also
-    # finds the kernel class with the most device time
-    cb.cpr_profile_begin(0xFF)
+    # warm-up; the first warm-up step (events around the launches of the production kernels: the
+    # mixing passes, the iteration loop, the rest) also finds the kernel with the most device time
+    prod_mask = sum(1 << cb.KERNEL_CLASSES.index(c) for c in ("mix", "loop", "other"))
+    cb.cpr_profile_begin(prod_mask)
     run()
     prof_all = cb.cpr_profile_end()
     for _ in range(max(0, args.warmup - 1)):
         run()
     torch.cuda.synchronize()
-    dom = max(prof_all, key=lambda c: prof_all[c][0] if c != "other" else -1)
+    dom = max(("mix", "loop"), key=lambda c: prof_all[c][0])
 
     # timed region 1: the production path (iteration loop as one graph launch), no profiler
     clocks = ClockSampler(local_rank)
@@ -199,16 +210,16 @@ def run_ours(args, rank, world, local_rank):
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    clk = clocks.stop()
     total_ms = ev0.elapsed_time(ev1)
     # timed region 2: the same steps with CUDA events around every launch of the dominant kernel
-    # (kernels inside the iteration loop are then launched one by one on the stream)
     torch.cuda.synchronize()
     cb.cpr_profile_begin(1 << cb.KERNEL_CLASSES.index(dom))
+    iters2 = 0
     for _ in range(args.steps):
-        run()
+        iters2 += run()["iters"]
     torch.cuda.synchronize()
     prof = cb.cpr_profile_end()
+    clk = clocks.stop()   # sampled across both timed regions
     # max over ranks of the time, sum over ranks of the work
     vals = torch.tensor([total_ms, it_ms, float(iters)], dtype=torch.float64, device=dev)
     if world > 1:
@@ -251,24 +262,30 @@ def run_ours(args, rank, world, local_rank):
 
     pk, pk_src = peaks()
     roof = None
-    alg = algorithmic(dom, w, P, X.element_size())
     dom_ms, dom_n = prof[dom]
+    alg = algorithmic(dom, w, P, X.element_size(), iters_per_launch=iters2 / max(1, dom_n))
     if alg is not None and dom_n > 0:
         per_launch_s = dom_ms / dom_n / 1e3
         if dom == "mix":
-            # SIMT FP32 mode product: bound by FP32 FMA issue (152 SMs x 128 lanes x 2 flop x max clock)
-            peak = SMS * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            ach = alg["flops"] / per_launch_s / 1e12
-            roof = {"bound": "alu", "kernel": "k_mix_mode (SIMT FP32 mode-n DCT product)", "achieved": ach,
-                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %d MHz" % pk.get("sm_max_mhz", 2070),
-                    "traffic": kernel_traffic(dom), "per_launch_ms": dom_ms / dom_n,
-                    "algorithmic_bytes": alg["bytes"], "algorithmic_flops": alg["flops"]}
+            # tcgen05 kind::tf32 with the 3xTF32 split: three tensor-core products per algorithmic
+            # multiply-add; peak = TF32 dense = measured BF16 (sustained, timed inside a long step) x
+            # the nominal TF32/BF16 ratio 1.1/2.25
+            peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * (1.1 / 2.25)
+            ach = 3.0 * alg["flops"] / per_launch_s / 1e12
+            roof = {"bound": "tensor", "kernel": "k_mix_tc (tcgen05 kind::tf32, 3xTF32 split, mode-n DCT product)",
+                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "peak_source": "%s bf16 sustained x 1.1/2.25" % pk_src,
+                    "achieved_note": "executed TF32 tensor flops = 3 x algorithmic (2 I_n P per launch)",
+                    "traffic": kernel_traffic("mix"), "per_launch_ms": dom_ms / dom_n,
+                    "algorithmic_bytes": alg["bytes"], "algorithmic_flops": alg["flops"],
+                    "hbm_frac": alg["bytes"] / per_launch_s / 1e9 / pk["hbm_gbs"]}
         else:
             ach = alg["bytes"] / per_launch_s / 1e9
-            roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / pk["hbm_gbs"], "peak_source": pk_src, "traffic": kernel_traffic(dom),
-                    "per_launch_ms": dom_ms / dom_n, "algorithmic_bytes": alg["bytes"]}
+            roof = {"bound": "hbm", "kernel": "k_cluster_run (whole iteration loop, one 16-CTA cluster)",
+                    "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                    "peak_source": pk_src, "traffic": kernel_traffic("loop"), "per_launch_ms": dom_ms / dom_n,
+                    "algorithmic_bytes": alg["bytes"], "algorithmic_flops": alg["flops"],
+                    "note": "latency-bound: per mode a chain of cluster barriers and dependent FP64 operations"}
     out = {
         "metric": "ALS iters/s", "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
@@ -285,7 +302,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_iters * (world if world > 1 else 1) / e2e_s, "unit": "iters/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "note": "wall clock per full call incl. H2D of X, mixing, iterations, unmixing, D2H"},
-        "kernel_ms_per_step": {c: prof_all[c][0] for c in prof_all},
+        "kernel_ms_per_step": {c: prof_all[c][0] for c in ("mix", "loop", "other")},
         "dominant_kernel": dom,
         "roofline": roof,
     }

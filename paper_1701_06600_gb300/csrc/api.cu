@@ -171,6 +171,7 @@ struct PhaseEvents {
 // Mixing buffers of one problem.
 struct MixBufs {
   float* W32[kMaxOrder] = {};
+  float* Wlo[kMaxOrder] = {};   // tensor-core path: low tf32 halves (W32 then holds the high halves)
   double* W64[kMaxOrder] = {};
   double* F64[kMaxOrder] = {};
   double* sg[kMaxOrder] = {};
@@ -189,6 +190,7 @@ struct Plan {
   int* d_counter = nullptr;
   double* d_normpart = nullptr;
   void* d_tmp = nullptr;     // shared ping-pong buffer of the mixing passes
+  void* d_tmp2 = nullptr;    // second pass buffer (tensor-core mixing reads unfoldings)
   int normblk = 0;
   size_t bytes = 0;
 };
@@ -230,7 +232,10 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws) {
   for (int b = 0; b < B; ++b) maxP = std::max(maxP, prod_dims(specs[b].X));
   pl.normblk = sumsq_blocks(maxP);
   pl.d_normpart = cv.take<double>(pl.normblk);
-  if (mix) pl.d_tmp = cv.take<unsigned char>((size_t)maxP * elem_size(pl.dtype));
+  if (mix) {
+    pl.d_tmp = cv.take<unsigned char>((size_t)maxP * elem_size(pl.dtype));
+    if (pl.dtype == CPR_F32) pl.d_tmp2 = cv.take<unsigned char>((size_t)maxP * elem_size(pl.dtype));
+  }
   GridInfo& g = pl.g;
   memset(&g, 0, sizeof(g));
   g.B = B;
@@ -302,6 +307,7 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws) {
         const size_t I = (size_t)p.dims[n];
         if (f64) mb.W64[n] = cv.take<double>(I * I);
         else mb.W32[n] = cv.take<float>(I * I);
+        if (pl.dtype == CPR_F32) mb.Wlo[n] = cv.take<float>(I * I);
         mb.F64[n] = cv.take<double>(I * I);
         mb.sg[n] = cv.take<double>(I);
       }
@@ -337,6 +343,45 @@ cpr_opts defaults() {
 }
 
 // Enqueue the mode loop and the fit/stop test of one outer iteration for the whole batch.
+// The N mixing passes X -> final (standard layout), Alg. 5 mixing step.  On the tensor cores when
+// every mode allows it (FP32, I_n a multiple of 4): pass 0 reads X directly, pass n >= 1 reads the
+// mode-n unfolding of the previous result (t2), results alternate through t1 and the last lands in
+// `final`; the last pass also writes its unfolding into rep_last when given (*wrote_rep_last).
+// Otherwise SIMT passes ping-pong between final and t1 so that the last lands in final.
+int enqueue_mixing(const void* src, void* final, void* t1, void* t2, void* rep_last, int dtype, int N,
+                   const int64_t* dims, float* const* W32, float* const* Wlo, double* const* W64, int* err,
+                   cudaStream_t s, int64_t& launches, bool* wrote_rep_last) {
+  bool tc = dtype == CPR_F32 && t2 != nullptr;
+  for (int n = 0; n < N && tc; ++n) tc = Wlo[n] != nullptr && mix_tc_supported(dtype, (int)dims[n]);
+  *wrote_rep_last = false;
+  if (tc) {
+    for (int n = 0; n < N; ++n)
+      CPR_LAUNCH(CPR_KERNEL_OTHER, launch_split_tf32(W32[n], W32[n], Wlo[n], dims[n] * dims[n], s));
+    const float* U = static_cast<const float*>(src);
+    for (int n = 0; n < N; ++n) {
+      if (n > 0) {
+        CPR_LAUNCH(CPR_KERNEL_OTHER, launch_unfold_copy(t1, t2, dtype, N, dims, n, s));
+        U = static_cast<const float*>(t2);
+      }
+      const bool last = n == N - 1;
+      float* ystd = static_cast<float*>(last ? final : t1);
+      float* yunf = (last && rep_last && n > 0) ? static_cast<float*>(rep_last) : nullptr;
+      CPR_LAUNCH(CPR_KERNEL_MIX, launch_mix_tc(U, ystd, yunf, W32[n], Wlo[n], N, dims, n, 1, err, s));
+      if (yunf) *wrote_rep_last = true;
+    }
+    return CPR_OK;
+  }
+  const void* cur_src = src;
+  void* bufs[2] = {final, t1};
+  int cur = (N % 2 == 1) ? 0 : 1;
+  for (int n = 0; n < N; ++n) {
+    CPR_LAUNCH(CPR_KERNEL_MIX, launch_mix_mode(cur_src, bufs[cur], dtype, N, dims, n, W32[n], W64[n], s));
+    cur_src = bufs[cur];
+    cur ^= 1;
+  }
+  return CPR_OK;
+}
+
 int enqueue_mode_update(const Plan& pl, int n, cudaStream_t s, int64_t& launches) {
   CPR_LAUNCH(CPR_KERNEL_CONTRACT, launch_sample_contract(pl.d_probs, pl.g, n, s));
   CPR_LAUNCH(CPR_KERNEL_SOLVE, launch_solve(pl.d_probs, pl.g, n, s));
@@ -454,6 +499,7 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
   const bool from_out = op[0].init_from_out != 0;
   for (int b = 0; b < B; ++b) {
     const Prob& p = pl.probs[b];
+    bool rep_last_done = false;
     // ||X|| on the caller's tensor (equal to the mixed tensor's norm, Alg. 5)
     CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq(Xs[b].data, p.dtype, p.P, pl.d_normpart, pl.normblk, s));
     CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq_finish(pl.d_normpart, pl.normblk, nullptr, pl.d_states + b, 1, s));
@@ -462,19 +508,13 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
       for (int n = 0; n < p.N; ++n)
         CPR_LAUNCH(CPR_KERNEL_OTHER, launch_build_mix_ops((int)p.dims[n], p.seed, p.b, n, mb.table, mb.W32[n], mb.W64[n],
                                                          mb.F64[n], mb.sg[n], s));
-      // mode passes alternate between the mixed-tensor buffer and the shared temporary so that
-      // the last pass lands in xhat
-      const void* src = Xs[b].data;
-      void* bufs[2] = {mb.xhat, pl.d_tmp};
-      int cur = (p.N % 2 == 1) ? 0 : 1;
-      for (int n = 0; n < p.N; ++n) {
-        CPR_LAUNCH(CPR_KERNEL_MIX, launch_mix_mode(src, bufs[cur], p.dtype, p.N, p.dims, n, mb.W32[n], mb.W64[n], s));
-        src = bufs[cur];
-        cur ^= 1;
-      }
+      if (int st = enqueue_mixing(Xs[b].data, mb.xhat, pl.d_tmp, pl.d_tmp2,
+                                  p.use_rep ? const_cast<void*>(p.Xrep[p.N - 1]) : nullptr, p.dtype, p.N, p.dims,
+                                  mb.W32, mb.Wlo, mb.W64, pl.d_counter + 2, s, launches, &rep_last_done))
+        return st;
     }
     if (p.use_rep)
-      for (int n = 1; n < p.N; ++n)
+      for (int n = 1; n < p.N - (rep_last_done ? 1 : 0); ++n)
         CPR_LAUNCH(CPR_KERNEL_OTHER, launch_unfold_copy(p.X, const_cast<void*>(p.Xrep[n]), p.dtype, p.N, p.dims, n, s));
     if (from_out) {
       for (int n = 1; n < p.N; ++n)
@@ -561,7 +601,10 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
   int loop_iters = 0;
   CPR_CUDA(cudaMemcpyAsync(&loop_iters, pl.d_counter, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (int st = ph.mark(3, s)) return st;
+  int dev_err = 0;
+  CPR_CUDA(cudaMemcpyAsync(&dev_err, pl.d_counter + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
   CPR_CUDA(cudaStreamSynchronize(s));
+  if (dev_err) return CPR_ETIMEOUT;
   launches += (int64_t)loop_iters * body_kernels;
   if (results) {
     for (int b = 0; b < B; ++b) {
@@ -788,36 +831,38 @@ int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, uint32_t b
   Carver cv(nullptr);
   int64_t imax = 0;
   for (int n = 0; n < N; ++n) imax = std::max(imax, X->dims[n]);
-  auto lay = [&](Carver& c, float** W32, double** W64, double** F64, double** sg, double** table, void** tmp) {
+  auto lay = [&](Carver& c, float** W32, float** Wlo, double** W64, double** F64, double** sg, double** table,
+                 void** tmp, void** tmp2, int** err) {
     for (int n = 0; n < N; ++n) {
       const size_t I = (size_t)X->dims[n];
       W32[n] = dt == CPR_F64 ? nullptr : c.take<float>(I * I);
+      Wlo[n] = dt == CPR_F32 ? c.take<float>(I * I) : nullptr;
       W64[n] = dt == CPR_F64 ? c.take<double>(I * I) : nullptr;
       F64[n] = c.take<double>(I * I);
       sg[n] = c.take<double>(I);
     }
     *table = c.take<double>((size_t)4 * imax);
     *tmp = c.take<unsigned char>((size_t)P * elem_size(dt));
+    *tmp2 = dt == CPR_F32 ? c.take<unsigned char>((size_t)P * elem_size(dt)) : nullptr;
+    *err = c.take<int>(1);
   };
-  float* W32[kMaxOrder];
+  float *W32[kMaxOrder], *Wlo[kMaxOrder];
   double *W64[kMaxOrder], *F64[kMaxOrder], *sg[kMaxOrder], *table;
-  void* tmp;
-  lay(cv, W32, W64, F64, sg, &table, &tmp);
+  void *tmp, *tmp2;
+  int* derr;
+  lay(cv, W32, Wlo, W64, F64, sg, &table, &tmp, &tmp2, &derr);
   if (int st = check_ws(ws, ws_bytes, align256(cv.off))) return st;
   Carver cw(ws);
-  lay(cw, W32, W64, F64, sg, &table, &tmp);
+  lay(cw, W32, Wlo, W64, F64, sg, &table, &tmp, &tmp2, &derr);
+  CPR_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), s));
   int64_t launches = 0;
   for (int n = 0; n < N; ++n)
     CPR_LAUNCH(CPR_KERNEL_OTHER,
                launch_build_mix_ops((int)X->dims[n], seed, b, n, table, W32[n], W64[n], F64[n], sg[n], s));
-  const void* src = X->data;
-  void* bufs[2] = {out_dev, tmp};
-  int cur = (N % 2 == 1) ? 0 : 1;
-  for (int n = 0; n < N; ++n) {
-    CPR_LAUNCH(CPR_KERNEL_MIX, launch_mix_mode(src, bufs[cur], dt, N, X->dims, n, W32[n], W64[n], s));
-    src = bufs[cur];
-    cur ^= 1;
-  }
+  bool unused = false;
+  if (int st = enqueue_mixing(X->data, out_dev, tmp, tmp2, nullptr, dt, N, X->dims, W32, Wlo, W64, derr, s, launches,
+                              &unused))
+    return st;
   return CPR_OK;
 }
 

@@ -1,0 +1,359 @@
+// Mode-n mixing product on the 5th-generation tensor cores (tcgen05, TMEM accumulators, TMA).
+//
+// One pass computes, for the column-major mode-n unfolding U = X_(n) (row j = fiber j, K = I_n
+// contiguous entries) and the mixing operator W = F_n D_n (I_n x I_n, row-major):
+//     C[j][c] = sum_k U[j][k] W[c][k]              (the fibers of X x_n W, Alg. 5 mixing step)
+// and writes C in the standard column-major layout of the tensor and, optionally, as the mode-n
+// unfolding of the result (C[j][c] at c + I_n j).  Both operands are K-major; tiles arrive by TMA
+// with the 128-byte swizzle, one thread issues tcgen05.mma (kind::tf32, M = 128, N = NT <= 256)
+// into a TMEM accumulator, four warps read it back with tcgen05.ld for the stores.
+//
+// Accuracy: tf32 keeps 10 explicit mantissa bits.  With three_x, every operand is split into
+// hi = x with its low 13 mantissa bits cleared and lo = x - hi (exact), and the product is
+// hi*hi + hi*lo + lo*hi (the dropped lo*lo term is below FP32 rounding): FP32-level results at
+// three MMAs per k-step.  W's halves come from global memory; the tile of U is split in shared
+// memory by the epilogue warps while they wait.
+//
+// Roles (256 threads): warp 0 lane 0 issues TMA; warp 1 owns TMEM and lane 0 issues MMAs;
+// warps 4-7 split the U tiles, then drain TMEM.  Two pipeline stages of 32 k-values.  Every
+// mbarrier wait is bounded: on expiry the kernel records an error and stops issuing work.
+#include <cuda.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace cpr {
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kBM = 128;             // rows (fibers) per tile
+constexpr int kBK = 32;              // k-values per stage (128 bytes of fp32)
+constexpr int kStages = 2;
+constexpr int kAStage = kBM * kBK * 4;         // 16 KB
+constexpr int kBStage = 256 * kBK * 4;         // 32 KB (room for NT = 256)
+constexpr int kStageBytes = 2 * kAStage + 2 * kBStage;
+constexpr int kBarOffset = kStages * kStageBytes;
+constexpr int kTcSmem = kBarOffset + 128 + 1024;   // + barriers + alignment slack
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+struct TcArgs {
+  int64_t J;          // rows (fibers)
+  int I;              // K = N extent
+  int NT, NB;         // columns per CTA, column blocks
+  int three_x;
+  int n, N;
+  int64_t dims[kMaxOrder];
+  int64_t st[kMaxOrder];
+  float* ystd;        // may be null
+  float* yunf;        // may be null
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on a phase of an mbarrier; false (and the CTA's error flag set) on expiry or if
+// another role already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* err) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try(b, parity)) return true;
+    if (*err) return false;
+  }
+  *err = 1;
+  return false;
+}
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_mix_tc(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmWhi,
+             const __grid_constant__ CUtensorMap tmWlo, TcArgs a) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kBarOffset);
+  uint64_t* full = bars;         // TMA landed (1 arrival + tx bytes)
+  uint64_t* conv = bars + 2;     // U tile split (128 arrivals)
+  uint64_t* empty = bars + 4;    // MMAs done with the stage (tcgen05.commit)
+  uint64_t* accum = bars + 6;    // every MMA done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 7);
+  volatile int* err = reinterpret_cast<volatile int*>(bars + 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nb = blockIdx.x % a.NB;
+  const int64_t mt = blockIdx.x / a.NB;
+  const int64_t j0 = mt * kBM;
+  const int c0 = nb * a.NT;
+  const int nk = (a.I + kBK - 1) / kBK;
+  auto A_hi = [&](int s) { return sm + s * kStageBytes; };
+  auto A_lo = [&](int s) { return sm + s * kStageBytes + kAStage; };
+  auto B_hi = [&](int s) { return sm + s * kStageBytes + 2 * kAStage; };
+  auto B_lo = [&](int s) { return sm + s * kStageBytes + 2 * kAStage + kBStage; };
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    *err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t bbytes = (uint32_t)a.NT * kBK * 4;
+
+  if (warp == 0) {
+    if (lane == 0) {   // producer
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i & 1;
+        if (i >= kStages && !mbar_wait(&empty[s], ((i - kStages) >> 1) & 1, err)) break;
+        mbar_expect_tx(&full[s], (uint32_t)kAStage + (a.three_x ? 2u : 1u) * bbytes);
+        tma_2d(A_hi(s), &tmU, i * kBK, (int)j0, &full[s]);
+        tma_2d(B_hi(s), &tmWhi, i * kBK, c0, &full[s]);
+        if (a.three_x) tma_2d(B_lo(s), &tmWlo, i * kBK, c0, &full[s]);
+        issued = i + 1;
+      }
+      if (*err) {   // never leave copies in flight: wait (bounded) for the last ones issued
+        for (int i = issued > kStages ? issued - kStages : 0; i < issued; ++i) {
+          const int s = i & 1;
+          for (uint32_t it = 0; it < kWaitLimit && !mbar_try(&full[s], (i >> 1) & 1); ++it) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {   // MMA issuer
+      const uint32_t idesc = idesc_tf32(kBM, a.NT);
+      bool ok = true;
+      for (int i = 0; i < nk && ok; ++i) {
+        const int s = i & 1;
+        if (!mbar_wait(&conv[s], (i >> 1) & 1, err)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = su32(A_hi(s)), al = su32(A_lo(s)), bh = su32(B_hi(s)), bl = su32(B_lo(s));
+#pragma unroll
+        for (int kk = 0; kk < kBK / 8; ++kk) {
+          const uint32_t off = kk * 32;   // 8 tf32 values
+          mma_tf32(tmem, sw128_desc(ah + off), sw128_desc(bh + off), idesc, (i | kk) != 0);
+          if (a.three_x) {
+            mma_tf32(tmem, sw128_desc(ah + off), sw128_desc(bl + off), idesc, 1u);
+            mma_tf32(tmem, sw128_desc(al + off), sw128_desc(bh + off), idesc, 1u);
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accum);
+    }
+  } else if (warp >= 4) {
+    const int ct = tid - 128;
+    for (int i = 0; i < nk; ++i) {   // split the U tiles into hi / lo halves
+      const int s = i & 1;
+      if (!mbar_wait(&full[s], (i >> 1) & 1, err)) break;
+      if (a.three_x) {
+        float4* hi = reinterpret_cast<float4*>(A_hi(s));
+        float4* lo = reinterpret_cast<float4*>(A_lo(s));
+        for (int v = ct; v < kAStage / 16; v += 128) {
+          const float4 x = hi[v];
+          const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+          hi[v] = h;
+          lo[v] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      mbar_arrive(&conv[s]);
+    }
+    // epilogue: TMEM lanes 32 (warp - 4) .. + 31 hold rows j0 + those lanes
+    const bool have = mbar_wait(accum, 0, err);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int rl = 32 * (warp - 4) + lane;
+    const int64_t j = j0 + rl;
+    const bool row_ok = have && j < a.J;
+    int64_t base = 0;
+    if (a.ystd && row_ok) {   // standard-layout offset of fiber j (Sec. 2.1 index map, inverted)
+      int64_t rem = j;
+      for (int m = 0; m < a.N; ++m) {
+        if (m == a.n) continue;
+        const int64_t im = rem % a.dims[m];
+        rem /= a.dims[m];
+        base += im * a.st[m];
+      }
+    }
+    const int64_t stn = a.st[a.n];
+    for (int cc = 0; cc < a.NT; cc += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * (warp - 4)) << 16) + (uint32_t)cc;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (!row_ok) continue;
+      const int cb = c0 + cc;
+      if (a.yunf) {
+        float* dst = a.yunf + j * a.I + cb;
+        if (cb + 16 <= a.I) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            reinterpret_cast<float4*>(dst)[q] =
+                make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
+                            __uint_as_float(v[4 * q + 3]));
+        } else {
+          for (int q = 0; q < 16 && cb + q < a.I; ++q) dst[q] = __uint_as_float(v[q]);
+        }
+      }
+      if (a.ystd) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (cb + q < a.I) a.ystd[base + (int64_t)(cb + q) * stn] = __uint_as_float(v[q]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+  }
+  if (tid == 0 && *err) atomicExch(a.err, 1);
+}
+
+__global__ void k_split_tf32(const float* __restrict__ w, float* __restrict__ hi, float* __restrict__ lo, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float x = w[i];
+  const float h = tf32_hi(x);
+  hi[i] = h;
+  lo[i] = x - h;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// 2D fp32 tensor map: rows of `inner` contiguous floats, `outer` rows, box {32, box_rows}, 128B swizzle.
+bool make_map(CUtensorMap* m, const float* base, int64_t inner, int64_t outer, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  const cuuint64_t strides[1] = {(cuuint64_t)inner * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool mix_tc_supported(int dtype, int I) { return dtype == CPR_F32 && I >= 1 && I % 4 == 0 && encode_fn() != nullptr; }
+
+cudaError_t launch_split_tf32(const float* w, float* hi, float* lo, int64_t n, cudaStream_t s) {
+  k_split_tf32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, hi, lo, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mix_tc(const float* U, float* ystd, float* yunf, const float* Whi, const float* Wlo, int N,
+                          const int64_t* dims, int n, int three_x, int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_mix_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  int64_t P = 1, st = 1;
+  for (int m = 0; m < N; ++m) {
+    a.dims[m] = dims[m];
+    a.st[m] = st;
+    st *= dims[m];
+    P *= dims[m];
+  }
+  const int I = (int)dims[n];
+  a.I = I;
+  a.J = P / I;
+  a.NB = (I + 255) / 256;
+  a.NT = ((I + a.NB - 1) / a.NB + 15) / 16 * 16;
+  a.three_x = three_x;
+  a.n = n;
+  a.N = N;
+  a.ystd = ystd;
+  a.yunf = yunf;
+  a.err = err;
+  CUtensorMap mU, mH, mL;
+  if (!make_map(&mU, U, I, a.J, kBM) || !make_map(&mH, Whi, I, I, a.NT) || !make_map(&mL, Wlo, I, I, a.NT))
+    return cudaErrorInvalidValue;
+  const int64_t mtiles = (a.J + kBM - 1) / kBM;
+  const int64_t blocks = mtiles * a.NB;
+  if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+  k_mix_tc<<<(unsigned)blocks, kTcThreads, kTcSmem, s>>>(mU, mH, mL, a);
+  return cudaGetLastError();
+}
+
+}  // namespace cpr

@@ -356,3 +356,17 @@ def test_unfolding_copies_give_identical_runs(cb, path, dims):
     np.testing.assert_array_equal(traces[0][0], traces[1][0])
     for A, B in zip(traces[0][1], traces[1][1]):
         np.testing.assert_array_equal(A, B)
+
+
+# ------------------------------------------------------------------------------------------------
+# a0 on the tensor cores: FP32 tensors whose dims are multiples of 4 take the tcgen05 path
+# (3xTF32, FP32-level accuracy); ragged tiles in every direction, several column blocks
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dims", [(64, 48, 40), (132, 20, 36), (300, 12, 8), (516, 8, 12), (16, 12, 20, 8),
+                                  (400, 400, 400)])
+def test_tensor_core_mixing_matches_oracle(cb, dims):
+    X = rand_tensor(dims, torch.float32, 11)
+    T = to_oracle_array(X, dims)
+    Y = cb.cpr_mix_tensor(X, dims, seed=5, b=0)
+    ref = mixing.mix_tensor(T, mixing.mixing_operators(5, 0, dims))
+    assert rel(to_oracle_array(Y, dims), ref) < 1e-5
