@@ -17,7 +17,7 @@
  *    the caller's workspace `ws` of at least cpr_workspace_size(...) bytes (256-byte aligned).
  *  - All device work is enqueued on the caller's `stream` (a cudaStream_t passed as void*; NULL
  *    means the legacy default stream).  Step entry points return right after enqueueing.  The
- *    whole-algorithm entry points (cpr_cprand, cpr_cprand_mix, cpr_cprand_batched) synchronize
+ *    whole-algorithm entry points (cpr_cp_als, cpr_cprand, cpr_cprand_mix, cpr_cprand_batched) synchronize
  *    the stream once at the end to fill cpr_result.
  *  - Return value: CPR_OK (0) or a CPR_E* status.  Arguments are checked on the host before any
  *    work is enqueued; a failed check enqueues nothing.  Device-detected conditions (a
@@ -54,7 +54,7 @@ enum {
   CPR_OK = 0,
   CPR_EINVAL = 1,      /* bad argument: order, rank, S < R, dims, dtype, null pointer, ... */
   CPR_EWORKSPACE = 2,  /* ws_bytes smaller than cpr_workspace_size() or ws misaligned */
-  CPR_ESINGULAR = 3,   /* sampled Gram matrix Z_S^T Z_S not positive definite */
+  CPR_ESINGULAR = 3,   /* Gram matrix (Z_S^T Z_S, or Z^T Z for CP-ALS) not positive definite */
   CPR_ENONFINITE = 4,  /* a NaN or Inf reached the fit estimate */
   CPR_ETIMEOUT = 5,    /* a bounded device-side wait expired */
   CPR_ECUDA = 6        /* a CUDA runtime call failed */
@@ -66,7 +66,9 @@ enum {
   CPR_METHOD_CPRAND_MIX = 1,
   CPR_METHOD_UPDATE = 2,   /* cpr_sampled_update */
   CPR_METHOD_FIT = 3,      /* cpr_fit_estimate */
-  CPR_METHOD_NORM = 4      /* cpr_tensor_norm */
+  CPR_METHOD_NORM = 4,     /* cpr_tensor_norm */
+  CPR_METHOD_CP_ALS = 5,   /* cpr_cp_als (S ignored) */
+  CPR_METHOD_MTTKRP = 6    /* cpr_mttkrp (S ignored; the size does not depend on the mode) */
 };
 
 typedef struct {
@@ -151,6 +153,25 @@ CPR_API size_t cpr_workspace_size(int method, const cpr_tensor* X, int R, int64_
  * Whole algorithms
  * ------------------------------------------------------------------------------------------- */
 
+/* CP-ALS (Alg. 1): the exact alternating least squares the randomized methods approximate.  Each
+ * outer iteration updates modes 1..N in turn: M = X_(n) Z^(n) (the exact MTTKRP over every entry of
+ * X, with Z^(n) the Khatri-Rao product of the other factors, built tile by tile and never stored),
+ * V = Hadamard product of the other factors' Grams A^(m)T A^(m) (Sec. 2.1), A^(n) = M V^-1 by an FP64
+ * Cholesky of V (Alg. 1 writes the pseudoinverse; a V that is not positive definite stops the run
+ * with CPR_ESINGULAR in result->status), then column normalization into lambda.  After each outer
+ * iteration the exact fit 1 - ||X - X~|| / ||X|| (Sec. 4.2) is formed from the last MTTKRP and the
+ * Grams, ||X - X~||^2 = ||X||^2 - 2 <X, X~> + ||X~||^2, without another pass over X, and drives the
+ * stopping rules (opts->fit_tol, max_iters, fixed_iters, noise_eta, stall_iters) on the device;
+ * result->fit_est holds that exact fit.  The MTTKRP multiplies in FP32 and sums in FP32 over at most
+ * 256 columns of X_(n) before folding into FP64 (FP64 throughout for an FP64 tensor); the Grams,
+ * solve, normalization and fit are FP64.  Before iterating, the call stores the mode-n unfoldings
+ * X_(n), n >= 2, as column-major copies in the workspace (N-1 extra copies of the tensor).  Initial
+ * factors of modes 2..N: Philox U[0,1) (stream 2, as cpr_cprand) or out->factors with
+ * opts->init_from_out.  opts->S-related fields and fit_samples are ignored; loop_path 3 launches
+ * every kernel from the host, any other value runs the iterations as one captured graph. */
+CPR_API int cpr_cp_als(const cpr_tensor* X, int R, const cpr_opts* opts, cpr_ktensor* out,
+                       cpr_result* result, void* ws, size_t ws_bytes, void* stream);
+
 /* CPRAND (Alg. 3): randomized ALS.  Each outer iteration updates modes 1..N in turn; the mode-n
  * update draws S fresh multi-indices, builds the sampled Khatri-Rao rows Z_S (Alg. 2), gathers
  * the matching mode-n fibers X_S, solves min ||Z_S A^T - X_S^T|| through the R x R normal
@@ -203,6 +224,14 @@ CPR_API int cpr_gather_fibers(const cpr_tensor* X, int mode, int64_t S, const in
 CPR_API int cpr_sampled_update(const cpr_tensor* X, cpr_ktensor* K, int mode, int64_t S, uint64_t seed,
                        uint32_t b, uint32_t t, cpr_result* result, void* ws, size_t ws_bytes,
                        void* stream);
+
+/* Exact MTTKRP (Alg. 1, the right-hand side of the mode-n update): M_dev (I_mode x R, row-major FP64)
+ * = X_(mode) Z^(mode) with Z^(mode) = A^(N) (.) ... (.) A^(mode+1) (.) A^(mode-1) (.) ... (.) A^(1)
+ * over K->factors as given (lambda is not applied).  FP32 products and FP32 sums over at most 256
+ * columns of X_(mode), folded into FP64 (FP64 throughout for an FP64 tensor).  For mode >= 1 the
+ * call first stores X_(mode) column-major in the workspace. */
+CPR_API int cpr_mttkrp(const cpr_tensor* X, const cpr_ktensor* K, int mode, double* M_dev, void* ws,
+                       size_t ws_bytes, void* stream);
 
 /* Sampled fit estimate (Sec. 3.4): F^ = 1 - sqrt(P * mean_i e_i^2) / ||X|| over P_hat entries
  * drawn from Philox stream 1 (seed, b), e_i = x_i - sum_r lambda_r prod_n A^(n)(i_n, r).  norm_x

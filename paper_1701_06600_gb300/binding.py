@@ -16,7 +16,7 @@ MAX_ORDER = 8
 MAX_RANK = 64
 F64, F32, BF16 = 0, 1, 2
 OK, EINVAL, EWORKSPACE, ESINGULAR, ENONFINITE, ETIMEOUT, ECUDA = range(7)
-METHOD_CPRAND, METHOD_CPRAND_MIX, METHOD_UPDATE, METHOD_FIT, METHOD_NORM = range(5)
+METHOD_CPRAND, METHOD_CPRAND_MIX, METHOD_UPDATE, METHOD_FIT, METHOD_NORM, METHOD_CP_ALS, METHOD_MTTKRP = range(7)
 
 _DTYPES = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 
@@ -61,6 +61,11 @@ _SIGS = {
     "cpr_sample_size": (ctypes.c_int64, [ctypes.c_int]),
     "cpr_workspace_size": (ctypes.c_size_t, [ctypes.c_int, ctypes.POINTER(CprTensor), ctypes.c_int,
                                              ctypes.c_int64, ctypes.POINTER(CprOpts)]),
+    "cpr_cp_als": (ctypes.c_int, [ctypes.POINTER(CprTensor), ctypes.c_int, ctypes.POINTER(CprOpts),
+                                  ctypes.POINTER(CprKtensor), ctypes.POINTER(CprResult), ctypes.c_void_p,
+                                  ctypes.c_size_t, ctypes.c_void_p]),
+    "cpr_mttkrp": (ctypes.c_int, [ctypes.POINTER(CprTensor), ctypes.POINTER(CprKtensor), ctypes.c_int,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "cpr_cprand": (ctypes.c_int, [ctypes.POINTER(CprTensor), ctypes.c_int, ctypes.c_int64, ctypes.POINTER(CprOpts),
                                   ctypes.POINTER(CprKtensor), ctypes.POINTER(CprResult), ctypes.c_void_p,
                                   ctypes.c_size_t, ctypes.c_void_p]),
@@ -269,6 +274,47 @@ def cpr_profile_end():
     cnt = (ctypes.c_int64 * len(KERNEL_CLASSES))()
     _check(lib().cpr_profile_end(ms, cnt), "cpr_profile_end")
     return {c: (ms[i], cnt[i]) for i, c in enumerate(KERNEL_CLASSES)}
+
+
+def cpr_cp_als(X, dims, R, opts=None, init=None, ws=None, stream=None):
+    """CP-ALS (Alg. 1) with the exact fit.  init: optional list of initial factors (modes 2..N used)."""
+    d = tensor_desc(X, dims)
+    o = opts if opts is not None else cpr_default_opts()
+    lam, factors = alloc_ktensor(dims, R, X.device)
+    if init is not None:
+        for n in range(1, len(dims)):
+            factors[n].copy_(init[n])
+        o.init_from_out = 1
+    k = ktensor_desc(lam, factors)
+    need = lib().cpr_workspace_size(METHOD_CP_ALS, ctypes.byref(d), int(R), 0, ctypes.byref(o))
+    if need == 0:
+        raise CprError(EINVAL, "cpr_cp_als")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, X.device)
+    res = CprResult()
+    st = lib().cpr_cp_als(ctypes.byref(d), int(R), ctypes.byref(o), ctypes.byref(k), ctypes.byref(res),
+                          ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()), _stream(stream))
+    _check(st, "cpr_cp_als")
+    return {"lam": lam, "factors": factors, "ws": ws, **result_dict(res)}
+
+
+def cpr_mttkrp(X, dims, factors, mode, stream=None):
+    """M = X_(mode) Z^(mode) (exact MTTKRP) over the given FP64 factors; returns I_mode x R FP64."""
+    R = int(factors[0].shape[1])
+    lam = torch.ones(R, dtype=torch.float64, device=X.device)
+    d = tensor_desc(X, dims)
+    fs = [f.contiguous() for f in factors]
+    k = ktensor_desc(lam, fs)
+    o = cpr_default_opts()
+    need = lib().cpr_workspace_size(METHOD_MTTKRP, ctypes.byref(d), R, 0, ctypes.byref(o))
+    if need == 0:
+        raise CprError(EINVAL, "cpr_workspace_size")
+    ws = workspace(need, X.device)
+    M = torch.empty((int(dims[mode]), R), dtype=torch.float64, device=X.device)
+    st = lib().cpr_mttkrp(ctypes.byref(d), ctypes.byref(k), int(mode), ctypes.c_void_p(M.data_ptr()),
+                          ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()), _stream(stream))
+    _check(st, "cpr_mttkrp")
+    return M
 
 
 def cpr_cprand(X, dims, R, S, opts=None, init=None, ws=None, stream=None):

@@ -218,8 +218,25 @@ void choose_split(int B, int64_t imax_mean, int S, int* spl, int* nsplit) {
   *nsplit = (int)((S + sp - 1) / sp);
 }
 
+// CP-ALS column split of the mode-n MTTKRP: about 8 CTAs per SM across the row tiles, at least 8
+// column tiles per split, splits a whole number of column tiles.
+void choose_als_split(Prob& p, int n) {
+  const int TI = mttkrp_tile_rows(p.als_rg, p.dtype), JT = mttkrp_tile_cols(p.als_rg, p.dtype);
+  const int64_t I = p.dims[n], J = p.P / I;
+  const int64_t rowtiles = (I + TI - 1) / TI;
+  int64_t ns = (152 * 8 + rowtiles - 1) / rowtiles;
+  const int64_t tiles = (J + JT - 1) / JT;
+  ns = std::max<int64_t>(1, std::min(ns, tiles / 8));
+  int64_t js = (J + ns - 1) / ns;
+  js = (js + JT - 1) / JT * JT;
+  p.jsplit[n] = js;
+  p.als_nsplit[n] = (int)((J + js - 1) / js);
+}
+
 // Lays out (ws == nullptr: measures) the buffers of B problems.  mix: also the mixing buffers.
-Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws) {
+// als: CP-ALS buffers (Grams, MTTKRP partials, unfolding copies of every mode when als_mode < 0,
+// else one copy buffer used for mode als_mode).
+Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws, int als = 0, int als_mode = -1) {
   Plan pl;
   pl.B = B;
   pl.mix = mix;
@@ -281,6 +298,21 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws) {
       p.Mpart = cv.take<unsigned char>((size_t)p.nsplit * imax * R * (f64 ? 8 : 4));
       p.Npart = cv.take<double>((size_t)((imax + kP2Rows - 1) / kP2Rows) * R);
     }
+    if (als) {
+      p.als_rg = mttkrp_rank_groups(R);
+      int64_t most = 1;
+      for (int n = 0; n < N; ++n) {
+        choose_als_split(p, n);
+        most = std::max<int64_t>(most, p.als_nsplit[n]);
+      }
+      const int64_t nrb = (imax + kAlsRows - 1) / kAlsRows;
+      for (int n = 0; n < N; ++n) p.gram[n] = cv.take<double>((size_t)R * R);
+      p.V = cv.take<double>((size_t)R * R);
+      p.L = cv.take<double>((size_t)R * R);
+      p.Gpart = cv.take<double>((size_t)nrb * R * R);
+      p.Npart = cv.take<double>((size_t)nrb);
+      p.Mpart = cv.take<double>((size_t)most * imax * R);
+    }
     p.P_hat = (int)sp.P_hat;
     if (p.P_hat > 0) {
       p.nfb = (p.P_hat + kFitThreads - 1) / kFitThreads;
@@ -316,10 +348,15 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws) {
       p.X = mb.xhat;
     }
     // the copies each mode-n gather reads
-    p.use_rep = (S > 0 && o && o->layout == 0) ? 1 : 0;
+    p.use_rep = ((S > 0 && o && o->layout == 0) || als) ? 1 : 0;
     p.Xrep[0] = p.X;
-    for (int n = 1; n < N; ++n)
-      p.Xrep[n] = p.use_rep ? (const void*)cv.take<unsigned char>((size_t)p.P * elem_size(pl.dtype)) : p.X;
+    if (als && als_mode >= 0) {
+      void* one = cv.take<unsigned char>((size_t)p.P * elem_size(pl.dtype));
+      for (int n = 1; n < N; ++n) p.Xrep[n] = n == als_mode ? one : nullptr;
+    } else {
+      for (int n = 1; n < N; ++n)
+        p.Xrep[n] = p.use_rep ? (const void*)cv.take<unsigned char>((size_t)p.P * elem_size(pl.dtype)) : p.X;
+    }
     // grid maxima
     g.max_S = std::max(g.max_S, S);
     g.max_spl = std::max(g.max_spl, p.spl);
@@ -414,7 +451,10 @@ cudaStream_t capture_stream() {
   return streams[dev];
 }
 
-int run_iterations_graph(const Plan& pl, int maxN, int cap, cudaStream_t s, int64_t* body_kernels) {
+// enqueue_body(capture_stream, condition_handle, kernel_count) enqueues one iteration and the kernel that
+// sets the condition.
+template <class Body>
+int run_graph_loop(Body&& enqueue_body, cudaStream_t s, int64_t* body_kernels) {
   cudaStream_t cs = capture_stream();
   if (!cs) return CPR_ECUDA;
   cudaGraph_t graph = nullptr;
@@ -443,7 +483,7 @@ int run_iterations_graph(const Plan& pl, int maxN, int cap, cudaStream_t s, int6
       break;
     }
     int64_t n_body = 0;
-    const int cst = enqueue_iteration(pl, maxN, cap, 1, (unsigned long long)h, cs, n_body);
+    const int cst = enqueue_body(cs, (unsigned long long)h, n_body);
     cudaGraph_t captured = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cs, &captured);
     if (cst != CPR_OK || ce != cudaSuccess) {
@@ -564,7 +604,10 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
   if (ncl > 0) {
     // the cluster kernel ran the whole loop
   } else if (use_graph) {
-    if (int st = run_iterations_graph(pl, maxN, cap, s, &body_kernels)) return st;
+    auto body = [&](cudaStream_t cs, unsigned long long h, int64_t& nb) {
+      return enqueue_iteration(pl, maxN, cap, 1, h, cs, nb);
+    };
+    if (int st = run_graph_loop(body, s, &body_kernels)) return st;
   } else {
     // profiling: plain stream launches (events around single kernels), stop flag polled per chunk
     int ran = 0, chunk = 4;
@@ -621,6 +664,103 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
   return CPR_OK;
 }
 
+// One outer iteration of CP-ALS (Alg. 1): per mode the Gram Hadamard product and its Cholesky
+// factor, the exact MTTKRP, the row solves (the last mode's solve also forms the exact fit and
+// applies the stopping rules); then the graph condition.
+int enqueue_als_iteration(const Plan& pl, int cap, int use_cond, unsigned long long cond, cudaStream_t s,
+                          int64_t& launches) {
+  const Prob& p = pl.probs[0];
+  for (int n = 0; n < p.N; ++n) {
+    CPR_LAUNCH(CPR_KERNEL_CHOL, launch_als_prep(pl.d_probs, p, n, s));
+    CPR_LAUNCH(CPR_KERNEL_CONTRACT, launch_mttkrp(pl.d_probs, p, n, s));
+    CPR_LAUNCH(CPR_KERNEL_SOLVE, launch_als_solve(pl.d_probs, p, n, s));
+  }
+  if (use_cond) CPR_LAUNCH(CPR_KERNEL_OTHER, launch_loop_cond(pl.d_probs, 1, pl.d_counter, cap, cond, s));
+  return CPR_OK;
+}
+
+int run_cp_als(const cpr_tensor* X, int R, const cpr_opts* opts, cpr_ktensor* out, cpr_result* result, void* ws,
+               size_t ws_bytes, cudaStream_t s) {
+  if (int st = check_tensor(X, true)) return st;
+  if (R < 1 || R > CPR_MAX_RANK) return CPR_EINVAL;
+  if (int st = check_ktensor(out, X, R)) return st;
+  cpr_opts o = opts ? *opts : defaults();
+  if (o.max_iters < 1 && o.fixed_iters < 1) return CPR_EINVAL;
+  if (o.loop_path < 0 || o.loop_path > 3) return CPR_EINVAL;
+  ProbSpec sp{X, R, 0, 0, &o, nullptr, nullptr};
+  const Plan measure = make_plan(1, &sp, 0, nullptr, 1, -1);
+  if (int st = check_ws(ws, ws_bytes, measure.bytes)) return st;
+  Plan pl = make_plan(1, &sp, 0, ws, 1, -1);
+  CPR_CUDA(prepare_kernel_attributes());
+  const Prob& p = pl.probs[0];
+  int64_t launches = 0;
+  PhaseEvents ph;
+  if (int st = ph.mark(0, s)) return st;
+  CPR_CUDA(cudaMemcpyAsync(pl.d_probs, pl.probs.data(), sizeof(Prob), cudaMemcpyHostToDevice, s));
+  CPR_CUDA(cudaMemsetAsync(pl.d_counter, 0, 4 * sizeof(int), s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_init_state(pl.d_probs, 1, s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq(X->data, p.dtype, p.P, pl.d_normpart, pl.normblk, s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq_finish(pl.d_normpart, pl.normblk, nullptr, pl.d_states, 1, s));
+  for (int n = 1; n < p.N; ++n)
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_unfold_copy(p.X, const_cast<void*>(p.Xrep[n]), p.dtype, p.N, p.dims, n, s));
+  const bool from_out = o.init_from_out != 0;
+  if (from_out)
+    for (int n = 1; n < p.N; ++n)
+      CPR_CUDA(cudaMemcpyAsync(p.A64[n], out->factors[n], sizeof(double) * p.dims[n] * p.R, cudaMemcpyDeviceToDevice,
+                               s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_init_factors(pl.d_probs, pl.g, from_out ? 1 : 0, s));
+  for (int n = 1; n < p.N; ++n) CPR_LAUNCH(CPR_KERNEL_OTHER, launch_als_gram(pl.d_probs, p, n, s));
+  if (int st = ph.mark(1, s)) return st;
+  const int cap = o.fixed_iters > 0 ? o.fixed_iters : o.max_iters;
+  const unsigned loop_classes = (1u << CPR_KERNEL_CONTRACT) | (1u << CPR_KERNEL_CHOL) | (1u << CPR_KERNEL_SOLVE);
+  const bool stream_only = o.loop_path == 3 || (prof().on && (prof().mask & loop_classes));
+  int64_t body_kernels = 0;
+  if (!stream_only) {
+    auto body = [&](cudaStream_t cs, unsigned long long h, int64_t& nb) {
+      return enqueue_als_iteration(pl, cap, 1, h, cs, nb);
+    };
+    if (int st = run_graph_loop(body, s, &body_kernels)) return st;
+  } else {
+    State hs;
+    int ran = 0, chunk = 4;
+    while (ran < cap) {
+      const int todo = std::min(chunk, cap - ran);
+      for (int c = 0; c < todo; ++c)
+        if (int st = enqueue_als_iteration(pl, cap, 0, 0ull, s, launches)) return st;
+      ran += todo;
+      CPR_CUDA(cudaMemcpyAsync(&hs, pl.d_states, sizeof(State), cudaMemcpyDeviceToHost, s));
+      CPR_CUDA(cudaStreamSynchronize(s));
+      if (hs.done) break;
+      chunk = std::min(chunk * 2, 16);
+    }
+  }
+  if (int st = ph.mark(2, s)) return st;
+  for (int n = 0; n < p.N; ++n) {
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_finalize(pl.d_probs, pl.g, n, s));
+    CPR_CUDA(cudaMemcpyAsync(out->factors[n], p.A64[n], sizeof(double) * p.dims[n] * p.R, cudaMemcpyDeviceToDevice,
+                             s));
+  }
+  CPR_CUDA(cudaMemcpyAsync(out->lambda, p.lambda, sizeof(double) * p.R, cudaMemcpyDeviceToDevice, s));
+  State h;
+  int loop_iters = 0;
+  CPR_CUDA(cudaMemcpyAsync(&h, pl.d_states, sizeof(State), cudaMemcpyDeviceToHost, s));
+  CPR_CUDA(cudaMemcpyAsync(&loop_iters, pl.d_counter, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (int st = ph.mark(3, s)) return st;
+  CPR_CUDA(cudaStreamSynchronize(s));
+  launches += (int64_t)loop_iters * body_kernels;
+  if (result) {
+    result->iters = h.iter;
+    result->status = h.status;
+    result->fit_est = h.last_fit;
+    result->norm_x = h.norm_x;
+    result->kernel_launches = launches;
+    result->ms_setup = ph.ms(0, 1);
+    result->ms_iterate = ph.ms(1, 2);
+    result->ms_finish = ph.ms(2, 3);
+  }
+  return CPR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -648,7 +788,7 @@ const char* cpr_status_string(int status) {
     case CPR_OK: return "ok";
     case CPR_EINVAL: return "invalid argument";
     case CPR_EWORKSPACE: return "workspace too small or misaligned";
-    case CPR_ESINGULAR: return "sampled Gram matrix is not positive definite";
+    case CPR_ESINGULAR: return "Gram matrix is not positive definite";
     case CPR_ENONFINITE: return "non-finite value in the fit estimate";
     case CPR_ETIMEOUT: return "bounded device wait expired";
     case CPR_ECUDA: return "CUDA runtime error";
@@ -688,6 +828,17 @@ size_t cpr_workspace_size(int method, const cpr_tensor* X, int R, int64_t S, con
     }
     case CPR_METHOD_NORM:
       return align256(sizeof(double) * (sumsq_blocks(prod_dims(X)) + 1)) + 256;
+    case CPR_METHOD_CP_ALS: {
+      if (R < 1 || R > CPR_MAX_RANK) return 0;
+      ProbSpec sp{X, R, 0, 0, &o, nullptr, nullptr};
+      return make_plan(1, &sp, 0, nullptr, 1, -1).bytes;
+    }
+    case CPR_METHOD_MTTKRP: {
+      if (R < 1 || R > CPR_MAX_RANK) return 0;
+      static double* dummy[CPR_MAX_ORDER] = {};
+      ProbSpec sp{X, R, 0, 0, &o, dummy, (double*)nullptr};
+      return make_plan(1, &sp, 0, nullptr, 1, 0).bytes;
+    }
     default:
       return 0;
   }
@@ -722,6 +873,41 @@ size_t cpr_batched_workspace_size(int B, const cpr_tensor* Xs, const int* Rs, co
 int cpr_cprand_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, const cpr_opts* opts, int mix,
                        cpr_ktensor* outs, cpr_result* results, void* ws, size_t ws_bytes, void* stream) {
   return run_batched(B, Xs, Rs, Ss, opts, mix ? 1 : 0, outs, results, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int cpr_cp_als(const cpr_tensor* X, int R, const cpr_opts* opts, cpr_ktensor* out, cpr_result* result, void* ws,
+               size_t ws_bytes, void* stream) {
+  return run_cp_als(X, R, opts, out, result, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int cpr_mttkrp(const cpr_tensor* X, const cpr_ktensor* K, int mode, double* M_dev, void* ws, size_t ws_bytes,
+               void* stream) {
+  if (int st = check_tensor(X, true)) return st;
+  if (!K || !M_dev) return CPR_EINVAL;
+  const int R = K->rank;
+  if (R < 1 || R > CPR_MAX_RANK) return CPR_EINVAL;
+  if (K->order != X->order) return CPR_EINVAL;
+  for (int n = 0; n < X->order; ++n)
+    if (K->dims[n] != X->dims[n] || !K->factors[n]) return CPR_EINVAL;
+  if (mode < 0 || mode >= X->order) return CPR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cpr_opts o = defaults();
+  ProbSpec sp{X, R, 0, 0, &o, K->factors, K->lambda};
+  const Plan measure = make_plan(1, &sp, 0, nullptr, 1, 0);
+  if (int st = check_ws(ws, ws_bytes, measure.bytes)) return st;
+  Plan pl = make_plan(1, &sp, 0, ws, 1, mode);
+  CPR_CUDA(prepare_kernel_attributes());
+  const Prob& p = pl.probs[0];
+  int64_t launches = 0;
+  CPR_CUDA(cudaMemcpyAsync(pl.d_probs, pl.probs.data(), sizeof(Prob), cudaMemcpyHostToDevice, s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_init_state(pl.d_probs, 1, s));
+  if (mode > 0)
+    CPR_LAUNCH(CPR_KERNEL_OTHER,
+               launch_unfold_copy(p.X, const_cast<void*>(p.Xrep[mode]), p.dtype, p.N, p.dims, mode, s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_init_factors(pl.d_probs, pl.g, 1, s));
+  CPR_LAUNCH(CPR_KERNEL_CONTRACT, launch_mttkrp(pl.d_probs, p, mode, s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_mttkrp_reduce(pl.d_probs, p, mode, M_dev, s));
+  return CPR_OK;
 }
 
 int cpr_sample_indices(const cpr_tensor* X, int mode, int64_t S, uint64_t seed, uint32_t b, uint32_t t,

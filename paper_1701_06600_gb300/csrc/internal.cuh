@@ -86,6 +86,14 @@ struct Prob {
   uint32_t b, t0;
 
   State* state;
+
+  // CP-ALS (Alg. 1): exact MTTKRP over the unfolding copies, Grams of the normalized factors
+  double* gram[kMaxOrder]; // per mode, R x R Gram A^T A of the normalized factor
+  double* V;               // R x R Hadamard product of the other modes' Grams (mode updated last)
+  int64_t jsplit[kMaxOrder];  // MTTKRP: unfolding columns per split, per mode
+  int32_t als_nsplit[kMaxOrder];  // MTTKRP: splits per mode
+  int32_t als_rg;          // MTTKRP: rank groups of 8 columns per thread tile (1, 2, 4 or 8)
+  int32_t pad2;
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -146,6 +154,71 @@ __device__ __forceinline__ bool arrive_last(State* st, uint32_t nblocks) {
   __syncthreads();
   if (last) __threadfence();
   return last != 0;
+}
+
+// Stopping rules of Sec. 4.2 for one problem after its fit (one thread): record the trace entry,
+// update the best fit and stall count, advance the iteration counter, set done when a rule fires.
+__device__ __forceinline__ void apply_stop_rules(const Prob& p, State* st, double fit) {
+  const int it = st->iter;
+  if (p.trace) p.trace[it] = fit;
+  const int t1 = it + 1;
+  bool stop = false;
+  if (!isfinite(fit)) {
+    st->status = CPR_ENONFINITE;
+    stop = true;
+  } else if (p.fixed_iters > 0) {
+    stop = t1 >= p.fixed_iters;
+  } else {
+    if (fit > st->best) {
+      st->best = fit;
+      st->stall = 0;
+    } else {
+      st->stall += 1;
+    }
+    if (t1 >= p.max_iters) stop = true;
+    if (t1 >= 2 && fabs(fit - st->last_fit) <= p.tol) stop = true;
+    if (p.eta >= 0.0 && fit >= 1.0 - 1.2 * p.eta) stop = true;
+    if (p.stall_iters > 0 && st->stall >= p.stall_iters) stop = true;
+  }
+  st->last_fit = fit;
+  st->iter = t1;
+  if (stop) st->done = 1;
+}
+
+// Cholesky G = L L^T in place (lower triangle), R x R in shared memory, by the whole block.
+// Returns false (on every thread) if a pivot is not positive relative to the largest diagonal.
+__device__ __forceinline__ bool block_cholesky(double* G, int R) {
+  __shared__ int bad;
+  __shared__ double maxdiag;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    double m = 0.0;
+    for (int k = 0; k < R; ++k) m = fmax(m, G[k * R + k]);
+    maxdiag = m;
+    bad = 0;
+  }
+  __syncthreads();
+  for (int k = 0; k < R; ++k) {
+    if (tid == 0) {
+      double d = G[k * R + k];
+      if (!(d > 1e-26 * maxdiag) || !isfinite(d)) {
+        bad = 1;
+        d = 1.0;
+      }
+      G[k * R + k] = sqrt(d);
+    }
+    __syncthreads();
+    const double dk = G[k * R + k];
+    for (int i = k + 1 + tid; i < R; i += blockDim.x) G[i * R + k] /= dk;
+    __syncthreads();
+    const int rem = R - k - 1;
+    for (int e = tid; e < rem * rem; e += blockDim.x) {
+      const int i = k + 1 + e / rem, c = k + 1 + e % rem;
+      if (c <= i) G[i * R + c] -= G[i * R + k] * G[c * R + k];
+    }
+    __syncthreads();
+  }
+  return bad == 0;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -209,6 +282,18 @@ __device__ __forceinline__ int64_t fiber_offset(const Prob& p, int n, const uint
   *stride = p.use_rep ? 1 : p.st[n];
   return off;
 }
+
+// CP-ALS (Alg. 1); every launch serves problem 0 of the table (CP-ALS runs one problem per call)
+int mttkrp_rank_groups(int R);
+int mttkrp_tile_rows(int rg, int dtype);
+int mttkrp_tile_cols(int rg, int dtype);
+cudaError_t launch_als_gram(const Prob* probs, const Prob& hp, int n, cudaStream_t s);
+cudaError_t launch_als_prep(const Prob* probs, const Prob& hp, int n, cudaStream_t s);
+cudaError_t launch_mttkrp(const Prob* probs, const Prob& hp, int n, cudaStream_t s);
+cudaError_t launch_als_solve(const Prob* probs, const Prob& hp, int n, cudaStream_t s);
+cudaError_t launch_mttkrp_reduce(const Prob* probs, const Prob& hp, int n, double* M, cudaStream_t s);
+cudaError_t prepare_als_attributes();
+constexpr int kAlsRows = 32;       // factor rows per block of the CP-ALS solve and Gram kernels
 
 // mixing on the tensor cores (FP32 tensors, I_n a multiple of 4)
 bool mix_tc_supported(int dtype, int I);

@@ -54,34 +54,6 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;  // valid in thread 0
 }
 
-// Stopping rules of Sec. 4.2 for one problem after its fit F (thread 0 only).
-__device__ void apply_stop_rules(const Prob& p, State* st, double fit) {
-  const int it = st->iter;
-  if (p.trace) p.trace[it] = fit;
-  const int t1 = it + 1;
-  bool stop = false;
-  if (!isfinite(fit)) {
-    st->status = CPR_ENONFINITE;
-    stop = true;
-  } else if (p.fixed_iters > 0) {
-    stop = t1 >= p.fixed_iters;
-  } else {
-    if (fit > st->best) {
-      st->best = fit;
-      st->stall = 0;
-    } else {
-      st->stall += 1;
-    }
-    if (t1 >= p.max_iters) stop = true;
-    if (t1 >= 2 && fabs(fit - st->last_fit) <= p.tol) stop = true;
-    if (p.eta >= 0.0 && fit >= 1.0 - 1.2 * p.eta) stop = true;
-    if (p.stall_iters > 0 && st->stall >= p.stall_iters) stop = true;
-  }
-  st->last_fit = fit;
-  st->iter = t1;
-  if (stop) st->done = 1;
-}
-
 // Partial sums of e_i^2 over the block's fit entries; the model entry is
 // sum_r w_r prod_n A^(n)(i_n, r) with w_r = lambda_r prod_n scale_n[r] (the lazy column scales).
 // The last block of the problem sums the partials (fixed order), forms the fit and applies the

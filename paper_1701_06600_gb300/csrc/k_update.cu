@@ -101,42 +101,6 @@ __host__ __device__ inline size_t p1_smem_bytes(int spl, int R, int acc_bytes) {
   return (size_t)kMaxSplit * 8 + (size_t)kMaxSplit * kMaxOrder * 4 + (size_t)zd * 8 + (size_t)spl * R * acc_bytes;
 }
 
-// Cholesky G = L L^T in place (lower triangle), R x R in shared memory, by the whole block.
-// Returns false (on every thread) if a pivot is not positive relative to the largest diagonal.
-__device__ bool block_cholesky(double* G, int R) {
-  __shared__ int bad;
-  __shared__ double maxdiag;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    double m = 0.0;
-    for (int k = 0; k < R; ++k) m = fmax(m, G[k * R + k]);
-    maxdiag = m;
-    bad = 0;
-  }
-  __syncthreads();
-  for (int k = 0; k < R; ++k) {
-    if (tid == 0) {
-      double d = G[k * R + k];
-      if (!(d > 1e-26 * maxdiag) || !isfinite(d)) {
-        bad = 1;
-        d = 1.0;
-      }
-      G[k * R + k] = sqrt(d);
-    }
-    __syncthreads();
-    const double dk = G[k * R + k];
-    for (int i = k + 1 + tid; i < R; i += blockDim.x) G[i * R + k] /= dk;
-    __syncthreads();
-    const int rem = R - k - 1;
-    for (int e = tid; e < rem * rem; e += blockDim.x) {
-      const int i = k + 1 + e / rem, c = k + 1 + e % rem;
-      if (c <= i) G[i * R + c] -= G[i * R + k] * G[c * R + k];
-    }
-    __syncthreads();
-  }
-  return bad == 0;
-}
-
 template <typename T, typename ACC, int MAXR>
 __global__ void __launch_bounds__(kP1Rows) k_sample_contract(const Prob* probs, int n) {
   const Prob& p = probs[blockIdx.y];
@@ -396,6 +360,7 @@ cudaError_t prepare_kernel_attributes() {
       p1_attr<__nv_bfloat16, float, 64>, p2_attr<double>, p2_attr<float>};
   for (auto f : fns)
     if ((e = f()) != cudaSuccess) return e;
+  if ((e = prepare_als_attributes()) != cudaSuccess) return e;
   if (dev < 32) done_mask |= 1 << dev;
   return cudaSuccess;
 }

@@ -42,7 +42,7 @@ def test_host_only_calls(libc):
     assert cb.cpr_sample_size(5) == 80 and cb.cpr_sample_size(6) == 108
     o = cb.cpr_default_opts()
     assert o.max_iters == 200 and o.fit_tol == 1e-4 and o.fit_samples == 16384 and o.noise_eta < 0
-    assert cb.cpr_status_string(cb.ESINGULAR).startswith("sampled Gram")
+    assert cb.cpr_status_string(cb.ESINGULAR).startswith("Gram matrix")
     d = cb.CprTensor()
     d.order, d.dtype = 3, cb.F32
     for n, v in enumerate((400, 400, 400)):
@@ -53,6 +53,11 @@ def test_host_only_calls(libc):
     assert mix > 2 * 400 ** 3 * 4     # mixed tensor + pass buffer live in the workspace
     assert lib.cpr_workspace_size(cb.METHOD_CPRAND, ctypes.byref(d), 10, 9, None) == 0   # S < R
     assert lib.cpr_workspace_size(cb.METHOD_CPRAND, ctypes.byref(d), 65, 900, None) == 0  # R too big
+    als = lib.cpr_workspace_size(cb.METHOD_CP_ALS, ctypes.byref(d), 10, 0, None)
+    assert als > 2 * 400 ** 3 * 4     # unfolding copies of modes 2 and 3 live in the workspace
+    one = lib.cpr_workspace_size(cb.METHOD_MTTKRP, ctypes.byref(d), 10, 0, None)
+    assert 400 ** 3 * 4 < one < als   # one unfolding copy
+    assert lib.cpr_workspace_size(cb.METHOD_CP_ALS, ctypes.byref(d), 65, 0, None) == 0
     d.order = 1
     assert lib.cpr_workspace_size(cb.METHOD_CPRAND, ctypes.byref(d), 2, 9, None) == 0
 
@@ -72,5 +77,7 @@ def test_bad_arguments_rejected_before_any_gpu_work(libc):
     d.data = 256          # never dereferenced: the ktensor check fails first
     assert lib.cpr_cprand(ctypes.byref(d), 2, 10, None, ctypes.byref(k), ctypes.byref(res), None, 0, None) \
         == cb.EINVAL
+    assert lib.cpr_cp_als(ctypes.byref(d), 2, None, ctypes.byref(k), ctypes.byref(res), None, 0, None) == cb.EINVAL
+    assert lib.cpr_mttkrp(ctypes.byref(d), ctypes.byref(k), 0, None, None, 0, None) == cb.EINVAL
     assert lib.cpr_sample_indices(ctypes.byref(d), 3, 10, 0, 0, 0, None, None, None) == cb.EINVAL
     assert lib.cpr_gather_fibers(ctypes.byref(d), 0, 10, None, None, None) == cb.EINVAL
