@@ -124,7 +124,13 @@ void give_event(cudaEvent_t e) {
 template <class F>
 int launch(int cls, cudaStream_t s, int64_t* launches, F&& f) {
   Profiler& p = prof();
-  const bool rec = p.on && ((p.mask >> cls) & 1u);
+  bool rec = p.on && ((p.mask >> cls) & 1u);
+  if (rec) {
+    // a launch recorded into a graph body runs later, many times: it cannot be timed with events
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cst) != cudaSuccess) return CPR_ECUDA;
+    rec = cst == cudaStreamCaptureStatusNone;
+  }
   cudaEvent_t a = nullptr, b = nullptr;
   if (rec) {
     a = take_event();
@@ -312,6 +318,7 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws, int als = 0, int
       p.Gpart = cv.take<double>((size_t)nrb * R * R);
       p.Npart = cv.take<double>((size_t)nrb);
       p.Mpart = cv.take<double>((size_t)most * imax * R);
+      p.Mfold = cv.take<double>((size_t)imax * R);
     }
     p.P_hat = (int)sp.P_hat;
     if (p.P_hat > 0) {
@@ -673,6 +680,7 @@ int enqueue_als_iteration(const Plan& pl, int cap, int use_cond, unsigned long l
   for (int n = 0; n < p.N; ++n) {
     CPR_LAUNCH(CPR_KERNEL_CHOL, launch_als_prep(pl.d_probs, p, n, s));
     CPR_LAUNCH(CPR_KERNEL_CONTRACT, launch_mttkrp(pl.d_probs, p, n, s));
+    CPR_LAUNCH(CPR_KERNEL_CONTRACT, launch_mttkrp_fold(pl.d_probs, p, n, nullptr, s));
     CPR_LAUNCH(CPR_KERNEL_SOLVE, launch_als_solve(pl.d_probs, p, n, s));
   }
   if (use_cond) CPR_LAUNCH(CPR_KERNEL_OTHER, launch_loop_cond(pl.d_probs, 1, pl.d_counter, cap, cond, s));
@@ -906,7 +914,7 @@ int cpr_mttkrp(const cpr_tensor* X, const cpr_ktensor* K, int mode, double* M_de
                launch_unfold_copy(p.X, const_cast<void*>(p.Xrep[mode]), p.dtype, p.N, p.dims, mode, s));
   CPR_LAUNCH(CPR_KERNEL_OTHER, launch_init_factors(pl.d_probs, pl.g, 1, s));
   CPR_LAUNCH(CPR_KERNEL_CONTRACT, launch_mttkrp(pl.d_probs, p, mode, s));
-  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_mttkrp_reduce(pl.d_probs, p, mode, M_dev, s));
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_mttkrp_fold(pl.d_probs, p, mode, M_dev, s));
   return CPR_OK;
 }
 

@@ -90,6 +90,7 @@ struct Prob {
   // CP-ALS (Alg. 1): exact MTTKRP over the unfolding copies, Grams of the normalized factors
   double* gram[kMaxOrder]; // per mode, R x R Gram A^T A of the normalized factor
   double* V;               // R x R Hadamard product of the other modes' Grams (mode updated last)
+  double* Mfold;           // imax x R: the MTTKRP of the mode being updated (split partials summed)
   int64_t jsplit[kMaxOrder];  // MTTKRP: unfolding columns per split, per mode
   int32_t als_nsplit[kMaxOrder];  // MTTKRP: splits per mode
   int32_t als_rg;          // MTTKRP: rank groups of 8 columns per thread tile (1, 2, 4 or 8)
@@ -291,7 +292,8 @@ cudaError_t launch_als_gram(const Prob* probs, const Prob& hp, int n, cudaStream
 cudaError_t launch_als_prep(const Prob* probs, const Prob& hp, int n, cudaStream_t s);
 cudaError_t launch_mttkrp(const Prob* probs, const Prob& hp, int n, cudaStream_t s);
 cudaError_t launch_als_solve(const Prob* probs, const Prob& hp, int n, cudaStream_t s);
-cudaError_t launch_mttkrp_reduce(const Prob* probs, const Prob& hp, int n, double* M, cudaStream_t s);
+// M == nullptr: into the problem's Mfold buffer
+cudaError_t launch_mttkrp_fold(const Prob* probs, const Prob& hp, int n, double* M, cudaStream_t s);
 cudaError_t prepare_als_attributes();
 constexpr int kAlsRows = 32;       // factor rows per block of the CP-ALS solve and Gram kernels
 

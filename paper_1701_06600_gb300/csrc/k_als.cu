@@ -10,7 +10,8 @@
 //                  built on the fly from the factor rows (never the whole Khatri-Rao matrix);
 //                  products in FP32 with FP32 sums over at most kMtFlush columns folded into FP64
 //                  (FP64 throughout for an FP64 tensor); partial M per column split in FP64
-//   k_als_solve    m_i = sum of the split partials (fixed order), a_i L L^T = m_i in FP64, rows
+//   k_mttkrp_fold  M = sum of the split partials in a fixed order, many blocks
+//   k_als_solve    a_i L L^T = m_i in FP64 for the rows m_i of M, rows
 //                  stored unnormalized; partial Grams of the new rows; the last block forms the
 //                  Gram of the new factor, lambda, the lazy column scales and, after the last
 //                  mode, the exact fit and the stopping rules
@@ -51,36 +52,70 @@ template <> __device__ __forceinline__ double to_acc<double, double>(double v) {
 template <> __device__ __forceinline__ float to_acc<float, float>(float v) { return v; }
 template <> __device__ __forceinline__ float to_acc<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// Builds rows [j0, j0 + JT) of Z^(n) (rank columns padded to RP with zeros) into Zs: Z(j, r) =
-// w_r prod_{m != n} A^(m)(j_m, r), (j_m) the multi-index of unfolding column j (Sec. 2.1 index map:
-// modes other than n in increasing order, the earliest fastest) and w_r the product of the lazy
-// column scales of those modes.
+// Z rows of a column tile (Z(j, r) = w_r prod_{m != n} A^(m)(j_m, r), (j_m) the multi-index of
+// unfolding column j under the Sec. 2.1 index map: modes other than n in increasing order, the
+// earliest fastest; w_r the product of those modes' lazy column scales).  Thread t owns column
+// jj = t / TPC of every tile and EPT consecutive rank columns of it; it keeps the multi-index of its
+// column and advances it by JT columns per tile (digit-wise addition with carry), so no division
+// runs per entry.
 template <typename ACC, int JT, int RP>
-__device__ __forceinline__ void build_z_tile(const Prob& p, int n, int64_t j0, int64_t je, const ACC* w,
-                                             ACC* Zs) {
-  const int R = p.R, N = p.N;
-  for (int e = threadIdx.x; e < JT * RP; e += kAlsThreads) {
-    const int jj = e / RP, r = e - jj * RP;
-    const int64_t j = j0 + jj;
-    ACC z = (ACC)0;
-    if (r < R && j < je) {
-      z = w[r];
-      int64_t rem = j;
-      for (int m = 0; m < N; ++m) {
-        if (m == n) continue;
-        const int64_t Im = p.dims[m];
-        const int64_t jm = rem % Im;
-        rem /= Im;
-        if constexpr (sizeof(ACC) == 8) z *= p.A64[m][jm * R + r];
-        else z *= p.A32[m][jm * R + r];
-      }
+struct ZBuilder {
+  static constexpr int TPC = kAlsThreads / JT;              // threads per column
+  static constexpr int EPT = RP >= TPC ? RP / TPC : 1;      // rank columns per thread
+  int jj, r0;
+  bool active;
+  int nm;                       // modes other than n
+  uint32_t idx[kMaxOrder - 1];  // multi-index of column jb + k JT + jj over those modes
+  uint32_t ext[kMaxOrder - 1];
+  const ACC* rows[kMaxOrder - 1];
+
+  __device__ void init(const Prob& p, int n, int64_t jfirst) {
+    const int t = threadIdx.x;
+    jj = t / TPC;
+    r0 = (t % TPC) * EPT;
+    active = r0 < RP;
+    nm = 0;
+    int64_t rem = jfirst + jj;
+    for (int m = 0; m < p.N; ++m) {
+      if (m == n) continue;
+      const int64_t Im = p.dims[m];
+      idx[nm] = (uint32_t)(rem % Im);
+      rem /= Im;
+      ext[nm] = (uint32_t)Im;
+      if constexpr (sizeof(ACC) == 8) rows[nm] = p.A64[m];
+      else rows[nm] = p.A32[m];
+      ++nm;
     }
-    Zs[e] = z;
   }
-}
+  // writes the tile's Z rows (zero where j >= je or r >= R), then advances to the next tile
+  __device__ void build(int64_t j0, int64_t je, int R, const ACC* w, ACC* Zs) {
+    if (active) {
+      const bool live = j0 + jj < je;
+      ACC z[EPT];
+#pragma unroll
+      for (int c = 0; c < EPT; ++c) z[c] = (live && r0 + c < R) ? w[r0 + c] : (ACC)0;
+      if (live) {
+        for (int q = 0; q < nm; ++q) {
+          const ACC* row = rows[q] + (int64_t)idx[q] * R + r0;
+#pragma unroll
+          for (int c = 0; c < EPT; ++c)
+            if (r0 + c < R) z[c] *= row[c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < EPT; ++c) Zs[jj * RP + r0 + c] = z[c];
+    }
+    uint32_t carry = JT;
+    for (int q = 0; q < nm && carry; ++q) {
+      const uint32_t v = idx[q] + carry;
+      idx[q] = v % ext[q];
+      carry = v / ext[q];
+    }
+  }
+};
 
 template <typename T, typename ACC, int RG>
-__global__ void __launch_bounds__(kAlsThreads) k_mttkrp(const Prob* probs, int n) {
+__global__ void __launch_bounds__(kAlsThreads, 3) k_mttkrp(const Prob* probs, int n) {
   using Sh = MtShape<ACC, RG>;
   constexpr int TI = Sh::TI, JT = Sh::JT, RP = Sh::RP, ROWG = Sh::ROWG, LPT = Sh::LPT;
   constexpr int kFlushTiles = kMtFlush / JT > 0 ? kMtFlush / JT : 1;
@@ -121,18 +156,20 @@ __global__ void __launch_bounds__(kAlsThreads) k_mttkrp(const Prob* probs, int n
   T ld[LPT];
   auto issue = [&](int64_t k) {
     const int64_t j0 = jb + k * JT;
+    const T* Yt = Y + j0 * I + i0;
 #pragma unroll
     for (int q = 0; q < LPT; ++q) {
       const int e = tid + q * kAlsThreads;
       const int jj = e / TI, ii = e - jj * TI;
-      const int64_t j = j0 + jj, i = i0 + ii;
-      ld[q] = (j < je && i < I) ? Y[j * I + i] : T(0.0f);
+      ld[q] = (j0 + jj < je && i0 + ii < I) ? Yt[(int64_t)jj * I + ii] : T(0.0f);
     }
   };
+  ZBuilder<ACC, JT, RP> zb;
+  zb.init(p, n, jb);
   auto commit = [&](int64_t k, int buf) {
 #pragma unroll
     for (int q = 0; q < LPT; ++q) Ys[buf][tid + q * kAlsThreads] = to_acc<ACC, T>(ld[q]);
-    build_z_tile<ACC, JT, RP>(p, n, jb + k * JT, je, w, Zs[buf]);
+    zb.build(jb + k * JT, je, R, w, Zs[buf]);
   };
   __syncthreads();   // w ready
   if (ntile > 0) {
@@ -326,7 +363,46 @@ cudaError_t launch_als_gram(const Prob* probs, const Prob& hp, int n, cudaStream
   return cudaGetLastError();
 }
 
-// Rows [i0, i0 + kAlsRows) of the new factor: m_i = sum of the split partials, a_i = m_i (L L^T)^-1
+// M = sum over splits of the MTTKRP partials, in a fixed order: a block owns 32 consecutive entries
+// of M (one per lane); warp w sums the splits s = w, w + kFoldWarps, ... (coalesced 256-byte reads),
+// then the warp sums are added in warp order.
+constexpr int kFoldWarps = 16;
+__global__ void __launch_bounds__(32 * kFoldWarps) k_mttkrp_fold(const Prob* probs, int n, double* M) {
+  const Prob& p = probs[blockIdx.y];
+  if (n >= p.N || is_done(p)) return;
+  const int64_t cnt = p.dims[n] * p.R;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  const double* Mp = reinterpret_cast<const double*>(p.Mpart);
+  const int ns = p.als_nsplit[n];
+  const int64_t stride = (int64_t)p.imax * p.R;
+  __shared__ double part[kFoldWarps][32];
+  double a0 = 0.0, a1 = 0.0;
+  if (e < cnt) {
+    int s = w;
+    for (; s + kFoldWarps < ns; s += 2 * kFoldWarps) {
+      a0 += Mp[s * stride + e];
+      a1 += Mp[(s + kFoldWarps) * stride + e];
+    }
+    if (s < ns) a0 += Mp[s * stride + e];
+  }
+  part[w][lane] = a0 + a1;
+  __syncthreads();
+  if (w == 0 && e < cnt) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kFoldWarps; ++q) t += part[q][lane];
+    M[e] = t;
+  }
+}
+
+cudaError_t launch_mttkrp_fold(const Prob* probs, const Prob& hp, int n, double* M, cudaStream_t s) {
+  const int64_t cnt = hp.dims[n] * hp.R;
+  k_mttkrp_fold<<<dim3((unsigned)((cnt + 31) / 32), 1), 32 * kFoldWarps, 0, s>>>(probs, n, M ? M : hp.Mfold);
+  return cudaGetLastError();
+}
+
+// Rows [i0, i0 + kAlsRows) of the new factor: m_i = the folded MTTKRP row, a_i = m_i (L L^T)^-1
 // by forward and backward substitution (FP64), stored unnormalized (FP64 and FP32).  Partial Gram
 // and partial <M, A> of the block; the last block finishes the Gram, lambda and scales and, for
 // the last mode, the exact fit and the stopping rules.
@@ -347,22 +423,9 @@ __global__ void __launch_bounds__(kAlsThreads) k_als_solve(const Prob* probs, in
   __shared__ double red[kAlsThreads / 32];
   const int tid = threadIdx.x;
   for (int e = tid; e < R * R; e += blockDim.x) Ls[(e / R) * R1 + e % R] = p.L[e];
-  const double* Mp = reinterpret_cast<const double*>(p.Mpart);
-  const int ns = p.als_nsplit[n];
-  const int64_t stride = (int64_t)p.imax * R;
   for (int e = tid; e < rows * R; e += blockDim.x) {
     const int li = e / R, r = e - li * R;
-    const double* src = Mp + (i0 + li) * R + r;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int q = 0;
-    for (; q + 4 <= ns; q += 4) {
-      a0 += src[(q + 0) * stride];
-      a1 += src[(q + 1) * stride];
-      a2 += src[(q + 2) * stride];
-      a3 += src[(q + 3) * stride];
-    }
-    for (; q < ns; ++q) a0 += src[q * stride];
-    const double m = (a0 + a1) + (a2 + a3);
+    const double m = p.Mfold[(i0 + li) * R + r];
     Mr[li * R1 + r] = m;
     Vr[li * R1 + r] = m;
   }
@@ -447,36 +510,6 @@ cudaError_t prepare_als_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_als_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_als_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram);
-}
-
-// M = sum of the split partials (the MTTKRP step entry point), I_n x R row-major FP64.
-__global__ void k_mttkrp_reduce(const Prob* probs, int n, double* M) {
-  const Prob& p = probs[blockIdx.y];
-  const int R = p.R;
-  const int64_t cnt = p.dims[n] * R;
-  const double* Mp = reinterpret_cast<const double*>(p.Mpart);
-  const int ns = p.als_nsplit[n];
-  const int64_t stride = (int64_t)p.imax * R;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int q = 0;
-    for (; q + 4 <= ns; q += 4) {
-      a0 += Mp[(q + 0) * stride + e];
-      a1 += Mp[(q + 1) * stride + e];
-      a2 += Mp[(q + 2) * stride + e];
-      a3 += Mp[(q + 3) * stride + e];
-    }
-    for (; q < ns; ++q) a0 += Mp[q * stride + e];
-    M[e] = (a0 + a1) + (a2 + a3);
-  }
-}
-
-cudaError_t launch_mttkrp_reduce(const Prob* probs, const Prob& hp, int n, double* M, cudaStream_t s) {
-  int64_t blocks = (hp.dims[n] * hp.R + 255) / 256;
-  if (blocks > 1024) blocks = 1024;
-  if (blocks < 1) blocks = 1;
-  k_mttkrp_reduce<<<dim3((unsigned)blocks, 1), 256, 0, s>>>(probs, n, M);
-  return cudaGetLastError();
 }
 
 }  // namespace cpr
