@@ -101,9 +101,12 @@ typedef struct {
   double* fit_trace_dev; /* device, >= max(max_iters, fixed_iters) doubles, or NULL */
   int32_t loop_path;     /* how the outer iterations are launched: 0 automatic (a thread-block
                             cluster per problem when every problem of the call fits one, else the
-                            captured graph); 1 clusters (CPR_EINVAL if a problem does not fit);
-                            2 captured graph; 3 plain stream launches.  Read from the first
-                            problem's options in a batched call. */
+                            captured graph); 1 clusters (every factor replicated in each CTA's
+                            shared memory when every problem fits that layout, else each factor's
+                            rows distributed over the CTAs; CPR_EINVAL if a problem fits neither);
+                            2 captured graph; 3 plain stream launches; 4 clusters with distributed
+                            factor rows only.  Read from the first problem's options in a batched
+                            call. */
   int32_t layout;        /* 0: before iterating, also store every mode-n unfolding X_(n) as its own
                             column-major copy (N-1 extra copies of the tensor in the workspace) so
                             that every sampled fiber is read contiguously; 1: gather every mode
@@ -213,7 +216,10 @@ CPR_API int cpr_sample_indices(const cpr_tensor* X, int mode, int64_t S, uint64_
                        uint32_t t, uint32_t* idx_dev, int64_t* off_dev, void* stream);
 
 /* Fiber gather X_S = (S X_(n)^T)^T (Sec. 3.2): xs_dev[i + I_n * j] = X[off_dev[j] + i * st_mode]
- * for i < I_n, j < S, a bit copy in X's dtype (I_n x S, column-major). */
+ * for i < I_n, j < S, a bit copy in X's dtype (I_n x S, column-major).  Fibers of stride 1 (mode 0,
+ * which also covers a mode-n unfolding stored column-major and described with mode n's extent
+ * first) are copied one warp per fiber with 16-byte vectors where the fiber's start, its
+ * destination and its length allow it; strided fibers element by element. */
 CPR_API int cpr_gather_fibers(const cpr_tensor* X, int mode, int64_t S, const int64_t* off_dev,
                       void* xs_dev, void* stream);
 

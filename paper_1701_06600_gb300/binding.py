@@ -38,7 +38,7 @@ class CprOpts(ctypes.Structure):
                 ("batch_index", ctypes.c_uint32), ("first_iter", ctypes.c_uint32),
                 ("fit_trace_dev", ctypes.c_void_p), ("loop_path", ctypes.c_int32), ("layout", ctypes.c_int32)]
 
-LOOP_AUTO, LOOP_CLUSTER, LOOP_GRAPH, LOOP_STREAM = range(4)
+LOOP_AUTO, LOOP_CLUSTER, LOOP_GRAPH, LOOP_STREAM, LOOP_CLUSTER_DIST = range(5)
 
 
 class CprResult(ctypes.Structure):
@@ -367,14 +367,19 @@ def cpr_sample_indices(dims, mode, S, seed, b=0, t=0, device="cuda", stream=None
     return idx[:S], off[:S]
 
 
-def cpr_gather_fibers(X, dims, mode, off, stream=None):
+def cpr_gather_fibers(X, dims, mode, off, out=None, stream=None):
+    """X_S (I_n x S view; column j = fiber j).  `out`: an optional caller buffer of S * I_n elements
+    of X's dtype that receives the fibers (reused across calls)."""
     d = tensor_desc(X, dims)
     S = off.numel()
-    out = torch.empty((S, int(dims[mode])), dtype=X.dtype, device=X.device)   # column j = fiber j
+    if out is None:
+        out = torch.empty((S, int(dims[mode])), dtype=X.dtype, device=X.device)
+    elif out.numel() != S * int(dims[mode]) or out.dtype != X.dtype or not out.is_contiguous():
+        raise ValueError("out must be a contiguous buffer of S * I_n elements of X's dtype")
     st = lib().cpr_gather_fibers(ctypes.byref(d), int(mode), int(S), ctypes.c_void_p(off.data_ptr()),
                                  ctypes.c_void_p(out.data_ptr()), _stream(stream))
     _check(st, "cpr_gather_fibers")
-    return out.T   # I_n x S view
+    return out.view(S, int(dims[mode])).T   # I_n x S view
 
 
 def cpr_sampled_update(X, dims, lam, factors, mode, S, seed, b=0, t=0, ws=None, stream=None):

@@ -586,25 +586,45 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
   const unsigned loop_classes = (1u << CPR_KERNEL_SAMPLE_SKR) | (1u << CPR_KERNEL_CONTRACT) | (1u << CPR_KERNEL_CHOL) |
                                 (1u << CPR_KERNEL_SOLVE) | (1u << CPR_KERNEL_NORMALIZE) | (1u << CPR_KERNEL_FIT);
   const int path = op[0].loop_path;
-  if (path < 0 || path > 3) return CPR_EINVAL;
+  if (path < 0 || path > 4) return CPR_EINVAL;
   const bool stream_only = path == 3 || (prof().on && (prof().mask & loop_classes));
-  // small problems: the whole loop in thread-block clusters (one cluster per problem at a time)
+  // small problems: the whole loop in thread-block clusters (one cluster per problem at a time);
+  // first choice: every factor replicated in each CTA of the cluster; else factor rows
+  // distributed over the CTAs
   int C = 16, csmem = -1, ncl = 0;
+  bool rep = false;
   if (!stream_only && path != 2) {
     int maxR = 0;
     for (int b = 0; b < B; ++b) maxR = std::max(maxR, pl.probs[b].R);
-    for (int c : {16, 8}) {
-      C = c;
-      csmem = cluster_smem_bytes(pl.probs.data(), B, C);
-      if (csmem < 0) continue;
-      ncl = cluster_capacity(pl.dtype, C, csmem, maxR);
-      if (ncl > 0) break;
+    if (path != 4) {
+      const int rs = loop_rep_smem_bytes(pl.probs.data(), B);
+      if (rs > 0) {
+        const int cap = loop_rep_capacity(pl.dtype, rs, maxR);
+        if (cap > 0) {
+          rep = true;
+          csmem = rs;
+          ncl = cap;
+        }
+      }
     }
-    if (path == 1 && ncl <= 0) return CPR_EINVAL;
+    if (!rep) {
+      for (int c : {16, 8}) {
+        C = c;
+        csmem = cluster_smem_bytes(pl.probs.data(), B, C);
+        if (csmem < 0) continue;
+        ncl = cluster_capacity(pl.dtype, C, csmem, maxR);
+        if (ncl > 0) break;
+      }
+    }
+    if ((path == 1 || path == 4) && ncl <= 0) return CPR_EINVAL;
     if (ncl > 0) {
       ncl = std::min(ncl, B);
       CPR_CUDA(cudaMemsetAsync(pl.d_counter + 1, 0, sizeof(int), s));
-      CPR_LAUNCH(CPR_KERNEL_LOOP, launch_cluster_run(pl.d_probs, B, pl.d_counter + 1, pl.dtype, C, csmem, ncl, maxR, s));
+      if (rep)
+        CPR_LAUNCH(CPR_KERNEL_LOOP, launch_loop_rep(pl.d_probs, B, pl.d_counter + 1, pl.dtype, csmem, ncl, maxR, s));
+      else
+        CPR_LAUNCH(CPR_KERNEL_LOOP,
+                   launch_cluster_run(pl.d_probs, B, pl.d_counter + 1, pl.dtype, C, csmem, ncl, maxR, s));
     }
   }
   const bool use_graph = !stream_only && ncl <= 0;
@@ -694,7 +714,7 @@ int run_cp_als(const cpr_tensor* X, int R, const cpr_opts* opts, cpr_ktensor* ou
   if (int st = check_ktensor(out, X, R)) return st;
   cpr_opts o = opts ? *opts : defaults();
   if (o.max_iters < 1 && o.fixed_iters < 1) return CPR_EINVAL;
-  if (o.loop_path < 0 || o.loop_path > 3) return CPR_EINVAL;
+  if (o.loop_path < 0 || o.loop_path > 4) return CPR_EINVAL;
   ProbSpec sp{X, R, 0, 0, &o, nullptr, nullptr};
   const Plan measure = make_plan(1, &sp, 0, nullptr, 1, -1);
   if (int st = check_ws(ws, ws_bytes, measure.bytes)) return st;

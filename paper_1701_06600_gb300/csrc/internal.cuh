@@ -255,6 +255,12 @@ int cluster_smem_bytes(const Prob* probs_host, int B, int C);
 int cluster_capacity(int dtype, int C, int smem, int maxR);
 cudaError_t launch_cluster_run(const Prob* probs, int B, int* queue, int dtype, int C, int smem, int nclusters,
                                int maxR, cudaStream_t s);
+// the whole iteration loop in 16-CTA clusters with every factor replicated in each CTA (the first
+// choice when every problem of the call fits)
+int loop_rep_smem_bytes(const Prob* probs_host, int B);
+int loop_rep_capacity(int dtype, int smem, int maxR);
+cudaError_t launch_loop_rep(const Prob* probs, int B, int* queue, int dtype, int smem, int nclusters, int maxR,
+                            cudaStream_t s);
 cudaError_t launch_sumsq(const void* X, int dtype, int64_t P, double* part, int nblk, cudaStream_t s);
 cudaError_t launch_sumsq_finish(const double* part, int nblk, double* out_norm, State* st,
                                 int nstates, cudaStream_t s);

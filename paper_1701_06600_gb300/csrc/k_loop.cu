@@ -1,0 +1,901 @@
+// The whole outer-iteration loop of CPRAND (Alg. 3, with the sampled fit of Sec. 3.4 and the
+// stopping rules of Sec. 4.2) in one 16-CTA thread-block cluster per problem, with every factor
+// matrix replicated in each CTA's shared memory.
+//
+// Work split: CTA c draws samples [c*spc, (c+1)*spc) of every mode update and owns factor rows
+// [c*rpc_n, (c+1)*rpc_n) of mode n.  Per mode update:
+//   1. SKR (Alg. 2): the Z_S rows of this CTA's samples from the local factor copies times their
+//      lazy column scales (FP64; an FP32/FP64 copy feeds the contraction).
+//   2. Contraction M_c = X_S,c Z_S,c for every row i_n (FP32 accumulation, FP64 for FP64 tensors)
+//      from the sampled fibers, which were copied into shared memory (cp.async) during the previous
+//      mode update: the sample draw of a mode update does not depend on the factors, so its fiber
+//      reads are issued one update ahead and never wait on HBM latency in the dependent chain.
+//      Each row's partial is stored straight into the shared memory of the CTA owning that row.
+//   3. Partial FP64 Gram of this CTA's Z rows, stored into every CTA's shared memory.
+//   4. Cluster barrier; every CTA sums the C partial Grams in one fixed order (identical G in all
+//      CTAs) and inverts it: Gauss-Jordan in FP32 on one warp (lane i holds row i of [G | I]), then
+//      Newton-Schulz steps X <- X + X (I - G X) in FP64 (one for FP32 tensors, two for FP64), which
+//      square the residual ||I - G X||; a residual above 1/4 or a bad FP32 pivot falls back to an
+//      FP64 Cholesky inverse (which also detects a singular Gram matrix).
+//   5. The CTA's rows: M rows summed over the C partials (fixed order), A = M G^-1 in FP64, written
+//      to the FP64 result and stored into every CTA's copy of the factor; column sums of squares
+//      of its rows are stored into every CTA.
+//   6. Cluster barrier; lambda and the lazy column scales from the C column partials (fixed order).
+// After the N modes each CTA evaluates its share of the P_hat fixed fit entries (indices and values
+// staged in shared memory once per problem) against the local factor copies; after a cluster
+// barrier every CTA sums the C partials in the same order and applies the stopping rules to its own
+// copy of the loop state, so all CTAs take the same decision.
+//
+// Data only ever moves by stores into other CTAs' shared memory followed by a cluster barrier
+// (release / acquire); no CTA reads another CTA's shared memory.  FP64 instructions issue at a low
+// rate on this GPU (one warp instruction occupies an SM sub-partition's FP64 pipe for tens of
+// cycles), so FP64 work is packed into as few warps as possible and spread over the four
+// sub-partitions, and reductions never run redundantly in every warp.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "internal.cuh"
+#include "small_spd.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace cpr {
+
+namespace {
+
+constexpr int kLT = 512;   // threads per CTA
+constexpr int kLC = 16;    // CTAs per cluster
+
+struct LoopSmem {          // byte offsets into the dynamic shared memory
+  int F[kMaxOrder];        // full factor m, I_m x R (ACC)
+  int fib[2];              // sampled fibers of a mode update: spc rows of ldf elements (T)
+  int ids[2];              // spc x kMaxOrder sampled indices
+  int offs[2];             // spc fiber offsets
+  int Zd, Zf;              // spc x R Z_S rows (FP64) and spc x zld (ACC, rows padded to 16 bytes)
+  int Mrecv;               // C x R x rpcmax partial M columns received for this CTA's rows (ACC)
+  int Grecv;               // C x NE partial Grams (packed upper triangle, FP64)
+  int colrecv;             // C x R column sums of squares
+  int fitrecv;             // C partial fit sums
+  int fidx, fx;            // fpc x N fit indices, fpc fit values (ACC)
+  int G, X, E, U, T2;      // R x R FP64
+  int Gf, Xf;              // R x R FP32 (Gauss-Jordan input and output)
+  int mrow, arow;          // rpcmax x R FP64
+  int cpart;               // R x nchmax FP64
+  int sc, lam, wr, dinv;   // N x R, R, R (fit weights, ACC), R FP64
+  int scomb;               // R: product of the other modes' lazy scales for the next mode update
+  int prow;                // 2 x 2 MAXR FP32: pivot rows of the Gauss-Jordan elimination
+  int red;                 // kLT FP64 (block reduction)
+  int bytes;
+  int ldf, spc, rpcmax, fpc, NE, nchmax, zld;
+};
+
+__host__ __device__ inline int al16(int x) { return (x + 15) / 16 * 16; }
+
+__host__ __device__ inline LoopSmem loop_layout(int N, int R, const int64_t* dims, int S, int P_hat, int tbytes,
+                                                int abytes) {
+  LoopSmem L;
+  int o = 0, maxI = 0;
+  L.rpcmax = 0;
+  for (int m = 0; m < kMaxOrder; ++m) L.F[m] = 0;
+  for (int m = 0; m < N; ++m) {
+    const int I = (int)dims[m];
+    maxI = I > maxI ? I : maxI;
+    const int rpc = (I + kLC - 1) / kLC;
+    L.rpcmax = rpc > L.rpcmax ? rpc : L.rpcmax;
+    L.F[m] = o;
+    o = al16(o + I * R * abytes);
+  }
+  L.spc = (S + kLC - 1) / kLC;
+  L.ldf = al16(maxI * tbytes) / tbytes;
+  L.NE = R * (R + 1) / 2;
+  L.fpc = (P_hat + kLC - 1) / kLC;
+  L.nchmax = (L.rpcmax + 7) / 8;
+  L.zld = (R * abytes + 15) / 16 * 16 / abytes;
+  for (int q = 0; q < 2; ++q) {
+    L.fib[q] = o;  o = al16(o + L.spc * L.ldf * tbytes);
+  }
+  for (int q = 0; q < 2; ++q) {
+    L.ids[q] = o;  o = al16(o + L.spc * kMaxOrder * 4);
+    L.offs[q] = o; o = al16(o + L.spc * 8);
+  }
+  L.Zd = o;      o = al16(o + L.spc * R * 8);
+  L.Zf = o;      o = al16(o + L.spc * L.zld * abytes);
+  L.Mrecv = o;   o = al16(o + kLC * L.rpcmax * R * abytes);
+  L.Grecv = o;   o = al16(o + kLC * L.NE * 8);
+  L.colrecv = o; o = al16(o + kLC * R * 8);
+  L.fitrecv = o; o = al16(o + kLC * 8);
+  L.fidx = o;    o = al16(o + L.fpc * N * 4);
+  L.fx = o;      o = al16(o + L.fpc * abytes);
+  L.G = o;       o = al16(o + R * R * 8);
+  L.X = o;       o = al16(o + R * R * 8);
+  L.E = o;       o = al16(o + R * R * 8);
+  L.U = o;       o = al16(o + R * R * 8);
+  L.T2 = o;      o = al16(o + R * R * 8);
+  L.Gf = o;      o = al16(o + R * R * 4);
+  L.Xf = o;      o = al16(o + R * R * 4);
+  L.mrow = o;    o = al16(o + L.rpcmax * R * 8);
+  L.arow = o;    o = al16(o + L.rpcmax * R * 8);
+  L.cpart = o;   o = al16(o + R * L.nchmax * 8);
+  L.sc = o;      o = al16(o + N * R * 8);
+  L.lam = o;     o = al16(o + R * 8);
+  L.wr = o;      o = al16(o + R * 8);
+  L.dinv = o;    o = al16(o + R * 8);
+  L.scomb = o;   o = al16(o + R * 8);
+  L.prow = o;    o = al16(o + 2 * 2 * 32 * 4);
+  L.red = o;     o = al16(o + kLT * 8);
+  L.bytes = o;
+  return L;
+}
+
+__device__ __forceinline__ uint32_t s32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  if constexpr (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s32(dst)), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s32(dst)), "l"(src), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+template <typename T> __device__ __forceinline__ float tof(T v);
+template <> __device__ __forceinline__ float tof<float>(float v) { return v; }
+template <> __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename ACC, typename T>
+__device__ __forceinline__ ACC to_acc(T v) {
+  if constexpr (sizeof(ACC) == 8) return (ACC)v;
+  else return tof<T>(v);
+}
+
+// Per-problem constants kept in shared memory (the descriptor in global memory is read once).
+struct LoopConst {
+  Prob p;
+  LoopSmem L;
+  int vec[kMaxOrder];      // bytes per cp.async of a mode's fiber copies (16, 8, 4), 0: plain loads
+  int gs, gg;              // Gram: samples split over gs lanes; sum of the C partials over gg lanes
+};
+
+// Draw the samples of mode update (t, n) for this CTA (Philox stream 0, counter (j, n, t, b)):
+// indices by mode and the storage offset of each sampled fiber in the copy that mode reads.
+__device__ __forceinline__ void draw_samples(const Prob& p, int n, uint32_t t, int j0, int cnt, uint32_t* ids,
+                                             int64_t* offs, int tt, int nth) {
+  for (int jj = tt; jj < cnt; jj += nth) {
+    const uint32_t j = (uint32_t)(j0 + jj);
+    const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
+    const uint4 w0 = philox10(make_uint4(j, counter_word1(kStreamSamples, 0, n), t, p.b), k0, k1);
+    uint4 w1 = make_uint4(0u, 0u, 0u, 0u);
+    if (p.N - 1 > 4) w1 = philox10(make_uint4(j, counter_word1(kStreamSamples, 1, n), t, p.b), k0, k1);
+    int k = 0;
+    for (int m = 0; m < p.N; ++m) {
+      uint32_t im = 0;
+      if (m != n) {
+        const uint32_t w = k < 4 ? word_of(w0, k) : word_of(w1, k - 4);
+        im = scale_index(w, (uint32_t)p.dims[m]);
+        ++k;
+      }
+      ids[jj * kMaxOrder + m] = im;
+    }
+    int64_t stride;
+    offs[jj] = fiber_offset(p, n, ids + jj * kMaxOrder, &stride);
+  }
+}
+
+// Copy the cnt sampled fibers of mode n into buf (row j at buf + j * ldf).  Asynchronous (one
+// commit group per call, possibly empty) unless vec == 0, when plain loads are used.
+template <typename T>
+__device__ __forceinline__ void fetch_fibers(const LoopConst& K, int n, const int64_t* offs, int cnt, T* buf, int tt,
+                                             int nth) {
+  const Prob& p = K.p;
+  const int I = (int)p.dims[n];
+  const int ldf = K.L.ldf;
+  const T* X = reinterpret_cast<const T*>(p.Xrep[n]);
+  const int64_t stn = p.use_rep ? 1 : p.st[n];
+  const int vec = K.vec[n];
+  const int tid = tt;
+  if (stn == 1 && vec >= 4) {
+    const int epc = vec / (int)sizeof(T);      // elements per copy
+    const int cpf = I / epc;                    // copies per fiber
+    const int total = cnt * cpf;
+    for (int e = tid; e < total; e += nth) {
+      const int j = e / cpf, q = e - j * cpf;
+      const T* src = X + offs[j] + (int64_t)q * epc;
+      T* dst = buf + j * ldf + q * epc;
+      if (vec == 16) cp_async<16>(dst, src);
+      else if (vec == 8) cp_async<8>(dst, src);
+      else cp_async<4>(dst, src);
+    }
+  } else if (vec >= 4) {                        // strided fibers, one element per copy
+    const int total = cnt * I;
+    for (int e = tid; e < total; e += nth) {
+      const int j = e / I, i = e - j * I;
+      const T* src = X + offs[j] + (int64_t)i * stn;
+      T* dst = buf + j * ldf + i;
+      if constexpr (sizeof(T) == 8) cp_async<8>(dst, src);
+      else cp_async<4>(dst, src);
+    }
+  } else {
+    const int total = cnt * I;
+    for (int e = tid; e < total; e += nth) {
+      const int j = e / I, i = e - j * I;
+      buf[j * ldf + i] = X[offs[j] + (int64_t)i * stn];
+    }
+  }
+  cp_async_commit();
+}
+
+// X0 = G^-1 by Gauss-Jordan elimination without pivoting (G symmetric positive definite) in FP32
+// on the calling warp: lane i holds row i of [G | I]; the pivot row of each step is broadcast
+// through shared memory (prow: 2 x 2 MAXR floats, alternating by step).  Reads the FP32 copy of G,
+// writes X0 in FP32 and returns false on every lane if a pivot is not positive relative to the
+// largest diagonal entry.
+template <int MAXR>
+__device__ bool gauss_jordan_f32(const float* Gf, float* Xf, float* prow, int R) {
+  static_assert(MAXR % 4 == 0, "rows move as float4");
+  const int lane = threadIdx.x & 31;
+  float a[MAXR], x[MAXR];
+#pragma unroll
+  for (int c = 0; c < MAXR; ++c) {
+    a[c] = (lane < R && c < R) ? Gf[lane * R + c] : 0.f;
+    x[c] = (lane == c) ? 1.f : 0.f;
+  }
+  float md = lane < R ? Gf[lane * R + lane] : 0.f;
+  for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < MAXR; ++k) {
+    if (k < R) {
+      float* pr = prow + (k & 1) * 2 * MAXR;
+      const bool own = lane == k;
+      if (own) {
+#pragma unroll
+        for (int c = 0; c < MAXR; c += 4) {
+          *reinterpret_cast<float4*>(pr + c) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+          *reinterpret_cast<float4*>(pr + MAXR + c) = make_float4(x[c], x[c + 1], x[c + 2], x[c + 3]);
+        }
+      }
+      __syncwarp();
+      const float piv = pr[k];
+      bad = bad || !(piv > 1e-6f * md) || !isfinite(piv);
+      const float inv = __frcp_rn(piv);
+      const float ak = a[k];
+#pragma unroll
+      for (int c = 0; c < MAXR; c += 4) {
+        if (c < R) {
+          const float4 pa = *reinterpret_cast<const float4*>(pr + c);
+          const float4 px = *reinterpret_cast<const float4*>(pr + MAXR + c);
+          const float pav[4] = {pa.x * inv, pa.y * inv, pa.z * inv, pa.w * inv};
+          const float pxv[4] = {px.x * inv, px.y * inv, px.z * inv, px.w * inv};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            a[c + q] = own ? pav[q] : fmaf(-ak, pav[q], a[c + q]);
+            x[c + q] = own ? pxv[q] : fmaf(-ak, pxv[q], x[c + q]);
+          }
+        }
+      }
+    }
+  }
+  if (lane < R) {
+#pragma unroll
+    for (int c = 0; c < MAXR; ++c)
+      if (c < R) Xf[lane * R + c] = x[c];
+  }
+  return !bad;
+}
+
+// The inverse X = G^-1 (FP64, R x R, shared memory) by every CTA of the cluster.
+// Every CTA of the cluster, after the FP32 Gauss-Jordan start Xf (ok = its pivots were good):
+// Newton-Schulz steps in FP64, or the FP64 Cholesky inverse when the start is unusable.
+__device__ void loop_refine(bool ok, const double* G, const float* Xf, double* X, double* E, double* U, double* T2,
+                            double* dinv, float* redf, int R, int ns_steps, int* s_bad) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  bool fast = ok;
+  const int RR = R * R;
+  if (fast) {
+    for (int e = tid; e < RR; e += kLT) X[e] = (double)Xf[e];
+    __syncthreads();
+  }
+  for (int it = 0; fast && it < ns_steps; ++it) {
+    float em = 0.f;
+    for (int e = tid; e < RR; e += kLT) {      // E = I - G X
+      const int r = e / R, c = e - r * R;
+      double a0 = 0.0, a1 = 0.0;
+      int l = 0;
+      for (; l + 1 < R; l += 2) {
+        a0 = fma(G[r * R + l], X[l * R + c], a0);
+        a1 = fma(G[r * R + l + 1], X[(l + 1) * R + c], a1);
+      }
+      if (l < R) a0 = fma(G[r * R + l], X[l * R + c], a0);
+      const double ev = (r == c ? 1.0 : 0.0) - (a0 + a1);
+      E[e] = ev;
+      em = fmaxf(em, fabsf((float)ev));
+    }
+    if (it == 0) {                             // convergence check in FP32: max |E| < 1/4
+      for (int o = 16; o > 0; o >>= 1) em = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, o));
+      if (lane == 0) redf[warp] = em;
+    }
+    __syncthreads();
+    if (it == 0) {
+      float m = 0.f;
+      for (int q = 0; q < (min(RR, kLT) + 31) / 32; ++q) m = fmaxf(m, redf[q]);
+      if (!(m < 0.25f)) {
+        fast = false;
+        break;
+      }
+    }
+    for (int e = tid; e < RR; e += kLT) {      // X + X E
+      const int r = e / R, c = e - r * R;
+      double a0 = 0.0, a1 = 0.0;
+      int l = 0;
+      for (; l + 1 < R; l += 2) {
+        a0 = fma(X[r * R + l], E[l * R + c], a0);
+        a1 = fma(X[r * R + l + 1], E[(l + 1) * R + c], a1);
+      }
+      if (l < R) a0 = fma(X[r * R + l], E[l * R + c], a0);
+      U[e] = X[e] + (a0 + a1);
+    }
+    __syncthreads();
+    for (int e = tid; e < RR; e += kLT) X[e] = U[e];
+    __syncthreads();
+  }
+  if (!fast) spd_inverse_fp64(G, X, U, T2, dinv, R, s_bad);
+}
+
+template <typename T, typename ACC, int MAXR>
+__device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::cluster_group& cl, int n, int cb,
+                                 int nn, uint32_t nt, int* s_bad, float* redf) {
+  const Prob& p = K.p;
+  const LoopSmem& L = K.L;
+  const int rank = (int)cl.block_rank(), tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int R = p.R, N = p.N, S = p.S;
+  const int I = (int)p.dims[n];
+  const int spc = L.spc;
+  const int cnt = max(0, min(S, rank * spc + spc) - rank * spc);
+  const int zld = L.zld;
+  double* sc = reinterpret_cast<double*>(sm + L.sc);
+  double* lam = reinterpret_cast<double*>(sm + L.lam);
+  double* scomb = reinterpret_cast<double*>(sm + L.scomb);
+  double* Zd = reinterpret_cast<double*>(sm + L.Zd);
+  ACC* Zf = reinterpret_cast<ACC*>(sm + L.Zf);
+  const uint32_t* ids = reinterpret_cast<const uint32_t*>(sm + L.ids[cb]);
+  const T* fib = reinterpret_cast<const T*>(sm + L.fib[cb]);
+  ACC* Mrecv = reinterpret_cast<ACC*>(sm + L.Mrecv);
+  double* Grecv = reinterpret_cast<double*>(sm + L.Grecv);
+  double* colrecv = reinterpret_cast<double*>(sm + L.colrecv);
+  double* G = reinterpret_cast<double*>(sm + L.G);
+  double* X = reinterpret_cast<double*>(sm + L.X);
+  float* Gf = reinterpret_cast<float*>(sm + L.Gf);
+  double* mrow = reinterpret_cast<double*>(sm + L.mrow);
+  double* arow = reinterpret_cast<double*>(sm + L.arow);
+  double* cpart = reinterpret_cast<double*>(sm + L.cpart);
+
+  // ---- 1. SKR rows of this CTA's samples (Alg. 2), from the local factor copies: the product of
+  // the sampled rows (exact in FP64 for up to two FP32 factors) times the combined lazy scale
+  for (int e = tid; e < cnt * zld; e += kLT) {
+    const int jj = e / zld, r = e - jj * zld;
+    if (r < R) {
+      double z = 1.0;
+#pragma unroll
+      for (int m = 0; m < kMaxOrder; ++m)
+        if (m < N && m != n) {
+          const ACC* Fm = reinterpret_cast<const ACC*>(sm + L.F[m]);
+          z *= (double)Fm[(int)ids[jj * kMaxOrder + m] * R + r];
+        }
+      z *= scomb[r];
+      Zd[jj * R + r] = z;
+      Zf[e] = (ACC)z;
+    } else {
+      Zf[e] = ACC(0);
+    }
+  }
+  cp_async_wait<0>();   // this update's fibers (issued during the previous update)
+  __syncthreads();
+
+  // ---- 2. partial M = X_S,c Z_S,c, every row, stored into the owner CTA's receive buffer
+  const int rpc = (I + kLC - 1) / kLC;
+  for (int i = tid; i < I; i += kLT) {
+    ACC acc[MAXR];
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) acc[r] = ACC(0);
+    constexpr int VZ = 16 / (int)sizeof(ACC);      // Z entries per 16-byte vector
+    for (int j = 0; j < cnt; ++j) {
+      const ACC x = to_acc<ACC, T>(fib[j * L.ldf + i]);
+      const ACC* z = Zf + j * zld;
+#pragma unroll
+      for (int v = 0; v < MAXR; v += VZ) {
+        if (v < R) {
+          if constexpr (VZ == 4) {
+            const float4 q = *reinterpret_cast<const float4*>(z + v);
+            acc[v] = fma(x, q.x, acc[v]);
+            acc[v + 1] = fma(x, q.y, acc[v + 1]);
+            acc[v + 2] = fma(x, q.z, acc[v + 2]);
+            acc[v + 3] = fma(x, q.w, acc[v + 3]);
+          } else {
+            const double2 q = *reinterpret_cast<const double2*>(z + v);
+            acc[v] = fma(x, q.x, acc[v]);
+            acc[v + 1] = fma(x, q.y, acc[v + 1]);
+          }
+        }
+      }
+    }
+    // column-major receive layout: lanes (consecutive rows) store to consecutive addresses
+    const int owner = i / rpc, li = i - owner * rpc;
+    ACC* dst = cl.map_shared_rank(Mrecv, owner) + rank * R * L.rpcmax + li;
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r)
+      if (r < R) dst[r * L.rpcmax] = acc[r];
+  }
+  // ---- 3. partial Gram of this CTA's Z rows (upper triangle, gs lanes per entry), to every CTA
+  {
+    const int gs = K.gs, ne = L.NE;
+    for (int t0 = 0; t0 < ne * gs; t0 += kLT) {
+      const int t = t0 + tid;
+      const int e = t / gs, s = t - e * gs;
+      double a = 0.0;
+      if (e < ne) {
+        // packed upper-triangle index e -> (r, c), c >= r
+        int r = 0, rem = e;
+        while (rem >= R - r) {
+          rem -= R - r;
+          ++r;
+        }
+        const int c = r + rem;
+        for (int jj = s; jj < cnt; jj += gs) a = fma(Zd[jj * R + r], Zd[jj * R + c], a);
+      }
+      for (int o = 1; o < gs; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (e < ne)
+        for (int q = s; q < kLC; q += gs) cl.map_shared_rank(Grecv, q)[rank * ne + e] = a;
+    }
+  }
+  cluster_arrive();
+  cluster_wait();   // every partial M row and Gram of the cluster has landed
+
+  // ---- 4. G = sum of the C partial Grams (fixed order, gg lanes per entry), inverse
+  {
+    const int gg = K.gg, ne = L.NE;
+    for (int t0 = 0; t0 < ne * gg; t0 += kLT) {
+      const int t = t0 + tid;
+      const int e = t / gg, g = t - e * gg;
+      double a = 0.0;
+      if (e < ne)
+        for (int q = g; q < kLC; q += gg) a += Grecv[q * ne + e];
+      for (int o = 1; o < gg; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (e < ne && g == 0) {
+        int r = 0, rem = e;
+        while (rem >= R - r) {
+          rem -= R - r;
+          ++r;
+        }
+        const int c = r + rem;
+        G[r * R + c] = a;
+        G[c * R + r] = a;
+        const float af = (float)a;
+        Gf[r * R + c] = af;
+        Gf[c * R + r] = af;
+      }
+    }
+  }
+  __syncthreads();
+  // FP32 Gauss-Jordan start on warp 0; meanwhile the other warps draw the next mode update's samples
+  // and issue its fiber copies (they depend on nothing computed here)
+  __shared__ int s_ok;
+  float* Xf = reinterpret_cast<float*>(sm + L.Xf);
+  if (warp == 0) {
+    const bool ok = gauss_jordan_f32<MAXR>(Gf, Xf, reinterpret_cast<float*>(sm + L.prow), R);
+    if (lane == 0) s_ok = ok ? 1 : 0;
+  } else {
+    const int nb = cb ^ 1;
+    const int j0 = rank * spc;
+    draw_samples(p, nn, nt, j0, cnt, reinterpret_cast<uint32_t*>(sm + L.ids[nb]),
+                 reinterpret_cast<int64_t*>(sm + L.offs[nb]), tid - 32, kLT - 32);
+    asm volatile("bar.sync 1, %0;" ::"n"(kLT - 32) : "memory");   // warps 1.. only
+    fetch_fibers<T>(K, nn, reinterpret_cast<const int64_t*>(sm + L.offs[nb]), cnt, reinterpret_cast<T*>(sm + L.fib[nb]),
+                    tid - 32, kLT - 32);
+  }
+  __syncthreads();
+  loop_refine(s_ok != 0, G, Xf, X, reinterpret_cast<double*>(sm + L.E), reinterpret_cast<double*>(sm + L.U),
+              reinterpret_cast<double*>(sm + L.T2), reinterpret_cast<double*>(sm + L.dinv), redf, R,
+              sizeof(ACC) == 8 ? 2 : 1, s_bad);
+
+  // ---- 5. this CTA's rows: M rows (fixed-order sum over the C partials), A = M G^-1 (FP64)
+  const int i0 = rank * rpc;
+  const int nrows = max(0, min(I, i0 + rpc) - i0);
+  for (int e = tid; e < nrows * R; e += kLT) {
+    const int li = e / R, r = e - li * R;
+    ACC a = ACC(0);
+#pragma unroll
+    for (int q = 0; q < kLC; ++q) a += Mrecv[(q * R + r) * L.rpcmax + li];
+    mrow[e] = (double)a;
+  }
+  __syncthreads();
+  ACC* Fn = reinterpret_cast<ACC*>(sm + L.F[n]);
+  double* A64n = p.A64[n] + (int64_t)i0 * R;
+  for (int e = tid; e < nrows * R; e += kLT) {
+    const int li = e / R, r = e - li * R;
+    const double* m = mrow + li * R;
+    double s0 = 0.0, s1 = 0.0;
+    int l = 0;
+    for (; l + 1 < R; l += 2) {
+      s0 = fma(m[l], X[l * R + r], s0);
+      s1 = fma(m[l + 1], X[(l + 1) * R + r], s1);
+    }
+    if (l < R) s0 = fma(m[l], X[l * R + r], s0);
+    const double a = s0 + s1;
+    arow[e] = a;
+    A64n[e] = a;                                    // FP64 result (read after the run)
+    const ACC af = (ACC)a;
+    const int off = i0 * R + e;
+#pragma unroll 4
+    for (int q = 0; q < kLC; ++q) cl.map_shared_rank(Fn, q)[off] = af;   // every CTA's copy
+  }
+  __syncthreads();
+  {
+    // column sums of squares of this CTA's rows: 8-row chunks, then a fixed-order sum
+    const int nch = (nrows + 7) / 8;
+    for (int e = tid; e < R * nch; e += kLT) {
+      const int r = e / nch, ch = e - r * nch;
+      double sq = 0.0;
+      for (int li = ch * 8; li < min(nrows, ch * 8 + 8); ++li) sq = fma(arow[li * R + r], arow[li * R + r], sq);
+      cpart[e] = sq;
+    }
+    __syncthreads();
+    // 16 destination CTAs x R columns: each (q, r) pair is one thread (a warp's stores to one CTA
+    // are contiguous)
+    for (int e = tid; e < R * kLC; e += kLT) {
+      const int q = e / R, r = e - q * R;
+      double sq = 0.0;
+      for (int ch = 0; ch < nch; ++ch) sq += cpart[r * nch + ch];
+      cl.map_shared_rank(colrecv, q)[rank * R + r] = sq;
+    }
+  }
+  cluster_arrive();
+  cluster_wait();   // new factor rows and column partials of every CTA have landed
+
+  // ---- 6. lambda and the lazy scales of mode n (4 lanes per column, fixed order)
+  const int nl = 4 * R;
+  if (tid < (nl + 31) / 32 * 32) {       // whole warps (the shuffles need every lane)
+    const bool v = tid < nl;
+    const int r = tid >> 2, g = tid & 3;
+    double a = 0.0;
+    if (v)
+      for (int q = g; q < kLC; q += 4) a += colrecv[q * R + r];
+    a += __shfl_xor_sync(0xffffffffu, a, 1);
+    a += __shfl_xor_sync(0xffffffffu, a, 2);
+    if (v && g == 0) {
+      const double y = a > 0.0 ? rsqrt64(a) : 0.0;
+      const double nrm = a * y;
+      const double scn = nrm > 0.0 ? y : 1.0;
+      lam[r] = nrm;
+      sc[n * R + r] = scn;
+      double c = 1.0;                        // combined scale of the modes other than nn
+      for (int m = 0; m < N; ++m)
+        if (m != nn) c *= (m == n ? scn : sc[m * R + r]);
+      scomb[r] = c;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, typename ACC, int MAXR>
+__global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, int* queue) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ LoopConst K;
+  __shared__ int s_prob, s_bad, s_done, s_status, s_iter, s_stall;
+  __shared__ double s_best, s_last;
+  __shared__ float redf[kLT / 32];
+  __shared__ double fitpart[4];
+  while (true) {
+    if (rank == 0 && tid == 0) s_prob = atomicAdd(queue, 1);
+    cl.sync();
+    const int b = *cl.map_shared_rank(&s_prob, 0);
+    cl.sync();
+    if (b >= B) break;
+    // the problem descriptor and the layout, once
+    {
+      const int words = (int)(sizeof(Prob) / 4);
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(probs + b);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&K.p);
+      for (int w = tid; w < words; w += kLT) dst[w] = src[w];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const Prob& p = K.p;
+      K.L = loop_layout(p.N, p.R, p.dims, p.S, p.P_hat, (int)sizeof(T), (int)sizeof(ACC));
+      for (int m = 0; m < kMaxOrder; ++m) {
+        int v = 0;
+        if (m < p.N) {
+          const bool contig = p.use_rep || m == 0;
+          const uintptr_t base = reinterpret_cast<uintptr_t>(p.Xrep[m]);
+          const int fb = (int)p.dims[m] * (int)sizeof(T);
+          if (contig) {
+            for (int w : {16, 8, 4})
+              if (v == 0 && w >= (int)sizeof(T) && fb % w == 0 && base % w == 0) v = w;
+          } else if (sizeof(T) >= 4) {
+            v = (int)sizeof(T);
+          }
+        }
+        K.vec[m] = v;
+      }
+      // Gram partial: gs lanes per entry; C-way sum: gg lanes per entry (fewest FP64 warp
+      // instructions per SM sub-partition)
+      const int ne = K.L.NE, spc = K.L.spc;
+      int best = 1 << 30;
+      for (int gs = 1; gs <= 8; gs <<= 1) {
+        const int warps = (ne * gs + 31) / 32;
+        const int cost = ((warps + 3) / 4) * ((spc + gs - 1) / gs + (gs > 1 ? 31 - __clz(gs) : 0)) * ((ne * gs + kLT - 1) / kLT);
+        if (cost < best) {
+          best = cost;
+          K.gs = gs;
+        }
+      }
+      best = 1 << 30;
+      for (int gg = 1; gg <= 8; gg <<= 1) {
+        const int warps = (ne * gg + 31) / 32;
+        const int cost = ((warps + 3) / 4) * (kLC / gg - 1 + (gg > 1 ? 31 - __clz(gg) : 0)) * ((ne * gg + kLT - 1) / kLT);
+        if (cost < best) {
+          best = cost;
+          K.gg = gg;
+        }
+      }
+    }
+    __syncthreads();
+    const Prob& p = K.p;
+    const LoopSmem& L = K.L;
+    const int R = p.R, N = p.N;
+    double* sc = reinterpret_cast<double*>(sm + L.sc);
+    double* lam = reinterpret_cast<double*>(sm + L.lam);
+    ACC* wr = reinterpret_cast<ACC*>(sm + L.wr);
+    double* red = reinterpret_cast<double*>(sm + L.red);
+    double* fitrecv = reinterpret_cast<double*>(sm + L.fitrecv);
+    uint32_t* fidx = reinterpret_cast<uint32_t*>(sm + L.fidx);
+    ACC* fx = reinterpret_cast<ACC*>(sm + L.fx);
+    State* st = p.state;
+    // every factor in full, the lazy scales, lambda, this CTA's fit entries
+    for (int m = 0; m < N; ++m) {
+      ACC* F = reinterpret_cast<ACC*>(sm + L.F[m]);
+      const int cntm = (int)p.dims[m] * R;
+      for (int e = tid; e < cntm; e += kLT) {
+        if constexpr (sizeof(ACC) == 8) F[e] = p.A64[m][e];
+        else F[e] = p.A32[m][e];
+      }
+    }
+    for (int e = tid; e < N * R; e += kLT) sc[e] = p.scale[e / R][e % R];
+    for (int r = tid; r < R; r += kLT) lam[r] = p.lambda[r];
+    const int f0 = rank * L.fpc;
+    const int fcnt = max(0, min(p.P_hat, f0 + L.fpc) - f0);
+    for (int e = tid; e < fcnt * N; e += kLT) fidx[e] = p.fit_idx[(int64_t)f0 * N + e];
+    for (int e = tid; e < fcnt; e += kLT) fx[e] = (ACC)p.fit_x[f0 + e];
+    if (tid == 0) {
+      s_done = st->done;
+      s_status = st->status;
+      s_iter = st->iter;
+      s_stall = st->stall;
+      s_best = st->best;
+      s_last = st->last_fit;
+      s_bad = 0;
+    }
+    const double fit_scale = (double)p.P / (double)p.P_hat;   // P / P_hat
+    const double inv_norm = 1.0 / st->norm_x;
+    // samples and fiber copies of the first mode update
+    const int spc = L.spc;
+    const int j0 = rank * spc;
+    const int cnt = max(0, min(p.S, j0 + spc) - j0);
+    draw_samples(p, 0, p.t0 + (uint32_t)st->iter, j0, cnt, reinterpret_cast<uint32_t*>(sm + L.ids[0]),
+                 reinterpret_cast<int64_t*>(sm + L.offs[0]), tid, kLT);
+    __syncthreads();
+    fetch_fibers<T>(K, 0, reinterpret_cast<const int64_t*>(sm + L.offs[0]), cnt, reinterpret_cast<T*>(sm + L.fib[0]),
+                    tid, kLT);
+    {
+      double* scomb = reinterpret_cast<double*>(sm + L.scomb);
+      for (int r = tid; r < R; r += kLT) {   // combined scale of the modes other than the first
+        double c = 1.0;
+        for (int m = 1; m < N; ++m) c *= sc[m * R + r];
+        scomb[r] = c;
+      }
+    }
+    cl.sync();   // every CTA initialized before any stores into another
+    const int cap = p.fixed_iters > 0 ? p.fixed_iters : p.max_iters;
+    int u = 0;   // mode updates run (selects the sample / fiber buffer)
+    while (!s_done && s_iter < cap) {
+      const uint32_t t = p.t0 + (uint32_t)s_iter;
+      for (int n = 0; n < N; ++n) {
+        const int cb = u & 1;
+        // the next mode update (its samples and fiber copies are issued during this one)
+        const int nn = n + 1 < N ? n + 1 : 0;
+        const uint32_t nt = n + 1 < N ? t : t + 1;
+        loop_mode_update<T, ACC, MAXR>(K, sm, cl, n, cb, nn, nt, &s_bad, redf);
+        ++u;
+        if (s_bad) break;   // identical in every CTA (same G, same factorization)
+      }
+      if (s_bad) {
+        if (tid == 0) {
+          s_status = CPR_ESINGULAR;
+          s_done = 1;
+        }
+        __syncthreads();
+        break;
+      }
+      // ---- sampled fit (Sec. 3.4) on this CTA's share of the fixed entries
+      for (int r = tid; r < R; r += kLT) {
+        double w = lam[r];
+        for (int m = 0; m < N; ++m) w *= sc[m * R + r];
+        wr[r] = (ACC)w;
+      }
+      __syncthreads();
+      double e2 = 0.0;
+      for (int jj = tid; jj < fcnt; jj += kLT) {
+        const uint32_t* id = fidx + jj * N;
+        const ACC* rows[kMaxOrder];
+#pragma unroll
+        for (int m = 0; m < kMaxOrder; ++m)
+          rows[m] = (m < N) ? reinterpret_cast<const ACC*>(sm + L.F[m]) + (int)id[m] * R : nullptr;
+        ACC acc = ACC(0);
+        for (int r = 0; r < R; ++r) {
+          ACC w = wr[r];
+#pragma unroll
+          for (int m = 0; m < kMaxOrder; ++m)
+            if (m < N) w *= rows[m][r];
+          acc += w;
+        }
+        double e;
+        if constexpr (sizeof(ACC) == 8) e = (double)fx[jj] - acc;
+        else e = (double)(fx[jj] - acc);
+        e2 = fma(e, e, e2);
+      }
+      red[tid] = e2;
+      __syncthreads();
+      if (warp < 4) {   // four warps (one per SM sub-partition) sum 128 values each
+        double a = red[warp * 128 + lane] + red[warp * 128 + 32 + lane];
+        a += red[warp * 128 + 64 + lane] + red[warp * 128 + 96 + lane];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) fitpart[warp] = a;
+      }
+      __syncthreads();
+      if (warp == 0 && lane < kLC) {
+        const double tot = (fitpart[0] + fitpart[1]) + (fitpart[2] + fitpart[3]);
+        cl.map_shared_rank(fitrecv, lane)[rank] = tot;
+      }
+      cluster_arrive();
+      cluster_wait();
+      if (warp == 0) {
+        double a = lane < kLC ? fitrecv[lane] : 0.0;
+        for (int o = 8; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) {
+          // F = 1 - sqrt(P mean e^2) / ||X||, the square root as v * rsqrt(v)
+          const double v = fit_scale * a;
+          const double fit = v > 0.0 ? 1.0 - v * rsqrt64(v) * inv_norm : (v == 0.0 ? 1.0 : NAN);
+          const int t1 = s_iter + 1;
+          bool stop = false;
+          if (!isfinite(fit)) {
+            s_status = CPR_ENONFINITE;
+            stop = true;
+          } else if (p.fixed_iters > 0) {
+            stop = t1 >= p.fixed_iters;
+          } else {
+            if (fit > s_best) {
+              s_best = fit;
+              s_stall = 0;
+            } else {
+              s_stall += 1;
+            }
+            if (t1 >= p.max_iters) stop = true;
+            if (t1 >= 2 && fabs(fit - s_last) <= p.tol) stop = true;
+            if (p.eta >= 0.0 && fit >= 1.0 - 1.2 * p.eta) stop = true;
+            if (p.stall_iters > 0 && s_stall >= p.stall_iters) stop = true;
+          }
+          if (rank == 0 && p.trace) p.trace[s_iter] = fit;
+          s_last = fit;
+          s_iter = t1;
+          if (stop) s_done = 1;
+        }
+      }
+      __syncthreads();
+    }
+    cp_async_wait<0>();   // the copies issued for an update that will not run
+    // publish the loop state, lambda and the lazy scales (CTA 0)
+    if (rank == 0) {
+      for (int e = tid; e < N * R; e += kLT) p.scale[e / R][e % R] = sc[e];
+      for (int r = tid; r < R; r += kLT) p.lambda[r] = lam[r];
+      if (tid == 0) {
+        st->done = 1;
+        st->status = s_status;
+        st->iter = s_iter;
+        st->stall = s_stall;
+        st->best = s_best;
+        st->last_fit = s_last;
+      }
+    }
+    __syncthreads();
+    cl.sync();  // no CTA reuses its shared memory while another may still store into it
+  }
+}
+
+template <typename T, typename ACC, int MAXR>
+cudaError_t loop_launch(const Prob* probs, int B, int* queue, int smem, int nclusters, cudaStream_t s, int query,
+                        int* capacity) {
+  auto kern = k_loop_rep<T, ACC, MAXR>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(kLC * (query ? 1 : nclusters)), 1, 1);
+  cfg.blockDim = dim3(kLT, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)kLC;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (query) {
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    *capacity = n;
+    return cudaSuccess;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, probs, B, queue);
+}
+
+template <typename T, typename ACC>
+cudaError_t loop_dispatch_r(int maxR, const Prob* probs, int B, int* queue, int smem, int ncl, cudaStream_t s,
+                            int query, int* cap) {
+  if (maxR <= 8) return loop_launch<T, ACC, 8>(probs, B, queue, smem, ncl, s, query, cap);
+  if (maxR <= 16) return loop_launch<T, ACC, 16>(probs, B, queue, smem, ncl, s, query, cap);
+  return loop_launch<T, ACC, 32>(probs, B, queue, smem, ncl, s, query, cap);
+}
+
+cudaError_t loop_dispatch(int dtype, int maxR, const Prob* probs, int B, int* queue, int smem, int ncl, cudaStream_t s,
+                          int query, int* cap) {
+  switch (dtype) {
+    case CPR_F64: return loop_dispatch_r<double, double>(maxR, probs, B, queue, smem, ncl, s, query, cap);
+    case CPR_F32: return loop_dispatch_r<float, float>(maxR, probs, B, queue, smem, ncl, s, query, cap);
+    default: return loop_dispatch_r<__nv_bfloat16, float>(maxR, probs, B, queue, smem, ncl, s, query, cap);
+  }
+}
+
+}  // namespace
+
+// Shared memory of the replicated-factor loop for the largest problem of a batch, or -1 if some
+// problem does not fit (rank above 32, or the layout above the per-CTA limit).
+int loop_rep_smem_bytes(const Prob* probs_host, int B) {
+  int most = 0;
+  for (int b = 0; b < B; ++b) {
+    const Prob& p = probs_host[b];
+    if (p.R > 32) return -1;
+    const int ab = p.dtype == CPR_F64 ? 8 : 4;
+    const int tb = p.dtype == CPR_F64 ? 8 : (p.dtype == CPR_F32 ? 4 : 2);
+    const LoopSmem L = loop_layout(p.N, p.R, p.dims, p.S, p.P_hat, tb, ab);
+    most = most > L.bytes ? most : L.bytes;
+  }
+  return most <= 200 * 1024 ? most : -1;
+}
+
+int loop_rep_capacity(int dtype, int smem, int maxR) {
+  int cap = 0;
+  if (loop_dispatch(dtype, maxR, nullptr, 0, nullptr, smem, 0, nullptr, 1, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return cap;
+}
+
+cudaError_t launch_loop_rep(const Prob* probs, int B, int* queue, int dtype, int smem, int nclusters, int maxR,
+                            cudaStream_t s) {
+  return loop_dispatch(dtype, maxR, probs, B, queue, smem, nclusters, s, 0, nullptr);
+}
+
+}  // namespace cpr

@@ -310,7 +310,7 @@ def test_loop_paths_agree(cb, dtype, mix):
     T = to_oracle_array(prob.X, dims)
     fn = cb.cpr_cprand_mix if mix else cb.cpr_cprand
     runs = {}
-    for path in (cb.LOOP_CLUSTER, cb.LOOP_GRAPH, cb.LOOP_STREAM):
+    for path in (cb.LOOP_CLUSTER, cb.LOOP_CLUSTER_DIST, cb.LOOP_GRAPH, cb.LOOP_STREAM):
         trace = torch.zeros(12, dtype=torch.float64, device=DEV)
         opts = cb.cpr_default_opts(seed=8, fixed_iters=12, fit_trace_dev=trace.data_ptr(), loop_path=path)
         out = fn(prob.X, dims, 4, 60, opts=opts)
@@ -340,12 +340,12 @@ def test_cluster_path_rejects_problems_that_do_not_fit(cb):
         cb.cpr_cprand(X, dims, 64, 100, opts=opts)
 
 
-@pytest.mark.parametrize("path", ["cluster", "graph"])
+@pytest.mark.parametrize("path", ["cluster", "cluster_dist", "graph"])
 @pytest.mark.parametrize("dims", [(41, 37, 29), (13, 11, 9, 7)])
 def test_unfolding_copies_give_identical_runs(cb, path, dims):
     # gathering each mode from its column-major unfolding reads the same values in the same order
     prob = make_problem(dims, 3, C=0.5, eta=0.01, seed=77, dtype=torch.float32, device=DEV)
-    lp = cb.LOOP_CLUSTER if path == "cluster" else cb.LOOP_GRAPH
+    lp = {"cluster": cb.LOOP_CLUSTER, "cluster_dist": cb.LOOP_CLUSTER_DIST, "graph": cb.LOOP_GRAPH}[path]
     traces = []
     for layout in (0, 1):
         trace = torch.zeros(6, dtype=torch.float64, device=DEV)
