@@ -401,16 +401,17 @@ int enqueue_mixing(const void* src, void* final, void* t1, void* t2, void* rep_l
   if (tc) {
     for (int n = 0; n < N; ++n)
       CPR_LAUNCH(CPR_KERNEL_OTHER, launch_split_tf32(W32[n], W32[n], Wlo[n], dims[n] * dims[n], s));
+    // pass n reads the mode-n unfolding of the previous result: the first pass writes the mode-2
+    // unfolding directly; later passes write the standard layout, transposed by an unfolding copy
     const float* U = static_cast<const float*>(src);
     for (int n = 0; n < N; ++n) {
-      if (n > 0) {
-        CPR_LAUNCH(CPR_KERNEL_OTHER, launch_unfold_copy(t1, t2, dtype, N, dims, n, s));
-        U = static_cast<const float*>(t2);
-      }
+      if (n > 1) CPR_LAUNCH(CPR_KERNEL_OTHER, launch_unfold_copy(t1, t2, dtype, N, dims, n, s));
+      if (n > 0) U = static_cast<const float*>(t2);
       const bool last = n == N - 1;
-      float* ystd = static_cast<float*>(last ? final : t1);
+      float* ystd = last ? static_cast<float*>(final) : (n == 0 ? nullptr : static_cast<float*>(t1));
+      float* ynext = (n == 0 && !last) ? static_cast<float*>(t2) : nullptr;
       float* yunf = (last && rep_last && n > 0) ? static_cast<float*>(rep_last) : nullptr;
-      CPR_LAUNCH(CPR_KERNEL_MIX, launch_mix_tc(U, ystd, yunf, W32[n], Wlo[n], N, dims, n, 1, err, s));
+      CPR_LAUNCH(CPR_KERNEL_MIX, launch_mix_tc(U, ystd, yunf, ynext, W32[n], Wlo[n], N, dims, n, 1, err, s));
       if (yunf) *wrote_rep_last = true;
     }
     return CPR_OK;

@@ -306,8 +306,8 @@ constexpr int kAlsRows = 32;       // factor rows per block of the CP-ALS solve 
 // mixing on the tensor cores (FP32 tensors, I_n a multiple of 4)
 bool mix_tc_supported(int dtype, int I);
 cudaError_t launch_split_tf32(const float* w, float* hi, float* lo, int64_t n, cudaStream_t s);
-cudaError_t launch_mix_tc(const float* U, float* ystd, float* yunf, const float* Whi, const float* Wlo, int N,
-                          const int64_t* dims, int n, int three_x, int* err, cudaStream_t s);
+cudaError_t launch_mix_tc(const float* U, float* ystd, float* yunf, float* ynext, const float* Whi, const float* Wlo,
+                          int N, const int64_t* dims, int n, int three_x, int* err, cudaStream_t s);
 
 // mixing (Alg. 5)
 cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, double* table, float* W32,

@@ -4,33 +4,36 @@
 //
 // Work split: CTA c draws samples [c*spc, (c+1)*spc) of every mode update and owns factor rows
 // [c*rpc_n, (c+1)*rpc_n) of mode n.  Per mode update:
-//   1. SKR (Alg. 2): the Z_S rows of this CTA's samples from the local factor copies times their
-//      lazy column scales (FP64; an FP32/FP64 copy feeds the contraction).
+//   1. SKR (Alg. 2): the Z_S rows of this CTA's samples from the local factor copies times the
+//      combined lazy column scale of the other modes (FP64; an FP32/FP64 copy feeds step 2).
 //   2. Contraction M_c = X_S,c Z_S,c for every row i_n (FP32 accumulation, FP64 for FP64 tensors)
-//      from the sampled fibers, which were copied into shared memory (cp.async) during the previous
-//      mode update: the sample draw of a mode update does not depend on the factors, so its fiber
-//      reads are issued one update ahead and never wait on HBM latency in the dependent chain.
-//      Each row's partial is stored straight into the shared memory of the CTA owning that row.
+//      from the sampled fibers, which were copied into shared memory during the previous mode update
+//      (one TMA bulk copy per contiguous fiber, cp.async otherwise): a mode update's sample draw
+//      does not depend on the factors, so its fiber reads are issued one update ahead and never wait
+//      on HBM in the dependent chain.  Each row's
+//      partial is stored straight into the shared memory of the CTA owning that row.
 //   3. Partial FP64 Gram of this CTA's Z rows, stored into every CTA's shared memory.
-//   4. Cluster barrier; every CTA sums the C partial Grams in one fixed order (identical G in all
-//      CTAs) and inverts it: Gauss-Jordan in FP32 on one warp (lane i holds row i of [G | I]), then
-//      Newton-Schulz steps X <- X + X (I - G X) in FP64 (one for FP32 tensors, two for FP64), which
-//      square the residual ||I - G X||; a residual above 1/4 or a bad FP32 pivot falls back to an
-//      FP64 Cholesky inverse (which also detects a singular Gram matrix).
+//   4. Cluster barrier (the next update's samples are drawn and its fiber copies issued between
+//      the barrier's arrive and wait); every CTA sums the C partial Grams in one fixed order
+//      (identical G everywhere) and inverts it: Gauss-Jordan elimination in FP32 with one thread
+//      per entry of [G | I], then Newton-Schulz steps X <- X + X (I - G X) in FP64 (one for FP32
+//      tensors, two for FP64), each squaring the residual ||I - G X||; a residual above 1/4 or a
+//      bad FP32 pivot falls back to an FP64 Cholesky inverse (which detects a singular Gram).
 //   5. The CTA's rows: M rows summed over the C partials (fixed order), A = M G^-1 in FP64, written
 //      to the FP64 result and stored into every CTA's copy of the factor; column sums of squares
-//      of its rows are stored into every CTA.
+//      of the rows are stored into every CTA.
 //   6. Cluster barrier; lambda and the lazy column scales from the C column partials (fixed order).
 // After the N modes each CTA evaluates its share of the P_hat fixed fit entries (indices and values
 // staged in shared memory once per problem) against the local factor copies; after a cluster
 // barrier every CTA sums the C partials in the same order and applies the stopping rules to its own
 // copy of the loop state, so all CTAs take the same decision.
 //
-// Data only ever moves by stores into other CTAs' shared memory followed by a cluster barrier
-// (release / acquire); no CTA reads another CTA's shared memory.  FP64 instructions issue at a low
-// rate on this GPU (one warp instruction occupies an SM sub-partition's FP64 pipe for tens of
-// cycles), so FP64 work is packed into as few warps as possible and spread over the four
-// sub-partitions, and reductions never run redundantly in every warp.
+// Data only moves by stores into other CTAs' shared memory followed by a cluster barrier (release /
+// acquire); no CTA reads another CTA's shared memory.  FP64 arithmetic issues at a low rate on this
+// GPU (a warp's DFMA occupies an SM sub-partition's FP64 pipe for about 76 cycles), so FP64 work is
+// packed into few warps spread over the four sub-partitions, and reductions never run redundantly
+// in every warp.  Factor copies and Z rows are stored with rows padded to 16 bytes so that they
+// move as vectors.
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -47,26 +50,26 @@ constexpr int kLT = 512;   // threads per CTA
 constexpr int kLC = 16;    // CTAs per cluster
 
 struct LoopSmem {          // byte offsets into the dynamic shared memory
-  int F[kMaxOrder];        // full factor m, I_m x R (ACC)
+  int F[kMaxOrder];        // full factor m, I_m x rp (ACC)
   int fib[2];              // sampled fibers of a mode update: spc rows of ldf elements (T)
   int ids[2];              // spc x kMaxOrder sampled indices
   int offs[2];             // spc fiber offsets
-  int Zd, Zf;              // spc x R Z_S rows (FP64) and spc x zld (ACC, rows padded to 16 bytes)
+  int Zd, Zf;              // spc x R Z_S rows (FP64) and spc x rp (ACC)
   int Mrecv;               // C x R x rpcmax partial M columns received for this CTA's rows (ACC)
   int Grecv;               // C x NE partial Grams (packed upper triangle, FP64)
   int colrecv;             // C x R column sums of squares
   int fitrecv;             // C partial fit sums
   int fidx, fx;            // fpc x N fit indices, fpc fit values (ACC)
-  int G, X, E, U, T2;      // R x R FP64
-  int Gf, Xf;              // R x R FP32 (Gauss-Jordan input and output)
+  int G, X, U, E, T2;      // R x R FP64
+  int Gf;                  // R x R FP32 copy of G
+  int gj;                  // 2 x R x 2R FP32: the Gauss-Jordan tableau, alternating by step
   int mrow, arow;          // rpcmax x R FP64
   int cpart;               // R x nchmax FP64
-  int sc, lam, wr, dinv;   // N x R, R, R (fit weights, ACC), R FP64
-  int scomb;               // R: product of the other modes' lazy scales for the next mode update
-  int prow;                // 2 x 2 MAXR FP32: pivot rows of the Gauss-Jordan elimination
+  int sc, lam, wr, dinv;   // N x R, R, rp (fit weights, ACC), R FP64
+  int scomb;               // R: product of the other modes' lazy scales for the coming mode update
   int red;                 // kLT FP64 (block reduction)
   int bytes;
-  int ldf, spc, rpcmax, fpc, NE, nchmax, zld;
+  int ldf, spc, rpcmax, fpc, NE, nchmax, rp;
 };
 
 __host__ __device__ inline int al16(int x) { return (x + 15) / 16 * 16; }
@@ -76,6 +79,7 @@ __host__ __device__ inline LoopSmem loop_layout(int N, int R, const int64_t* dim
   LoopSmem L;
   int o = 0, maxI = 0;
   L.rpcmax = 0;
+  L.rp = (R * abytes + 15) / 16 * 16 / abytes;
   for (int m = 0; m < kMaxOrder; ++m) L.F[m] = 0;
   for (int m = 0; m < N; ++m) {
     const int I = (int)dims[m];
@@ -83,14 +87,13 @@ __host__ __device__ inline LoopSmem loop_layout(int N, int R, const int64_t* dim
     const int rpc = (I + kLC - 1) / kLC;
     L.rpcmax = rpc > L.rpcmax ? rpc : L.rpcmax;
     L.F[m] = o;
-    o = al16(o + I * R * abytes);
+    o = al16(o + I * L.rp * abytes);
   }
   L.spc = (S + kLC - 1) / kLC;
   L.ldf = al16(maxI * tbytes) / tbytes;
   L.NE = R * (R + 1) / 2;
   L.fpc = (P_hat + kLC - 1) / kLC;
   L.nchmax = (L.rpcmax + 7) / 8;
-  L.zld = (R * abytes + 15) / 16 * 16 / abytes;
   for (int q = 0; q < 2; ++q) {
     L.fib[q] = o;  o = al16(o + L.spc * L.ldf * tbytes);
   }
@@ -99,7 +102,7 @@ __host__ __device__ inline LoopSmem loop_layout(int N, int R, const int64_t* dim
     L.offs[q] = o; o = al16(o + L.spc * 8);
   }
   L.Zd = o;      o = al16(o + L.spc * R * 8);
-  L.Zf = o;      o = al16(o + L.spc * L.zld * abytes);
+  L.Zf = o;      o = al16(o + L.spc * L.rp * abytes);
   L.Mrecv = o;   o = al16(o + kLC * L.rpcmax * R * abytes);
   L.Grecv = o;   o = al16(o + kLC * L.NE * 8);
   L.colrecv = o; o = al16(o + kLC * R * 8);
@@ -108,20 +111,19 @@ __host__ __device__ inline LoopSmem loop_layout(int N, int R, const int64_t* dim
   L.fx = o;      o = al16(o + L.fpc * abytes);
   L.G = o;       o = al16(o + R * R * 8);
   L.X = o;       o = al16(o + R * R * 8);
-  L.E = o;       o = al16(o + R * R * 8);
   L.U = o;       o = al16(o + R * R * 8);
+  L.E = o;       o = al16(o + R * R * 8);
   L.T2 = o;      o = al16(o + R * R * 8);
   L.Gf = o;      o = al16(o + R * R * 4);
-  L.Xf = o;      o = al16(o + R * R * 4);
+  L.gj = o;      o = al16(o + 2 * R * 2 * R * 4);
   L.mrow = o;    o = al16(o + L.rpcmax * R * 8);
   L.arow = o;    o = al16(o + L.rpcmax * R * 8);
   L.cpart = o;   o = al16(o + R * L.nchmax * 8);
   L.sc = o;      o = al16(o + N * R * 8);
   L.lam = o;     o = al16(o + R * 8);
-  L.wr = o;      o = al16(o + R * 8);
+  L.wr = o;      o = al16(o + L.rp * 8);
   L.dinv = o;    o = al16(o + R * 8);
   L.scomb = o;   o = al16(o + R * 8);
-  L.prow = o;    o = al16(o + 2 * 2 * 32 * 4);
   L.red = o;     o = al16(o + kLT * 8);
   L.bytes = o;
   return L;
@@ -137,8 +139,36 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s32(dst)), "l"(src), "n"(B) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(s32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on a phase of an mbarrier: false if it did not complete within the limit.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* b, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 24); ++it)
+    if (mbar_try(b, parity)) return true;
+  return false;
+}
+// One TMA bulk copy global -> this CTA's shared memory, completing bytes on the mbarrier.
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   s32(dst)),
+               "l"(src), "r"(bytes), "r"(s32(b))
+               : "memory");
+}
 
 __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
@@ -158,14 +188,17 @@ struct LoopConst {
   Prob p;
   LoopSmem L;
   int vec[kMaxOrder];      // bytes per cp.async of a mode's fiber copies (16, 8, 4), 0: plain loads
+  int bulk[kMaxOrder];     // 1: a mode's fibers are contiguous and 16-byte aligned: one TMA bulk copy each
   int gs, gg;              // Gram: samples split over gs lanes; sum of the C partials over gg lanes
+  unsigned char ne_r[32 * 33 / 2];   // packed upper-triangle entry e -> (row, column)
+  unsigned char ne_c[32 * 33 / 2];
 };
 
 // Draw the samples of mode update (t, n) for this CTA (Philox stream 0, counter (j, n, t, b)):
 // indices by mode and the storage offset of each sampled fiber in the copy that mode reads.
 __device__ __forceinline__ void draw_samples(const Prob& p, int n, uint32_t t, int j0, int cnt, uint32_t* ids,
-                                             int64_t* offs, int tt, int nth) {
-  for (int jj = tt; jj < cnt; jj += nth) {
+                                             int64_t* offs) {
+  for (int jj = threadIdx.x; jj < cnt; jj += kLT) {
     const uint32_t j = (uint32_t)(j0 + jj);
     const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
     const uint4 w0 = philox10(make_uint4(j, counter_word1(kStreamSamples, 0, n), t, p.b), k0, k1);
@@ -186,177 +219,113 @@ __device__ __forceinline__ void draw_samples(const Prob& p, int n, uint32_t t, i
   }
 }
 
-// Copy the cnt sampled fibers of mode n into buf (row j at buf + j * ldf).  Asynchronous (one
-// commit group per call, possibly empty) unless vec == 0, when plain loads are used.
+// Copy the cnt sampled fibers of mode n into buf (row j at buf + j * ldf).  Contiguous, aligned
+// fibers: one TMA bulk copy per fiber, all issued by thread 0 after it armed the buffer's mbarrier
+// with the total byte count (returns true; the consumer waits on that barrier).  Otherwise cp.async
+// copies (one commit group per call, possibly empty), or plain loads when no cp.async width fits.
 template <typename T>
-__device__ __forceinline__ void fetch_fibers(const LoopConst& K, int n, const int64_t* offs, int cnt, T* buf, int tt,
-                                             int nth) {
+__device__ __forceinline__ bool fetch_fibers(const LoopConst& K, int n, const int64_t* offs, int cnt, T* buf,
+                                             uint64_t* bar) {
   const Prob& p = K.p;
   const int I = (int)p.dims[n];
   const int ldf = K.L.ldf;
   const T* X = reinterpret_cast<const T*>(p.Xrep[n]);
   const int64_t stn = p.use_rep ? 1 : p.st[n];
   const int vec = K.vec[n];
-  const int tid = tt;
+  const int tid = threadIdx.x;
+  if (K.bulk[n]) {
+    if (tid == 0) {
+      const uint32_t fb = (uint32_t)I * (uint32_t)sizeof(T);
+      mbar_expect_tx(bar, fb * (uint32_t)cnt);
+      for (int j = 0; j < cnt; ++j) bulk_copy(buf + j * ldf, X + offs[j], fb, bar);
+    }
+    return true;
+  }
   if (stn == 1 && vec >= 4) {
     const int epc = vec / (int)sizeof(T);      // elements per copy
     const int cpf = I / epc;                    // copies per fiber
-    const int total = cnt * cpf;
-    for (int e = tid; e < total; e += nth) {
-      const int j = e / cpf, q = e - j * cpf;
-      const T* src = X + offs[j] + (int64_t)q * epc;
-      T* dst = buf + j * ldf + q * epc;
-      if (vec == 16) cp_async<16>(dst, src);
-      else if (vec == 8) cp_async<8>(dst, src);
-      else cp_async<4>(dst, src);
+    for (int j = 0; j < cnt; ++j) {
+      const T* src = X + offs[j];
+      T* dst = buf + j * ldf;
+      for (int q = tid; q < cpf; q += kLT) {
+        if (vec == 16) cp_async<16>(dst + q * epc, src + (int64_t)q * epc);
+        else if (vec == 8) cp_async<8>(dst + q * epc, src + (int64_t)q * epc);
+        else cp_async<4>(dst + q * epc, src + (int64_t)q * epc);
+      }
     }
   } else if (vec >= 4) {                        // strided fibers, one element per copy
-    const int total = cnt * I;
-    for (int e = tid; e < total; e += nth) {
-      const int j = e / I, i = e - j * I;
-      const T* src = X + offs[j] + (int64_t)i * stn;
-      T* dst = buf + j * ldf + i;
-      if constexpr (sizeof(T) == 8) cp_async<8>(dst, src);
-      else cp_async<4>(dst, src);
-    }
+    for (int j = 0; j < cnt; ++j)
+      for (int i = tid; i < I; i += kLT) {
+        if constexpr (sizeof(T) == 8) cp_async<8>(buf + j * ldf + i, X + offs[j] + (int64_t)i * stn);
+        else cp_async<4>(buf + j * ldf + i, X + offs[j] + (int64_t)i * stn);
+      }
   } else {
-    const int total = cnt * I;
-    for (int e = tid; e < total; e += nth) {
-      const int j = e / I, i = e - j * I;
-      buf[j * ldf + i] = X[offs[j] + (int64_t)i * stn];
-    }
+    for (int j = 0; j < cnt; ++j)
+      for (int i = tid; i < I; i += kLT) buf[j * ldf + i] = X[offs[j] + (int64_t)i * stn];
   }
   cp_async_commit();
+  return false;
 }
 
-// X0 = G^-1 by Gauss-Jordan elimination without pivoting (G symmetric positive definite) in FP32
-// on the calling warp: lane i holds row i of [G | I]; the pivot row of each step is broadcast
-// through shared memory (prow: 2 x 2 MAXR floats, alternating by step).  Reads the FP32 copy of G,
-// writes X0 in FP32 and returns false on every lane if a pivot is not positive relative to the
-// largest diagonal entry.
-template <int MAXR>
-__device__ bool gauss_jordan_f32(const float* Gf, float* Xf, float* prow, int R) {
-  static_assert(MAXR % 4 == 0, "rows move as float4");
-  const int lane = threadIdx.x & 31;
-  float a[MAXR], x[MAXR];
-#pragma unroll
-  for (int c = 0; c < MAXR; ++c) {
-    a[c] = (lane < R && c < R) ? Gf[lane * R + c] : 0.f;
-    x[c] = (lane == c) ? 1.f : 0.f;
+// Wait for the fibers of the buffer about to be read: its mbarrier phase when they came by TMA
+// bulk copies (bounded; a wait that runs out sets *s_tout), and any cp.async groups.
+__device__ __forceinline__ void wait_fibers(uint64_t* fbar, int b, uint32_t& fpar, uint32_t fblk, int* s_tout) {
+  if ((fblk >> b) & 1u) {
+    if (!mbar_wait_bounded(fbar + b, (fpar >> b) & 1u)) *s_tout = 1;
+    fpar ^= 1u << b;
   }
-  float md = lane < R ? Gf[lane * R + lane] : 0.f;
-  for (int o = 16; o > 0; o >>= 1) md = fmaxf(md, __shfl_xor_sync(0xffffffffu, md, o));
+  cp_async_wait_all();
+}
+
+// X0 = G^-1 in FP32 by Gauss-Jordan elimination without pivoting (G symmetric positive definite),
+// one thread per entry of the R x 2R tableau [G | I], one block barrier per step (tableaus
+// alternate between the two halves of gj).  Returns (the same in every thread) false when a pivot
+// is not positive relative to the largest diagonal entry md; X0 is then columns R.. of the final
+// tableau: gj[(R & 1) * 2R^2 + i * 2R + R + c].
+template <int MAXR>
+__device__ bool gauss_jordan_block(const float* Gf, float* gj, int R, float md) {
+  constexpr int EPT = (2 * MAXR * MAXR + kLT - 1) / kLT;   // tableau entries per thread
+  const int W = 2 * R, nent = R * W, tid = threadIdx.x;
+  int ei[EPT], ec[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * kLT;
+    ei[q] = e / W;
+    ec[q] = e - ei[q] * W;
+    if (e < nent) gj[e] = ec[q] < R ? Gf[ei[q] * R + ec[q]] : (ec[q] - R == ei[q] ? 1.f : 0.f);
+  }
+  __syncthreads();
   bool bad = false;
+  for (int k = 0; k < R; ++k) {
+    const float* o = gj + (k & 1) * nent;
+    float* w = gj + ((k + 1) & 1) * nent;
+    const float piv = o[k * W + k];
+    bad = bad || !(piv > 1e-6f * md) || !isfinite(piv);
+    const float inv = 1.f / piv;
 #pragma unroll
-  for (int k = 0; k < MAXR; ++k) {
-    if (k < R) {
-      float* pr = prow + (k & 1) * 2 * MAXR;
-      const bool own = lane == k;
-      if (own) {
-#pragma unroll
-        for (int c = 0; c < MAXR; c += 4) {
-          *reinterpret_cast<float4*>(pr + c) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
-          *reinterpret_cast<float4*>(pr + MAXR + c) = make_float4(x[c], x[c + 1], x[c + 2], x[c + 3]);
-        }
-      }
-      __syncwarp();
-      const float piv = pr[k];
-      bad = bad || !(piv > 1e-6f * md) || !isfinite(piv);
-      const float inv = __frcp_rn(piv);
-      const float ak = a[k];
-#pragma unroll
-      for (int c = 0; c < MAXR; c += 4) {
-        if (c < R) {
-          const float4 pa = *reinterpret_cast<const float4*>(pr + c);
-          const float4 px = *reinterpret_cast<const float4*>(pr + MAXR + c);
-          const float pav[4] = {pa.x * inv, pa.y * inv, pa.z * inv, pa.w * inv};
-          const float pxv[4] = {px.x * inv, px.y * inv, px.z * inv, px.w * inv};
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            a[c + q] = own ? pav[q] : fmaf(-ak, pav[q], a[c + q]);
-            x[c + q] = own ? pxv[q] : fmaf(-ak, pxv[q], x[c + q]);
-          }
-        }
+    for (int q = 0; q < EPT; ++q) {
+      const int e = tid + q * kLT;
+      if (e < nent) {
+        const float pkc = o[k * W + ec[q]] * inv;
+        w[e] = ei[q] == k ? pkc : fmaf(-o[ei[q] * W + k], pkc, o[e]);
       }
     }
-  }
-  if (lane < R) {
-#pragma unroll
-    for (int c = 0; c < MAXR; ++c)
-      if (c < R) Xf[lane * R + c] = x[c];
+    __syncthreads();
   }
   return !bad;
 }
 
-// The inverse X = G^-1 (FP64, R x R, shared memory) by every CTA of the cluster.
-// Every CTA of the cluster, after the FP32 Gauss-Jordan start Xf (ok = its pivots were good):
-// Newton-Schulz steps in FP64, or the FP64 Cholesky inverse when the start is unusable.
-__device__ void loop_refine(bool ok, const double* G, const float* Xf, double* X, double* E, double* U, double* T2,
-                            double* dinv, float* redf, int R, int ns_steps, int* s_bad) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  bool fast = ok;
-  const int RR = R * R;
-  if (fast) {
-    for (int e = tid; e < RR; e += kLT) X[e] = (double)Xf[e];
-    __syncthreads();
-  }
-  for (int it = 0; fast && it < ns_steps; ++it) {
-    float em = 0.f;
-    for (int e = tid; e < RR; e += kLT) {      // E = I - G X
-      const int r = e / R, c = e - r * R;
-      double a0 = 0.0, a1 = 0.0;
-      int l = 0;
-      for (; l + 1 < R; l += 2) {
-        a0 = fma(G[r * R + l], X[l * R + c], a0);
-        a1 = fma(G[r * R + l + 1], X[(l + 1) * R + c], a1);
-      }
-      if (l < R) a0 = fma(G[r * R + l], X[l * R + c], a0);
-      const double ev = (r == c ? 1.0 : 0.0) - (a0 + a1);
-      E[e] = ev;
-      em = fmaxf(em, fabsf((float)ev));
-    }
-    if (it == 0) {                             // convergence check in FP32: max |E| < 1/4
-      for (int o = 16; o > 0; o >>= 1) em = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, o));
-      if (lane == 0) redf[warp] = em;
-    }
-    __syncthreads();
-    if (it == 0) {
-      float m = 0.f;
-      for (int q = 0; q < (min(RR, kLT) + 31) / 32; ++q) m = fmaxf(m, redf[q]);
-      if (!(m < 0.25f)) {
-        fast = false;
-        break;
-      }
-    }
-    for (int e = tid; e < RR; e += kLT) {      // X + X E
-      const int r = e / R, c = e - r * R;
-      double a0 = 0.0, a1 = 0.0;
-      int l = 0;
-      for (; l + 1 < R; l += 2) {
-        a0 = fma(X[r * R + l], E[l * R + c], a0);
-        a1 = fma(X[r * R + l + 1], E[(l + 1) * R + c], a1);
-      }
-      if (l < R) a0 = fma(X[r * R + l], E[l * R + c], a0);
-      U[e] = X[e] + (a0 + a1);
-    }
-    __syncthreads();
-    for (int e = tid; e < RR; e += kLT) X[e] = U[e];
-    __syncthreads();
-  }
-  if (!fast) spd_inverse_fp64(G, X, U, T2, dinv, R, s_bad);
-}
-
 template <typename T, typename ACC, int MAXR>
 __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::cluster_group& cl, int n, int cb,
-                                 int nn, uint32_t nt, int* s_bad, float* redf) {
+                                 int nn, uint32_t nt, int* s_bad, unsigned* s_em, uint64_t* fbar, uint32_t& fpar,
+                                 uint32_t& fblk, int* s_tout) {
   const Prob& p = K.p;
   const LoopSmem& L = K.L;
-  const int rank = (int)cl.block_rank(), tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rank = (int)cl.block_rank(), tid = threadIdx.x;
   const int R = p.R, N = p.N, S = p.S;
   const int I = (int)p.dims[n];
-  const int spc = L.spc;
+  const int spc = L.spc, rp = L.rp, ne = L.NE;
   const int cnt = max(0, min(S, rank * spc + spc) - rank * spc);
-  const int zld = L.zld;
   double* sc = reinterpret_cast<double*>(sm + L.sc);
   double* lam = reinterpret_cast<double*>(sm + L.lam);
   double* scomb = reinterpret_cast<double*>(sm + L.scomb);
@@ -368,7 +337,6 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
   double* Grecv = reinterpret_cast<double*>(sm + L.Grecv);
   double* colrecv = reinterpret_cast<double*>(sm + L.colrecv);
   double* G = reinterpret_cast<double*>(sm + L.G);
-  double* X = reinterpret_cast<double*>(sm + L.X);
   float* Gf = reinterpret_cast<float*>(sm + L.Gf);
   double* mrow = reinterpret_cast<double*>(sm + L.mrow);
   double* arow = reinterpret_cast<double*>(sm + L.arow);
@@ -376,15 +344,15 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
 
   // ---- 1. SKR rows of this CTA's samples (Alg. 2), from the local factor copies: the product of
   // the sampled rows (exact in FP64 for up to two FP32 factors) times the combined lazy scale
-  for (int e = tid; e < cnt * zld; e += kLT) {
-    const int jj = e / zld, r = e - jj * zld;
+  for (int e = tid; e < cnt * rp; e += kLT) {
+    const int jj = e / rp, r = e - jj * rp;
     if (r < R) {
       double z = 1.0;
 #pragma unroll
       for (int m = 0; m < kMaxOrder; ++m)
         if (m < N && m != n) {
           const ACC* Fm = reinterpret_cast<const ACC*>(sm + L.F[m]);
-          z *= (double)Fm[(int)ids[jj * kMaxOrder + m] * R + r];
+          z *= (double)Fm[(int)ids[jj * kMaxOrder + m] * rp + r];
         }
       z *= scomb[r];
       Zd[jj * R + r] = z;
@@ -393,19 +361,21 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
       Zf[e] = ACC(0);
     }
   }
-  cp_async_wait<0>();   // this update's fibers (issued during the previous update)
+  wait_fibers(fbar, cb, fpar, fblk, s_tout);   // this update's fibers (issued during the previous update)
   __syncthreads();
 
   // ---- 2. partial M = X_S,c Z_S,c, every row, stored into the owner CTA's receive buffer
   const int rpc = (I + kLC - 1) / kLC;
+  constexpr int VZ = 16 / (int)sizeof(ACC);      // Z entries per 16-byte vector
   for (int i = tid; i < I; i += kLT) {
     ACC acc[MAXR];
 #pragma unroll
     for (int r = 0; r < MAXR; ++r) acc[r] = ACC(0);
-    constexpr int VZ = 16 / (int)sizeof(ACC);      // Z entries per 16-byte vector
+    const T* fi = fib + i;
+#pragma unroll 2
     for (int j = 0; j < cnt; ++j) {
-      const ACC x = to_acc<ACC, T>(fib[j * L.ldf + i]);
-      const ACC* z = Zf + j * zld;
+      const ACC x = to_acc<ACC, T>(fi[j * L.ldf]);
+      const ACC* z = Zf + j * rp;
 #pragma unroll
       for (int v = 0; v < MAXR; v += VZ) {
         if (v < R) {
@@ -432,19 +402,13 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
   }
   // ---- 3. partial Gram of this CTA's Z rows (upper triangle, gs lanes per entry), to every CTA
   {
-    const int gs = K.gs, ne = L.NE;
+    const int gs = K.gs;
     for (int t0 = 0; t0 < ne * gs; t0 += kLT) {
       const int t = t0 + tid;
       const int e = t / gs, s = t - e * gs;
       double a = 0.0;
       if (e < ne) {
-        // packed upper-triangle index e -> (r, c), c >= r
-        int r = 0, rem = e;
-        while (rem >= R - r) {
-          rem -= R - r;
-          ++r;
-        }
-        const int c = r + rem;
+        const int r = K.ne_r[e], c = K.ne_c[e];
         for (int jj = s; jj < cnt; jj += gs) a = fma(Zd[jj * R + r], Zd[jj * R + c], a);
       }
       for (int o = 1; o < gs; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -453,11 +417,21 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
     }
   }
   cluster_arrive();
+  // independent work while the barrier completes: the next mode update's samples and fiber copies
+  draw_samples(p, nn, nt, rank * spc, cnt, reinterpret_cast<uint32_t*>(sm + L.ids[cb ^ 1]),
+               reinterpret_cast<int64_t*>(sm + L.offs[cb ^ 1]));
+  if (tid == 0) *s_em = 0u;
+  __syncthreads();
+  if (fetch_fibers<T>(K, nn, reinterpret_cast<const int64_t*>(sm + L.offs[cb ^ 1]), cnt,
+                     reinterpret_cast<T*>(sm + L.fib[cb ^ 1]), fbar + (cb ^ 1)))
+    fblk |= 1u << (cb ^ 1);
+  else
+    fblk &= ~(1u << (cb ^ 1));
   cluster_wait();   // every partial M row and Gram of the cluster has landed
 
-  // ---- 4. G = sum of the C partial Grams (fixed order, gg lanes per entry), inverse
+  // ---- 4. G = sum of the C partial Grams (fixed order, gg lanes per entry); FP32 copy; max diag
   {
-    const int gg = K.gg, ne = L.NE;
+    const int gg = K.gg;
     for (int t0 = 0; t0 < ne * gg; t0 += kLT) {
       const int t = t0 + tid;
       const int e = t / gg, g = t - e * gg;
@@ -466,41 +440,93 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
         for (int q = g; q < kLC; q += gg) a += Grecv[q * ne + e];
       for (int o = 1; o < gg; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
       if (e < ne && g == 0) {
-        int r = 0, rem = e;
-        while (rem >= R - r) {
-          rem -= R - r;
-          ++r;
-        }
-        const int c = r + rem;
+        const int r = K.ne_r[e], c = K.ne_c[e];
         G[r * R + c] = a;
         G[c * R + r] = a;
         const float af = (float)a;
         Gf[r * R + c] = af;
         Gf[c * R + r] = af;
+        if (r == c && af > 0.f) atomicMax(s_em, __float_as_uint(af));   // positive floats order as ints
       }
     }
   }
   __syncthreads();
-  // FP32 Gauss-Jordan start on warp 0; meanwhile the other warps draw the next mode update's samples
-  // and issue its fiber copies (they depend on nothing computed here)
-  __shared__ int s_ok;
-  float* Xf = reinterpret_cast<float*>(sm + L.Xf);
-  if (warp == 0) {
-    const bool ok = gauss_jordan_f32<MAXR>(Gf, Xf, reinterpret_cast<float*>(sm + L.prow), R);
-    if (lane == 0) s_ok = ok ? 1 : 0;
-  } else {
-    const int nb = cb ^ 1;
-    const int j0 = rank * spc;
-    draw_samples(p, nn, nt, j0, cnt, reinterpret_cast<uint32_t*>(sm + L.ids[nb]),
-                 reinterpret_cast<int64_t*>(sm + L.offs[nb]), tid - 32, kLT - 32);
-    asm volatile("bar.sync 1, %0;" ::"n"(kLT - 32) : "memory");   // warps 1.. only
-    fetch_fibers<T>(K, nn, reinterpret_cast<const int64_t*>(sm + L.offs[nb]), cnt, reinterpret_cast<T*>(sm + L.fib[nb]),
-                    tid - 32, kLT - 32);
+  const float md = __uint_as_float(*s_em);
+  float* gj = reinterpret_cast<float*>(sm + L.gj);
+  const bool ok = gauss_jordan_block<MAXR>(Gf, gj, R, md);
+  const int W = 2 * R;
+  const float* X0 = gj + (R & 1) * (R * W) + R;   // X0(i, c) = X0[i * W + c]
+  double* X = reinterpret_cast<double*>(sm + L.X);
+  {
+    // ---- Newton-Schulz refinement in FP64 (or the FP64 Cholesky inverse)
+    double* U = reinterpret_cast<double*>(sm + L.U);
+    double* E = reinterpret_cast<double*>(sm + L.E);
+    const int RR = R * R;
+    bool fast = ok;
+    const int steps = sizeof(ACC) == 8 ? 2 : 1;
+    if (tid == 0) *s_em = 0u;
+    __syncthreads();
+    for (int it = 0; fast && it < steps; ++it) {
+      // E = I - G X  (X: the FP32 start in the first step)
+      for (int e = tid; e < RR; e += kLT) {
+        const int r = e / R, c = e - r * R;
+        const double* g = G + r * R;
+        double a0 = 0.0, a1 = 0.0;
+        int l = 0;
+        if (it == 0) {
+          for (; l + 1 < R; l += 2) {
+            a0 = fma(g[l], (double)X0[l * W + c], a0);
+            a1 = fma(g[l + 1], (double)X0[(l + 1) * W + c], a1);
+          }
+          if (l < R) a0 = fma(g[l], (double)X0[l * W + c], a0);
+        } else {
+          for (; l + 1 < R; l += 2) {
+            a0 = fma(g[l], X[l * R + c], a0);
+            a1 = fma(g[l + 1], X[(l + 1) * R + c], a1);
+          }
+          if (l < R) a0 = fma(g[l], X[l * R + c], a0);
+        }
+        const double ev = (r == c ? 1.0 : 0.0) - (a0 + a1);
+        E[e] = ev;
+        if (it == 0) atomicMax(s_em, __float_as_uint(fabsf((float)ev)));
+      }
+      __syncthreads();
+      if (it == 0 && !(__uint_as_float(*s_em) < 0.25f)) {
+        fast = false;
+        break;
+      }
+      // X_new = X + X E
+      for (int e = tid; e < RR; e += kLT) {
+        const int r = e / R, c = e - r * R;
+        double a0 = 0.0, a1 = 0.0, x;
+        int l = 0;
+        if (it == 0) {
+          const float* xr = X0 + r * W;
+          for (; l + 1 < R; l += 2) {
+            a0 = fma((double)xr[l], E[l * R + c], a0);
+            a1 = fma((double)xr[l + 1], E[(l + 1) * R + c], a1);
+          }
+          if (l < R) a0 = fma((double)xr[l], E[l * R + c], a0);
+          x = (double)xr[c];
+        } else {
+          const double* xr = X + r * R;
+          for (; l + 1 < R; l += 2) {
+            a0 = fma(xr[l], E[l * R + c], a0);
+            a1 = fma(xr[l + 1], E[(l + 1) * R + c], a1);
+          }
+          if (l < R) a0 = fma(xr[l], E[l * R + c], a0);
+          x = xr[c];
+        }
+        U[e] = x + (a0 + a1);
+      }
+      __syncthreads();
+      for (int e = tid; e < RR; e += kLT) X[e] = U[e];
+      __syncthreads();
+    }
+    if (!fast)
+      spd_inverse_fp64(G, X, U, reinterpret_cast<double*>(sm + L.T2), reinterpret_cast<double*>(sm + L.dinv), R,
+                       s_bad);
   }
-  __syncthreads();
-  loop_refine(s_ok != 0, G, Xf, X, reinterpret_cast<double*>(sm + L.E), reinterpret_cast<double*>(sm + L.U),
-              reinterpret_cast<double*>(sm + L.T2), reinterpret_cast<double*>(sm + L.dinv), redf, R,
-              sizeof(ACC) == 8 ? 2 : 1, s_bad);
 
   // ---- 5. this CTA's rows: M rows (fixed-order sum over the C partials), A = M G^-1 (FP64)
   const int i0 = rank * rpc;
@@ -529,7 +555,7 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
     arow[e] = a;
     A64n[e] = a;                                    // FP64 result (read after the run)
     const ACC af = (ACC)a;
-    const int off = i0 * R + e;
+    const int off = (i0 + li) * rp + r;
 #pragma unroll 4
     for (int q = 0; q < kLC; ++q) cl.map_shared_rank(Fn, q)[off] = af;   // every CTA's copy
   }
@@ -588,9 +614,11 @@ __global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, i
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ LoopConst K;
   __shared__ int s_prob, s_bad, s_done, s_status, s_iter, s_stall;
+  __shared__ unsigned s_em;
+  __shared__ int s_tout;
   __shared__ double s_best, s_last;
-  __shared__ float redf[kLT / 32];
   __shared__ double fitpart[4];
+  __shared__ __align__(8) uint64_t fbar[2];   // completion of the TMA bulk fiber copies, per buffer
   while (true) {
     if (rank == 0 && tid == 0) s_prob = atomicAdd(queue, 1);
     cl.sync();
@@ -615,14 +643,20 @@ __global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, i
           const uintptr_t base = reinterpret_cast<uintptr_t>(p.Xrep[m]);
           const int fb = (int)p.dims[m] * (int)sizeof(T);
           if (contig) {
-            for (int w : {16, 8, 4})
-              if (v == 0 && w >= (int)sizeof(T) && fb % w == 0 && base % w == 0) v = w;
+            if (fb % 16 == 0 && base % 16 == 0) v = 16;
+            else if (fb % 8 == 0 && base % 8 == 0) v = 8;
+            else if (fb % 4 == 0 && base % 4 == 0 && sizeof(T) <= 4) v = 4;
           } else if (sizeof(T) >= 4) {
             v = (int)sizeof(T);
           }
         }
         K.vec[m] = v;
+        K.bulk[m] = (m < p.N && (p.use_rep || m == 0) && v == 16) ? 1 : 0;
       }
+      mbar_init(&fbar[0]);
+      mbar_init(&fbar[1]);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      s_tout = 0;
       // Gram partial: gs lanes per entry; C-way sum: gg lanes per entry (fewest FP64 warp
       // instructions per SM sub-partition)
       const int ne = K.L.NE, spc = K.L.spc;
@@ -644,11 +678,17 @@ __global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, i
           K.gg = gg;
         }
       }
+      int e = 0;
+      for (int r = 0; r < p.R; ++r)
+        for (int c = r; c < p.R; ++c, ++e) {
+          K.ne_r[e] = (unsigned char)r;
+          K.ne_c[e] = (unsigned char)c;
+        }
     }
     __syncthreads();
     const Prob& p = K.p;
     const LoopSmem& L = K.L;
-    const int R = p.R, N = p.N;
+    const int R = p.R, N = p.N, rp = L.rp;
     double* sc = reinterpret_cast<double*>(sm + L.sc);
     double* lam = reinterpret_cast<double*>(sm + L.lam);
     ACC* wr = reinterpret_cast<ACC*>(sm + L.wr);
@@ -657,13 +697,18 @@ __global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, i
     uint32_t* fidx = reinterpret_cast<uint32_t*>(sm + L.fidx);
     ACC* fx = reinterpret_cast<ACC*>(sm + L.fx);
     State* st = p.state;
-    // every factor in full, the lazy scales, lambda, this CTA's fit entries
+    // every factor in full (rows padded with zeros), the lazy scales, lambda, this CTA's fit entries
     for (int m = 0; m < N; ++m) {
       ACC* F = reinterpret_cast<ACC*>(sm + L.F[m]);
-      const int cntm = (int)p.dims[m] * R;
+      const int cntm = (int)p.dims[m] * rp;
       for (int e = tid; e < cntm; e += kLT) {
-        if constexpr (sizeof(ACC) == 8) F[e] = p.A64[m][e];
-        else F[e] = p.A32[m][e];
+        const int i = e / rp, r = e - i * rp;
+        ACC v = ACC(0);
+        if (r < R) {
+          if constexpr (sizeof(ACC) == 8) v = p.A64[m][(int64_t)i * R + r];
+          else v = p.A32[m][(int64_t)i * R + r];
+        }
+        F[e] = v;
       }
     }
     for (int e = tid; e < N * R; e += kLT) sc[e] = p.scale[e / R][e % R];
@@ -672,6 +717,7 @@ __global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, i
     const int fcnt = max(0, min(p.P_hat, f0 + L.fpc) - f0);
     for (int e = tid; e < fcnt * N; e += kLT) fidx[e] = p.fit_idx[(int64_t)f0 * N + e];
     for (int e = tid; e < fcnt; e += kLT) fx[e] = (ACC)p.fit_x[f0 + e];
+    for (int r = tid; r < rp; r += kLT) wr[r] = ACC(0);
     if (tid == 0) {
       s_done = st->done;
       s_status = st->status;
@@ -688,10 +734,12 @@ __global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, i
     const int j0 = rank * spc;
     const int cnt = max(0, min(p.S, j0 + spc) - j0);
     draw_samples(p, 0, p.t0 + (uint32_t)st->iter, j0, cnt, reinterpret_cast<uint32_t*>(sm + L.ids[0]),
-                 reinterpret_cast<int64_t*>(sm + L.offs[0]), tid, kLT);
+                 reinterpret_cast<int64_t*>(sm + L.offs[0]));
     __syncthreads();
-    fetch_fibers<T>(K, 0, reinterpret_cast<const int64_t*>(sm + L.offs[0]), cnt, reinterpret_cast<T*>(sm + L.fib[0]),
-                    tid, kLT);
+    uint32_t fpar = 0u, fblk = 0u;   // per fiber buffer: mbarrier phase parity; last fetch was TMA bulk
+    if (fetch_fibers<T>(K, 0, reinterpret_cast<const int64_t*>(sm + L.offs[0]), cnt,
+                        reinterpret_cast<T*>(sm + L.fib[0]), &fbar[0]))
+      fblk = 1u;
     {
       double* scomb = reinterpret_cast<double*>(sm + L.scomb);
       for (int r = tid; r < R; r += kLT) {   // combined scale of the modes other than the first
@@ -710,7 +758,7 @@ __global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, i
         // the next mode update (its samples and fiber copies are issued during this one)
         const int nn = n + 1 < N ? n + 1 : 0;
         const uint32_t nt = n + 1 < N ? t : t + 1;
-        loop_mode_update<T, ACC, MAXR>(K, sm, cl, n, cb, nn, nt, &s_bad, redf);
+        loop_mode_update<T, ACC, MAXR>(K, sm, cl, n, cb, nn, nt, &s_bad, &s_em, fbar, fpar, fblk, &s_tout);
         ++u;
         if (s_bad) break;   // identical in every CTA (same G, same factorization)
       }
@@ -729,29 +777,49 @@ __global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, i
         wr[r] = (ACC)w;
       }
       __syncthreads();
-      double e2 = 0.0;
+      constexpr int VZ = 16 / (int)sizeof(ACC);
+      ACC e2a = ACC(0);           // this thread's entries (at most a few), in the accumulation type
       for (int jj = tid; jj < fcnt; jj += kLT) {
         const uint32_t* id = fidx + jj * N;
         const ACC* rows[kMaxOrder];
 #pragma unroll
         for (int m = 0; m < kMaxOrder; ++m)
-          rows[m] = (m < N) ? reinterpret_cast<const ACC*>(sm + L.F[m]) + (int)id[m] * R : nullptr;
+          rows[m] = (m < N) ? reinterpret_cast<const ACC*>(sm + L.F[m]) + (int)id[m] * rp : nullptr;
         ACC acc = ACC(0);
-        for (int r = 0; r < R; ++r) {
-          ACC w = wr[r];
 #pragma unroll
-          for (int m = 0; m < kMaxOrder; ++m)
-            if (m < N) w *= rows[m][r];
-          acc += w;
+        for (int v = 0; v < MAXR; v += VZ) {
+          if (v < R) {
+            if constexpr (VZ == 4) {
+              float4 w = *reinterpret_cast<const float4*>(wr + v);
+#pragma unroll
+              for (int m = 0; m < kMaxOrder; ++m)
+                if (m < N) {
+                  const float4 q = *reinterpret_cast<const float4*>(rows[m] + v);
+                  w.x *= q.x;
+                  w.y *= q.y;
+                  w.z *= q.z;
+                  w.w *= q.w;
+                }
+              acc += (w.x + w.y) + (w.z + w.w);
+            } else {
+              double2 w = *reinterpret_cast<const double2*>(wr + v);
+#pragma unroll
+              for (int m = 0; m < kMaxOrder; ++m)
+                if (m < N) {
+                  const double2 q = *reinterpret_cast<const double2*>(rows[m] + v);
+                  w.x *= q.x;
+                  w.y *= q.y;
+                }
+              acc += w.x + w.y;
+            }
+          }
         }
-        double e;
-        if constexpr (sizeof(ACC) == 8) e = (double)fx[jj] - acc;
-        else e = (double)(fx[jj] - acc);
-        e2 = fma(e, e, e2);
+        const ACC e = fx[jj] - acc;
+        e2a = fma(e, e, e2a);
       }
-      red[tid] = e2;
+      red[tid] = (double)e2a;
       __syncthreads();
-      if (warp < 4) {   // four warps (one per SM sub-partition) sum 128 values each
+      if (warp < 4) {   // four warps (one per SM sub-partition) sum 128 values each in FP64
         double a = red[warp * 128 + lane] + red[warp * 128 + 32 + lane];
         a += red[warp * 128 + 64 + lane] + red[warp * 128 + 96 + lane];
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -798,7 +866,7 @@ __global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, i
       }
       __syncthreads();
     }
-    cp_async_wait<0>();   // the copies issued for an update that will not run
+    wait_fibers(fbar, u & 1, fpar, fblk, &s_tout);   // the copies issued for an update that will not run
     // publish the loop state, lambda and the lazy scales (CTA 0)
     if (rank == 0) {
       for (int e = tid; e < N * R; e += kLT) p.scale[e / R][e % R] = sc[e];
@@ -814,6 +882,7 @@ __global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, i
     }
     __syncthreads();
     cl.sync();  // no CTA reuses its shared memory while another may still store into it
+    if (tid == 0 && s_tout) st->status = CPR_ETIMEOUT;   // after CTA 0 published the state
   }
 }
 

@@ -169,27 +169,41 @@ cudaError_t launch_mix_mode(const void* X, void* Y, int dtype, int N, const int6
 
 // Mode-n unfolding X_(n) stored column-major: with X viewed as [L][I_n][Rr] (L = prod_{m<n} I_m
 // fastest), Y[i + I_n (l + L r)] = X[l + L (i + I_n r)].  Column j = l + L r of X_(n) is the mode-n
-// fiber with unfolding index j (the index map of Sec. 2.1), contiguous in Y.  32 x 32 tiles through
-// shared memory: coalesced reads along l, coalesced writes along i.
+// fiber with unfolding index j (the index map of Sec. 2.1), contiguous in Y.  64 x 64 tiles through
+// shared memory, 256 threads: every thread issues its 16 loads (coalesced along l) before its first
+// store (coalesced along i), so a block keeps 16 KB of reads in flight.
 template <typename T>
 __global__ void __launch_bounds__(256) k_unfold_copy(const T* __restrict__ X, T* __restrict__ Y, int64_t L, int64_t I,
                                                      int64_t Rr) {
-  __shared__ T tile[32][33];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
-  const int64_t l0 = (int64_t)blockIdx.x * 32, i0 = (int64_t)blockIdx.y * 32;
+  __shared__ T tile[64][65];
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;   // 32 lanes x 8 warps
+  const int64_t l0 = (int64_t)blockIdx.x * 64, i0 = (int64_t)blockIdx.y * 64;
   for (int64_t r = blockIdx.z; r < Rr; r += gridDim.z) {
     const T* Xr = X + r * L * I;
     T* Yr = Y + r * L * I;
+    T v[16];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int64_t i = i0 + ty + 8 * k, l = l0 + tx;
-      if (l < L && i < I) tile[ty + 8 * k][tx] = Xr[l + L * i];
+    for (int k = 0; k < 8; ++k) {
+      const int64_t i = i0 + wy + 8 * k;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t l = l0 + lane + 32 * h;
+        v[2 * k + h] = (l < L && i < I) ? Xr[l + L * i] : T(0);
+      }
     }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) tile[wy + 8 * k][lane + 32 * h] = v[2 * k + h];
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int64_t l = l0 + ty + 8 * k, i = i0 + tx;
-      if (l < L && i < I) Yr[i + I * l] = tile[tx][ty + 8 * k];
+    for (int k = 0; k < 8; ++k) {
+      const int64_t l = l0 + wy + 8 * k;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t i = i0 + lane + 32 * h;
+        if (l < L && i < I) Yr[i + I * l] = tile[lane + 32 * h][wy + 8 * k];
+      }
     }
     __syncthreads();
   }
@@ -200,7 +214,7 @@ cudaError_t launch_unfold_copy(const void* X, void* Y, int dtype, int N, const i
   for (int m = 0; m < n; ++m) L *= dims[m];
   for (int m = n + 1; m < N; ++m) Rr *= dims[m];
   const int64_t I = dims[n];
-  const dim3 grid((unsigned)((L + 31) / 32), (unsigned)((I + 31) / 32), (unsigned)(Rr < 65535 ? Rr : 65535));
+  const dim3 grid((unsigned)((L + 63) / 64), (unsigned)((I + 63) / 64), (unsigned)(Rr < 65535 ? Rr : 65535));
   switch (dtype) {
     case CPR_F64: k_unfold_copy<double><<<grid, 256, 0, s>>>((const double*)X, (double*)Y, L, I, Rr); break;
     case CPR_F32: k_unfold_copy<float><<<grid, 256, 0, s>>>((const float*)X, (float*)Y, L, I, Rr); break;
@@ -210,53 +224,35 @@ cudaError_t launch_unfold_copy(const void* X, void* Y, int dtype, int N, const i
   return cudaGetLastError();
 }
 
-// A = D F^T A^ in FP64: a block computes 32 rows i of A (all R columns); F and A^ are staged through
-// shared memory in 32-row chunks of k so every global load is coalesced and many are in flight.
-constexpr int kUnmixRows = 32;
+// A = D F^T A^ in FP64 (Alg. 5, unmixing).  FP64 arithmetic is the bound here, so the work is
+// spread over the whole GPU: a block computes 4 rows of A (4R outputs), each output's dot product
+// of length I is split over ks lanes (k = s, s + ks, ...) whose partials are summed by a fixed
+// butterfly of shuffles; F and A^ are read through the read-only cache (both are L2-resident).
+constexpr int kUnmixRows = 4;
 __global__ void __launch_bounds__(256) k_unmix(const double* __restrict__ Ahat, double* __restrict__ A,
                                                const double* __restrict__ F64, const double* __restrict__ signs,
                                                int I, int R) {
-  __shared__ double Ft[kUnmixRows][kUnmixRows + 1];   // Ft[kk][ii] = F[k0+kk][i0+ii]
-  __shared__ double Ah[kUnmixRows][kMaxRank];          // Ah[kk][r] = A^[k0+kk][r]
   const int i0 = blockIdx.x * kUnmixRows;
-  const int tid = threadIdx.x;
-  // thread owns output entries (ii, r) for e = tid, tid + 256, ...
-  double acc[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) acc[u] = 0.0;
-  for (int k0 = 0; k0 < I; k0 += kUnmixRows) {
-    for (int e = tid; e < kUnmixRows * kUnmixRows; e += blockDim.x) {
-      const int kk = e / kUnmixRows, ii = e % kUnmixRows;
-      const int k = k0 + kk, i = i0 + ii;
-      Ft[kk][ii] = (k < I && i < I) ? F64[(int64_t)k * I + i] : 0.0;
+  const int nout = kUnmixRows * R;
+  int ks = 1;   // lanes per output: a power of two (a divisor of the warp width)
+  while (ks < 32 && ks * 2 * nout <= (int)blockDim.x) ks *= 2;
+  const int t = threadIdx.x, o = t / ks, s = t - o * ks;
+  const int ii = o / R, r = o - ii * R, i = i0 + ii;
+  const bool valid = o < nout && i < I;
+  double a0 = 0.0, a1 = 0.0;
+  if (valid) {
+    const double* f = F64 + i;     // F[k][i] at k * I + i
+    const double* ah = Ahat + r;   // A^[k][r] at k * R + r
+    int k = s;
+    for (; k + ks < I; k += 2 * ks) {
+      a0 = fma(__ldg(f + (int64_t)k * I), __ldg(ah + (int64_t)k * R), a0);
+      a1 = fma(__ldg(f + (int64_t)(k + ks) * I), __ldg(ah + (int64_t)(k + ks) * R), a1);
     }
-    for (int e = tid; e < kUnmixRows * R; e += blockDim.x) {
-      const int kk = e / R, r = e % R;
-      const int k = k0 + kk;
-      Ah[kk][r] = (k < I) ? Ahat[(int64_t)k * R + r] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = tid + u * 256;
-      if (e < kUnmixRows * R) {
-        const int ii = e / R, r = e % R;
-        double a = acc[u];
-        for (int kk = 0; kk < kUnmixRows; ++kk) a = fma(Ft[kk][ii], Ah[kk][r], a);
-        acc[u] = a;
-      }
-    }
-    __syncthreads();
+    if (k < I) a0 = fma(__ldg(f + (int64_t)k * I), __ldg(ah + (int64_t)k * R), a0);
   }
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const int e = tid + u * 256;
-    if (e < kUnmixRows * R) {
-      const int ii = e / R, r = e % R;
-      const int i = i0 + ii;
-      if (i < I) A[(int64_t)i * R + r] = signs[i] * acc[u];
-    }
-  }
+  double acc = a0 + a1;
+  for (int w = 1; w < ks; w <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
+  if (valid && s == 0) A[(int64_t)i * R + r] = signs[i] * acc;
 }
 
 cudaError_t launch_unmix(const double* Ahat, double* A, const double* F64, const double* signs, int I, int R,

@@ -4,7 +4,8 @@
 // contiguous entries) and the mixing operator W = F_n D_n (I_n x I_n, row-major):
 //     C[j][c] = sum_k U[j][k] W[c][k]              (the fibers of X x_n W, Alg. 5 mixing step)
 // and writes C in the standard column-major layout of the tensor and, optionally, as the mode-n
-// unfolding of the result (C[j][c] at c + I_n j).  Both operands are K-major; tiles arrive by TMA
+// unfolding of the result (C[j][c] at c + I_n j) and, in the first pass, as the mode-2 unfolding
+// the second pass reads (then the standard layout is not needed).  Both operands are K-major; tiles arrive by TMA
 // with the 128-byte swizzle, one thread issues tcgen05.mma (kind::tf32, M = 128, N = NT <= 256)
 // into a TMEM accumulator, four warps read it back with tcgen05.ld for the stores.
 //
@@ -48,6 +49,7 @@ struct TcArgs {
   int64_t st[kMaxOrder];
   float* ystd;        // may be null
   float* yunf;        // may be null
+  float* ynext;       // first pass only (n = 0), may be null: the result as the mode-2 unfolding
   int* err;
 };
 
@@ -259,6 +261,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int q = 0; q < 16; ++q)
           if (cb + q < a.I) a.ystd[base + (int64_t)(cb + q) * stn] = __uint_as_float(v[q]);
       }
+      if (a.ynext) {
+        // first pass: row j = (i_2, i_3, ...) with i_2 fastest, column cb + q = i_1; in the
+        // column-major mode-2 unfolding that entry sits at i_2 + I_2 (i_1 + I_1 rest), so the lanes
+        // of a warp (consecutive i_2) store consecutive addresses for every column
+        const int64_t I2 = a.dims[1];
+        const int64_t i2 = j % I2, rest = j / I2;
+        float* dst = a.ynext + i2 + I2 * ((int64_t)a.I * rest + cb);
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (cb + q < a.I) dst[I2 * q] = __uint_as_float(v[q]);
+      }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
@@ -318,8 +331,9 @@ cudaError_t launch_split_tf32(const float* w, float* hi, float* lo, int64_t n, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_mix_tc(const float* U, float* ystd, float* yunf, const float* Whi, const float* Wlo, int N,
-                          const int64_t* dims, int n, int three_x, int* err, cudaStream_t s) {
+cudaError_t launch_mix_tc(const float* U, float* ystd, float* yunf, float* ynext, const float* Whi, const float* Wlo,
+                          int N, const int64_t* dims, int n, int three_x, int* err, cudaStream_t s) {
+  if (ynext && n != 0) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_mix_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
@@ -345,6 +359,7 @@ cudaError_t launch_mix_tc(const float* U, float* ystd, float* yunf, const float*
   a.N = N;
   a.ystd = ystd;
   a.yunf = yunf;
+  a.ynext = ynext;
   a.err = err;
   CUtensorMap mU, mH, mL;
   if (!make_map(&mU, U, I, a.J, kBM) || !make_map(&mH, Whi, I, I, a.NT) || !make_map(&mL, Wlo, I, I, a.NT))
