@@ -457,7 +457,7 @@ def run_ours(args, rank, world, local_rank):
                     "hbm_frac": alg["bytes"] / per_launch_s / 1e9 / pk["hbm_gbs"]}
         else:
             ach = alg["bytes"] / per_launch_s / 1e9
-            roof = {"bound": "hbm", "kernel": "k_cluster_run (whole iteration loop, one 16-CTA cluster)",
+            roof = {"bound": "hbm", "kernel": "k_loop_rep (whole iteration loop in one 16-CTA cluster, factors replicated per CTA)",
                     "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
                     "peak_source": pk_src, "traffic": kernel_traffic("loop"), "per_launch_ms": dom_ms / dom_n,
                     "algorithmic_bytes": alg["bytes"], "algorithmic_flops": alg["flops"],

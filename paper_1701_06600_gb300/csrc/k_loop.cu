@@ -189,6 +189,8 @@ struct LoopConst {
   LoopSmem L;
   int vec[kMaxOrder];      // bytes per cp.async of a mode's fiber copies (16, 8, 4), 0: plain loads
   int bulk[kMaxOrder];     // 1: a mode's fibers are contiguous and 16-byte aligned: one TMA bulk copy each
+  int draw_late;           // 1: every mode copies by TMA and R^2 <= 384: the next update's samples are
+                           // drawn (and copies issued) by the warps idle during the FP64 refinement
   int gs, gg;              // Gram: samples split over gs lanes; sum of the C partials over gg lanes
   unsigned char ne_r[32 * 33 / 2];   // packed upper-triangle entry e -> (row, column)
   unsigned char ne_c[32 * 33 / 2];
@@ -265,6 +267,40 @@ __device__ __forceinline__ bool fetch_fibers(const LoopConst& K, int n, const in
   }
   cp_async_commit();
   return false;
+}
+
+// The next mode update's samples drawn by the threads [base, kLT) while the others refine the
+// inverse, each drawing thread issuing the TMA bulk copy of its own fiber (every mode's fibers are
+// contiguous and aligned when this is used); thread `base` arms the buffer's mbarrier.  An mbarrier
+// transaction count may go transiently negative, so the arming need not precede the copies.
+template <typename T>
+__device__ __forceinline__ void draw_and_copy(const LoopConst& K, int n, uint32_t t, int j0, int cnt, uint32_t* ids,
+                                              int64_t* offs, T* buf, uint64_t* bar, int base) {
+  const Prob& p = K.p;
+  const uint32_t fb = (uint32_t)p.dims[n] * (uint32_t)sizeof(T);
+  const T* X = reinterpret_cast<const T*>(p.Xrep[n]);
+  if ((int)threadIdx.x == base) mbar_expect_tx(bar, fb * (uint32_t)cnt);
+  for (int jj = (int)threadIdx.x - base; jj < cnt; jj += kLT - base) {
+    const uint32_t j = (uint32_t)(j0 + jj);
+    const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
+    const uint4 w0 = philox10(make_uint4(j, counter_word1(kStreamSamples, 0, n), t, p.b), k0, k1);
+    uint4 w1 = make_uint4(0u, 0u, 0u, 0u);
+    if (p.N - 1 > 4) w1 = philox10(make_uint4(j, counter_word1(kStreamSamples, 1, n), t, p.b), k0, k1);
+    int k = 0;
+    for (int m = 0; m < p.N; ++m) {
+      uint32_t im = 0;
+      if (m != n) {
+        const uint32_t w = k < 4 ? word_of(w0, k) : word_of(w1, k - 4);
+        im = scale_index(w, (uint32_t)p.dims[m]);
+        ++k;
+      }
+      ids[jj * kMaxOrder + m] = im;
+    }
+    int64_t stride;
+    const int64_t off = fiber_offset(p, n, ids + jj * kMaxOrder, &stride);
+    offs[jj] = off;
+    bulk_copy(buf + jj * K.L.ldf, X + off, fb, bar);
+  }
 }
 
 // Wait for the fibers of the buffer about to be read: its mbarrier phase when they came by TMA
@@ -418,15 +454,18 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
   }
   cluster_arrive();
   // independent work while the barrier completes: the next mode update's samples and fiber copies
-  draw_samples(p, nn, nt, rank * spc, cnt, reinterpret_cast<uint32_t*>(sm + L.ids[cb ^ 1]),
-               reinterpret_cast<int64_t*>(sm + L.offs[cb ^ 1]));
+  // (unless the idle warps of the refinement step issue them)
   if (tid == 0) *s_em = 0u;
-  __syncthreads();
-  if (fetch_fibers<T>(K, nn, reinterpret_cast<const int64_t*>(sm + L.offs[cb ^ 1]), cnt,
-                     reinterpret_cast<T*>(sm + L.fib[cb ^ 1]), fbar + (cb ^ 1)))
-    fblk |= 1u << (cb ^ 1);
-  else
-    fblk &= ~(1u << (cb ^ 1));
+  if (!K.draw_late) {
+    draw_samples(p, nn, nt, rank * spc, cnt, reinterpret_cast<uint32_t*>(sm + L.ids[cb ^ 1]),
+                 reinterpret_cast<int64_t*>(sm + L.offs[cb ^ 1]));
+    __syncthreads();
+    if (fetch_fibers<T>(K, nn, reinterpret_cast<const int64_t*>(sm + L.offs[cb ^ 1]), cnt,
+                       reinterpret_cast<T*>(sm + L.fib[cb ^ 1]), fbar + (cb ^ 1)))
+      fblk |= 1u << (cb ^ 1);
+    else
+      fblk &= ~(1u << (cb ^ 1));
+  }
   cluster_wait();   // every partial M row and Gram of the cluster has landed
 
   // ---- 4. G = sum of the C partial Grams (fixed order, gg lanes per entry); FP32 copy; max diag
@@ -458,7 +497,8 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
   const float* X0 = gj + (R & 1) * (R * W) + R;   // X0(i, c) = X0[i * W + c]
   double* X = reinterpret_cast<double*>(sm + L.X);
   {
-    // ---- Newton-Schulz refinement in FP64 (or the FP64 Cholesky inverse)
+    // ---- Newton-Schulz refinement in FP64 (or the FP64 Cholesky inverse).  The first step writes
+    // X directly (it reads the FP32 start); a second step (FP64 tensors) writes U, the result.
     double* U = reinterpret_cast<double*>(sm + L.U);
     double* E = reinterpret_cast<double*>(sm + L.E);
     const int RR = R * R;
@@ -466,8 +506,11 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
     const int steps = sizeof(ACC) == 8 ? 2 : 1;
     if (tid == 0) *s_em = 0u;
     __syncthreads();
+    const int dbase = (RR + 31) / 32 * 32;   // first thread not computing an entry of E
+    bool drawn = false;
     for (int it = 0; fast && it < steps; ++it) {
       // E = I - G X  (X: the FP32 start in the first step)
+      float em = 0.f;
       for (int e = tid; e < RR; e += kLT) {
         const int r = e / R, c = e - r * R;
         const double* g = G + r * R;
@@ -488,7 +531,17 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
         }
         const double ev = (r == c ? 1.0 : 0.0) - (a0 + a1);
         E[e] = ev;
-        if (it == 0) atomicMax(s_em, __float_as_uint(fabsf((float)ev)));
+        em = fmaxf(em, fabsf((float)ev));
+      }
+      if (it == 0) {
+        const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(em));
+        if ((tid & 31) == 0 && wm) atomicMax(s_em, wm);
+        if (K.draw_late && tid >= dbase) {
+          draw_and_copy<T>(K, nn, nt, rank * spc, cnt, reinterpret_cast<uint32_t*>(sm + L.ids[cb ^ 1]),
+                           reinterpret_cast<int64_t*>(sm + L.offs[cb ^ 1]), reinterpret_cast<T*>(sm + L.fib[cb ^ 1]),
+                           fbar + (cb ^ 1), dbase);
+        }
+        drawn = true;
       }
       __syncthreads();
       if (it == 0 && !(__uint_as_float(*s_em) < 0.25f)) {
@@ -496,6 +549,7 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
         break;
       }
       // X_new = X + X E
+      double* Xout = it == 0 ? X : U;
       for (int e = tid; e < RR; e += kLT) {
         const int r = e / R, c = e - r * R;
         double a0 = 0.0, a1 = 0.0, x;
@@ -517,15 +571,22 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
           if (l < R) a0 = fma(xr[l], E[l * R + c], a0);
           x = xr[c];
         }
-        U[e] = x + (a0 + a1);
+        Xout[e] = x + (a0 + a1);
       }
       __syncthreads();
-      for (int e = tid; e < RR; e += kLT) X[e] = U[e];
-      __syncthreads();
+      if (it == steps - 1 && steps == 2) X = U;   // the result of the second step
     }
-    if (!fast)
+    if (K.draw_late && !drawn) {   // the refinement did not run: draw with every thread
+      draw_and_copy<T>(K, nn, nt, rank * spc, cnt, reinterpret_cast<uint32_t*>(sm + L.ids[cb ^ 1]),
+                       reinterpret_cast<int64_t*>(sm + L.offs[cb ^ 1]), reinterpret_cast<T*>(sm + L.fib[cb ^ 1]),
+                       fbar + (cb ^ 1), 0);
+    }
+    if (K.draw_late) fblk |= 1u << (cb ^ 1);
+    if (!fast) {
+      X = reinterpret_cast<double*>(sm + L.X);
       spd_inverse_fp64(G, X, U, reinterpret_cast<double*>(sm + L.T2), reinterpret_cast<double*>(sm + L.dinv), R,
                        s_bad);
+    }
   }
 
   // ---- 5. this CTA's rows: M rows (fixed-order sum over the C partials), A = M G^-1 (FP64)
@@ -652,6 +713,11 @@ __global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, i
         }
         K.vec[m] = v;
         K.bulk[m] = (m < p.N && (p.use_rep || m == 0) && v == 16) ? 1 : 0;
+      }
+      {
+        int all_bulk = 1;
+        for (int m = 0; m < p.N; ++m) all_bulk &= K.bulk[m];
+        K.draw_late = (all_bulk && p.R * p.R <= kLT - 128) ? 1 : 0;
       }
       mbar_init(&fbar[0]);
       mbar_init(&fbar[1]);

@@ -1,0 +1,161 @@
+"""Full-size parity cases for the workloads the bench does not time.
+
+* 100^4 BF16 (rank 16, congruence 0.5, 1% noise; R = 16, S = 450): whole CPRAND-MIX runs to the
+  paper's stopping rules; the final true fit is within 1e-3 of the FP64 oracle's, and the sampled-fit
+  trace is compared with the oracle's per iteration.
+* 64 independent 3-way FP32 problems (dims U[64, 512], rank U[4, 32], congruence U[0, 0.9], 1% noise,
+  S = 10 R ln R) in one batched call: every problem finishes with status OK; sampled problems match
+  the same problem run alone and the FP64 oracle.
+* 1500^3 FP32 (rank 50, congruence 0.5, 0.1% noise; R = 50, S = 2000): one mode update per mode
+  against the oracle's least-squares solve on the same sampled fibers (gathered by torch indexing,
+  independent of the library's gather); a two-iteration CPRAND-MIX run whose sampled fit agrees with
+  the exact fit of its factors (FP64, computed slab by slab on the device).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cp, mixing, streams
+from synth import batch_problem_specs, make_problem, to_oracle_array
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def cb():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1701_06600_gb300 import binding
+    return binding
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def true_fit_device(X, dims, lam, factors, slab=64):
+    """Exact fit 1 - ||X - X~|| / ||X|| of a 3-way CP model, FP64 on the device one slab of the last
+    mode at a time (torch operations only)."""
+    I1, I2, I3 = dims
+    A, B, C = [f.double() for f in factors]
+    AB = (B[:, None, :] * A[None, :, :]).reshape(I1 * I2, -1) * lam.double()[None, :]   # row i1 + I1 i2
+    Xv = X.view(I3, I1 * I2)
+    err2 = 0.0
+    nx2 = 0.0
+    for k0 in range(0, I3, slab):
+        k1 = min(I3, k0 + slab)
+        model = C[k0:k1] @ AB.T                       # (slab, I1 I2): entry (k, i1 + I1 i2)
+        xs = Xv[k0:k1].double()
+        err2 += float(torch.sum((xs - model) ** 2))
+        nx2 += float(torch.sum(xs * xs))
+    return 1.0 - np.sqrt(err2) / np.sqrt(nx2)
+
+
+# ------------------------------------------------------------------------------------------------
+# 100^4 BF16
+# ------------------------------------------------------------------------------------------------
+def test_bf16_100x4_reaches_fp64_oracle_fit(cb):
+    dims, R, S = (100, 100, 100, 100), 16, 450
+    prob = make_problem(dims, 16, C=0.5, eta=0.01, seed=1003, dtype=torch.bfloat16, device=DEV)
+    T = to_oracle_array(prob.X, dims)
+    trace = torch.zeros(200, dtype=torch.float64, device=DEV)
+    opts = cb.cpr_default_opts(seed=2003, noise_eta=0.01, fit_trace_dev=trace.data_ptr())
+    out = cb.cpr_cprand_mix(prob.X, dims, R, S, opts=opts)
+    assert out["status"] == cb.OK
+    ref = mixing.cprand_mix(T, R, S, seed=2003, rule=cp.StopRule(eta=0.01))
+    f_gpu = cp.exact_fit(T, out["lam"].cpu().numpy(), [A.cpu().numpy() for A in out["factors"]])
+    f_ref = cp.exact_fit(T, ref["lam"], ref["factors"])
+    assert abs(f_gpu - f_ref) < 1e-3, (f_gpu, f_ref, out["iters"], ref["iters"])
+    # per-iteration error of the BF16-stored run's sampled fit against the FP64 oracle's
+    k = min(out["iters"], ref["iters"])
+    err = np.abs(trace.cpu().numpy()[:k] - ref["fits"][:k])
+    print("100^4 BF16: iterations gpu %d oracle %d, final fit gpu %.6f oracle %.6f, per-iteration "
+          "|dF^| max %.2e last %.2e" % (out["iters"], ref["iters"], f_gpu, f_ref, err.max(), err[-1]))
+    assert np.all(np.isfinite(err)) and err[-1] < 1e-3
+
+
+# ------------------------------------------------------------------------------------------------
+# 64 uneven problems in one batched call
+# ------------------------------------------------------------------------------------------------
+def test_batch_of_64_uneven_problems(cb):
+    specs = batch_problem_specs(1004, B=64)
+    Xs, dims_l, Rs, Ss, opts = [], [], [], [], []
+    for b, sp in enumerate(specs):
+        prob = make_problem(sp["dims"], sp["R"], C=sp["C"], eta=0.01, seed=1000 * (b + 1) + 4,
+                            dtype=torch.float32, device=DEV)
+        Xs.append(prob.X)
+        dims_l.append(sp["dims"])
+        Rs.append(sp["R"])
+        Ss.append(max(sp["R"], cp.sample_size(sp["R"])))
+        opts.append(cb.cpr_default_opts(seed=2004, batch_index=b, noise_eta=0.01))
+    outs, _ = cb.cpr_cprand_batched(Xs, dims_l, Rs, Ss, opts, mix=True)
+    torch.cuda.synchronize()
+    fits = []
+    for b in range(64):
+        assert outs[b]["status"] == cb.OK, (b, outs[b]["status"])
+        f = true_fit_device(Xs[b], dims_l[b], outs[b]["lam"], outs[b]["factors"])
+        fits.append(f)
+        assert np.isfinite(f) and f > 0.5, (b, f)
+    # the batch draws exactly what each problem draws alone: a few problems re-run on their own
+    sizes = [int(np.prod(d)) for d in dims_l]
+    picks = sorted({int(np.argmin(sizes)), int(np.argmax(Rs)), int(np.argmax(sizes)), 31})
+    for b in picks:
+        single = cb.cpr_cprand_mix(Xs[b], dims_l[b], Rs[b], Ss[b], opts=opts[b])
+        f_single = true_fit_device(Xs[b], dims_l[b], single["lam"], single["factors"])
+        assert abs(fits[b] - f_single) < 1e-3, (b, fits[b], f_single)
+    # and the FP64 oracle on three moderate problems (congruence below 0.6, so the stopping point
+    # does not depend on the trajectory inside a swamp)
+    cand = [b for b in np.argsort(sizes) if specs[b]["C"] < 0.6][:3]
+    for b in cand:
+        T = to_oracle_array(Xs[b], dims_l[b])
+        ref = mixing.cprand_mix(T, Rs[b], Ss[b], seed=2004, b=int(b), rule=cp.StopRule(eta=0.01))
+        f_ref = cp.exact_fit(T, ref["lam"], ref["factors"])
+        assert abs(fits[b] - f_ref) < 1e-3, (int(b), fits[b], f_ref)
+
+
+# ------------------------------------------------------------------------------------------------
+# 1500^3 FP32
+# ------------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def big(cb):
+    dims = (1500, 1500, 1500)
+    prob = make_problem(dims, 50, C=0.5, eta=0.001, seed=1005, dtype=torch.float32, device=DEV)
+    yield dims, prob.X
+    del prob
+    torch.cuda.empty_cache()
+
+
+def test_1500_cubed_update_matches_oracle_on_gathered_fibers(cb, big):
+    dims, X = big
+    R, S = 50, 2000
+    rng = np.random.default_rng(6)
+    f0 = [rng.random((d, R)).astype(np.float32).astype(np.float64) for d in dims]
+    Xv = X.view(*dims[::-1]).permute(2, 1, 0)            # Xv[i1, i2, i3]
+    for n in range(3):
+        facs = [torch.tensor(f, device=DEV) for f in f0]
+        lam = torch.empty(R, dtype=torch.float64, device=DEV)
+        st = cb.cpr_sampled_update(X, dims, lam, facs, n, S, seed=2005, b=0, t=n)
+        assert st == cb.OK
+        idx = streams.ls_sample_indices(2005, 0, n, n, S, dims)
+        sel = tuple(torch.as_tensor(idx[:, m], device=DEV) for m in range(3) if m != n)
+        X_S = torch.movedim(Xv, n, -1)[sel].T.double().cpu().numpy()     # I_n x S
+        A_ref, lam_ref = cp.normalize_columns(cp.sampled_ls(cp.skr(f0, idx, n), X_S))
+        assert rel(facs[n].cpu().numpy(), A_ref) < 1e-4, n
+        assert rel(lam.cpu().numpy(), lam_ref) < 1e-4, n
+
+
+def test_1500_cubed_mix_run_fit_estimate_matches_exact_fit(cb, big):
+    dims, X = big
+    R, S = 50, 2000
+    trace = torch.zeros(2, dtype=torch.float64, device=DEV)
+    opts = cb.cpr_default_opts(seed=2005, fixed_iters=2, fit_trace_dev=trace.data_ptr())
+    out = cb.cpr_cprand_mix(X, dims, R, S, opts=opts)
+    assert out["status"] == cb.OK and out["iters"] == 2
+    tr = trace.cpu().numpy()
+    f_true = true_fit_device(X, dims, out["lam"], out["factors"])
+    print("1500^3: sampled fit %.6f %.6f, exact fit %.6f, setup %.1f ms, iterations %.1f ms"
+          % (tr[0], tr[1], f_true, out["ms_setup"], out["ms_iterate"]))
+    assert np.all(np.isfinite(tr)) and tr[1] > tr[0]
+    # the sampled estimate over 2^14 fixed entries tracks the exact fit (Sec. 3.4)
+    assert abs(tr[1] - f_true) < 2e-3, (tr[1], f_true)
