@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="skip the studies that run after the timed regions (time to fit, the plain FP64 "
+                         "GPU form, the gather bandwidth); used for profiler runs")
     return ap.parse_args()
 
 
@@ -403,7 +406,7 @@ def run_ours(args, rank, world, local_rank):
     # cores), for the library and for the plain FP64 GPU form on the same GPU
     cpu = None
     ttf = plain_out = gather = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.skip_extras:
         if not args.no_cpu_baseline:
             cpu = cpu_baseline(X, dims, seconds=60.0)
         plain_fp64_gpu(X, dims, w, seed=w["philox_seed"])                     # warm-up (library handles)
@@ -491,6 +494,8 @@ def run_ours(args, rank, world, local_rank):
         out["gather"] = dict(gather, peak_GBs=pk["hbm_gbs"], peak_source=pk_src,
                              kernel="k_gather_contig (one warp per fiber, 16-byte vectors) / "
                                     "k_gather_only (strided, one element per thread)")
+    if cpu is None and rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(X, dims, seconds=60.0)
     if cpu is not None:
         out["cpu_baseline"] = cpu
     if world > 1:
