@@ -269,10 +269,11 @@ def time_to_fit_ours(cb, X, dims, w, opts_kw, target, max_k):
     return {"seconds": float(np.median(ts[1:])), "iters": k_hit, "true_fit": fits[-1]}, fits
 
 
-def gather_bandwidth(cb, X, dims, S=1 << 16, reps=20):
-    """The fiber gather (Sec. 3.2) on its own at a size that can fill HBM: S sampled mode-1 fibers
-    (contiguous, 16-byte vectors) and S sampled mode-3 fibers of the standard layout (stride
-    I_1 I_2: one 32-byte sector per element), CUDA events over `reps` launches each."""
+def gather_bandwidth(cb, X, dims, S=1 << 18, reps=10):
+    """The fiber gather (Sec. 3.2) on its own at a size that fills HBM: S sampled mode-1 fibers
+    (contiguous, 16-byte vectors; 2^18 fibers of 400 FP32 = 419 MB read and written per launch) and S
+    sampled mode-3 fibers of the standard layout (stride I_1 I_2: one 32-byte sector per element),
+    CUDA events over `reps` launches each."""
     import torch
     out = {}
     I = dims[0]

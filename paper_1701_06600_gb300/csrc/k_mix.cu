@@ -173,22 +173,24 @@ cudaError_t launch_mix_mode(const void* X, void* Y, int dtype, int N, const int6
 // shared memory, 256 threads: every thread issues its 16 loads (coalesced along l) before its first
 // store (coalesced along i), so a block keeps 16 KB of reads in flight.
 template <typename T>
-__global__ void __launch_bounds__(256) k_unfold_copy(const T* __restrict__ X, T* __restrict__ Y, int64_t L, int64_t I,
-                                                     int64_t Rr) {
+__global__ void __launch_bounds__(256, 4) k_unfold_copy(const T* __restrict__ X, T* __restrict__ Y, int64_t L,
+                                                        int64_t I, int64_t Rr) {
   __shared__ T tile[64][65];
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;   // 32 lanes x 8 warps
   const int64_t l0 = (int64_t)blockIdx.x * 64, i0 = (int64_t)blockIdx.y * 64;
+  const int nl = (int)(L - l0 < 64 ? L - l0 : 64), ni = (int)(I - i0 < 64 ? I - i0 : 64);   // tile extents
   for (int64_t r = blockIdx.z; r < Rr; r += gridDim.z) {
-    const T* Xr = X + r * L * I;
-    T* Yr = Y + r * L * I;
+    const T* src = X + r * L * I + l0 + i0 * L;   // tile origin in X (l fastest)
+    T* dst = Y + r * L * I + i0 + l0 * I;         // tile origin in Y (i fastest)
     T v[16];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int64_t i = i0 + wy + 8 * k;
+      const int i = wy + 8 * k;
+      const T* row = src + (int64_t)i * L;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int64_t l = l0 + lane + 32 * h;
-        v[2 * k + h] = (l < L && i < I) ? Xr[l + L * i] : T(0);
+        const int l = lane + 32 * h;
+        v[2 * k + h] = (l < nl && i < ni) ? row[l] : T(0);
       }
     }
 #pragma unroll
@@ -198,11 +200,12 @@ __global__ void __launch_bounds__(256) k_unfold_copy(const T* __restrict__ X, T*
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int64_t l = l0 + wy + 8 * k;
+      const int l = wy + 8 * k;
+      T* col = dst + (int64_t)l * I;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int64_t i = i0 + lane + 32 * h;
-        if (l < L && i < I) Yr[i + I * l] = tile[lane + 32 * h][wy + 8 * k];
+        const int i = lane + 32 * h;
+        if (l < nl && i < ni) col[i] = tile[i][l];
       }
     }
     __syncthreads();

@@ -460,17 +460,22 @@ __global__ void k_gather_only(const T* X, int64_t I, int64_t st, int64_t S, cons
 }
 
 // Contiguous fibers (stride 1, the first mode or a column-major unfolding copy): one warp per
-// fiber, grid-stride over the fibers; a fiber whose start and destination are 16-byte aligned and
-// whose length is a multiple of the vector moves as 16-byte vectors, four loads in flight per lane
-// before the stores, else element by element.
+// fiber, grid-stride over the fibers, the next fiber's offset loaded ahead; a fiber whose start and
+// destination are 16-byte aligned and whose length is a multiple of the vector moves as 16-byte
+// vectors with all of a lane's loads (up to 4 per 128 vectors) issued before its stores, else
+// element by element.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather_contig(const T* __restrict__ X, int64_t I, int64_t S,
                                                        const int64_t* __restrict__ off, T* __restrict__ out) {
   constexpr int E = 16 / (int)sizeof(T);
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < S; j += nw) {
-    const T* src = X + off[j];
+  int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t oj = j < S ? __ldg(off + j) : 0;
+  for (; j < S; j += nw) {
+    const int64_t jn = j + nw;
+    const int64_t on = jn < S ? __ldg(off + jn) : 0;   // next fiber's offset, in flight meanwhile
+    const T* src = X + oj;
     T* dst = out + j * I;
     const bool vec = I % E == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0 &&
                      (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
@@ -478,18 +483,23 @@ __global__ void __launch_bounds__(256) k_gather_contig(const T* __restrict__ X, 
       const uint4* s4 = reinterpret_cast<const uint4*>(src);
       uint4* d4 = reinterpret_cast<uint4*>(dst);
       const int64_t nv = I / E;
-      int64_t v = lane;
-      for (; v + 96 < nv; v += 128) {
-        const uint4 a = __ldg(s4 + v), b = __ldg(s4 + v + 32), c = __ldg(s4 + v + 64), d = __ldg(s4 + v + 96);
-        d4[v] = a;
-        d4[v + 32] = b;
-        d4[v + 64] = c;
-        d4[v + 96] = d;
+      for (int64_t v0 = 0; v0 < nv; v0 += 128) {
+        uint4 a[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t v = v0 + lane + 32 * q;
+          if (v < nv) a[q] = __ldg(s4 + v);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t v = v0 + lane + 32 * q;
+          if (v < nv) d4[v] = a[q];
+        }
       }
-      for (; v < nv; v += 32) d4[v] = __ldg(s4 + v);
     } else {
       for (int64_t i = lane; i < I; i += 32) dst[i] = src[i];
     }
+    oj = on;
   }
 }
 

@@ -54,8 +54,9 @@ def test_sampler_bit_exact(cb, dims, n, S, t, b):
 # a2: fiber gather (bit-exact)
 # ------------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float64])
-@pytest.mark.parametrize("dims", [(37, 29, 41), (1, 30, 20), (11, 7, 5, 9, 3)])
+@pytest.mark.parametrize("dims", [(37, 29, 41), (1, 30, 20), (11, 7, 5, 9, 3), (64, 40, 24), (400, 13, 11)])
 def test_gather_bit_exact(cb, dtype, dims):
+    # first-mode fibers of 64 or 400 entries take the 16-byte vector path (whole-warp fibers)
     X = rand_tensor(dims, dtype, 1)
     T = to_oracle_array(X, dims)
     for n in range(len(dims)):
