@@ -198,6 +198,28 @@ def test_cprand_fp64_stopping_rules_match_oracle(cb):
         assert abs(out["fit_est"] - ref["fits"][-1]) < 1e-9
 
 
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-10), (torch.float32, 1e-5)])
+def test_checkpoint_resume_continues_the_run(cb, dtype, tol):
+    # the draws of iteration t depend only on (seed, t, mode, batch index): 10 iterations, then 10
+    # more started from the returned factors with the iteration counter continued, give the
+    # 20-iteration run (up to the rounding of folding the lazy column scales into the checkpoint)
+    dims = (48, 40, 36)
+    prob = make_problem(dims, 4, C=0.5, eta=0.01, seed=19, dtype=dtype, device=DEV)
+    tr20 = torch.zeros(20, dtype=torch.float64, device=DEV)
+    full = cb.cpr_cprand(prob.X, dims, 4, 60, opts=cb.cpr_default_opts(seed=12, fixed_iters=20,
+                                                                       fit_trace_dev=tr20.data_ptr()))
+    first = cb.cpr_cprand(prob.X, dims, 4, 60, opts=cb.cpr_default_opts(seed=12, fixed_iters=10))
+    tr10 = torch.zeros(10, dtype=torch.float64, device=DEV)
+    resumed = cb.cpr_cprand(prob.X, dims, 4, 60, init=first["factors"],
+                            opts=cb.cpr_default_opts(seed=12, fixed_iters=10, first_iter=10,
+                                                     fit_trace_dev=tr10.data_ptr()))
+    assert resumed["iters"] == 10 and resumed["status"] == cb.OK
+    np.testing.assert_allclose(tr10.cpu().numpy(), tr20.cpu().numpy()[10:], rtol=0, atol=tol)
+    for A, B in zip(resumed["factors"], full["factors"]):
+        assert rel(A.cpu().numpy(), B.cpu().numpy()) < tol
+    assert rel(resumed["lam"].cpu().numpy(), full["lam"].cpu().numpy()) < tol
+
+
 def test_repeated_samples_make_square_system_singular(cb):
     # S = R drawn with replacement: a repeated multi-index repeats a row of Z_S, so the sampled
     # least-squares problem is rank deficient and the update must report it rather than solve it
