@@ -15,9 +15,10 @@
 // three MMAs per k-step.  W's halves come from global memory; the tile of U is split in shared
 // memory by the epilogue warps while they wait.
 //
-// Roles (256 threads): warp 0 lane 0 issues TMA; warp 1 owns TMEM and lane 0 issues MMAs;
-// warps 4-7 split the U tiles, then drain TMEM.  Two pipeline stages of 32 k-values.  Every
-// mbarrier wait is bounded: on expiry the kernel records an error and stops issuing work.
+// Roles (256 threads, one persistent CTA per SM): warp 0 lane 0 issues TMA; warp 1 owns TMEM (two
+// accumulator buffers) and lane 0 issues MMAs; warps 2-3 split the U tiles; warps 4-7 drain TMEM.
+// Two pipeline stages of 32 k-values, continuous across tiles.  Every mbarrier wait is bounded: on
+// expiry the kernel records an error and stops issuing work.
 #include <cuda.h>
 #include <string.h>
 
@@ -36,7 +37,7 @@ constexpr int kAStage = kBM * kBK * 4;         // 16 KB
 constexpr int kBStage = 256 * kBK * 4;         // 32 KB (room for NT = 256)
 constexpr int kStageBytes = 2 * kAStage + 2 * kBStage;
 constexpr int kBarOffset = kStages * kStageBytes;
-constexpr int kTcSmem = kBarOffset + 128 + 1024;   // + barriers + alignment slack
+constexpr int kTcSmem = kBarOffset + 256 + 1024;   // + barriers + alignment slack
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 struct TcArgs {
@@ -110,23 +111,29 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
+// One mode-n product, persistent: CTA c takes output tiles c, c + gridDim.x, ... (tile t = (row block
+// t / NB, column block t % NB)).  The TMA ring of kStages stages runs continuously across tiles, and
+// the accumulator is double-buffered in TMEM (2 x 256 columns), so the epilogue of one tile overlaps
+// the MMAs of the next.
+//   warp 0, lane 0: TMA producer      warp 1: TMEM owner, lane 0 issues the MMAs
+//   warps 2-3: split the U tiles into TF32 hi / lo halves      warps 4-7: epilogue (TMEM -> global)
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_mix_tc(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmWhi,
              const __grid_constant__ CUtensorMap tmWlo, TcArgs a) {
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kBarOffset);
-  uint64_t* full = bars;         // TMA landed (1 arrival + tx bytes)
-  uint64_t* conv = bars + 2;     // U tile split (128 arrivals)
-  uint64_t* empty = bars + 4;    // MMAs done with the stage (tcgen05.commit)
-  uint64_t* accum = bars + 6;    // every MMA done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 7);
-  volatile int* err = reinterpret_cast<volatile int*>(bars + 8);
+  uint64_t* full = bars;                   // TMA landed (1 arrival + tx bytes)
+  uint64_t* conv = bars + kStages;         // U tile split (64 arrivals)
+  uint64_t* empty = bars + 2 * kStages;    // MMAs done with the stage (tcgen05.commit)
+  uint64_t* accf = bars + 3 * kStages;     // accumulator buffer b complete (tcgen05.commit), 2 buffers
+  uint64_t* acce = accf + 2;               // accumulator buffer b drained (128 arrivals), 2 buffers
+  uint64_t* fin = acce + 2;                // every MMA issued by this CTA complete
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
+  volatile int* err = reinterpret_cast<volatile int*>(fin + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nb = blockIdx.x % a.NB;
-  const int64_t mt = blockIdx.x / a.NB;
-  const int64_t j0 = mt * kBM;
-  const int c0 = nb * a.NT;
+  const int64_t mtiles = (a.J + kBM - 1) / kBM;
+  const int64_t ntiles = mtiles * a.NB;
   const int nk = (a.I + kBK - 1) / kBK;
   auto A_hi = [&](int s) { return sm + s * kStageBytes; };
   auto A_lo = [&](int s) { return sm + s * kStageBytes + kAStage; };
@@ -136,15 +143,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 128);
+      mbar_init(&conv[s], 64);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 128);
+    }
+    mbar_init(fin, 1);
     *err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(256));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -154,21 +165,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t bbytes = (uint32_t)a.NT * kBK * 4;
 
   if (warp == 0) {
-    if (lane == 0) {   // producer
-      int issued = 0;
-      for (int i = 0; i < nk; ++i) {
-        const int s = i & 1;
-        if (i >= kStages && !mbar_wait(&empty[s], ((i - kStages) >> 1) & 1, err)) break;
-        mbar_expect_tx(&full[s], (uint32_t)kAStage + (a.three_x ? 2u : 1u) * bbytes);
-        tma_2d(A_hi(s), &tmU, i * kBK, (int)j0, &full[s]);
-        tma_2d(B_hi(s), &tmWhi, i * kBK, c0, &full[s]);
-        if (a.three_x) tma_2d(B_lo(s), &tmWlo, i * kBK, c0, &full[s]);
-        issued = i + 1;
+    if (lane == 0) {   // producer: one continuous ring over all of this CTA's tiles
+      int64_t it = 0, issued = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int nb = (int)(t % a.NB);
+        const int j0 = (int)((t / a.NB) * kBM);
+        const int c0 = nb * a.NT;
+        for (int i = 0; i < nk; ++i, ++it) {
+          const int s = (int)(it % kStages);
+          const uint32_t use = (uint32_t)(it / kStages);
+          if (it >= kStages && !mbar_wait(&empty[s], (use - 1) & 1, err)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], (uint32_t)kAStage + (a.three_x ? 2u : 1u) * bbytes);
+          tma_2d(A_hi(s), &tmU, i * kBK, j0, &full[s]);
+          tma_2d(B_hi(s), &tmWhi, i * kBK, c0, &full[s]);
+          if (a.three_x) tma_2d(B_lo(s), &tmWlo, i * kBK, c0, &full[s]);
+          issued = it + 1;
+        }
       }
       if (*err) {   // never leave copies in flight: wait (bounded) for the last ones issued
-        for (int i = issued > kStages ? issued - kStages : 0; i < issued; ++i) {
-          const int s = i & 1;
-          for (uint32_t it = 0; it < kWaitLimit && !mbar_try(&full[s], (i >> 1) & 1); ++it) {
+        for (int64_t q = issued > kStages ? issued - kStages : 0; q < issued; ++q) {
+          const int s = (int)(q % kStages);
+          for (uint32_t w = 0; w < kWaitLimit && !mbar_try(&full[s], (uint32_t)(q / kStages) & 1); ++w) {
           }
         }
       }
@@ -176,109 +197,143 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {   // MMA issuer
       const uint32_t idesc = idesc_tf32(kBM, a.NT);
+      int64_t it = 0, tl = 0;
       bool ok = true;
-      for (int i = 0; i < nk && ok; ++i) {
-        const int s = i & 1;
-        if (!mbar_wait(&conv[s], (i >> 1) & 1, err)) {
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+        const int b = (int)(tl & 1);
+        const uint32_t ub = (uint32_t)(tl >> 1);
+        if (tl >= 2 && !mbar_wait(&acce[b], (ub - 1) & 1, err)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ah = su32(A_hi(s)), al = su32(A_lo(s)), bh = su32(B_hi(s)), bl = su32(B_lo(s));
+        const uint32_t d = tmem + (uint32_t)(b * 256);
+        for (int i = 0; i < nk; ++i, ++it) {
+          const int s = (int)(it % kStages);
+          if (!mbar_wait(&conv[s], (uint32_t)(it / kStages) & 1, err)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t ah = su32(A_hi(s)), al = su32(A_lo(s)), bh = su32(B_hi(s)), bl = su32(B_lo(s));
 #pragma unroll
-        for (int kk = 0; kk < kBK / 8; ++kk) {
-          const uint32_t off = kk * 32;   // 8 tf32 values
-          mma_tf32(tmem, sw128_desc(ah + off), sw128_desc(bh + off), idesc, (i | kk) != 0);
-          if (a.three_x) {
-            mma_tf32(tmem, sw128_desc(ah + off), sw128_desc(bl + off), idesc, 1u);
-            mma_tf32(tmem, sw128_desc(al + off), sw128_desc(bh + off), idesc, 1u);
+          for (int kk = 0; kk < kBK / 8; ++kk) {
+            const uint32_t off = kk * 32;   // 8 tf32 values
+            mma_tf32(d, sw128_desc(ah + off), sw128_desc(bh + off), idesc, (i | kk) != 0);
+            if (a.three_x) {
+              mma_tf32(d, sw128_desc(ah + off), sw128_desc(bl + off), idesc, 1u);
+              mma_tf32(d, sw128_desc(al + off), sw128_desc(bh + off), idesc, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&accf[b]);
+      }
+      // every MMA this CTA issued has completed before the TMEM is released
+      mma_commit(fin);
+      for (uint32_t w = 0; w < kWaitLimit && !mbar_try(fin, 0); ++w) {
+      }
+    }
+  } else if (warp < 4) {
+    // split the U tiles into hi / lo halves (64 threads)
+    const int ct = tid - 64;
+    int64_t it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int i = 0; i < nk; ++i, ++it) {
+        const int s = (int)(it % kStages);
+        if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1, err)) {
+          ok = false;
+          break;
+        }
+        if (a.three_x) {
+          float4* hi = reinterpret_cast<float4*>(A_hi(s));
+          float4* lo = reinterpret_cast<float4*>(A_lo(s));
+#pragma unroll 4
+          for (int v = ct; v < kAStage / 16; v += 64) {
+            const float4 x = hi[v];
+            const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+            hi[v] = h;
+            lo[v] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        mbar_arrive(&conv[s]);
+      }
+    }
+  } else {
+    // epilogue: TMEM lanes 32 (warp - 4) .. + 31 hold rows j0 + those lanes of the tile
+    int64_t tl = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+      const int b = (int)(tl & 1);
+      if (!mbar_wait(&accf[b], (uint32_t)(tl >> 1) & 1, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int nb = (int)(t % a.NB);
+      const int64_t j0 = (t / a.NB) * kBM;
+      const int c0 = nb * a.NT;
+      const int rl = 32 * (warp - 4) + lane;
+      const int64_t j = j0 + rl;
+      const bool row_ok = j < a.J;
+      int64_t base = 0;
+      if (a.ystd && row_ok) {   // standard-layout offset of fiber j (Sec. 2.1 index map, inverted)
+        int64_t rem = j;
+        for (int m = 0; m < a.N; ++m) {
+          if (m == a.n) continue;
+          const int64_t im = rem % a.dims[m];
+          rem /= a.dims[m];
+          base += im * a.st[m];
+        }
+      }
+      const int64_t stn = a.st[a.n];
+      for (int cc = 0; cc < a.NT; cc += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp - 4)) << 16) + (uint32_t)(b * 256 + cc);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!row_ok) continue;
+        const int cb = c0 + cc;
+        if (a.yunf) {
+          float* dst = a.yunf + j * a.I + cb;
+          if (cb + 16 <= a.I) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              reinterpret_cast<float4*>(dst)[q] =
+                  make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
+                              __uint_as_float(v[4 * q + 3]));
+          } else {
+            for (int q = 0; q < 16 && cb + q < a.I; ++q) dst[q] = __uint_as_float(v[q]);
           }
         }
-        mma_commit(&empty[s]);
-      }
-      mma_commit(accum);
-    }
-  } else if (warp >= 4) {
-    const int ct = tid - 128;
-    for (int i = 0; i < nk; ++i) {   // split the U tiles into hi / lo halves
-      const int s = i & 1;
-      if (!mbar_wait(&full[s], (i >> 1) & 1, err)) break;
-      if (a.three_x) {
-        float4* hi = reinterpret_cast<float4*>(A_hi(s));
-        float4* lo = reinterpret_cast<float4*>(A_lo(s));
-        for (int v = ct; v < kAStage / 16; v += 128) {
-          const float4 x = hi[v];
-          const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
-          hi[v] = h;
-          lo[v] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      }
-      mbar_arrive(&conv[s]);
-    }
-    // epilogue: TMEM lanes 32 (warp - 4) .. + 31 hold rows j0 + those lanes
-    const bool have = mbar_wait(accum, 0, err);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int rl = 32 * (warp - 4) + lane;
-    const int64_t j = j0 + rl;
-    const bool row_ok = have && j < a.J;
-    int64_t base = 0;
-    if (a.ystd && row_ok) {   // standard-layout offset of fiber j (Sec. 2.1 index map, inverted)
-      int64_t rem = j;
-      for (int m = 0; m < a.N; ++m) {
-        if (m == a.n) continue;
-        const int64_t im = rem % a.dims[m];
-        rem /= a.dims[m];
-        base += im * a.st[m];
-      }
-    }
-    const int64_t stn = a.st[a.n];
-    for (int cc = 0; cc < a.NT; cc += 16) {
-      uint32_t v[16];
-      const uint32_t taddr = tmem + ((uint32_t)(32 * (warp - 4)) << 16) + (uint32_t)cc;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (!row_ok) continue;
-      const int cb = c0 + cc;
-      if (a.yunf) {
-        float* dst = a.yunf + j * a.I + cb;
-        if (cb + 16 <= a.I) {
+        if (a.ystd) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            reinterpret_cast<float4*>(dst)[q] =
-                make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
-                            __uint_as_float(v[4 * q + 3]));
-        } else {
-          for (int q = 0; q < 16 && cb + q < a.I; ++q) dst[q] = __uint_as_float(v[q]);
+          for (int q = 0; q < 16; ++q)
+            if (cb + q < a.I) a.ystd[base + (int64_t)(cb + q) * stn] = __uint_as_float(v[q]);
+        }
+        if (a.ynext) {
+          // first pass: row j = (i_2, i_3, ...) with i_2 fastest, column cb + q = i_1; in the
+          // column-major mode-2 unfolding that entry sits at i_2 + I_2 (i_1 + I_1 rest), so the lanes
+          // of a warp (consecutive i_2) store consecutive addresses for every column
+          const int64_t I2 = a.dims[1];
+          const int64_t i2 = j % I2, rest = j / I2;
+          float* dst = a.ynext + i2 + I2 * ((int64_t)a.I * rest + cb);
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (cb + q < a.I) dst[I2 * q] = __uint_as_float(v[q]);
         }
       }
-      if (a.ystd) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q)
-          if (cb + q < a.I) a.ystd[base + (int64_t)(cb + q) * stn] = __uint_as_float(v[q]);
-      }
-      if (a.ynext) {
-        // first pass: row j = (i_2, i_3, ...) with i_2 fastest, column cb + q = i_1; in the
-        // column-major mode-2 unfolding that entry sits at i_2 + I_2 (i_1 + I_1 rest), so the lanes
-        // of a warp (consecutive i_2) store consecutive addresses for every column
-        const int64_t I2 = a.dims[1];
-        const int64_t i2 = j % I2, rest = j / I2;
-        float* dst = a.ynext + i2 + I2 * ((int64_t)a.I * rest + cb);
-#pragma unroll
-        for (int q = 0; q < 16; ++q)
-          if (cb + q < a.I) dst[I2 * q] = __uint_as_float(v[q]);
-      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&acce[b]);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
   if (tid == 0 && *err) atomicExch(a.err, 1);
 }
@@ -365,8 +420,16 @@ cudaError_t launch_mix_tc(const float* U, float* ystd, float* yunf, float* ynext
   if (!make_map(&mU, U, I, a.J, kBM) || !make_map(&mH, Whi, I, I, a.NT) || !make_map(&mL, Wlo, I, I, a.NT))
     return cudaErrorInvalidValue;
   const int64_t mtiles = (a.J + kBM - 1) / kBM;
-  const int64_t blocks = mtiles * a.NB;
-  if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+  const int64_t tiles = mtiles * a.NB;
+  if (a.J > INT32_MAX) return cudaErrorInvalidValue;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                     cudaSuccess)
+      sms = 148;
+  }
+  const int64_t blocks = tiles < sms ? tiles : sms;   // one persistent CTA per SM
   k_mix_tc<<<(unsigned)blocks, kTcThreads, kTcSmem, s>>>(mU, mH, mL, a);
   return cudaGetLastError();
 }
