@@ -250,7 +250,7 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws, int als = 0, int
   Carver cv(ws);
   pl.d_probs = cv.take<Prob>(B);
   pl.d_states = cv.take<State>(B);
-  pl.d_counter = cv.take<int>(4);
+  pl.d_counter = cv.take<int>(16);   // [0] iterations, [1] cluster queue, [2] device error, [4..] mixing maxima
   int64_t maxP = 0;
   for (int b = 0; b < B; ++b) maxP = std::max(maxP, prod_dims(specs[b].X));
   pl.normblk = sumsq_blocks(maxP);
@@ -394,10 +394,35 @@ cpr_opts defaults() {
 // Otherwise SIMT passes ping-pong between final and t1 so that the last lands in final.
 int enqueue_mixing(const void* src, void* final, void* t1, void* t2, void* rep_last, int dtype, int N,
                    const int64_t* dims, float* const* W32, float* const* Wlo, double* const* W64, int* err,
-                   cudaStream_t s, int64_t& launches, bool* wrote_rep_last) {
+                   unsigned* amax, cudaStream_t s, int64_t& launches, bool* wrote_rep_last) {
   bool tc = dtype == CPR_F32 && t2 != nullptr;
   for (int n = 0; n < N && tc; ++n) tc = Wlo[n] != nullptr && mix_tc_supported(dtype, (int)dims[n]);
+  bool tc16 = tc && amax != nullptr;
+  for (int n = 0; n < N && tc16; ++n) tc16 = mix_tc16_supported(dtype, (int)dims[n]);
   *wrote_rep_last = false;
+  if (tc16) {
+    // FP16-split tensor-core passes: W's FP16 halves go into the Wlo buffer (2 I^2 halves = I^2
+    // floats); amax[n] = largest |entry| of pass n's input (the input tensor's from a max pass)
+    int64_t P = 1;
+    for (int n = 0; n < N; ++n) P *= dims[n];
+    CPR_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned) * (size_t)(N + 1), s));
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_absmax(src, dtype, P, amax, s));
+    for (int n = 0; n < N; ++n)
+      CPR_LAUNCH(CPR_KERNEL_OTHER, launch_split_f16(W32[n], Wlo[n], dims[n] * dims[n], s));
+    const float* U = static_cast<const float*>(src);
+    for (int n = 0; n < N; ++n) {
+      if (n > 1) CPR_LAUNCH(CPR_KERNEL_OTHER, launch_unfold_copy(t1, t2, dtype, N, dims, n, s));
+      if (n > 0) U = static_cast<const float*>(t2);
+      const bool last = n == N - 1;
+      float* ystd = last ? static_cast<float*>(final) : (n == 0 ? nullptr : static_cast<float*>(t1));
+      float* ynext = (n == 0 && !last) ? static_cast<float*>(t2) : nullptr;
+      float* yunf = (last && rep_last && n > 0) ? static_cast<float*>(rep_last) : nullptr;
+      CPR_LAUNCH(CPR_KERNEL_MIX, launch_mix_tc16(U, ystd, yunf, ynext, Wlo[n], N, dims, n, amax + n,
+                                                 last ? nullptr : amax + n + 1, err, s));
+      if (yunf) *wrote_rep_last = true;
+    }
+    return CPR_OK;
+  }
   if (tc) {
     for (int n = 0; n < N; ++n)
       CPR_LAUNCH(CPR_KERNEL_OTHER, launch_split_tf32(W32[n], W32[n], Wlo[n], dims[n] * dims[n], s));
@@ -558,7 +583,8 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
                                                          mb.F64[n], mb.sg[n], s));
       if (int st = enqueue_mixing(Xs[b].data, mb.xhat, pl.d_tmp, pl.d_tmp2,
                                   p.use_rep ? const_cast<void*>(p.Xrep[p.N - 1]) : nullptr, p.dtype, p.N, p.dims,
-                                  mb.W32, mb.Wlo, mb.W64, pl.d_counter + 2, s, launches, &rep_last_done))
+                                  mb.W32, mb.Wlo, mb.W64, pl.d_counter + 2,
+                                  reinterpret_cast<unsigned*>(pl.d_counter + 4), s, launches, &rep_last_done))
         return st;
     }
     if (p.use_rep)
@@ -1059,7 +1085,7 @@ int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, uint32_t b
     *table = c.take<double>((size_t)4 * imax);
     *tmp = c.take<unsigned char>((size_t)P * elem_size(dt));
     *tmp2 = dt == CPR_F32 ? c.take<unsigned char>((size_t)P * elem_size(dt)) : nullptr;
-    *err = c.take<int>(1);
+    *err = c.take<int>(16);   // [0] device error, [4..] mixing maxima
   };
   float *W32[kMaxOrder], *Wlo[kMaxOrder];
   double *W64[kMaxOrder], *F64[kMaxOrder], *sg[kMaxOrder], *table;
@@ -1075,8 +1101,8 @@ int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, uint32_t b
     CPR_LAUNCH(CPR_KERNEL_OTHER,
                launch_build_mix_ops((int)X->dims[n], seed, b, n, table, W32[n], W64[n], F64[n], sg[n], s));
   bool unused = false;
-  if (int st = enqueue_mixing(X->data, out_dev, tmp, tmp2, nullptr, dt, N, X->dims, W32, Wlo, W64, derr, s, launches,
-                              &unused))
+  if (int st = enqueue_mixing(X->data, out_dev, tmp, tmp2, nullptr, dt, N, X->dims, W32, Wlo, W64, derr,
+                              reinterpret_cast<unsigned*>(derr + 4), s, launches, &unused))
     return st;
   return CPR_OK;
 }

@@ -309,6 +309,14 @@ cudaError_t launch_split_tf32(const float* w, float* hi, float* lo, int64_t n, c
 cudaError_t launch_mix_tc(const float* U, float* ystd, float* yunf, float* ynext, const float* Whi, const float* Wlo,
                           int N, const int64_t* dims, int n, int three_x, int* err, cudaStream_t s);
 
+// mixing with FP16 operand halves (FP32 tensors, every I_n a multiple of 8)
+bool mix_tc16_supported(int dtype, int I);
+cudaError_t launch_split_f16(const float* w, void* out16, int64_t n, cudaStream_t s);
+cudaError_t launch_absmax(const void* X, int dtype, int64_t P, unsigned* out, cudaStream_t s);
+cudaError_t launch_mix_tc16(const float* U, float* ystd, float* yunf, float* ynext, const void* W16, int N,
+                            const int64_t* dims, int n, const unsigned* amax_in, unsigned* amax_out, int* err,
+                            cudaStream_t s);
+
 // mixing (Alg. 5)
 cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, double* table, float* W32,
                                  double* W64, double* F64, double* signs, cudaStream_t s);

@@ -20,6 +20,7 @@
 // Two pipeline stages of 32 k-values, continuous across tiles.  Every mbarrier wait is bounded: on
 // expiry the kernel records an error and stops issuing work.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <string.h>
 
 #include <mutex>
@@ -110,6 +111,29 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// ---- FP16 split path -------------------------------------------------------------------------
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle (32 FP16 per row), 8-row groups 512 bytes
+// apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+// Instruction descriptor: D = F32, A = B = F16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// x (already scaled by a power of two into FP16 range) = hi + lo with hi, lo FP16: lo carries the
+// next 11 bits, so hi*hi + hi*lo + lo*hi reproduces a product to about 2^-21.
+__device__ __forceinline__ void split_f16(float x, __half& h, __half& l) {
+  h = __float2half_rn(x);
+  l = __float2half_rn(x - __half2float(h));
+}
 
 // One mode-n product, persistent: CTA c takes output tiles c, c + gridDim.x, ... (tile t = (row block
 // t / NB, column block t % NB)).  The TMA ring of kStages stages runs continuously across tiles, and
@@ -338,6 +362,291 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (tid == 0 && *err) atomicExch(a.err, 1);
 }
 
+constexpr int kStagesH = 3;
+constexpr int kA32Stage = kBM * kBK * 4;        // 16 KB: the FP32 U tile as TMA lands it (128B swizzle)
+constexpr int kA16Stage = kBM * kBK * 2;        // 8 KB: one FP16 half of the U tile (64B swizzle)
+constexpr int kB16Stage = 256 * kBK * 2;        // 16 KB: one FP16 half of the W tile (room for NT = 256)
+constexpr int kStageBytesH = kA32Stage + 2 * kA16Stage + 2 * kB16Stage;   // 64 KB
+constexpr int kBarOffsetH = kStagesH * kStageBytesH;
+constexpr int kTcSmemH = kBarOffsetH + 256 + 1024;
+constexpr int kWScaleExp = 14;                  // W (|w| <= 1) is stored times 2^14 in FP16
+
+// The same persistent mode-n product with both operands split into FP16 halves and three
+// tcgen05.mma kind::f16 per 16 k-values (hi*hi + hi*lo + lo*hi): twice the tensor rate of the TF32
+// split at the same accuracy.  U is scaled by 2^ea so that max |U| < 2^14 (ea from *amax_in, the
+// largest |entry| of the pass's input), W by 2^14 (pre-split in global memory); the epilogue undoes
+// both scalings exactly and, when amax_out is set, records the largest |entry| of the result (the
+// next pass's scale).  Three pipeline stages of 32 k-values: the FP32 tile lands by TMA, warps 2-3
+// write its FP16 halves in the 64-byte swizzled layout the MMA reads.
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_mix_tc16(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmWhi,
+               const __grid_constant__ CUtensorMap tmWlo, TcArgs a, const unsigned* __restrict__ amax_in,
+               unsigned* amax_out) {
+  extern __shared__ unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kBarOffsetH);
+  uint64_t* full = bars;
+  uint64_t* conv = bars + kStagesH;
+  uint64_t* empty = bars + 2 * kStagesH;
+  uint64_t* accf = bars + 3 * kStagesH;
+  uint64_t* acce = accf + 2;
+  uint64_t* fin = acce + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
+  volatile int* err = reinterpret_cast<volatile int*>(fin + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t mtiles = (a.J + kBM - 1) / kBM;
+  const int64_t ntiles = mtiles * a.NB;
+  const int nk = (a.I + kBK - 1) / kBK;
+  auto A32 = [&](int s) { return sm + s * kStageBytesH; };
+  auto A_hi = [&](int s) { return sm + s * kStageBytesH + kA32Stage; };
+  auto A_lo = [&](int s) { return sm + s * kStageBytesH + kA32Stage + kA16Stage; };
+  auto B_hi = [&](int s) { return sm + s * kStageBytesH + kA32Stage + 2 * kA16Stage; };
+  auto B_lo = [&](int s) { return sm + s * kStageBytesH + kA32Stage + 2 * kA16Stage + kB16Stage; };
+  // scale of U: max |U| * 2^ea < 2^14
+  int ea = 0;
+  {
+    const float m = __uint_as_float(*amax_in);
+    if (m > 0.f && isfinite(m)) {
+      int e;
+      frexpf(m, &e);   // m = f 2^e, f in [0.5, 1)
+      ea = 14 - e;
+    }
+  }
+  const float uscale = ldexpf(1.f, ea);
+  const float oscale = ldexpf(1.f, -(ea + kWScaleExp));
+
+  if (tid == 0) {
+    for (int s = 0; s < kStagesH; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 64);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 128);
+    }
+    mbar_init(fin, 1);
+    *err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t bbytes = (uint32_t)a.NT * kBK * 2;
+
+  if (warp == 0) {
+    if (lane == 0) {   // producer
+      int64_t it = 0, issued = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int nb = (int)(t % a.NB);
+        const int j0 = (int)((t / a.NB) * kBM);
+        const int c0 = nb * a.NT;
+        for (int i = 0; i < nk; ++i, ++it) {
+          const int s = (int)(it % kStagesH);
+          const uint32_t use = (uint32_t)(it / kStagesH);
+          if (it >= kStagesH && !mbar_wait(&empty[s], (use - 1) & 1, err)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], (uint32_t)kA32Stage + 2u * bbytes);
+          tma_2d(A32(s), &tmU, i * kBK, j0, &full[s]);
+          tma_2d(B_hi(s), &tmWhi, i * kBK, c0, &full[s]);
+          tma_2d(B_lo(s), &tmWlo, i * kBK, c0, &full[s]);
+          issued = it + 1;
+        }
+      }
+      if (*err) {
+        for (int64_t q = issued > kStagesH ? issued - kStagesH : 0; q < issued; ++q) {
+          const int s = (int)(q % kStagesH);
+          for (uint32_t w = 0; w < kWaitLimit && !mbar_try(&full[s], (uint32_t)(q / kStagesH) & 1); ++w) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {   // MMA issuer
+      const uint32_t idesc = idesc_f16(kBM, a.NT);
+      int64_t it = 0, tl = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+        const int b = (int)(tl & 1);
+        const uint32_t ub = (uint32_t)(tl >> 1);
+        if (tl >= 2 && !mbar_wait(&acce[b], (ub - 1) & 1, err)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(b * 256);
+        for (int i = 0; i < nk; ++i, ++it) {
+          const int s = (int)(it % kStagesH);
+          if (!mbar_wait(&conv[s], (uint32_t)(it / kStagesH) & 1, err)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t ah = su32(A_hi(s)), al = su32(A_lo(s)), bh = su32(B_hi(s)), bl = su32(B_lo(s));
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {
+            const uint32_t off = kk * 32;   // 16 FP16 values
+            mma_f16(d, sw64_desc(ah + off), sw64_desc(bh + off), idesc, (i | kk) != 0);
+            mma_f16(d, sw64_desc(ah + off), sw64_desc(bl + off), idesc, 1u);
+            mma_f16(d, sw64_desc(al + off), sw64_desc(bh + off), idesc, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&accf[b]);
+      }
+      mma_commit(fin);
+      for (uint32_t w = 0; w < kWaitLimit && !mbar_try(fin, 0); ++w) {
+      }
+    }
+  } else if (warp < 4) {
+    // FP16 halves of the U tile: work item = (row r, 16-byte FP16 chunk q of 8 k-values)
+    const int ct = tid - 64;
+    int64_t it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int i = 0; i < nk; ++i, ++it) {
+        const int s = (int)(it % kStagesH);
+        if (!mbar_wait(&full[s], (uint32_t)(it / kStagesH) & 1, err)) {
+          ok = false;
+          break;
+        }
+        const unsigned char* src = A32(s);
+        unsigned char* hi = A_hi(s);
+        unsigned char* lo = A_lo(s);
+#pragma unroll 2
+        for (int w = ct; w < kBM * 4; w += 64) {
+          const int r = w >> 2, q = w & 3;
+          // FP32 chunks 2q and 2q+1 of row r in the 128-byte swizzled tile: chunk c sits at c ^ (r & 7)
+          const float4 x0 = *reinterpret_cast<const float4*>(src + r * 128 + (((2 * q) ^ (r & 7)) << 4));
+          const float4 x1 = *reinterpret_cast<const float4*>(src + r * 128 + (((2 * q + 1) ^ (r & 7)) << 4));
+          const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+          __align__(16) __half hv[8], lv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) split_f16(xv[u] * uscale, hv[u], lv[u]);
+          // FP16 chunk q of row r in the 64-byte swizzled tile sits at q ^ ((r >> 1) & 3)
+          const int dst = r * 64 + ((q ^ ((r >> 1) & 3)) << 4);
+          *reinterpret_cast<uint4*>(hi + dst) = *reinterpret_cast<const uint4*>(hv);
+          *reinterpret_cast<uint4*>(lo + dst) = *reinterpret_cast<const uint4*>(lv);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&conv[s]);
+      }
+    }
+  } else {
+    // epilogue: TMEM lanes 32 (warp - 4) .. + 31 hold rows j0 + those lanes of the tile
+    int64_t tl = 0;
+    float vmax = 0.f;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+      const int b = (int)(tl & 1);
+      if (!mbar_wait(&accf[b], (uint32_t)(tl >> 1) & 1, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int nb = (int)(t % a.NB);
+      const int64_t j0 = (t / a.NB) * kBM;
+      const int c0 = nb * a.NT;
+      const int rl = 32 * (warp - 4) + lane;
+      const int64_t j = j0 + rl;
+      const bool row_ok = j < a.J;
+      int64_t base = 0;
+      if (a.ystd && row_ok) {
+        int64_t rem = j;
+        for (int m = 0; m < a.N; ++m) {
+          if (m == a.n) continue;
+          const int64_t im = rem % a.dims[m];
+          rem /= a.dims[m];
+          base += im * a.st[m];
+        }
+      }
+      const int64_t stn = a.st[a.n];
+      for (int cc = 0; cc < a.NT; cc += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * (warp - 4)) << 16) + (uint32_t)(b * 256 + cc);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!row_ok) continue;
+        const int cb = c0 + cc;
+        float y[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          y[q] = __uint_as_float(v[q]) * oscale;
+          if (cb + q < a.I) vmax = fmaxf(vmax, fabsf(y[q]));
+        }
+        if (a.yunf) {
+          float* dst = a.yunf + j * a.I + cb;
+          if (cb + 16 <= a.I) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              reinterpret_cast<float4*>(dst)[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+          } else {
+            for (int q = 0; q < 16 && cb + q < a.I; ++q) dst[q] = y[q];
+          }
+        }
+        if (a.ystd) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (cb + q < a.I) a.ystd[base + (int64_t)(cb + q) * stn] = y[q];
+        }
+        if (a.ynext) {
+          const int64_t I2 = a.dims[1];
+          const int64_t i2 = j % I2, rest = j / I2;
+          float* dst = a.ynext + i2 + I2 * ((int64_t)a.I * rest + cb);
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (cb + q < a.I) dst[I2 * q] = y[q];
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&acce[b]);
+    }
+    if (amax_out) {   // the largest |entry| of the result: the next pass's scale
+      const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(vmax));
+      if (lane == 0 && m) atomicMax(amax_out, m);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+  if (tid == 0 && *err) atomicExch(a.err, 1);
+}
+
+// W (FP32, |w| <= 1) times 2^14 as FP16 halves: hi in out[0, n), lo in out[n, 2n).
+__global__ void k_split_f16(const float* __restrict__ w, __half* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  __half h, l;
+  split_f16(ldexpf(w[i], kWScaleExp), h, l);
+  out[i] = h;
+  out[n + i] = l;
+}
+
+// Largest |x| over a tensor (as the bit pattern of a non-negative float, for atomicMax).
+template <typename T>
+__global__ void __launch_bounds__(256) k_absmax(const T* __restrict__ X, int64_t P, unsigned* out) {
+  float m = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+    float x;
+    if constexpr (sizeof(T) == 2) x = __bfloat162float(X[i]);
+    else x = (float)X[i];
+    m = fmaxf(m, fabsf(x));
+  }
+  const unsigned r = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+  if ((threadIdx.x & 31) == 0 && r) atomicMax(out, r);
+}
+
 __global__ void k_split_tf32(const float* __restrict__ w, float* __restrict__ hi, float* __restrict__ lo, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -377,7 +686,91 @@ bool make_map(CUtensorMap* m, const float* base, int64_t inner, int64_t outer, i
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2D FP16 tensor map: rows of `inner` contiguous halves, `outer` rows, box {32, box_rows}, 64B swizzle.
+bool make_map16(CUtensorMap* m, const __half* base, int64_t inner, int64_t outer, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  const cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
+
+bool mix_tc16_supported(int dtype, int I) {
+  return dtype == CPR_F32 && I >= 1 && I % 8 == 0 && encode_fn() != nullptr;
+}
+
+cudaError_t launch_split_f16(const float* w, void* out16, int64_t n, cudaStream_t s) {
+  k_split_f16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, static_cast<__half*>(out16), n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_absmax(const void* X, int dtype, int64_t P, unsigned* out, cudaStream_t s) {
+  int64_t blocks = (P + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  switch (dtype) {
+    case CPR_F64: k_absmax<double><<<(unsigned)blocks, 256, 0, s>>>((const double*)X, P, out); break;
+    case CPR_F32: k_absmax<float><<<(unsigned)blocks, 256, 0, s>>>((const float*)X, P, out); break;
+    default: k_absmax<__nv_bfloat16><<<(unsigned)blocks, 256, 0, s>>>((const __nv_bfloat16*)X, P, out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mix_tc16(const float* U, float* ystd, float* yunf, float* ynext, const void* W16, int N,
+                            const int64_t* dims, int n, const unsigned* amax_in, unsigned* amax_out, int* err,
+                            cudaStream_t s) {
+  if (ynext && n != 0) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_mix_tc16, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemH);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  int64_t P = 1, st = 1;
+  for (int m = 0; m < N; ++m) {
+    a.dims[m] = dims[m];
+    a.st[m] = st;
+    st *= dims[m];
+    P *= dims[m];
+  }
+  const int I = (int)dims[n];
+  a.I = I;
+  a.J = P / I;
+  a.NB = (I + 255) / 256;
+  a.NT = ((I + a.NB - 1) / a.NB + 15) / 16 * 16;
+  a.three_x = 1;
+  a.n = n;
+  a.N = N;
+  a.ystd = ystd;
+  a.yunf = yunf;
+  a.ynext = ynext;
+  a.err = err;
+  const __half* Wh = static_cast<const __half*>(W16);
+  CUtensorMap mU, mH, mL;
+  if (!make_map(&mU, U, I, a.J, kBM) || !make_map16(&mH, Wh, I, I, a.NT) ||
+      !make_map16(&mL, Wh + (int64_t)I * I, I, I, a.NT))
+    return cudaErrorInvalidValue;
+  if (a.J > INT32_MAX) return cudaErrorInvalidValue;
+  const int64_t tiles = ((a.J + kBM - 1) / kBM) * a.NB;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                     cudaSuccess)
+      sms = 148;
+  }
+  const int64_t blocks = tiles < sms ? tiles : sms;
+  k_mix_tc16<<<(unsigned)blocks, kTcThreads, kTcSmemH, s>>>(mU, mH, mL, a, amax_in, amax_out);
+  return cudaGetLastError();
+}
 
 bool mix_tc_supported(int dtype, int I) { return dtype == CPR_F32 && I >= 1 && I % 4 == 0 && encode_fn() != nullptr; }
 
