@@ -247,8 +247,11 @@ CPR_API int cpr_fit_estimate(const cpr_tensor* X, const cpr_ktensor* K, int64_t 
                      void* stream);
 
 /* Mixing preprocess (Alg. 5, mixing step): out_dev = X x_1 F_1 D_1 ... x_N F_N D_N, mode 1
- * first, in X's dtype and layout (FP32 accumulation; FP64 for an FP64 tensor).  out_dev must
- * not overlap X.  ws from cpr_workspace_size(CPR_METHOD_CPRAND_MIX, ...) is enough. */
+ * first, in X's dtype and layout.  FP32 tensors: tensor-core mode products with both operands split
+ * into two halves (FP16 halves scaled by powers of two when every I_n is a multiple of 8, else TF32
+ * halves; about 2^-21 relative per product) accumulated in FP32; BF16 tensors: FP32 SIMT products;
+ * FP64 tensors: FP64.  out_dev must not overlap X.  ws from
+ * cpr_workspace_size(CPR_METHOD_CPRAND_MIX, ...) is enough. */
 CPR_API int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, uint32_t b, void* ws,
                    size_t ws_bytes, void* stream);
 

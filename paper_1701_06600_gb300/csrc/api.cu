@@ -394,7 +394,7 @@ cpr_opts defaults() {
 // Otherwise SIMT passes ping-pong between final and t1 so that the last lands in final.
 int enqueue_mixing(const void* src, void* final, void* t1, void* t2, void* rep_last, int dtype, int N,
                    const int64_t* dims, float* const* W32, float* const* Wlo, double* const* W64, int* err,
-                   unsigned* amax, cudaStream_t s, int64_t& launches, bool* wrote_rep_last) {
+                   unsigned* amax, bool amax0_ready, cudaStream_t s, int64_t& launches, bool* wrote_rep_last) {
   bool tc = dtype == CPR_F32 && t2 != nullptr;
   for (int n = 0; n < N && tc; ++n) tc = Wlo[n] != nullptr && mix_tc_supported(dtype, (int)dims[n]);
   bool tc16 = tc && amax != nullptr;
@@ -405,8 +405,10 @@ int enqueue_mixing(const void* src, void* final, void* t1, void* t2, void* rep_l
     // floats); amax[n] = largest |entry| of pass n's input (the input tensor's from a max pass)
     int64_t P = 1;
     for (int n = 0; n < N; ++n) P *= dims[n];
-    CPR_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned) * (size_t)(N + 1), s));
-    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_absmax(src, dtype, P, amax, s));
+    if (!amax0_ready) {   // else the norm pass already recorded amax[0] (and cleared the rest)
+      CPR_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned) * (size_t)(N + 1), s));
+      CPR_LAUNCH(CPR_KERNEL_OTHER, launch_absmax(src, dtype, P, amax, s));
+    }
     for (int n = 0; n < N; ++n)
       CPR_LAUNCH(CPR_KERNEL_OTHER, launch_split_f16(W32[n], Wlo[n], dims[n] * dims[n], s));
     const float* U = static_cast<const float*>(src);
@@ -573,8 +575,11 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
   for (int b = 0; b < B; ++b) {
     const Prob& p = pl.probs[b];
     bool rep_last_done = false;
-    // ||X|| on the caller's tensor (equal to the mixed tensor's norm, Alg. 5)
-    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq(Xs[b].data, p.dtype, p.P, pl.d_normpart, pl.normblk, s));
+    // ||X|| on the caller's tensor (equal to the mixed tensor's norm, Alg. 5); for CPRAND-MIX the same
+    // pass records the largest |x| (the scale of the first FP16-split mixing pass)
+    unsigned* amax = mix ? reinterpret_cast<unsigned*>(pl.d_counter + 4) : nullptr;
+    if (amax) CPR_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned) * (size_t)(p.N + 1), s));
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq(Xs[b].data, p.dtype, p.P, pl.d_normpart, pl.normblk, s, amax));
     CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq_finish(pl.d_normpart, pl.normblk, nullptr, pl.d_states + b, 1, s));
     if (mix) {
       const MixBufs& mb = pl.mixb[b];
@@ -583,8 +588,8 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
                                                          mb.F64[n], mb.sg[n], s));
       if (int st = enqueue_mixing(Xs[b].data, mb.xhat, pl.d_tmp, pl.d_tmp2,
                                   p.use_rep ? const_cast<void*>(p.Xrep[p.N - 1]) : nullptr, p.dtype, p.N, p.dims,
-                                  mb.W32, mb.Wlo, mb.W64, pl.d_counter + 2,
-                                  reinterpret_cast<unsigned*>(pl.d_counter + 4), s, launches, &rep_last_done))
+                                  mb.W32, mb.Wlo, mb.W64, pl.d_counter + 2, amax, true, s, launches,
+                                  &rep_last_done))
         return st;
     }
     if (p.use_rep)
@@ -683,14 +688,22 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
   // outputs (unmixed for CPRAND-MIX)
   for (int b = 0; b < B; ++b) {
     const Prob& p = pl.probs[b];
-    for (int n = 0; n < p.N; ++n) {
-      if (mix) {
-        CPR_LAUNCH(CPR_KERNEL_OTHER, launch_unmix(p.A64[n], outs[b].factors[n], pl.mixb[b].F64[n], pl.mixb[b].sg[n],
-                                                  (int)p.dims[n], p.R, s));
-      } else {
+    if (mix) {
+      UnmixArgs u{};
+      u.N = p.N;
+      u.R = p.R;
+      for (int n = 0; n < p.N; ++n) {
+        u.Ahat[n] = p.A64[n];
+        u.A[n] = outs[b].factors[n];
+        u.F[n] = pl.mixb[b].F64[n];
+        u.sg[n] = pl.mixb[b].sg[n];
+        u.I[n] = (int)p.dims[n];
+      }
+      CPR_LAUNCH(CPR_KERNEL_OTHER, launch_unmix_all(u, s));
+    } else {
+      for (int n = 0; n < p.N; ++n)
         CPR_CUDA(cudaMemcpyAsync(outs[b].factors[n], p.A64[n], sizeof(double) * p.dims[n] * p.R,
                                  cudaMemcpyDeviceToDevice, s));
-      }
     }
     CPR_CUDA(cudaMemcpyAsync(outs[b].lambda, p.lambda, sizeof(double) * p.R, cudaMemcpyDeviceToDevice, s));
   }
@@ -1102,7 +1115,7 @@ int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, uint32_t b
                launch_build_mix_ops((int)X->dims[n], seed, b, n, table, W32[n], W64[n], F64[n], sg[n], s));
   bool unused = false;
   if (int st = enqueue_mixing(X->data, out_dev, tmp, tmp2, nullptr, dt, N, X->dims, W32, Wlo, W64, derr,
-                              reinterpret_cast<unsigned*>(derr + 4), s, launches, &unused))
+                              reinterpret_cast<unsigned*>(derr + 4), false, s, launches, &unused))
     return st;
   return CPR_OK;
 }

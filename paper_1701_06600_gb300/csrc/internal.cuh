@@ -261,7 +261,8 @@ int loop_rep_smem_bytes(const Prob* probs_host, int B);
 int loop_rep_capacity(int dtype, int smem, int maxR);
 cudaError_t launch_loop_rep(const Prob* probs, int B, int* queue, int dtype, int smem, int nclusters, int maxR,
                             cudaStream_t s);
-cudaError_t launch_sumsq(const void* X, int dtype, int64_t P, double* part, int nblk, cudaStream_t s);
+cudaError_t launch_sumsq(const void* X, int dtype, int64_t P, double* part, int nblk, cudaStream_t s,
+                         unsigned* amax = nullptr);
 cudaError_t launch_sumsq_finish(const double* part, int nblk, double* out_norm, State* st,
                                 int nstates, cudaStream_t s);
 int sumsq_blocks(int64_t P);
@@ -324,5 +325,15 @@ cudaError_t launch_mix_mode(const void* X, void* Y, int dtype, int N, const int6
                             const float* W32, const double* W64, cudaStream_t s);
 cudaError_t launch_unmix(const double* Ahat, double* A, const double* F64, const double* signs,
                          int I, int R, cudaStream_t s);
+struct UnmixArgs {        // every mode of one problem: A[n] = D_n F_n^T Ahat[n]
+  const double* Ahat[kMaxOrder];
+  double* A[kMaxOrder];
+  const double* F[kMaxOrder];
+  const double* sg[kMaxOrder];
+  int I[kMaxOrder];
+  int first_block[kMaxOrder];   // filled by the launcher
+  int N, R;
+};
+cudaError_t launch_unmix_all(const UnmixArgs& u, cudaStream_t s);
 
 }  // namespace cpr

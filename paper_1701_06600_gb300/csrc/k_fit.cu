@@ -153,11 +153,13 @@ int sumsq_blocks(int64_t P) {
 }
 
 // Each thread keeps 8 independent loads in flight (16-byte vectors where the data allows); squares
-// are summed in FP32 within a vector and folded into an FP64 accumulator.
+// are summed in FP32 within a vector and folded into an FP64 accumulator.  When amax is given, the
+// largest |x| is also recorded there (as the bit pattern of a non-negative float, for atomicMax).
 template <typename T>
-__global__ void __launch_bounds__(256) k_sumsq(const T* __restrict__ X, int64_t P, double* part) {
+__global__ void __launch_bounds__(256) k_sumsq(const T* __restrict__ X, int64_t P, double* part, unsigned* amax) {
   __shared__ double red[8];
   double acc = 0.0;
+  float mx = 0.f;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   constexpr int VEC = 16 / sizeof(T);   // elements per 16-byte vector
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(256) k_sumsq(const T* __restrict__ X, int64_t 
       if constexpr (sizeof(T) == 8) {
         acc = fma((double)e[0], (double)e[0], acc);
         acc = fma((double)e[1], (double)e[1], acc);
+        mx = fmaxf(mx, fmaxf(fabsf((float)e[0]), fabsf((float)e[1])));
       } else {
         float f = 0.0f;
 #pragma unroll
@@ -183,6 +186,7 @@ __global__ void __launch_bounds__(256) k_sumsq(const T* __restrict__ X, int64_t 
           if constexpr (sizeof(T) == 4) x = e[w];
           else x = __bfloat162float(e[w]);
           f = fmaf(x, x, f);
+          mx = fmaxf(mx, fabsf(x));
         }
         acc += (double)f;
       }
@@ -196,6 +200,7 @@ __global__ void __launch_bounds__(256) k_sumsq(const T* __restrict__ X, int64_t 
       if constexpr (sizeof(T) == 2) x = (double)__bfloat162float(e[w]);
       else x = (double)e[w];
       acc = fma(x, x, acc);
+      mx = fmaxf(mx, fabsf((float)x));
     }
   }
   for (int64_t i = nvec * VEC + tid; i < P; i += nthr) {   // tail (or everything if unaligned)
@@ -203,16 +208,22 @@ __global__ void __launch_bounds__(256) k_sumsq(const T* __restrict__ X, int64_t 
     if constexpr (sizeof(T) == 2) x = (double)__bfloat162float(X[i]);
     else x = (double)X[i];
     acc = fma(x, x, acc);
+    mx = fmaxf(mx, fabsf((float)x));
+  }
+  if (amax) {
+    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(amax, m);
   }
   const double t = block_sum(acc, red);
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-cudaError_t launch_sumsq(const void* X, int dtype, int64_t P, double* part, int nblk, cudaStream_t s) {
+cudaError_t launch_sumsq(const void* X, int dtype, int64_t P, double* part, int nblk, cudaStream_t s,
+                         unsigned* amax) {
   switch (dtype) {
-    case CPR_F64: k_sumsq<double><<<nblk, 256, 0, s>>>((const double*)X, P, part); break;
-    case CPR_F32: k_sumsq<float><<<nblk, 256, 0, s>>>((const float*)X, P, part); break;
-    default: k_sumsq<__nv_bfloat16><<<nblk, 256, 0, s>>>((const __nv_bfloat16*)X, P, part);
+    case CPR_F64: k_sumsq<double><<<nblk, 256, 0, s>>>((const double*)X, P, part, amax); break;
+    case CPR_F32: k_sumsq<float><<<nblk, 256, 0, s>>>((const float*)X, P, part, amax); break;
+    default: k_sumsq<__nv_bfloat16><<<nblk, 256, 0, s>>>((const __nv_bfloat16*)X, P, part, amax);
   }
   return cudaGetLastError();
 }

@@ -227,41 +227,87 @@ cudaError_t launch_unfold_copy(const void* X, void* Y, int dtype, int N, const i
   return cudaGetLastError();
 }
 
-// A = D F^T A^ in FP64 (Alg. 5, unmixing).  FP64 arithmetic is the bound here, so the work is
-// spread over the whole GPU: a block computes 4 rows of A (4R outputs), each output's dot product
-// of length I is split over ks lanes (k = s, s + ks, ...) whose partials are summed by a fixed
-// butterfly of shuffles; F and A^ are read through the read-only cache (both are L2-resident).
-constexpr int kUnmixRows = 4;
-__global__ void __launch_bounds__(256) k_unmix(const double* __restrict__ Ahat, double* __restrict__ A,
-                                               const double* __restrict__ F64, const double* __restrict__ signs,
-                                               int I, int R) {
-  const int i0 = blockIdx.x * kUnmixRows;
-  const int nout = kUnmixRows * R;
-  int ks = 1;   // lanes per output: a power of two (a divisor of the warp width)
+// A = D F^T A^ in FP64 (Alg. 5, unmixing) for every mode in one launch.  FP64 arithmetic bounds it,
+// so the work is spread over the whole GPU: a block computes 8 rows i of one mode's A (8R outputs);
+// chunks of 32 k of F (8 consecutive entries of each row k: 64 contiguous bytes) and of A^ (R
+// contiguous entries per row) are staged in shared memory; each output's sum over k is split over
+// ks threads (a power of two) whose partials are combined by a fixed butterfly of shuffles.
+constexpr int kUnmixRows = 8, kUnmixK = 32;
+__global__ void __launch_bounds__(256) k_unmix(UnmixArgs u) {
+  __shared__ double Fc[kUnmixK][kUnmixRows];
+  __shared__ double Ac[kUnmixK][kMaxRank];
+  int n = 0;
+  while (n + 1 < u.N && (int)blockIdx.x >= u.first_block[n + 1]) ++n;
+  const int I = u.I[n], R = u.R;
+  const int i0 = ((int)blockIdx.x - u.first_block[n]) * kUnmixRows;
+  const double* __restrict__ F = u.F[n];
+  const double* __restrict__ Ah = u.Ahat[n];
+  const int nout = kUnmixRows * R;   // up to 512: two output groups of blockDim.x / ks
+  int ks = 1;
   while (ks < 32 && ks * 2 * nout <= (int)blockDim.x) ks *= 2;
-  const int t = threadIdx.x, o = t / ks, s = t - o * ks;
-  const int ii = o / R, r = o - ii * R, i = i0 + ii;
-  const bool valid = o < nout && i < I;
-  double a0 = 0.0, a1 = 0.0;
-  if (valid) {
-    const double* f = F64 + i;     // F[k][i] at k * I + i
-    const double* ah = Ahat + r;   // A^[k][r] at k * R + r
-    int k = s;
-    for (; k + ks < I; k += 2 * ks) {
-      a0 = fma(__ldg(f + (int64_t)k * I), __ldg(ah + (int64_t)k * R), a0);
-      a1 = fma(__ldg(f + (int64_t)(k + ks) * I), __ldg(ah + (int64_t)(k + ks) * R), a1);
+  const int t = threadIdx.x, s = t % ks, og = (int)blockDim.x / ks;
+  double a0[2] = {0.0, 0.0}, a1[2] = {0.0, 0.0};
+  for (int k0 = 0; k0 < I; k0 += kUnmixK) {
+    const int kc = min(kUnmixK, I - k0);
+    for (int e = t; e < kUnmixK * kUnmixRows; e += blockDim.x) {
+      const int kk = e / kUnmixRows, q = e - kk * kUnmixRows;
+      Fc[kk][q] = (kk < kc && i0 + q < I) ? F[(int64_t)(k0 + kk) * I + i0 + q] : 0.0;
     }
-    if (k < I) a0 = fma(__ldg(f + (int64_t)k * I), __ldg(ah + (int64_t)k * R), a0);
+    for (int e = t; e < kc * R; e += blockDim.x) {
+      const int kk = e / R, c = e - kk * R;
+      Ac[kk][c] = Ah[(int64_t)(k0 + kk) * R + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int o = t / ks + g * og;
+      if (o < nout) {
+        const int ii = o / R, r = o - ii * R;
+        int kk = s;
+        for (; kk + ks < kc; kk += 2 * ks) {
+          a0[g] = fma(Fc[kk][ii], Ac[kk][r], a0[g]);
+          a1[g] = fma(Fc[kk + ks][ii], Ac[kk + ks][r], a1[g]);
+        }
+        if (kk < kc) a0[g] = fma(Fc[kk][ii], Ac[kk][r], a0[g]);
+      }
+    }
+    __syncthreads();
   }
-  double acc = a0 + a1;
-  for (int w = 1; w < ks; w <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
-  if (valid && s == 0) A[(int64_t)i * R + r] = signs[i] * acc;
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const int o = t / ks + g * og;
+    double acc = a0[g] + a1[g];
+    for (int w = 1; w < ks; w <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
+    if (o < nout && s == 0) {
+      const int ii = o / R, r = o - ii * R, i = i0 + ii;
+      if (i < I) u.A[n][(int64_t)i * R + r] = u.sg[n][i] * acc;
+    }
+  }
+}
+
+cudaError_t launch_unmix_all(const UnmixArgs& u_in, cudaStream_t s) {
+  UnmixArgs u = u_in;
+  int blocks = 0;
+  for (int n = 0; n < u.N; ++n) {
+    u.first_block[n] = blocks;
+    blocks += (u.I[n] + kUnmixRows - 1) / kUnmixRows;
+  }
+  if (blocks <= 0) return cudaSuccess;
+  k_unmix<<<blocks, 256, 0, s>>>(u);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_unmix(const double* Ahat, double* A, const double* F64, const double* signs, int I, int R,
                          cudaStream_t s) {
-  k_unmix<<<(I + kUnmixRows - 1) / kUnmixRows, 256, 0, s>>>(Ahat, A, F64, signs, I, R);
-  return cudaGetLastError();
+  UnmixArgs u{};
+  u.N = 1;
+  u.R = R;
+  u.Ahat[0] = Ahat;
+  u.A[0] = A;
+  u.F[0] = F64;
+  u.sg[0] = signs;
+  u.I[0] = I;
+  return launch_unmix_all(u, s);
 }
 
 }  // namespace cpr

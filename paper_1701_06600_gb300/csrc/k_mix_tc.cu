@@ -362,13 +362,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (tid == 0 && *err) atomicExch(a.err, 1);
 }
 
-constexpr int kStagesH = 3;
+constexpr int kStagesA = 4;                     // FP32 U staging ring (refilled as soon as it is converted)
+constexpr int kStagesO = 3;                     // operand ring (FP16 halves of U and W, consumed by the MMAs)
 constexpr int kA32Stage = kBM * kBK * 4;        // 16 KB: the FP32 U tile as TMA lands it (128B swizzle)
 constexpr int kA16Stage = kBM * kBK * 2;        // 8 KB: one FP16 half of the U tile (64B swizzle)
 constexpr int kB16Stage = 256 * kBK * 2;        // 16 KB: one FP16 half of the W tile (room for NT = 256)
-constexpr int kStageBytesH = kA32Stage + 2 * kA16Stage + 2 * kB16Stage;   // 64 KB
-constexpr int kBarOffsetH = kStagesH * kStageBytesH;
+constexpr int kOpStage = 2 * kA16Stage + 2 * kB16Stage;   // 48 KB
+constexpr int kOpOffset = kStagesA * kA32Stage;           // 64 KB
+constexpr int kBarOffsetH = kOpOffset + kStagesO * kOpStage;   // 208 KB
 constexpr int kTcSmemH = kBarOffsetH + 256 + 1024;
+constexpr int kConvWarps = 6;                   // converter warps (8 .. 13)
+constexpr int kTcThreadsH = (8 + kConvWarps) * 32;   // 14 warps
 constexpr int kWScaleExp = 14;                  // W (|w| <= 1) is stored times 2^14 in FP16
 
 // The same persistent mode-n product with both operands split into FP16 halves and three
@@ -376,32 +380,38 @@ constexpr int kWScaleExp = 14;                  // W (|w| <= 1) is stored times 
 // split at the same accuracy.  U is scaled by 2^ea so that max |U| < 2^14 (ea from *amax_in, the
 // largest |entry| of the pass's input), W by 2^14 (pre-split in global memory); the epilogue undoes
 // both scalings exactly and, when amax_out is set, records the largest |entry| of the result (the
-// next pass's scale).  Three pipeline stages of 32 k-values: the FP32 tile lands by TMA, warps 2-3
-// write its FP16 halves in the 64-byte swizzled layout the MMA reads.
-__global__ void __launch_bounds__(kTcThreads, 1)
+// next pass's scale).  Two rings: the FP32 U tiles (HBM) land in a 4-deep staging ring that is
+// released as soon as they are converted, so their loads run far ahead of the MMAs; the FP16 halves
+// of U (written by the converter warps in the 64-byte swizzled layout the MMA reads) and of W (TMA)
+// fill a 3-deep operand ring released by the MMAs.
+//   warp 0: U producer   warp 1: TMEM owner and MMA issuer   warp 2: W producer
+//   warps 4-7: epilogue (TMEM lane quarters 0-3)   warps 8-13: converter   warp 3: idle
+__global__ void __launch_bounds__(kTcThreadsH, 1)
     k_mix_tc16(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmWhi,
                const __grid_constant__ CUtensorMap tmWlo, TcArgs a, const unsigned* __restrict__ amax_in,
                unsigned* amax_out) {
   extern __shared__ unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kBarOffsetH);
-  uint64_t* full = bars;
-  uint64_t* conv = bars + kStagesH;
-  uint64_t* empty = bars + 2 * kStagesH;
-  uint64_t* accf = bars + 3 * kStagesH;
-  uint64_t* acce = accf + 2;
-  uint64_t* fin = acce + 2;
+  uint64_t* a_full = bars;                        // U tile landed (1 arrival + tx)
+  uint64_t* a_empty = a_full + kStagesA;          // U tile converted (one arrival per converter thread)
+  uint64_t* w_full = a_empty + kStagesA;          // W halves landed (1 arrival + tx)
+  uint64_t* conv = w_full + kStagesO;             // U halves written (one arrival per converter thread)
+  uint64_t* o_empty = conv + kStagesO;            // MMAs done with the operand stage (tcgen05.commit)
+  uint64_t* accf = o_empty + kStagesO;            // accumulator buffer b complete, 2 buffers
+  uint64_t* acce = accf + 2;                      // accumulator buffer b drained (128 arrivals), 2 buffers
+  uint64_t* fin = acce + 2;                       // every MMA issued by this CTA complete
   uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* err = reinterpret_cast<volatile int*>(fin + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t mtiles = (a.J + kBM - 1) / kBM;
   const int64_t ntiles = mtiles * a.NB;
   const int nk = (a.I + kBK - 1) / kBK;
-  auto A32 = [&](int s) { return sm + s * kStageBytesH; };
-  auto A_hi = [&](int s) { return sm + s * kStageBytesH + kA32Stage; };
-  auto A_lo = [&](int s) { return sm + s * kStageBytesH + kA32Stage + kA16Stage; };
-  auto B_hi = [&](int s) { return sm + s * kStageBytesH + kA32Stage + 2 * kA16Stage; };
-  auto B_lo = [&](int s) { return sm + s * kStageBytesH + kA32Stage + 2 * kA16Stage + kB16Stage; };
+  auto A32 = [&](int s) { return sm + s * kA32Stage; };
+  auto A_hi = [&](int s) { return sm + kOpOffset + s * kOpStage; };
+  auto A_lo = [&](int s) { return sm + kOpOffset + s * kOpStage + kA16Stage; };
+  auto B_hi = [&](int s) { return sm + kOpOffset + s * kOpStage + 2 * kA16Stage; };
+  auto B_lo = [&](int s) { return sm + kOpOffset + s * kOpStage + 2 * kA16Stage + kB16Stage; };
   // scale of U: max |U| * 2^ea < 2^14
   int ea = 0;
   {
@@ -416,10 +426,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const float oscale = ldexpf(1.f, -(ea + kWScaleExp));
 
   if (tid == 0) {
-    for (int s = 0; s < kStagesH; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 64);
-      mbar_init(&empty[s], 1);
+    for (int s = 0; s < kStagesA; ++s) {
+      mbar_init(&a_full[s], 1);
+      mbar_init(&a_empty[s], 32 * kConvWarps);
+    }
+    for (int s = 0; s < kStagesO; ++s) {
+      mbar_init(&w_full[s], 1);
+      mbar_init(&conv[s], 32 * kConvWarps);
+      mbar_init(&o_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
@@ -439,8 +453,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmem = *tslot;
   const uint32_t bbytes = (uint32_t)a.NT * kBK * 2;
 
-  if (warp == 0) {
-    if (lane == 0) {   // producer
+  if (warp == 0 || warp == 2) {
+    if (lane == 0) {   // producers: U tiles (warp 0) and W halves (warp 2), each in its own ring
+      const bool isU = warp == 0;
+      const int S = isU ? kStagesA : kStagesO;
+      uint64_t* fullb = isU ? a_full : w_full;
+      uint64_t* emptyb = isU ? a_empty : o_empty;
       int64_t it = 0, issued = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -448,23 +466,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int j0 = (int)((t / a.NB) * kBM);
         const int c0 = nb * a.NT;
         for (int i = 0; i < nk; ++i, ++it) {
-          const int s = (int)(it % kStagesH);
-          const uint32_t use = (uint32_t)(it / kStagesH);
-          if (it >= kStagesH && !mbar_wait(&empty[s], (use - 1) & 1, err)) {
+          const int s = (int)(it % S);
+          const uint32_t use = (uint32_t)(it / S);
+          if (it >= S && !mbar_wait(&emptyb[s], (use - 1) & 1, err)) {
             ok = false;
             break;
           }
-          mbar_expect_tx(&full[s], (uint32_t)kA32Stage + 2u * bbytes);
-          tma_2d(A32(s), &tmU, i * kBK, j0, &full[s]);
-          tma_2d(B_hi(s), &tmWhi, i * kBK, c0, &full[s]);
-          tma_2d(B_lo(s), &tmWlo, i * kBK, c0, &full[s]);
+          if (isU) {
+            mbar_expect_tx(&fullb[s], (uint32_t)kA32Stage);
+            tma_2d(A32(s), &tmU, i * kBK, j0, &fullb[s]);
+          } else {
+            mbar_expect_tx(&fullb[s], 2u * bbytes);
+            tma_2d(B_hi(s), &tmWhi, i * kBK, c0, &fullb[s]);
+            tma_2d(B_lo(s), &tmWlo, i * kBK, c0, &fullb[s]);
+          }
           issued = it + 1;
         }
       }
-      if (*err) {
-        for (int64_t q = issued > kStagesH ? issued - kStagesH : 0; q < issued; ++q) {
-          const int s = (int)(q % kStagesH);
-          for (uint32_t w = 0; w < kWaitLimit && !mbar_try(&full[s], (uint32_t)(q / kStagesH) & 1); ++w) {
+      if (*err) {   // never leave copies in flight: wait (bounded) for the last ones issued
+        for (int64_t q = issued > S ? issued - S : 0; q < issued; ++q) {
+          const int s = (int)(q % S);
+          for (uint32_t w = 0; w < kWaitLimit && !mbar_try(&fullb[s], (uint32_t)(q / S) & 1); ++w) {
           }
         }
       }
@@ -484,8 +506,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(b * 256);
         for (int i = 0; i < nk; ++i, ++it) {
-          const int s = (int)(it % kStagesH);
-          if (!mbar_wait(&conv[s], (uint32_t)(it / kStagesH) & 1, err)) {
+          const int s = (int)(it % kStagesO);
+          const uint32_t ph = (uint32_t)(it / kStagesO) & 1;
+          if (!mbar_wait(&conv[s], ph, err) || !mbar_wait(&w_full[s], ph, err)) {
             ok = false;
             break;
           }
@@ -498,7 +521,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mma_f16(d, sw64_desc(ah + off), sw64_desc(bl + off), idesc, 1u);
             mma_f16(d, sw64_desc(al + off), sw64_desc(bh + off), idesc, 1u);
           }
-          mma_commit(&empty[s]);
+          mma_commit(&o_empty[s]);
         }
         if (ok) mma_commit(&accf[b]);
       }
@@ -506,41 +529,50 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (uint32_t w = 0; w < kWaitLimit && !mbar_try(fin, 0); ++w) {
       }
     }
-  } else if (warp < 4) {
-    // FP16 halves of the U tile: work item = (row r, 16-byte FP16 chunk q of 8 k-values)
-    const int ct = tid - 64;
+  } else if (warp >= 8) {
+    // converter (32 kConvWarps threads): FP16 halves of the U tile; work item = (row r, FP16 chunk q)
+    const int ct = tid - 256;
     int64_t it = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       for (int i = 0; i < nk; ++i, ++it) {
-        const int s = (int)(it % kStagesH);
-        if (!mbar_wait(&full[s], (uint32_t)(it / kStagesH) & 1, err)) {
+        const int sa = (int)(it % kStagesA), so = (int)(it % kStagesO);
+        if (!mbar_wait(&a_full[sa], (uint32_t)(it / kStagesA) & 1, err) ||
+            (it >= kStagesO && !mbar_wait(&o_empty[so], (uint32_t)(it / kStagesO - 1) & 1, err))) {
           ok = false;
           break;
         }
-        const unsigned char* src = A32(s);
-        unsigned char* hi = A_hi(s);
-        unsigned char* lo = A_lo(s);
+        const unsigned char* src = A32(sa);
+        unsigned char* hi = A_hi(so);
+        unsigned char* lo = A_lo(so);
 #pragma unroll 2
-        for (int w = ct; w < kBM * 4; w += 64) {
+        for (int w = ct; w < kBM * 4; w += 32 * kConvWarps) {
           const int r = w >> 2, q = w & 3;
           // FP32 chunks 2q and 2q+1 of row r in the 128-byte swizzled tile: chunk c sits at c ^ (r & 7)
           const float4 x0 = *reinterpret_cast<const float4*>(src + r * 128 + (((2 * q) ^ (r & 7)) << 4));
           const float4 x1 = *reinterpret_cast<const float4*>(src + r * 128 + (((2 * q + 1) ^ (r & 7)) << 4));
-          const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-          __align__(16) __half hv[8], lv[8];
+          const float xv[8] = {x0.x * uscale, x0.y * uscale, x0.z * uscale, x0.w * uscale,
+                               x1.x * uscale, x1.y * uscale, x1.z * uscale, x1.w * uscale};
+          uint32_t hw[4], lw[4];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) split_f16(xv[u] * uscale, hv[u], lv[u]);
+          for (int u = 0; u < 4; ++u) {
+            const __half2 h2 = __floats2half2_rn(xv[2 * u], xv[2 * u + 1]);
+            const float2 hf = __half22float2(h2);
+            const __half2 l2 = __floats2half2_rn(xv[2 * u] - hf.x, xv[2 * u + 1] - hf.y);
+            hw[u] = *reinterpret_cast<const uint32_t*>(&h2);
+            lw[u] = *reinterpret_cast<const uint32_t*>(&l2);
+          }
           // FP16 chunk q of row r in the 64-byte swizzled tile sits at q ^ ((r >> 1) & 3)
           const int dst = r * 64 + ((q ^ ((r >> 1) & 3)) << 4);
-          *reinterpret_cast<uint4*>(hi + dst) = *reinterpret_cast<const uint4*>(hv);
-          *reinterpret_cast<uint4*>(lo + dst) = *reinterpret_cast<const uint4*>(lv);
+          *reinterpret_cast<uint4*>(hi + dst) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(lo + dst) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&conv[s]);
+        mbar_arrive(&a_empty[sa]);
+        mbar_arrive(&conv[so]);
       }
     }
-  } else {
+  } else if (warp >= 4) {
     // epilogue: TMEM lanes 32 (warp - 4) .. + 31 hold rows j0 + those lanes of the tile
     int64_t tl = 0;
     float vmax = 0.f;
@@ -768,7 +800,7 @@ cudaError_t launch_mix_tc16(const float* U, float* ystd, float* yunf, float* yne
       sms = 148;
   }
   const int64_t blocks = tiles < sms ? tiles : sms;
-  k_mix_tc16<<<(unsigned)blocks, kTcThreads, kTcSmemH, s>>>(mU, mH, mL, a, amax_in, amax_out);
+  k_mix_tc16<<<(unsigned)blocks, kTcThreadsH, kTcSmemH, s>>>(mU, mH, mL, a, amax_in, amax_out);
   return cudaGetLastError();
 }
 

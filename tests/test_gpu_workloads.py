@@ -161,3 +161,19 @@ def test_1500_cubed_mix_run_fit_estimate_matches_exact_fit(cb, big):
     assert np.all(np.isfinite(tr)) and tr[1] > tr[0]
     # the sampled estimate over 2^14 fixed entries tracks the exact fit (Sec. 3.4)
     assert abs(tr[1] - f_true) < 2e-3, (tr[1], f_true)
+
+
+def test_1500_cubed_cp_als_exact_fit_matches_direct_evaluation(cb, big):
+    # the exact CP-ALS (Alg. 1) baseline on the same tensor: its fit, formed from the last MTTKRP and
+    # the Gram matrices without another pass over X, equals the fit of its factors evaluated
+    # directly; the timings of both methods are printed side by side
+    dims, X = big
+    R = 50
+    out = cb.cpr_cp_als(X, dims, R, opts=cb.cpr_default_opts(seed=2005, fixed_iters=2))
+    assert out["status"] == cb.OK and out["iters"] == 2
+    f_direct = true_fit_device(X, dims, out["lam"], out["factors"])
+    mix = cb.cpr_cprand_mix(X, dims, R, 2000, opts=cb.cpr_default_opts(seed=2005, fixed_iters=2))
+    print("1500^3 R=50, 2 outer iterations: CP-ALS setup %.1f ms, iterations %.1f ms (exact fit %.6f); "
+          "CPRAND-MIX setup %.1f ms, iterations %.1f ms"
+          % (out["ms_setup"], out["ms_iterate"], out["fit_est"], mix["ms_setup"], mix["ms_iterate"]))
+    assert abs(out["fit_est"] - f_direct) < 1e-6, (out["fit_est"], f_direct)
