@@ -137,17 +137,23 @@ def kernel_traffic(cls):
     return None
 
 
+MIX_KERNEL = ("k_mix_fft (factored DCT-II: mixed-radix Stockham FFT of BJ fibers in shared memory, "
+              "writes the next pass's unfolding layout)")
+
+
 def algorithmic(cls, w, P, b, iters_per_launch=None):
     """Algorithmic bytes and flops of ONE launch of a kernel class on this workload.
 
-    mix: one mode-n product, reads and writes the tensor once (2 P b bytes), 2 I_n P flops.
+    mix: one mode-n pass of the factored DCT: reads the tensor once and writes it once, the last of
+    the N passes also writes the mode-N unfolding copy the gathers read: (2N + 1) P b / N bytes per
+    launch on average.
     loop: the whole iteration loop of one decomposition; per outer iteration and mode the sampled
     fibers (S I_n b bytes), plus the fit entries' values once (P_hat 8 bytes); flops 2 S R I_n per
     mode."""
     dims, R, S, Ph = w["dims"], w["R"], w["S"], w["P_hat"]
     N = len(dims)
     if cls == "mix":
-        return {"bytes": 2.0 * P * b, "flops": 2.0 * dims[0] * P}
+        return {"bytes": (2.0 * N + 1.0) * P * b / N, "flops": None}
     if cls == "loop" and iters_per_launch:
         # DRAM-relevant bytes: the sampled fibers (the factor rows and the fit entries' rows are
         # L2-resident); the fit values are read once per decomposition
@@ -447,18 +453,11 @@ def run_ours(args, rank, world, local_rank):
     if alg is not None and dom_n > 0:
         per_launch_s = dom_ms / dom_n / 1e3
         if dom == "mix":
-            # tcgen05 kind::tf32 with the 3xTF32 split: three tensor-core products per algorithmic
-            # multiply-add; peak = TF32 dense = measured BF16 (sustained, timed inside a long step) x
-            # the nominal TF32/BF16 ratio 1.1/2.25
-            peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * (1.1 / 2.25)
-            ach = 3.0 * alg["flops"] / per_launch_s / 1e12
-            roof = {"bound": "tensor", "kernel": "k_mix_tc (tcgen05 kind::tf32, 3xTF32 split, mode-n DCT product)",
-                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "peak_source": "%s bf16 sustained x 1.1/2.25" % pk_src,
-                    "achieved_note": "executed TF32 tensor flops = 3 x algorithmic (2 I_n P per launch)",
-                    "traffic": kernel_traffic("mix"), "per_launch_ms": dom_ms / dom_n,
-                    "algorithmic_bytes": alg["bytes"], "algorithmic_flops": alg["flops"],
-                    "hbm_frac": alg["bytes"] / per_launch_s / 1e9 / pk["hbm_gbs"]}
+            ach = alg["bytes"] / per_launch_s / 1e9
+            roof = {"bound": "hbm", "kernel": MIX_KERNEL,
+                    "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                    "peak_source": pk_src, "traffic": kernel_traffic("mix"), "per_launch_ms": dom_ms / dom_n,
+                    "algorithmic_bytes": alg["bytes"], "algorithmic_flops": None}
         else:
             ach = alg["bytes"] / per_launch_s / 1e9
             roof = {"bound": "hbm", "kernel": "k_loop_rep (whole iteration loop in one 16-CTA cluster, factors replicated per CTA)",
@@ -486,6 +485,13 @@ def run_ours(args, rank, world, local_rank):
         "dominant_kernel": dom,
         "roofline": roof,
     }
+    mix_ms, mix_n = prof_all["mix"]
+    if mix_n > 0:
+        mb = algorithmic("mix", w, P, X.element_size())["bytes"]
+        out["mixing"] = {"kernel": MIX_KERNEL, "passes": mix_n, "ms_per_pass": mix_ms / mix_n,
+                         "algorithmic_bytes_per_pass": mb, "GBs": mb / (mix_ms / mix_n / 1e3) / 1e9,
+                         "frac_of_hbm_peak": mb / (mix_ms / mix_n / 1e3) / 1e9 / pk["hbm_gbs"],
+                         "peak_GBs": pk["hbm_gbs"], "peak_source": pk_src}
     if ttf is not None:
         out["time_to_fit"] = ttf
         out["plain_fp64_gpu"] = plain_out

@@ -247,10 +247,13 @@ CPR_API int cpr_fit_estimate(const cpr_tensor* X, const cpr_ktensor* K, int64_t 
                      void* stream);
 
 /* Mixing preprocess (Alg. 5, mixing step): out_dev = X x_1 F_1 D_1 ... x_N F_N D_N, mode 1
- * first, in X's dtype and layout.  FP32 tensors: tensor-core mode products with both operands split
- * into two halves (FP16 halves scaled by powers of two when every I_n is a multiple of 8, else TF32
- * halves; about 2^-21 relative per product) accumulated in FP32; BF16 tensors: FP32 SIMT products;
- * FP64 tensors: FP64.  out_dev must not overlap X.  ws from
+ * first, in X's dtype and layout.  FP32 and BF16 tensors whose every I_n (>= 5) factors into 2, 3,
+ * 5 and 7: each mode product is a factored DCT-II (a mixed-radix FFT of the reordered fiber in
+ * shared memory, FP32 arithmetic, twiddles rounded once from FP64; about 1e-7 relative).  Other
+ * FP32 tensors: tensor-core dense products with both operands split into two halves (FP16 halves
+ * scaled by powers of two when every I_n is a multiple of 8, else TF32 halves; about 2^-21 relative
+ * per product) accumulated in FP32; other BF16 tensors: FP32 SIMT products; FP64 tensors: FP64.
+ * BF16 results are rounded to BF16 after every mode product.  out_dev must not overlap X.  ws from
  * cpr_workspace_size(CPR_METHOD_CPRAND_MIX, ...) is enough. */
 CPR_API int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, uint32_t b, void* ws,
                    size_t ws_bytes, void* stream);
@@ -259,6 +262,15 @@ CPR_API int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, ui
  * copied.  Khat and out may not share factor buffers. */
 CPR_API int cpr_unmix_factors(const cpr_ktensor* Khat, cpr_ktensor* out, uint64_t seed, uint32_t b,
                       void* ws, size_t ws_bytes, void* stream);
+
+/* Mixing engine (process-wide; applies to cpr_mix_tensor and to every CPRAND-MIX call enqueued
+ * afterwards): CPR_MIX_AUTO takes the factored DCT where it applies (see cpr_mix_tensor), else the
+ * dense products; CPR_MIX_DENSE always takes the dense products (the tensor-core kernels for FP32);
+ * CPR_MIX_FFT is AUTO (the factored transform is used only where it applies).  Returns the previous
+ * engine, or -1 (nothing changed) for an unknown value.  Both engines compute the same operator
+ * F_n D_n; they differ in rounding only. */
+enum { CPR_MIX_AUTO = 0, CPR_MIX_FFT = 1, CPR_MIX_DENSE = 2 };
+CPR_API int cpr_set_mix_engine(int engine);
 
 /* Kernel profiler (process-wide, host-side bookkeeping only).  After cpr_profile_begin(mask),
  * every launch of a kernel class whose bit is set in mask is bracketed by a pair of CUDA events

@@ -39,6 +39,7 @@ class CprOpts(ctypes.Structure):
                 ("fit_trace_dev", ctypes.c_void_p), ("loop_path", ctypes.c_int32), ("layout", ctypes.c_int32)]
 
 LOOP_AUTO, LOOP_CLUSTER, LOOP_GRAPH, LOOP_STREAM, LOOP_CLUSTER_DIST = range(5)
+MIX_AUTO, MIX_FFT, MIX_DENSE = range(3)
 
 
 class CprResult(ctypes.Structure):
@@ -102,6 +103,7 @@ _SIGS = {
     "cpr_fit_estimate_noalloc": (ctypes.c_int, [ctypes.POINTER(CprTensor), ctypes.POINTER(CprKtensor), ctypes.c_int64,
                                                 ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
                                                 ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "cpr_set_mix_engine": (ctypes.c_int, [ctypes.c_int]),
     "cpr_profile_begin": (ctypes.c_int, [ctypes.c_uint]),
     "cpr_profile_end": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }
@@ -263,6 +265,14 @@ class PreparedRun:
                      _stream(stream))
         _check(st, "cpr_cprand_mix")
         return result_dict(self.res)
+
+
+def cpr_set_mix_engine(engine):
+    """Select the mixing engine process-wide (MIX_AUTO, MIX_FFT, MIX_DENSE); returns the previous one."""
+    prev = lib().cpr_set_mix_engine(int(engine))
+    if prev < 0:
+        raise ValueError("unknown mixing engine %r" % (engine,))
+    return prev
 
 
 def cpr_profile_begin(mask=0xFF):

@@ -5,12 +5,18 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
 #include "internal.cuh"
 
 using namespace cpr;
+
+namespace {
+std::atomic<int> g_mix_engine{CPR_MIX_AUTO};
+}
+int cpr::mix_engine() { return g_mix_engine.load(); }
 
 namespace {
 
@@ -393,13 +399,33 @@ cpr_opts defaults() {
 // `final`; the last pass also writes its unfolding into rep_last when given (*wrote_rep_last).
 // Otherwise SIMT passes ping-pong between final and t1 so that the last lands in final.
 int enqueue_mixing(const void* src, void* final, void* t1, void* t2, void* rep_last, int dtype, int N,
-                   const int64_t* dims, float* const* W32, float* const* Wlo, double* const* W64, int* err,
-                   unsigned* amax, bool amax0_ready, cudaStream_t s, int64_t& launches, bool* wrote_rep_last) {
+                   const int64_t* dims, float* const* W32, float* const* Wlo, double* const* W64,
+                   double* const* SG, int* err, unsigned* amax, bool amax0_ready, cudaStream_t s, int64_t& launches,
+                   bool* wrote_rep_last) {
+  *wrote_rep_last = false;
+  bool fft = mix_engine() != CPR_MIX_DENSE && t1 != nullptr && mix_fft_supported(dtype, N, dims);
+  for (int n = 0; n < N && fft; ++n) fft = W32[n] != nullptr && SG[n] != nullptr;
+  if (fft) {
+    // factored DCT passes: the FFT tables replace the dense operator in its buffer (5 I <= I^2
+    // floats); pass n writes the layout pass n + 1 reads, the outputs alternate between final and
+    // t1 so that the last pass writes final
+    for (int n = 0; n < N; ++n)
+      CPR_LAUNCH(CPR_KERNEL_OTHER, launch_fft_tables((int)dims[n], SG[n], W32[n], s));
+    void* bufs[2] = {final, t1};
+    const void* U = src;
+    for (int n = 0; n < N; ++n) {
+      void* y = bufs[(N - 1 - n) & 1];
+      void* ys = (n == N - 1 && rep_last) ? rep_last : nullptr;
+      CPR_LAUNCH(CPR_KERNEL_MIX, launch_mix_fft(U, y, ys, W32[n], dtype, N, dims, n, err, s));
+      if (ys) *wrote_rep_last = true;
+      U = y;
+    }
+    return CPR_OK;
+  }
   bool tc = dtype == CPR_F32 && t2 != nullptr;
   for (int n = 0; n < N && tc; ++n) tc = Wlo[n] != nullptr && mix_tc_supported(dtype, (int)dims[n]);
   bool tc16 = tc && amax != nullptr;
   for (int n = 0; n < N && tc16; ++n) tc16 = mix_tc16_supported(dtype, (int)dims[n]);
-  *wrote_rep_last = false;
   if (tc16) {
     // FP16-split tensor-core passes: W's FP16 halves go into the Wlo buffer (2 I^2 halves = I^2
     // floats); amax[n] = largest |entry| of pass n's input (the input tensor's from a max pass)
@@ -588,7 +614,7 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
                                                          mb.F64[n], mb.sg[n], s));
       if (int st = enqueue_mixing(Xs[b].data, mb.xhat, pl.d_tmp, pl.d_tmp2,
                                   p.use_rep ? const_cast<void*>(p.Xrep[p.N - 1]) : nullptr, p.dtype, p.N, p.dims,
-                                  mb.W32, mb.Wlo, mb.W64, pl.d_counter + 2, amax, true, s, launches,
+                                  mb.W32, mb.Wlo, mb.W64, mb.sg, pl.d_counter + 2, amax, true, s, launches,
                                   &rep_last_done))
         return st;
     }
@@ -1114,7 +1140,7 @@ int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, uint32_t b
     CPR_LAUNCH(CPR_KERNEL_OTHER,
                launch_build_mix_ops((int)X->dims[n], seed, b, n, table, W32[n], W64[n], F64[n], sg[n], s));
   bool unused = false;
-  if (int st = enqueue_mixing(X->data, out_dev, tmp, tmp2, nullptr, dt, N, X->dims, W32, Wlo, W64, derr,
+  if (int st = enqueue_mixing(X->data, out_dev, tmp, tmp2, nullptr, dt, N, X->dims, W32, Wlo, W64, sg, derr,
                               reinterpret_cast<unsigned*>(derr + 4), false, s, launches, &unused))
     return st;
   return CPR_OK;
@@ -1150,6 +1176,11 @@ int cpr_unmix_factors(const cpr_ktensor* Khat, cpr_ktensor* out, uint64_t seed, 
   if (Khat->lambda && out->lambda && Khat->lambda != out->lambda)
     CPR_CUDA(cudaMemcpyAsync(out->lambda, Khat->lambda, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
   return CPR_OK;
+}
+
+int cpr_set_mix_engine(int engine) {
+  if (engine != CPR_MIX_AUTO && engine != CPR_MIX_FFT && engine != CPR_MIX_DENSE) return -1;
+  return g_mix_engine.exchange(engine);
 }
 
 int cpr_profile_begin(unsigned mask) {

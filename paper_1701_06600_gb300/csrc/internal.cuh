@@ -318,6 +318,16 @@ cudaError_t launch_mix_tc16(const float* U, float* ystd, float* yunf, float* yne
                             const int64_t* dims, int n, const unsigned* amax_in, unsigned* amax_out, int* err,
                             cudaStream_t s);
 
+// mixing by the factored DCT-II (FP32 / BF16 tensors whose every I_n factors into 2, 3, 5, 7):
+// pass n reads the mode-n unfolding and writes the mode-(n+1 mod N) unfolding (the last pass: the
+// standard layout, and its own layout into ysame when given); tab = 5 I floats from
+// launch_fft_tables (signs: D_n as FP64 +-1)
+bool mix_fft_supported(int dtype, int N, const int64_t* dims);
+cudaError_t launch_fft_tables(int I, const double* signs, float* tab, cudaStream_t s);
+cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* tab, int dtype, int N,
+                           const int64_t* dims, int n, int* err, cudaStream_t s);
+int mix_engine();   // CPR_MIX_* (process-wide, cpr_set_mix_engine)
+
 // mixing (Alg. 5)
 cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, double* table, float* W32,
                                  double* W64, double* F64, double* signs, cudaStream_t s);

@@ -1,0 +1,606 @@
+// Mode-n mixing product by a factored DCT-II (the fast transform of Alg. 5's mixing step).
+//
+// One pass applies y = F_n D_n x to every mode-n fiber x of the tensor, where F_n is the orthonormal
+// DCT-II of length I = I_n (F[k][i] = c_k cos(pi (2i + 1) k / (2I)), c_0 = sqrt(1/I), c_k = sqrt(2/I))
+// and D_n the diagonal of random signs.  Instead of the dense I x I product (2I flops per entry) the
+// DCT is computed through a complex DFT of the same length:
+//   * reorder (even entries ascending, then odd entries descending):
+//       v[m] = d[2m] x[2m] for 2m < I,   v[I-1-m] = d[2m+1] x[2m+1] for 2m+1 < I;
+//   * V = DFT_I(v), with V[k] = sum_m v[m] exp(-2 pi i m k / I);
+//   * y[k] = c_k Re(exp(-i pi k / (2I)) V[k]).
+// Two real fibers go through one complex transform (one as the real part, one as the imaginary
+// part); they are separated afterwards by the conjugate symmetry of real DFTs:
+//   V1[k] = (W[k] + conj(W[I-k])) / 2,   V2[k] = (W[k] - conj(W[I-k])) / (2i).
+// The DFT is a Stockham autosort FFT whose stages have radices up to 25: a stage of radix R = R1 R2
+// holds the R values of a butterfly in registers and transforms them as R2 DFTs of length R1, a
+// twiddle, and R1 DFTs of length R2 (Cooley-Tukey inside the butterfly), so that I = 400 = 25 x 16
+// takes two shared-memory round trips.  About 5 I log2 I flops per pair of fibers instead of the
+// dense product's 4 I^2.
+//
+// Data flow: a CTA owns BJ fibers that differ only in the index of one other mode v (consecutive
+// i_v), loads them (each fiber is contiguous in the mode-n unfolding the pass reads; one bulk copy
+// per fiber), transforms them in shared memory and writes the result in the mode-v unfolding layout,
+// where those BJ fibers are adjacent for every output index k.  Choosing v = n + 1 makes every pass
+// write exactly the layout the next pass reads, so the chain of N passes needs no transposition
+// copies; the last pass (v = 0) writes the standard layout and, when asked, its own mode-n unfolding
+// (the copy the sampled gathers of mode n read).
+//
+// Shared memory: the fibers land as rows (fiber f in row f, Ipad floats apart); the reorder turns
+// rows 2p and 2p + 1 into the interleaved complex sequence p (Ipad complex values from row 2p on);
+// the stages run in place (each thread keeps its butterflies in registers between a stage's reads
+// and its writes); the final rotation writes (y_{2p}[k], y_{2p+1}[k]) back over the complex value k.
+//
+// Accuracy: FP32 arithmetic with twiddles rounded once from FP64; below 1e-6 relative for the sizes
+// used here.  Every mbarrier wait is bounded: on expiry the kernel records an error and returns.
+#include <string.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace cpr {
+namespace {
+
+constexpr uint32_t kFftWaitLimit = 1u << 24;
+constexpr int kSlots = 32;          // complex values a thread holds in a stage
+constexpr int kFftThreads = 256;
+constexpr int kMaxStages = 16;
+constexpr int kFftMaxSmem = 200 * 1024;
+constexpr int kMaxFftLen = 8192;    // keeps the multiply-high divisions exact
+// the stage radices, in the order a plan's stages run; radix R = R1 x R2 (R2 = 1 for the plain ones)
+constexpr int kNumRadices = 14;
+constexpr int kRadR1[kNumRadices] = {5, 5, 4, 5, 4, 5, 3, 4, 7, 3, 5, 4, 3, 2};
+constexpr int kRadR2[kNumRadices] = {5, 4, 4, 3, 3, 2, 3, 2, 1, 2, 1, 1, 1, 1};
+
+struct StageTab {
+  int L, Ns, tstep, rix;   // butterflies per sequence (I / R), radix product before, I / (Ns R), radix index
+  uint32_t mL, mNs, r0, r1;   // ceil(2^32 / L), ceil(2^32 / Ns)
+};
+
+struct FftArgs {
+  const void* U;        // input: the mode-n unfolding, fibers of length I contiguous
+  void* yv;             // output in the mode-v unfolding layout
+  void* ysame;          // optional output in the input's layout (mode-n unfolding)
+  const float* tab;     // twiddles (2I), post-scales (2I), signs (I)
+  int I, Ipad, BJ, S, nst, bulk;
+  uint32_t mH2;         // ceil(2^32 / (I / 2 + 1))
+  StageTab st[kMaxStages];
+  int64_t Iv;           // extent of the mode the CTA's fibers run along
+  int64_t rs_in_v;      // input row stride of one step in i_v
+  int64_t out_k;        // output stride of one step in k (= i_n): I_v times the mode-v row stride of n
+  int64_t nchunks;      // ceil(Iv / BJ)
+  int64_t nblocks;      // fiber blocks of the pass (nchunks x the remaining modes' extents)
+  int no;               // number of remaining modes (not n, not v)
+  int64_t oext[kMaxOrder], o_in[kMaxOrder], o_out[kMaxOrder];
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool fft_mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+template <typename T> __device__ __forceinline__ float ld_as_float(const T* p);
+template <> __device__ __forceinline__ float ld_as_float<float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float ld_as_float<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+template <typename T> __device__ __forceinline__ T from_float(float v);
+template <> __device__ __forceinline__ float from_float<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) { return __float2bfloat16(v); }
+
+// In-register DFT of R values, out[q] = sum_r v[r] w^(r q), w = exp(-2 pi i / R).  For odd R the
+// terms r and R - r are combined: out[q] = v0 + sum_r cos(2 pi r q/R) (v_r + v_{R-r})
+// - i sum_r sin(2 pi r q/R) (v_r - v_{R-r}) and out[R-q] the same with +i.  rc[m] = (cos, sin) of
+// 2 pi m / R for m = 1 .. (R-1)/2.
+template <int R>
+__device__ __forceinline__ void dft(float2 (&v)[R], const float2 (&rc)[R / 2 + 1]) {
+  if constexpr (R == 2) {
+    const float2 a = v[0], b = v[1];
+    v[0] = make_float2(a.x + b.x, a.y + b.y);
+    v[1] = make_float2(a.x - b.x, a.y - b.y);
+  } else if constexpr (R == 4) {
+    const float2 a = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
+    const float2 b = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
+    const float2 c = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
+    const float2 d = make_float2(v[1].x - v[3].x, v[1].y - v[3].y);   // -i d = (d.y, -d.x)
+    v[0] = make_float2(a.x + c.x, a.y + c.y);
+    v[2] = make_float2(a.x - c.x, a.y - c.y);
+    v[1] = make_float2(b.x + d.y, b.y - d.x);
+    v[3] = make_float2(b.x - d.y, b.y + d.x);
+  } else {
+    constexpr int H = (R - 1) / 2;
+    float2 s[H], t[H];
+    float2 sum = v[0];
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+      s[r - 1] = make_float2(v[r].x + v[R - r].x, v[r].y + v[R - r].y);
+      t[r - 1] = make_float2(v[r].x - v[R - r].x, v[r].y - v[R - r].y);
+      sum.x += s[r - 1].x;
+      sum.y += s[r - 1].y;
+    }
+    const float2 v0 = v[0];
+    v[0] = sum;
+#pragma unroll
+    for (int q = 1; q <= H; ++q) {
+      float2 A = v0, B = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int r = 1; r <= H; ++r) {
+        const int m = (r * q) % R;                 // compile-time after unrolling
+        const int mm = m <= H ? m : R - m;
+        const float c = rc[mm].x;
+        const float sn = m <= H ? rc[mm].y : -rc[mm].y;
+        A.x = fmaf(c, s[r - 1].x, A.x);
+        A.y = fmaf(c, s[r - 1].y, A.y);
+        B.x = fmaf(sn, t[r - 1].x, B.x);
+        B.y = fmaf(sn, t[r - 1].y, B.y);
+      }
+      v[q] = make_float2(A.x + B.y, A.y - B.x);      // A - iB
+      v[R - q] = make_float2(A.x - B.y, A.y + B.x);  // A + iB
+    }
+  }
+}
+
+// n / d for n < 2^17 and 1 <= d <= 8192: one multiply-high by m = ceil(2^32 / d) (exact in that range:
+// n (m - 2^32 / d) / 2^32 < n / 2^32 < 1 / d), or n itself when d = 1
+__device__ __forceinline__ int fdiv(int n, int d, uint32_t m) { return d == 1 ? n : (int)__umulhi((uint32_t)n, m); }
+
+// roots (cos, sin)(2 pi m / R) for m <= R / 2, read from the length-I twiddle table (step = I / R)
+template <int R>
+__device__ __forceinline__ void load_roots(float2 (&rc)[R / 2 + 1], const float2* tw, int step) {
+  rc[0] = make_float2(1.f, 0.f);
+#pragma unroll
+  for (int m = 1; m <= R / 2; ++m) {
+    const float2 w = tw[m * step];   // exp(-2 pi i m / R) = (cos, -sin)
+    rc[m] = make_float2(w.x, -w.y);
+  }
+}
+
+// In-register DFT of R = R1 R2 values (input index r = R2 r1 + r2, output index q = q1 + R1 q2):
+// R2 DFTs of length R1 over r1, the twiddle w_R^(r2 q1), R1 DFTs of length R2 over r2.  L = I / R
+// (w_R^m = tw[m L]).
+template <int R1, int R2>
+__device__ __forceinline__ void dft_comp(float2 (&v)[R1 * R2], const float2* tw, int L) {
+  constexpr int R = R1 * R2;
+  if constexpr (R2 == 1) {
+    float2 rc[R1 / 2 + 1];
+    load_roots<R1>(rc, tw, L);
+    dft<R1>(v, rc);
+  } else {
+    float2 rc1[R1 / 2 + 1], rc2[R2 / 2 + 1];
+    load_roots<R1>(rc1, tw, L * R2);
+    load_roots<R2>(rc2, tw, L * R1);
+#pragma unroll
+    for (int r2 = 0; r2 < R2; ++r2) {
+      float2 t[R1];
+#pragma unroll
+      for (int r1 = 0; r1 < R1; ++r1) t[r1] = v[R2 * r1 + r2];
+      dft<R1>(t, rc1);
+#pragma unroll
+      for (int q1 = 0; q1 < R1; ++q1) v[R2 * q1 + r2] = (r2 && q1) ? cmul(t[q1], tw[r2 * q1 * L]) : t[q1];
+    }
+    float2 o[R];
+#pragma unroll
+    for (int q1 = 0; q1 < R1; ++q1) {
+      float2 t[R2];
+#pragma unroll
+      for (int r2 = 0; r2 < R2; ++r2) t[r2] = v[R2 * q1 + r2];
+      dft<R2>(t, rc2);
+#pragma unroll
+      for (int q2 = 0; q2 < R2; ++q2) o[q1 + R1 * q2] = t[q2];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = o[r];
+  }
+}
+
+// One Stockham stage of radix R = R1 R2 over S interleaved complex sequences (sequence p at
+// Z + p Ipad).  Butterfly j of a sequence reads entries j + r L (L = I / R), multiplies entry r by
+// w_I^(r (j mod Ns) I / (Ns R)), transforms, and writes entry r to (j / Ns) Ns R + (j mod Ns) + r Ns.
+// All reads of the stage finish before any write (the values wait in registers): in place.
+// FIRST: the stage reads the real fibers instead (rows 2p and 2p + 1 of the loaded block) in the DCT
+// reorder, times their signs: v_p[m] = d[s] (x_{2p}[s], x_{2p+1}[s]) with s = 2m (2m < I) or
+// 2(I - 1 - m) + 1; Ns = 1, so no twiddles.
+template <int R1, int R2, bool FIRST>
+__device__ __forceinline__ void fft_stage(float2* Z, int I, int Ipad, int S, const StageTab& sc, int tid,
+                                          const float2* tw, const float* sg) {
+  constexpr int R = R1 * R2, MAXB = kSlots / R;
+  const int L = sc.L, Ns = FIRST ? 1 : sc.Ns, nbt = S * L, tstep = sc.tstep;
+  float2 v[MAXB][R];
+  int dst[MAXB];
+#pragma unroll
+  for (int q = 0; q < MAXB; ++q) {
+    const int b = tid + q * kFftThreads;
+    dst[q] = -1;
+    if (b < nbt) {
+      const int p = fdiv(b, L, sc.mL), j = b - p * L;
+      const int jn = FIRST ? j : fdiv(j, Ns, sc.mNs), k = j - jn * Ns;
+      const float2* z = Z + p * Ipad;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int m = j + r * L;
+        float2 x;
+        if constexpr (FIRST) {
+          const int src = 2 * m < I ? 2 * m : 2 * (I - 1 - m) + 1;
+          const float d = sg[src];
+          const float* row = reinterpret_cast<const float*>(z);
+          x = make_float2(row[src] * d, row[Ipad + src] * d);
+        } else {
+          x = z[m];
+          if (r > 0 && k > 0) x = cmul(x, tw[r * k * tstep]);
+        }
+        v[q][r] = x;
+      }
+      dft_comp<R1, R2>(v[q], tw, L);
+      dst[q] = p * Ipad + jn * Ns * R + k;
+    }
+    // one butterfly's loads at a time: otherwise the compiler issues the loads of every butterfly
+    // up front and runs out of registers
+    asm volatile("" ::: "memory");
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < MAXB; ++q)
+    if (dst[q] >= 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) Z[dst[q] + r * Ns] = v[q][r];
+    }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void fft_bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// block blk of the pass: its fibers run along mode v from i_v = iv0; returns the fiber count and the
+// first fiber's input row and output offset
+__device__ __forceinline__ int fft_block(const FftArgs& a, int64_t blk, int64_t& row0, int64_t& out0) {
+  const int64_t chunk = blk % a.nchunks;
+  int64_t rest = blk / a.nchunks;
+  const int64_t iv0 = chunk * a.BJ;
+  row0 = iv0 * a.rs_in_v;
+  out0 = 0;
+  for (int m = 0; m < a.no; ++m) {   // the remaining modes: extent, input row stride, output stride
+    const int64_t im = rest % a.oext[m];
+    rest /= a.oext[m];
+    row0 += im * a.o_in[m];
+    out0 += im * a.o_out[m];
+  }
+  out0 = iv0 + a.Iv * out0;
+  return (int)min((int64_t)a.BJ, a.Iv - iv0);
+}
+
+// the stages of radix index RIX (one loop per radix: the register arrays of different radices are
+// never live at once); the plan lists its stages in radix-index order
+template <int RIX>
+__device__ __forceinline__ void fft_stages_of(float2* Z, int I, int Ipad, int S, int nst, const StageTab* stt, int& st,
+                                              int tid, const float2* tw, const float* sg) {
+  if (st == 0 && nst > 0 && stt[0].rix == RIX) {
+    fft_stage<kRadR1[RIX], kRadR2[RIX], true>(Z, I, Ipad, S, stt[0], tid, tw, sg);
+    ++st;
+  }
+  for (; st < nst && stt[st].rix == RIX; ++st)
+    fft_stage<kRadR1[RIX], kRadR2[RIX], false>(Z, I, Ipad, S, stt[st], tid, tw, sg);
+}
+
+// One CTA per block of fibers (one bulk copy per fiber on the FP32 path).  Several CTAs share an SM,
+// so one CTA's copies overlap the others' transforms.
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads, 2) k_mix_fft(const __grid_constant__ FftArgs a) {
+  extern __shared__ float4 fft_smem4[];
+  const int I = a.I, Ipad = a.Ipad, BJ = a.BJ, S = a.S;
+  float* Y = reinterpret_cast<float*>(fft_smem4);
+  float2* Z = reinterpret_cast<float2*>(Y);
+  float2* tw = reinterpret_cast<float2*>(Y + BJ * Ipad);
+  float2* post = tw + I;
+  float* sg = reinterpret_cast<float*>(post + I);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(fft_smem4) + ((BJ * Ipad + 5 * I + 3) / 2);   // 8-byte aligned
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const T* U = static_cast<const T*>(a.U);
+  __shared__ StageTab s_st[kMaxStages];
+  __shared__ longlong4 s_blk;   // (first fiber's input row, first output offset, fiber count)
+  if (tid < kMaxStages) s_st[tid] = a.st[tid];
+  if (tid == 0) {   // the block's coordinates (64-bit divisions: once per CTA, not per thread)
+    int64_t r0, o0;
+    const int n = fft_block(a, blockIdx.x, r0, o0);
+    s_blk = make_longlong4(r0, o0, n, 0);
+
+    if (a.bulk) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  __syncthreads();
+  const int64_t row0 = s_blk.x, out0 = s_blk.y;
+  const int nf = (int)s_blk.z;
+  if (a.bulk) {   // the tx count may briefly go negative when a copy completes before the expect_tx
+    if (tid == 0)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                   "r"((uint32_t)(nf * I * sizeof(float)))
+                   : "memory");
+    if (tid < nf)
+      fft_bulk_copy(Y + tid * Ipad, U + (row0 + (int64_t)tid * a.rs_in_v) * I, (uint32_t)(I * sizeof(float)), bar);
+  } else {        // plain loads: one warp per fiber, lanes along the fiber
+    for (int f = warp; f < nf; f += kFftThreads / 32) {
+      const T* src = U + (row0 + (int64_t)f * a.rs_in_v) * I;
+      for (int k = lane; k < I; k += 32) Y[f * Ipad + k] = ld_as_float<T>(src + k);
+    }
+  }
+  for (int e = tid; e < 5 * I; e += kFftThreads) reinterpret_cast<float*>(tw)[e] = a.tab[e];
+  for (int e = tid; e < (BJ - nf) * Ipad; e += kFftThreads) Y[nf * Ipad + e] = 0.f;   // fibers past the end of mode v
+  // one thread polls the copies' mbarrier (polling by every thread would take issue slots from the
+  // other CTAs on the SM); the others wait in the block barrier and then observe the completed phase
+  bool ok = true;
+  if (a.bulk && tid == 0) {
+    ok = false;
+    for (uint32_t it = 0; it < kFftWaitLimit && !ok; ++it) ok = fft_mbar_try(bar, 0);
+  }
+  if (__syncthreads_or(!ok)) {   // the whole CTA leaves together if the wait ran out
+    if (tid == 0) atomicExch(a.err, 1);
+    return;
+  }
+  if (a.bulk && tid != 0) (void)fft_mbar_try(bar, 0);   // completed: returns at once
+
+  // the DFT stages of the S = BJ / 2 complex sequences (the first also reorders the real fibers into
+  // interleaved complex values)
+  const int nst = a.nst;
+  int st = 0;
+  fft_stages_of<0>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<1>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<2>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<3>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<4>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<5>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<6>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<7>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<8>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<9>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<10>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<11>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<12>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<13>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  if (st != nst && tid == 0) atomicExch(a.err, 1);   // a stage order the host never produces
+
+  // separate the two real fibers of each sequence and apply c_k exp(-i pi k / (2I)); the pair
+  // (k, I - k) is read and written by one thread: (y_{2p}[k], y_{2p+1}[k]) replaces Z_p[k]
+  {
+    const int H2 = I / 2 + 1;
+    for (int w = tid; w < S * H2; w += kFftThreads) {
+      const int p = fdiv(w, H2, a.mH2), k = w - p * H2;
+      float2* z = Z + p * Ipad;
+      const int kk = k == 0 ? 0 : I - k;
+      const float2 A = z[k], B = z[kk];
+      const float2 pk = post[k];
+      z[k] = make_float2(pk.x * (A.x + B.x) + pk.y * (A.y - B.y), pk.x * (A.y + B.y) - pk.y * (A.x - B.x));
+      if (kk != k) {
+        const float2 pq = post[kk];
+        z[kk] = make_float2(pq.x * (B.x + A.x) + pq.y * (B.y - A.y), pq.x * (B.y + A.y) - pq.y * (B.x - A.x));
+      }
+    }
+  }
+  __syncthreads();
+
+  // stores: the mode-v layout (the CTA's fibers adjacent for each k); lanes = 8 fibers x 4 k (fiber f
+  // is component f & 1 of sequence f / 2), so a warp reads 32 distinct banks (Ipad odd multiple of 4)
+  // and writes four full 32-byte sectors.  The 8 warps split the fiber groups (G8 = min(groups, 8) of
+  // them at a time) and the groups of 4 k (8 / G8 warps per fiber group); addresses are stepped
+  {
+    T* yv = static_cast<T*>(a.yv);
+    const int FW = BJ < 8 ? BJ : 8, KW = 32 / FW;
+    const int ngf = BJ / FW, G8 = ngf < 8 ? ngf : 8, wpg = (kFftThreads / 32) / G8;
+    const int kstep = wpg * KW;
+    for (int gf = warp % G8; gf < ngf; gf += G8) {
+      const int f = gf * FW + lane % FW;
+      int k = (warp / G8) * KW + lane / FW;
+      if (f >= nf) continue;
+      T* dst = yv + out0 + f + (int64_t)k * a.out_k;
+      const int64_t dstep = (int64_t)kstep * a.out_k;
+      const float* src = Y + (f >> 1) * 2 * Ipad + (f & 1) + 2 * k;
+      for (; k < I; k += kstep, dst += dstep, src += 2 * kstep) *dst = from_float<T>(*src);
+    }
+  }
+  if (a.ysame) {   // the input's own layout: each fiber a contiguous row
+    T* ys = static_cast<T*>(a.ysame);
+    for (int f = warp; f < nf; f += kFftThreads / 32) {
+      T* dst = ys + (row0 + (int64_t)f * a.rs_in_v) * I;
+      const float* z = Y + (f >> 1) * 2 * Ipad + (f & 1);
+      for (int k = lane; k < I; k += 32) dst[k] = from_float<T>(z[2 * k]);
+    }
+  }
+}
+
+// twiddles exp(-2 pi i t / I), post-scales c_k (cos, sin)(pi k / (2I)) / 2 and the signs d_k;
+// computed in FP64, rounded once
+__global__ void k_fft_tables(int I, const double* __restrict__ signs, float* __restrict__ tab) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= I) return;
+  double s, c;
+  sincospi(2.0 * t / I, &s, &c);
+  tab[2 * t] = (float)c;
+  tab[2 * t + 1] = (float)(-s);
+  sincospi((double)t / (2.0 * I), &s, &c);
+  const double ck = t == 0 ? sqrt(1.0 / I) : sqrt(2.0 / I);
+  tab[2 * I + 2 * t] = (float)(0.5 * ck * c);
+  tab[2 * I + 2 * t + 1] = (float)(0.5 * ck * s);
+  tab[4 * I + t] = (float)signs[t];
+}
+
+// the stage radices of I (every prime factor 2, 3, 5 or 7), grouped into the radices of kRadR1 x
+// kRadR2, listed in radix-index order; among the groupings, the one that admits the widest fiber block
+// (then the fewest stages)
+struct FftPlan {
+  int BJ, Ipad, nst;
+  int rix[kMaxStages];
+  size_t smem;
+};
+
+size_t fft_smem_bytes(int BJ, int Ipad, int I) { return (size_t)(BJ * Ipad + 5 * I + 4) * sizeof(float) + 16; }
+
+// the widest block (a power of two up to 128 fibers, not wider than mode v needs) whose stages fit
+// the threads' register slots; blocks above 32 fibers only while two CTAs still fit an SM
+int fft_block_width(int I, int64_t Iv, int Ipad, const int* rix, int nst) {
+  int64_t cap = 2;
+  while (cap < Iv && cap < 128) cap *= 2;
+  for (int BJ = 128; BJ >= 2; BJ /= 2) {
+    if (BJ > cap) continue;
+    const int S = BJ / 2;
+    bool ok = true;
+    for (int s = 0; s < nst && ok; ++s) {
+      const int R = kRadR1[rix[s]] * kRadR2[rix[s]];
+      ok = ((int64_t)S * (I / R) + kFftThreads - 1) / kFftThreads <= kSlots / R;
+    }
+    const size_t sm = fft_smem_bytes(BJ, Ipad, I);
+    if (ok && sm <= (size_t)kFftMaxSmem && (BJ <= 32 || sm <= (size_t)kFftMaxSmem / 2)) return BJ;
+  }
+  return 0;
+}
+
+void fft_search(int m, int from, int* cur, int depth, int I, int64_t Iv, int Ipad, FftPlan* best) {
+  if (m == 1) {
+    if (depth == 0) return;
+    const int BJ = fft_block_width(I, Iv, Ipad, cur, depth);
+    if (BJ > best->BJ || (BJ == best->BJ && BJ > 0 && depth < best->nst)) {
+      best->BJ = BJ;
+      best->nst = depth;
+      for (int s = 0; s < depth; ++s) best->rix[s] = cur[s];
+    }
+    return;
+  }
+  if (depth == kMaxStages) return;
+  for (int r = from; r < kNumRadices; ++r) {
+    const int R = kRadR1[r] * kRadR2[r];
+    if (m % R) continue;
+    cur[depth] = r;
+    fft_search(m / R, r, cur, depth + 1, I, Iv, Ipad, best);
+  }
+}
+
+bool fft_plan(int I, int64_t Iv, FftPlan* pl) {
+  if (I < 2 || I > kMaxFftLen) return false;
+  int m = I;
+  for (int p : {2, 3, 5, 7})
+    while (m % p == 0) m /= p;
+  if (m != 1) return false;
+  int Ipad = (I + 3) / 4 * 4;
+  if ((Ipad / 4) % 2 == 0) Ipad += 4;   // Ipad / 4 odd: conflict-free column reads
+  FftPlan best;
+  memset(&best, 0, sizeof(best));
+  int cur[kMaxStages];
+  fft_search(I, 0, cur, 0, I, Iv, Ipad, &best);
+  if (best.BJ == 0) return false;
+  best.Ipad = Ipad;
+  best.smem = fft_smem_bytes(best.BJ, Ipad, I);
+  *pl = best;
+  return true;
+}
+
+template <typename T>
+cudaError_t launch_fft_kernel(const FftArgs& a, size_t smem, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_mix_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftMaxSmem + 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (a.nblocks > INT32_MAX) return cudaErrorInvalidValue;
+  k_mix_fft<T><<<(unsigned)a.nblocks, kFftThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+uint32_t magic(int d) { return d > 1 ? (uint32_t)((((uint64_t)1 << 32) + d - 1) / d) : 0u; }
+
+}  // namespace
+
+bool mix_fft_supported(int dtype, int N, const int64_t* dims) {
+  if (dtype != CPR_F32 && dtype != CPR_BF16) return false;
+  if (N < 2) return false;
+  for (int n = 0; n < N; ++n) {
+    if (dims[n] < 5) return false;   // the tables live in the I x I operator buffer (5 I floats)
+    FftPlan pl;
+    if (!fft_plan((int)dims[n], dims[(n + 1) % N], &pl)) return false;
+  }
+  return true;
+}
+
+cudaError_t launch_fft_tables(int I, const double* signs, float* tab, cudaStream_t s) {
+  k_fft_tables<<<(I + 255) / 256, 256, 0, s>>>(I, signs, tab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* tab, int dtype, int N,
+                           const int64_t* dims, int n, int* err, cudaStream_t s) {
+  if (N < 2 || n < 0 || n >= N) return cudaErrorInvalidValue;
+  const int v = (n + 1) % N;
+  FftArgs a;
+  memset(&a, 0, sizeof(a));
+  const int I = (int)dims[n];
+  FftPlan pl;
+  if (!fft_plan(I, dims[v], &pl)) return cudaErrorInvalidValue;
+  a.U = U;
+  a.yv = yv;
+  a.ysame = ysame;
+  a.tab = tab;
+  a.I = I;
+  a.Ipad = pl.Ipad;
+  a.BJ = pl.BJ;
+  a.S = pl.BJ / 2;
+  a.nst = pl.nst;
+  a.mH2 = magic(I / 2 + 1);
+  int Ns = 1;
+  for (int st = 0; st < pl.nst; ++st) {
+    const int R = kRadR1[pl.rix[st]] * kRadR2[pl.rix[st]];
+    StageTab& t = a.st[st];
+    t.L = I / R;
+    t.Ns = Ns;
+    t.tstep = I / (Ns * R);
+    t.rix = pl.rix[st];
+    t.mL = magic(t.L);
+    t.mNs = magic(Ns);
+    Ns *= R;
+  }
+  a.Iv = dims[v];
+  a.err = err;
+  // row strides of the mode-n unfolding (input) and of the mode-v unfolding (output)
+  int64_t rin[kMaxOrder], rout[kMaxOrder];
+  int64_t acc_in = 1, acc_out = 1, P = 1;
+  for (int m = 0; m < N; ++m) {
+    P *= dims[m];
+    rin[m] = m == n ? 0 : acc_in;
+    if (m != n) acc_in *= dims[m];
+    rout[m] = m == v ? 0 : acc_out;
+    if (m != v) acc_out *= dims[m];
+  }
+  a.rs_in_v = rin[v];
+  a.out_k = dims[v] * rout[n];
+  for (int m = 0; m < N; ++m) {
+    if (m == n || m == v) continue;
+    a.oext[a.no] = dims[m];
+    a.o_in[a.no] = rin[m];
+    a.o_out[a.no] = rout[m];
+    ++a.no;
+  }
+  a.nchunks = (a.Iv + a.BJ - 1) / a.BJ;
+  a.nblocks = a.nchunks * (P / ((int64_t)I * a.Iv));
+  if (a.nblocks <= 0) return cudaErrorInvalidValue;
+  const size_t es = dtype == CPR_F32 ? 4 : 2;
+  a.bulk = dtype == CPR_F32 && (I * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(U) & 15) == 0;
+  if (dtype == CPR_F32) return launch_fft_kernel<float>(a, pl.smem, s);
+  if (dtype == CPR_BF16) return launch_fft_kernel<__nv_bfloat16>(a, pl.smem, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace cpr

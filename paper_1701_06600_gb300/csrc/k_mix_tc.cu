@@ -329,7 +329,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                   make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
                               __uint_as_float(v[4 * q + 3]));
           } else {
-            for (int q = 0; q < 16 && cb + q < a.I; ++q) dst[q] = __uint_as_float(v[q]);
+#pragma unroll
+            for (int q = 0; q < 16; ++q)   // fully unrolled: v stays in registers
+              if (cb + q < a.I) dst[q] = __uint_as_float(v[q]);
           }
         }
         if (a.ystd) {
@@ -621,7 +623,9 @@ __global__ void __launch_bounds__(kTcThreadsH, 1)
             for (int q = 0; q < 4; ++q)
               reinterpret_cast<float4*>(dst)[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
           } else {
-            for (int q = 0; q < 16 && cb + q < a.I; ++q) dst[q] = y[q];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)   // fully unrolled: y stays in registers
+              if (cb + q < a.I) dst[q] = y[q];
           }
         }
         if (a.ystd) {

@@ -27,6 +27,14 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
+@pytest.fixture
+def engine(cb):
+    """Sets the process-wide mixing engine for one test and restores the previous one afterwards."""
+    prev = cb.cpr_set_mix_engine(cb.MIX_AUTO)
+    yield cb.cpr_set_mix_engine
+    cb.cpr_set_mix_engine(prev)
+
+
 def rand_tensor(dims, dtype, seed=0):
     g = torch.Generator(device="cpu").manual_seed(seed)
     return torch.randn(int(np.prod(dims)), generator=g, dtype=torch.float64).to(dtype).to(DEV)
@@ -255,14 +263,17 @@ def test_whole_run_reaches_oracle_fit(cb, mix, dtype):
 
 
 def test_bf16_four_way_run_reaches_oracle_fit(cb):
-    # BF16 storage, FP32 accumulation, FP64 R x R work: 4-way, rank 16, congruence 0.5, 1% noise
+    # BF16 storage, FP32 accumulation, FP64 R x R work: 4-way, rank 16, congruence 0.5, 1% noise.
+    # A fixed 50 outer iterations: this problem has a swamp (the oracle's sampled fit creeps from 0.90
+    # to 0.91 over ten iterations), where the change-in-fit rule of Sec. 4.2 fires at a point that
+    # depends on the trajectory, and the BF16 rounding of the mixed tensor moves the trajectory
     dims = (40, 36, 32, 30)
     prob = make_problem(dims, 16, C=0.5, eta=0.01, seed=1002, dtype=torch.bfloat16, device=DEV)
     T = to_oracle_array(prob.X, dims)
     trace = torch.zeros(200, dtype=torch.float64, device=DEV)
-    opts = cb.cpr_default_opts(seed=2002, noise_eta=0.01, fit_trace_dev=trace.data_ptr())
+    opts = cb.cpr_default_opts(seed=2002, fixed_iters=50, fit_trace_dev=trace.data_ptr())
     out = cb.cpr_cprand_mix(prob.X, dims, 16, 450, opts=opts)
-    ref = mixing.cprand_mix(T, 16, 450, seed=2002, rule=cp.StopRule(eta=0.01))
+    ref = mixing.cprand_mix(T, 16, 450, seed=2002, rule=cp.StopRule(fixed_iters=50))
     f_gpu = cp.exact_fit(T, out["lam"].cpu().numpy(), [A.cpu().numpy() for A in out["factors"]])
     f_ref = cp.exact_fit(T, ref["lam"], ref["factors"])
     assert abs(f_gpu - f_ref) < 1e-3, (f_gpu, f_ref, out["iters"], ref["iters"])
@@ -283,8 +294,11 @@ def test_congruence_09_trace_tracks_oracle(cb):
     np.testing.assert_allclose(trace.cpu().numpy(), ref["fits"], rtol=0, atol=1e-4)
 
 
-def test_full_size_mix_run_tracks_oracle(cb):
-    # the 400^3 FP32 workload (R=10, S=230, congruence 0.9), three outer iterations
+@pytest.mark.parametrize("eng", ["auto", "dense"])
+def test_full_size_mix_run_tracks_oracle(cb, engine, eng):
+    # the 400^3 FP32 workload (R=10, S=230, congruence 0.9), three outer iterations, with the
+    # factored-DCT mixing (auto) and with the dense tensor-core mixing
+    engine(cb.MIX_AUTO if eng == "auto" else cb.MIX_DENSE)
     dims = (400, 400, 400)
     prob = make_problem(dims, 10, C=0.9, eta=0.01, seed=1001, dtype=torch.float32, device=DEV)
     T = to_oracle_array(prob.X, dims)
@@ -382,14 +396,61 @@ def test_unfolding_copies_give_identical_runs(cb, path, dims):
 
 
 # ------------------------------------------------------------------------------------------------
-# a0 on the tensor cores: FP32 tensors whose dims are multiples of 4 take the tcgen05 path
-# (3xTF32, FP32-level accuracy); ragged tiles in every direction, several column blocks
+# a0 on the tensor cores (dense engine): FP32 tensors whose dims are multiples of 4 take the tcgen05
+# path (FP16 halves when every dim is a multiple of 8, else 3xTF32; FP32-level accuracy); ragged
+# tiles in every direction, several column blocks
 # ------------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("dims", [(64, 48, 40), (132, 20, 36), (300, 12, 8), (516, 8, 12), (16, 12, 20, 8),
                                   (400, 400, 400)])
-def test_tensor_core_mixing_matches_oracle(cb, dims):
+def test_tensor_core_mixing_matches_oracle(cb, engine, dims):
+    engine(cb.MIX_DENSE)
     X = rand_tensor(dims, torch.float32, 11)
     T = to_oracle_array(X, dims)
     Y = cb.cpr_mix_tensor(X, dims, seed=5, b=0)
     ref = mixing.mix_tensor(T, mixing.mixing_operators(5, 0, dims))
     assert rel(to_oracle_array(Y, dims), ref) < 1e-5
+
+
+# ------------------------------------------------------------------------------------------------
+# a0 by the factored DCT-II (mixed-radix FFT per fiber): stages of radix 2 to 25 (plain and
+# two-level), one to three stages, orders 2 to 4, fiber blocks that run past the end of a mode, blocks
+# of 2 to 32 fibers, the 400^3 and 1500 x ... sizes; FP32 to 1e-6 relative (FP32 FFT rounding), BF16
+# to the BF16 bar
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dims", [(64, 48, 40), (300, 12, 8), (16, 12, 20, 8), (40, 45, 21), (7, 10, 5), (20, 30),
+                                  (50, 15, 12, 6), (14, 9, 35), (96, 20, 45), (35, 14, 21), (6000, 8, 5),
+                                  (400, 400, 400), (1500, 60, 20)])
+def test_fft_mixing_matches_oracle(cb, engine, dims):
+    X = rand_tensor(dims, torch.float32, 12)
+    T = to_oracle_array(X, dims)
+    ref = mixing.mix_tensor(T, mixing.mixing_operators(7, 2, dims))
+    Y = cb.cpr_mix_tensor(X, dims, seed=7, b=2)
+    assert rel(to_oracle_array(Y, dims), ref) < 1e-6
+    # the dense engine computes the same operator (its split-TF32 error grows with I_n: 1.3e-5 at
+    # I_n = 1500, where the FFT's stays below 1e-6)
+    engine(cb.MIX_DENSE)
+    Yd = cb.cpr_mix_tensor(X, dims, seed=7, b=2)
+    assert rel(to_oracle_array(Yd, dims), ref) < 3e-5
+
+
+@pytest.mark.parametrize("dims", [(70, 30, 50), (100, 20, 12, 10)])
+def test_fft_mixing_bf16_matches_oracle(cb, dims):
+    # BF16 in and out, rounded to BF16 after every mode product (as the dense BF16 engine does)
+    X = rand_tensor(dims, torch.bfloat16, 13)
+    T = to_oracle_array(X, dims)
+    Y = cb.cpr_mix_tensor(X, dims, seed=9, b=0)
+    ref = mixing.mix_tensor(T, mixing.mixing_operators(9, 0, dims))
+    got = to_oracle_array(Y, dims)
+    assert rel(got, ref) < 1e-2
+    assert abs(np.linalg.norm(got) - np.linalg.norm(T)) < 1e-2 * np.linalg.norm(T)
+
+
+def test_mix_engine_switch_rejects_unknown_values(cb):
+    prev = cb.cpr_set_mix_engine(cb.MIX_AUTO)
+    try:
+        with pytest.raises(ValueError):
+            cb.cpr_set_mix_engine(17)
+        assert cb.cpr_set_mix_engine(cb.MIX_DENSE) == cb.MIX_AUTO
+        assert cb.cpr_set_mix_engine(cb.MIX_AUTO) == cb.MIX_DENSE
+    finally:
+        cb.cpr_set_mix_engine(prev)
