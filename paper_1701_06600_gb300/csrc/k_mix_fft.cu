@@ -43,7 +43,6 @@ namespace {
 
 constexpr uint32_t kFftWaitLimit = 1u << 24;
 constexpr int kSlots = 32;          // complex values a thread holds in a stage
-constexpr int kFftThreads = 256;
 constexpr int kMaxStages = 16;
 constexpr int kFftMaxSmem = 200 * 1024;
 constexpr int kMaxFftLen = 8192;    // keeps the multiply-high divisions exact
@@ -212,7 +211,7 @@ __device__ __forceinline__ void dft_comp(float2 (&v)[R1 * R2], const float2* tw,
 // FIRST: the stage reads the real fibers instead (rows 2p and 2p + 1 of the loaded block) in the DCT
 // reorder, times their signs: v_p[m] = d[s] (x_{2p}[s], x_{2p+1}[s]) with s = 2m (2m < I) or
 // 2(I - 1 - m) + 1; Ns = 1, so no twiddles.
-template <int R1, int R2, bool FIRST>
+template <int R1, int R2, bool FIRST, int TPB>
 __device__ __forceinline__ void fft_stage(float2* Z, int I, int Ipad, int S, const StageTab& sc, int tid,
                                           const float2* tw, const float* sg) {
   constexpr int R = R1 * R2, MAXB = kSlots / R;
@@ -221,7 +220,7 @@ __device__ __forceinline__ void fft_stage(float2* Z, int I, int Ipad, int S, con
   int dst[MAXB];
 #pragma unroll
   for (int q = 0; q < MAXB; ++q) {
-    const int b = tid + q * kFftThreads;
+    const int b = tid + q * TPB;
     dst[q] = -1;
     if (b < nbt) {
       const int p = fdiv(b, L, sc.mL), j = b - p * L;
@@ -286,21 +285,21 @@ __device__ __forceinline__ int fft_block(const FftArgs& a, int64_t blk, int64_t&
 
 // the stages of radix index RIX (one loop per radix: the register arrays of different radices are
 // never live at once); the plan lists its stages in radix-index order
-template <int RIX>
+template <int RIX, int TPB>
 __device__ __forceinline__ void fft_stages_of(float2* Z, int I, int Ipad, int S, int nst, const StageTab* stt, int& st,
                                               int tid, const float2* tw, const float* sg) {
   if (st == 0 && nst > 0 && stt[0].rix == RIX) {
-    fft_stage<kRadR1[RIX], kRadR2[RIX], true>(Z, I, Ipad, S, stt[0], tid, tw, sg);
+    fft_stage<kRadR1[RIX], kRadR2[RIX], true, TPB>(Z, I, Ipad, S, stt[0], tid, tw, sg);
     ++st;
   }
   for (; st < nst && stt[st].rix == RIX; ++st)
-    fft_stage<kRadR1[RIX], kRadR2[RIX], false>(Z, I, Ipad, S, stt[st], tid, tw, sg);
+    fft_stage<kRadR1[RIX], kRadR2[RIX], false, TPB>(Z, I, Ipad, S, stt[st], tid, tw, sg);
 }
 
 // One CTA per block of fibers (one bulk copy per fiber on the FP32 path).  Several CTAs share an SM,
 // so one CTA's copies overlap the others' transforms.
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads, 2) k_mix_fft(const __grid_constant__ FftArgs a) {
+template <typename T, int TPB>
+__global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_fft(const __grid_constant__ FftArgs a) {
   extern __shared__ float4 fft_smem4[];
   const int I = a.I, Ipad = a.Ipad, BJ = a.BJ, S = a.S;
   float* Y = reinterpret_cast<float*>(fft_smem4);
@@ -335,13 +334,13 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_mix_fft(const __grid_constan
     if (tid < nf)
       fft_bulk_copy(Y + tid * Ipad, U + (row0 + (int64_t)tid * a.rs_in_v) * I, (uint32_t)(I * sizeof(float)), bar);
   } else {        // plain loads: one warp per fiber, lanes along the fiber
-    for (int f = warp; f < nf; f += kFftThreads / 32) {
+    for (int f = warp; f < nf; f += TPB / 32) {
       const T* src = U + (row0 + (int64_t)f * a.rs_in_v) * I;
       for (int k = lane; k < I; k += 32) Y[f * Ipad + k] = ld_as_float<T>(src + k);
     }
   }
-  for (int e = tid; e < 5 * I; e += kFftThreads) reinterpret_cast<float*>(tw)[e] = a.tab[e];
-  for (int e = tid; e < (BJ - nf) * Ipad; e += kFftThreads) Y[nf * Ipad + e] = 0.f;   // fibers past the end of mode v
+  for (int e = tid; e < 5 * I; e += TPB) reinterpret_cast<float*>(tw)[e] = a.tab[e];
+  for (int e = tid; e < (BJ - nf) * Ipad; e += TPB) Y[nf * Ipad + e] = 0.f;   // fibers past the end of mode v
   // one thread polls the copies' mbarrier (polling by every thread would take issue slots from the
   // other CTAs on the SM); the others wait in the block barrier and then observe the completed phase
   bool ok = true;
@@ -359,27 +358,27 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_mix_fft(const __grid_constan
   // interleaved complex values)
   const int nst = a.nst;
   int st = 0;
-  fft_stages_of<0>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
-  fft_stages_of<1>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
-  fft_stages_of<2>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
-  fft_stages_of<3>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
-  fft_stages_of<4>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
-  fft_stages_of<5>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
-  fft_stages_of<6>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
-  fft_stages_of<7>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
-  fft_stages_of<8>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
-  fft_stages_of<9>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
-  fft_stages_of<10>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
-  fft_stages_of<11>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
-  fft_stages_of<12>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
-  fft_stages_of<13>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<0, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<1, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<2, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<3, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<4, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<5, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<6, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<7, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<8, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<9, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<10, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<11, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<12, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
+  fft_stages_of<13, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
   if (st != nst && tid == 0) atomicExch(a.err, 1);   // a stage order the host never produces
 
   // separate the two real fibers of each sequence and apply c_k exp(-i pi k / (2I)); the pair
   // (k, I - k) is read and written by one thread: (y_{2p}[k], y_{2p+1}[k]) replaces Z_p[k]
   {
     const int H2 = I / 2 + 1;
-    for (int w = tid; w < S * H2; w += kFftThreads) {
+    for (int w = tid; w < S * H2; w += TPB) {
       const int p = fdiv(w, H2, a.mH2), k = w - p * H2;
       float2* z = Z + p * Ipad;
       const int kk = k == 0 ? 0 : I - k;
@@ -396,12 +395,13 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_mix_fft(const __grid_constan
 
   // stores: the mode-v layout (the CTA's fibers adjacent for each k); lanes = 8 fibers x 4 k (fiber f
   // is component f & 1 of sequence f / 2), so a warp reads 32 distinct banks (Ipad odd multiple of 4)
-  // and writes four full 32-byte sectors.  The 8 warps split the fiber groups (G8 = min(groups, 8) of
-  // them at a time) and the groups of 4 k (8 / G8 warps per fiber group); addresses are stepped
+  // and writes four full 32-byte sectors.  The NW warps split the fiber groups (G8 = min(groups, NW)
+  // of them at a time) and the groups of 4 k (NW / G8 warps per fiber group); addresses are stepped
   {
     T* yv = static_cast<T*>(a.yv);
     const int FW = BJ < 8 ? BJ : 8, KW = 32 / FW;
-    const int ngf = BJ / FW, G8 = ngf < 8 ? ngf : 8, wpg = (kFftThreads / 32) / G8;
+    constexpr int NW = TPB / 32;
+    const int ngf = BJ / FW, G8 = ngf < NW ? ngf : NW, wpg = NW / G8;
     const int kstep = wpg * KW;
     for (int gf = warp % G8; gf < ngf; gf += G8) {
       const int f = gf * FW + lane % FW;
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_mix_fft(const __grid_constan
   }
   if (a.ysame) {   // the input's own layout: each fiber a contiguous row
     T* ys = static_cast<T*>(a.ysame);
-    for (int f = warp; f < nf; f += kFftThreads / 32) {
+    for (int f = warp; f < nf; f += TPB / 32) {
       T* dst = ys + (row0 + (int64_t)f * a.rs_in_v) * I;
       const float* z = Y + (f >> 1) * 2 * Ipad + (f & 1);
       for (int k = lane; k < I; k += 32) dst[k] = from_float<T>(z[2 * k]);
@@ -441,9 +441,10 @@ __global__ void k_fft_tables(int I, const double* __restrict__ signs, float* __r
 
 // the stage radices of I (every prime factor 2, 3, 5 or 7), grouped into the radices of kRadR1 x
 // kRadR2, listed in radix-index order; among the groupings, the one that admits the widest fiber block
-// (then the fewest stages)
+// (then the fewest stages).  CTAs of 128 threads (four per SM) unless that narrows the block below 8
+// fibers where 256 threads (two per SM) would not
 struct FftPlan {
-  int BJ, Ipad, nst;
+  int tpb, BJ, Ipad, nst;
   int rix[kMaxStages];
   size_t smem;
 };
@@ -451,28 +452,29 @@ struct FftPlan {
 size_t fft_smem_bytes(int BJ, int Ipad, int I) { return (size_t)(BJ * Ipad + 5 * I + 4) * sizeof(float) + 16; }
 
 // the widest block (a power of two up to 128 fibers, not wider than mode v needs) whose stages fit
-// the threads' register slots; blocks above 32 fibers only while two CTAs still fit an SM
-int fft_block_width(int I, int64_t Iv, int Ipad, const int* rix, int nst) {
+// the threads' register slots, within the shared memory that lets 512 / tpb CTAs share an SM
+int fft_block_width(int I, int64_t Iv, int Ipad, const int* rix, int nst, int tpb) {
   int64_t cap = 2;
   while (cap < Iv && cap < 128) cap *= 2;
+  const size_t smem_cap = (size_t)kFftMaxSmem / (512 / tpb);
   for (int BJ = 128; BJ >= 2; BJ /= 2) {
     if (BJ > cap) continue;
     const int S = BJ / 2;
     bool ok = true;
     for (int s = 0; s < nst && ok; ++s) {
       const int R = kRadR1[rix[s]] * kRadR2[rix[s]];
-      ok = ((int64_t)S * (I / R) + kFftThreads - 1) / kFftThreads <= kSlots / R;
+      ok = ((int64_t)S * (I / R) + tpb - 1) / tpb <= kSlots / R;
     }
     const size_t sm = fft_smem_bytes(BJ, Ipad, I);
-    if (ok && sm <= (size_t)kFftMaxSmem && (BJ <= 32 || sm <= (size_t)kFftMaxSmem / 2)) return BJ;
+    if (ok && sm <= (size_t)kFftMaxSmem && (BJ <= 8 || sm <= smem_cap)) return BJ;
   }
   return 0;
 }
 
-void fft_search(int m, int from, int* cur, int depth, int I, int64_t Iv, int Ipad, FftPlan* best) {
+void fft_search(int m, int from, int* cur, int depth, int I, int64_t Iv, int Ipad, int tpb, FftPlan* best) {
   if (m == 1) {
     if (depth == 0) return;
-    const int BJ = fft_block_width(I, Iv, Ipad, cur, depth);
+    const int BJ = fft_block_width(I, Iv, Ipad, cur, depth, tpb);
     if (BJ > best->BJ || (BJ == best->BJ && BJ > 0 && depth < best->nst)) {
       best->BJ = BJ;
       best->nst = depth;
@@ -485,7 +487,7 @@ void fft_search(int m, int from, int* cur, int depth, int I, int64_t Iv, int Ipa
     const int R = kRadR1[r] * kRadR2[r];
     if (m % R) continue;
     cur[depth] = r;
-    fft_search(m / R, r, cur, depth + 1, I, Iv, Ipad, best);
+    fft_search(m / R, r, cur, depth + 1, I, Iv, Ipad, tpb, best);
   }
 }
 
@@ -497,27 +499,34 @@ bool fft_plan(int I, int64_t Iv, FftPlan* pl) {
   if (m != 1) return false;
   int Ipad = (I + 3) / 4 * 4;
   if ((Ipad / 4) % 2 == 0) Ipad += 4;   // Ipad / 4 odd: conflict-free column reads
-  FftPlan best;
-  memset(&best, 0, sizeof(best));
-  int cur[kMaxStages];
-  fft_search(I, 0, cur, 0, I, Iv, Ipad, &best);
-  if (best.BJ == 0) return false;
-  best.Ipad = Ipad;
-  best.smem = fft_smem_bytes(best.BJ, Ipad, I);
-  *pl = best;
+  FftPlan best[2];
+  const int tpbs[2] = {128, 256};
+  for (int t = 0; t < 2; ++t) {
+    memset(&best[t], 0, sizeof(FftPlan));
+    int cur[kMaxStages];
+    fft_search(I, 0, cur, 0, I, Iv, Ipad, tpbs[t], &best[t]);
+    best[t].tpb = tpbs[t];
+  }
+  const int want = (int)std::min<int64_t>(8, Iv);
+  const int pick = (best[0].BJ > 0 && (best[0].BJ >= want || best[0].BJ >= best[1].BJ)) ? 0 : 1;
+  if (best[pick].BJ == 0) return false;
+  *pl = best[pick];
+  pl->Ipad = Ipad;
+  pl->smem = fft_smem_bytes(pl->BJ, Ipad, I);
   return true;
 }
 
-template <typename T>
+template <typename T, int TPB>
 cudaError_t launch_fft_kernel(const FftArgs& a, size_t smem, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_mix_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftMaxSmem + 1024);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_mix_fft<T, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftMaxSmem + 1024);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   if (a.nblocks > INT32_MAX) return cudaErrorInvalidValue;
-  k_mix_fft<T><<<(unsigned)a.nblocks, kFftThreads, smem, s>>>(a);
+  k_mix_fft<T, TPB><<<(unsigned)a.nblocks, TPB, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -598,8 +607,11 @@ cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* ta
   if (a.nblocks <= 0) return cudaErrorInvalidValue;
   const size_t es = dtype == CPR_F32 ? 4 : 2;
   a.bulk = dtype == CPR_F32 && (I * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(U) & 15) == 0;
-  if (dtype == CPR_F32) return launch_fft_kernel<float>(a, pl.smem, s);
-  if (dtype == CPR_BF16) return launch_fft_kernel<__nv_bfloat16>(a, pl.smem, s);
+  if (dtype == CPR_F32)
+    return pl.tpb == 128 ? launch_fft_kernel<float, 128>(a, pl.smem, s) : launch_fft_kernel<float, 256>(a, pl.smem, s);
+  if (dtype == CPR_BF16)
+    return pl.tpb == 128 ? launch_fft_kernel<__nv_bfloat16, 128>(a, pl.smem, s)
+                         : launch_fft_kernel<__nv_bfloat16, 256>(a, pl.smem, s);
   return cudaErrorInvalidValue;
 }
 
