@@ -9,6 +9,7 @@ Modules
   streams    which Philox draw feeds which random quantity of the method
   cp         §2.1 tensor algebra, CP-ALS (Alg. 1), SKR (Alg. 2), CPRAND (Alg. 3), stopping rules
   mixing     DCT-II mixing, CPRAND-MIX in its real form (Alg. 5)
+  mixing_fft unitary-DFT mixing, CPRAND-MIX in its complex form (Alg. 4, real LS of eq. (rcLS))
   coherence  leverage scores and coherence (§2.2, §3.2.2)
 
 Parity unpinned: nothing.  Every function is pinned by a test in tests/test_oracle_*.py against

@@ -264,8 +264,10 @@ __device__ void cluster_mode_update(const Prob& p, int n, uint32_t t, unsigned c
       if (m < N && m != n) v[m] = factor_row<ACC, C>(cl, sm, Lo, m, ids[jj * kMaxOrder + m], R)[r];
     double z = 1.0;
 #pragma unroll
-    for (int m = 0; m < kMaxOrder; ++m)
-      if (m < N && m != n) z *= (double)v[m] * sc[m * R + r];
+    for (int m = 0; m < kMaxOrder; ++m) {
+      if (m >= N) break;   // a branch, not predicated-off FP64 multiplies (they still occupy the pipe)
+      if (m != n) z *= (double)v[m] * sc[m * R + r];
+    }
     Zd[e] = z;
     Zf[e] = (ACC)z;
   }

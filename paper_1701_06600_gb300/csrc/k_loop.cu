@@ -383,14 +383,15 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
   for (int e = tid; e < cnt * rp; e += kLT) {
     const int jj = e / rp, r = e - jj * rp;
     if (r < R) {
-      double z = 1.0;
-#pragma unroll
-      for (int m = 0; m < kMaxOrder; ++m)
-        if (m < N && m != n) {
+      // a loop over the N - 1 other modes only: predicated-off FP64 multiplies of a loop unrolled to
+      // the maximum order would still occupy the FP64 pipe
+      double z = scomb[r];
+#pragma unroll 1
+      for (int m = 0; m < N; ++m)
+        if (m != n) {
           const ACC* Fm = reinterpret_cast<const ACC*>(sm + L.F[m]);
           z *= (double)Fm[(int)ids[jj * kMaxOrder + m] * rp + r];
         }
-      z *= scomb[r];
       Zd[jj * R + r] = z;
       Zf[e] = (ACC)z;
     } else {
