@@ -263,6 +263,24 @@ CPR_API int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, ui
 CPR_API int cpr_unmix_factors(const cpr_ktensor* Khat, cpr_ktensor* out, uint64_t seed, uint32_t b,
                       void* ws, size_t ws_bytes, void* stream);
 
+/* CPRAND-MIX in its complex form (Alg. 4), the paper's experimental variant: every mode is mixed with
+ * F_n D_n, F_n the unitary DFT (D_n the Philox signs of cpr_cprand_mix), so the mixed tensor is
+ * complex; the factors stay real.  A mode-n update unmixes the S sampled fibers of the mixed tensor
+ * in mode n (D_n F_n^* per fiber), forms the sampled rows of the Khatri-Rao product of the mixed
+ * factors F_m D_m A^(m), and solves the least squares over real A^(n) by stacking real and imaginary
+ * parts (eq. (rcLS)); then normalizes and mixes the new factor.  Samples, initial factors and fit
+ * entries use the Philox streams of cpr_cprand_mix; the stopping rules of Sec. 4.2 are checked on the
+ * host after each outer iteration (the sampled fit on X with the real factors).
+ *   X: FP32, every I_n in [5, 1600] a product of 2, 3, 5 and 7; R <= CPR_MAX_RANK; S >= R.
+ *   out: caller-owned real factors (I_n x R, FP64) and lambda, returned normalized in the original
+ *   basis (no unmixing step).  opts->init_from_out must be 0.  ws: at least
+ *   cpr_cprand_mix_fft_workspace_size(...) bytes (about (N + 1) complex copies of the tensor).
+ * Returns CPR_EINVAL for unsupported shapes or types; device-detected conditions (singular Gram,
+ * non-finite fit) in result->status.  Synchronizes the stream once per outer iteration. */
+CPR_API size_t cpr_cprand_mix_fft_workspace_size(const cpr_tensor* X, int R, int64_t S, const cpr_opts* opts);
+CPR_API int cpr_cprand_mix_fft(const cpr_tensor* X, int R, int64_t S, const cpr_opts* opts, cpr_ktensor* out,
+                               cpr_result* result, void* ws, size_t ws_bytes, void* stream);
+
 /* Mixing engine (process-wide; applies to cpr_mix_tensor and to every CPRAND-MIX call enqueued
  * afterwards): CPR_MIX_AUTO takes the factored DCT where it applies (see cpr_mix_tensor), else the
  * dense products; CPR_MIX_DENSE always takes the dense products (the tensor-core kernels for FP32);

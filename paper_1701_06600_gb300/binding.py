@@ -74,6 +74,12 @@ _SIGS = {
                                       ctypes.POINTER(CprOpts), ctypes.POINTER(CprKtensor),
                                       ctypes.POINTER(CprResult), ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.c_void_p]),
+    "cpr_cprand_mix_fft": (ctypes.c_int, [ctypes.POINTER(CprTensor), ctypes.c_int, ctypes.c_int64,
+                                      ctypes.POINTER(CprOpts), ctypes.POINTER(CprKtensor),
+                                      ctypes.POINTER(CprResult), ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.c_void_p]),
+    "cpr_cprand_mix_fft_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(CprTensor), ctypes.c_int, ctypes.c_int64,
+                                                          ctypes.POINTER(CprOpts)]),
     "cpr_batched_workspace_size": (ctypes.c_size_t, [ctypes.c_int, ctypes.POINTER(CprTensor),
                                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
                                                      ctypes.POINTER(CprOpts), ctypes.c_int]),
@@ -336,6 +342,24 @@ def cpr_cprand(X, dims, R, S, opts=None, init=None, ws=None, stream=None):
 def cpr_cprand_mix(X, dims, R, S, opts=None, init=None, ws=None, stream=None):
     """CPRAND-MIX, real-transform form (Alg. 5); factors are returned unmixed."""
     return _run_whole("cpr_cprand_mix", METHOD_CPRAND_MIX, X, dims, R, S, opts, init, ws, stream)
+
+
+def cpr_cprand_mix_fft(X, dims, R, S, opts=None, ws=None, stream=None):
+    """CPRAND-MIX, complex-transform form (Alg. 4): unitary-DFT mixing, real factors."""
+    d = tensor_desc(X, dims)
+    o = opts if opts is not None else cpr_default_opts()
+    lam, factors = alloc_ktensor(dims, R, X.device)
+    k = ktensor_desc(lam, factors)
+    need = lib().cpr_cprand_mix_fft_workspace_size(ctypes.byref(d), int(R), int(S), ctypes.byref(o))
+    if need == 0:
+        raise CprError(EINVAL, "cpr_cprand_mix_fft_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, X.device)
+    res = CprResult()
+    st = lib().cpr_cprand_mix_fft(ctypes.byref(d), int(R), int(S), ctypes.byref(o), ctypes.byref(k), ctypes.byref(res),
+                                  ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()), _stream(stream))
+    _check(st, "cpr_cprand_mix_fft")
+    return {"lam": lam, "factors": factors, "ws": ws, **result_dict(res)}
 
 
 def cpr_cprand_batched(Xs, dims_list, Rs, Ss, opts_list=None, mix=False, ws=None, stream=None):

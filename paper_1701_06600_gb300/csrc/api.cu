@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -967,6 +968,214 @@ size_t cpr_batched_workspace_size(int B, const cpr_tensor* Xs, const int* Rs, co
 int cpr_cprand_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, const cpr_opts* opts, int mix,
                        cpr_ktensor* outs, cpr_result* results, void* ws, size_t ws_bytes, void* stream) {
   return run_batched(B, Xs, Rs, Ss, opts, mix ? 1 : 0, outs, results, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+// ---- CPRAND-MIX in its complex form (Alg. 4): unitary-DFT mixing, real factors, host-driven loop ----
+namespace {
+struct CfLayout {
+  double* signs[kMaxOrder];
+  double* table;
+  float* tab[kMaxOrder];
+  float2* W[kMaxOrder];
+  float2* Xh;                // the mixed tensor, standard layout (complex)
+  float2* tmp;               // the other buffer of the pass chain
+  float2* rep[kMaxOrder];    // mode-n unfolding copies, n >= 1
+  float2* Ah[kMaxOrder];     // mixed factors
+  uint32_t* idx;             // S x N
+  float* Xr;                 // Imax x 2S
+  double* Zr;                // 2S x R
+  double* G;
+  double* Gi;
+  double* M;                 // Imax x R
+  uint32_t* fidx;            // P_hat x N
+  double* fx;                // P_hat
+  double* fpart;             // fit partial sums
+  double* npart;             // norm partial sums
+  int* err;                  // [0] wait expired, [1] singular Gram
+};
+
+size_t cf_layout(Carver& c, const cpr_tensor* X, int R, int64_t S, int64_t P_hat, CfLayout& L) {
+  const int N = X->order;
+  const int64_t P = prod_dims(X);
+  int64_t imax = 0;
+  for (int n = 0; n < N; ++n) imax = std::max(imax, X->dims[n]);
+  for (int n = 0; n < N; ++n) {
+    const size_t I = (size_t)X->dims[n];
+    L.signs[n] = c.take<double>(I);
+    L.tab[n] = c.take<float>(5 * I);
+    L.W[n] = c.take<float2>(I * I);
+    L.Ah[n] = c.take<float2>(I * (size_t)R);
+  }
+  L.table = c.take<double>((size_t)4 * imax);
+  L.Xh = c.take<float2>((size_t)P);
+  L.tmp = c.take<float2>((size_t)P);
+  L.rep[0] = L.Xh;
+  for (int n = 1; n < N; ++n) L.rep[n] = c.take<float2>((size_t)P);
+  L.idx = c.take<uint32_t>((size_t)S * N);
+  L.Xr = c.take<float>((size_t)imax * 2 * S);
+  L.Zr = c.take<double>((size_t)2 * S * R);
+  L.G = c.take<double>((size_t)R * R);
+  L.Gi = c.take<double>((size_t)R * R);
+  L.M = c.take<double>((size_t)imax * R);
+  L.fidx = c.take<uint32_t>((size_t)P_hat * N);
+  L.fx = c.take<double>((size_t)P_hat);
+  L.fpart = c.take<double>((size_t)cf_fit_blocks((int)P_hat));
+  L.npart = c.take<double>((size_t)sumsq_blocks(P));
+  L.err = c.take<int>(4);
+  return align256(c.off) + 256;
+}
+
+int cf_check(const cpr_tensor* X, int R, int64_t S, const cpr_opts& o) {
+  if (int st = check_tensor(X, false)) return st;
+  if (X->dtype != CPR_F32 || check_rank_samples(R, S)) return CPR_EINVAL;
+  if (!mix_cfft_supported(X->order, X->dims)) return CPR_EINVAL;
+  for (int n = 0; n < X->order; ++n)
+    if (X->dims[n] > 1600) return CPR_EINVAL;   // the unmixing kernel stages 16 fibers in shared memory
+  if (o.fit_samples < 1 || o.fit_samples > INT32_MAX || S > INT32_MAX / 2) return CPR_EINVAL;
+  return CPR_OK;
+}
+}  // namespace
+
+size_t cpr_cprand_mix_fft_workspace_size(const cpr_tensor* X, int R, int64_t S, const cpr_opts* opts) {
+  const cpr_opts o = opts ? *opts : defaults();
+  if (cf_check(X, R, S, o)) return 0;
+  Carver c(nullptr);
+  CfLayout L;
+  return cf_layout(c, X, R, S, o.fit_samples, L);
+}
+
+int cpr_cprand_mix_fft(const cpr_tensor* X, int R, int64_t S, const cpr_opts* opts, cpr_ktensor* out,
+                       cpr_result* result, void* ws, size_t ws_bytes, void* stream) {
+  const cpr_opts o = opts ? *opts : defaults();
+  if (!X || !X->data) return CPR_EINVAL;
+  if (int st = cf_check(X, R, S, o)) return st;
+  if (int st = check_ktensor(out, X, R)) return st;
+  if (o.init_from_out) return CPR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = X->order;
+  const int64_t P = prod_dims(X);
+  const int Ph = (int)o.fit_samples;
+  Carver cm(nullptr);
+  CfLayout L;
+  if (int st = check_ws(ws, ws_bytes, cf_layout(cm, X, R, S, Ph, L))) return st;
+  Carver cw(ws);
+  cf_layout(cw, X, R, S, Ph, L);
+  int64_t launches = 0;
+  PhaseEvents ph;
+  if (int st = ph.mark(0, s)) return st;
+  CPR_CUDA(cudaMemsetAsync(L.err, 0, 4 * sizeof(int), s));
+  // ||X|| (FP64 partial sums, summed on the host in a fixed order)
+  const int nblk = sumsq_blocks(P);
+  CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq(X->data, X->dtype, P, L.npart, nblk, s));
+  // operators: signs (Philox), FFT tables, W = F D; the mixed tensor by N unitary-DFT passes
+  for (int n = 0; n < N; ++n) {
+    const int I = (int)X->dims[n];
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_build_mix_ops(I, o.seed, o.batch_index, n, L.table, nullptr, nullptr, nullptr,
+                                                      L.signs[n], s));
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_fft_tables(I, L.signs[n], L.tab[n], s));
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_cf_ops(I, L.signs[n], L.W[n], s));
+  }
+  {
+    void* bufs[2] = {L.Xh, L.tmp};
+    const void* U = X->data;
+    for (int n = 0; n < N; ++n) {
+      void* y = bufs[(N - 1 - n) & 1];
+      void* ys = n == N - 1 ? static_cast<void*>(L.rep[N - 1]) : nullptr;
+      CPR_LAUNCH(CPR_KERNEL_MIX, launch_mix_cfft(U, n == 0, y, ys, L.tab[n], N, X->dims, n, L.err, s));
+      U = y;
+    }
+    for (int n = 1; n < N - 1; ++n)   // 8-byte entries: the unfolding copy moves them as FP64 words
+      CPR_LAUNCH(CPR_KERNEL_OTHER, launch_unfold_copy(L.Xh, L.rep[n], CPR_F64, N, X->dims, n, s));
+  }
+  // initial factors (the init stream, as CPRAND) and their mixed copies; the fit entries
+  for (int m = 1; m < N; ++m) {
+    const int I = (int)X->dims[m];
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_cf_init(I, R, m, o.seed, o.batch_index, out->factors[m], s));
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_cf_mix_factor(I, R, L.W[m], out->factors[m], L.Ah[m], s));
+  }
+  CPR_LAUNCH(CPR_KERNEL_OTHER,
+             launch_cf_fit_setup(static_cast<const float*>(X->data), N, X->dims, R, Ph, o.seed, o.batch_index, L.fidx,
+                                 L.fx, s));
+  std::vector<double> npart(nblk);
+  CPR_CUDA(cudaMemcpyAsync(npart.data(), L.npart, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s));
+  CPR_CUDA(cudaStreamSynchronize(s));
+  double nx2 = 0.0;
+  for (double v : npart) nx2 += v;
+  const double normx = sqrt(nx2);
+  if (int st = ph.mark(1, s)) return st;
+  // outer iterations; the stopping rules of Sec. 4.2 on the host after every iteration
+  const int cap = o.fixed_iters > 0 ? o.fixed_iters : o.max_iters;
+  const int fb = cf_fit_blocks(Ph);
+  std::vector<double> fpart(fb);
+  int errs[4] = {0, 0, 0, 0};
+  double best = -1e300, last = 0.0, fit = 0.0;
+  int iters = 0, stall = 0, status = CPR_OK;
+  const float2* Ahc[kMaxOrder];
+  const double* Ac[kMaxOrder];
+  for (int m = 0; m < N; ++m) {
+    Ahc[m] = L.Ah[m];
+    Ac[m] = out->factors[m];
+  }
+  while (iters < cap) {
+    const uint32_t t = o.first_iter + (uint32_t)iters;
+    for (int n = 0; n < N; ++n) {
+      CPR_LAUNCH(CPR_KERNEL_SAMPLE_SKR,
+                 launch_sample_only(X->data, N, X->dims, n, S, o.seed, o.batch_index, t, L.idx, nullptr, s));
+      CPR_LAUNCH(CPR_KERNEL_SOLVE, launch_cf_update(L.rep[n], L.idx, L.W[n], Ahc, N, X->dims, n, (int)S, R, L.Xr,
+                                                    L.Zr, L.G, L.Gi, L.M, out->factors[n], out->lambda, L.err + 1, s));
+      CPR_LAUNCH(CPR_KERNEL_SOLVE, launch_cf_mix_factor((int)X->dims[n], R, L.W[n], out->factors[n], L.Ah[n], s));
+    }
+    CPR_LAUNCH(CPR_KERNEL_FIT, launch_cf_fit(Ac, out->lambda, N, X->dims, R, Ph, L.fidx, L.fx, L.fpart, s));
+    CPR_CUDA(cudaMemcpyAsync(fpart.data(), L.fpart, sizeof(double) * fb, cudaMemcpyDeviceToHost, s));
+    CPR_CUDA(cudaMemcpyAsync(errs, L.err, sizeof(errs), cudaMemcpyDeviceToHost, s));
+    CPR_CUDA(cudaStreamSynchronize(s));
+    double e2 = 0.0;
+    for (double v : fpart) e2 += v;
+    const double v = (double)P / (double)Ph * e2;
+    fit = 1.0 - sqrt(v) / normx;
+    if (o.fit_trace_dev) CPR_CUDA(cudaMemcpyAsync(o.fit_trace_dev + iters, &fit, sizeof(double), cudaMemcpyHostToDevice, s));
+    ++iters;
+    bool stop = false;
+    if (errs[0]) {
+      status = CPR_ETIMEOUT;
+      stop = true;
+    } else if (errs[1]) {
+      status = CPR_ESINGULAR;
+      stop = true;
+    } else if (!std::isfinite(fit)) {
+      status = CPR_ENONFINITE;
+      stop = true;
+    } else if (o.fixed_iters > 0) {
+      stop = iters >= o.fixed_iters;
+    } else {
+      if (fit > best) {
+        best = fit;
+        stall = 0;
+      } else {
+        ++stall;
+      }
+      if (iters >= o.max_iters) stop = true;
+      if (iters >= 2 && fabs(fit - last) <= o.fit_tol) stop = true;
+      if (o.noise_eta >= 0.0 && fit >= 1.0 - 1.2 * o.noise_eta) stop = true;
+      if (o.stall_iters > 0 && stall >= o.stall_iters) stop = true;
+    }
+    last = fit;
+    if (stop) break;
+  }
+  if (int st = ph.mark(2, s)) return st;
+  if (int st = ph.mark(3, s)) return st;
+  CPR_CUDA(cudaStreamSynchronize(s));
+  if (result) {
+    result->iters = iters;
+    result->status = status;
+    result->fit_est = fit;
+    result->norm_x = normx;
+    result->kernel_launches = launches;
+    result->ms_setup = ph.ms(0, 1);
+    result->ms_iterate = ph.ms(1, 2);
+    result->ms_finish = ph.ms(2, 3);
+  }
+  return CPR_OK;
 }
 
 int cpr_cp_als(const cpr_tensor* X, int R, const cpr_opts* opts, cpr_ktensor* out, cpr_result* result, void* ws,

@@ -327,6 +327,24 @@ cudaError_t launch_fft_tables(int I, const double* signs, float* tab, cudaStream
 cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* tab, int dtype, int N,
                            const int64_t* dims, int n, int* err, cudaStream_t s);
 int mix_engine();   // CPR_MIX_* (process-wide, cpr_set_mix_engine)
+// the unitary DFT passes of the complex form (Alg. 4): complex (float2) output; the first pass reads
+// the real FP32 tensor (real_in), later passes complex input; tab as for launch_mix_fft
+bool mix_cfft_supported(int N, const int64_t* dims);
+cudaError_t launch_mix_cfft(const void* U, bool real_in, void* yv, void* ysame, const float* tab, int N,
+                            const int64_t* dims, int n, int* err, cudaStream_t s);
+
+// CPRAND-MIX in its complex form (Alg. 4), k_mixc.cu
+cudaError_t launch_cf_ops(int I, const double* signs, float2* W, cudaStream_t s);
+cudaError_t launch_cf_init(int I, int R, int m, uint64_t seed, uint32_t b, double* A, cudaStream_t s);
+cudaError_t launch_cf_mix_factor(int I, int R, const float2* W, const double* A, float2* Ah, cudaStream_t s);
+cudaError_t launch_cf_update(const float2* Xn, const uint32_t* idx, const float2* W, const float2* const* Ah,
+                             int N, const int64_t* dims, int n, int S, int R, float* Xr, double* Zr, double* G,
+                             double* Gi, double* M, double* A, double* lam, int* bad, cudaStream_t s);
+cudaError_t launch_cf_fit_setup(const float* X, int N, const int64_t* dims, int R, int P_hat, uint64_t seed,
+                                uint32_t b, uint32_t* idx, double* xv, cudaStream_t s);
+int cf_fit_blocks(int P_hat);
+cudaError_t launch_cf_fit(const double* const* A, const double* lam, int N, const int64_t* dims, int R, int P_hat,
+                          const uint32_t* idx, const double* xv, double* part, cudaStream_t s);
 
 // mixing (Alg. 5)
 cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, double* table, float* W32,

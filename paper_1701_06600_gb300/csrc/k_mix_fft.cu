@@ -63,6 +63,7 @@ struct FftArgs {
   const float* tab;     // twiddles (2I), post-scales (2I), signs (I)
   int I, Ipad, BJ, S, nst, bulk;
   uint32_t mH2;         // ceil(2^32 / (I / 2 + 1))
+  float cscale;         // complex transform: 1 / sqrt(I) (the unitary DFT)
   StageTab st[kMaxStages];
   int64_t Iv;           // extent of the mode the CTA's fibers run along
   int64_t rs_in_v;      // input row stride of one step in i_v
@@ -423,6 +424,104 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_fft(const __grid_constan
   }
 }
 
+// ---- the unitary DFT of the complex form of CPRAND-MIX (Alg. 4) ----
+// A CTA owns BJ fibers, each its own complex sequence (fiber f at Z + f Ipad, interleaved): the
+// fibers are loaded times the signs of the mode (real fibers get a zero imaginary part), transformed
+// by the same Stockham stages (the first has no twiddles) and scaled by 1 / sqrt(I) on the way out to
+// the mode-v unfolding layout (and, when asked, the input's own layout).
+template <int RIX, int TPB>
+__device__ __forceinline__ void cfft_stages_of(float2* Z, int I, int Ipad, int S, int nst, const StageTab* stt,
+                                               int& st, int tid, const float2* tw) {
+  for (; st < nst && stt[st].rix == RIX; ++st)
+    fft_stage<kRadR1[RIX], kRadR2[RIX], false, TPB>(Z, I, Ipad, S, stt[st], tid, tw, nullptr);
+}
+
+template <typename TIN, int TPB>
+__global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_cfft(const __grid_constant__ FftArgs a) {
+  extern __shared__ float4 fft_smem4[];
+  const int I = a.I, Ipad = a.Ipad, BJ = a.BJ, S = a.S;
+  float2* Z = reinterpret_cast<float2*>(fft_smem4);
+  float2* tw = Z + BJ * Ipad;
+  const float* sg = reinterpret_cast<const float*>(tw + 2 * I);   // after the (unused) post-scales
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __shared__ StageTab s_st[kMaxStages];
+  __shared__ longlong4 s_blk;
+  if (tid < kMaxStages) s_st[tid] = a.st[tid];
+  if (tid == 0) {
+    int64_t r0, o0;
+    const int n = fft_block(a, blockIdx.x, r0, o0);
+    s_blk = make_longlong4(r0, o0, n, 0);
+  }
+  for (int e = tid; e < 5 * I; e += TPB) reinterpret_cast<float*>(tw)[e] = a.tab[e];
+  __syncthreads();
+  const int64_t row0 = s_blk.x, out0 = s_blk.y;
+  const int nf = (int)s_blk.z;
+  const TIN* U = static_cast<const TIN*>(a.U);
+  for (int f = warp; f < BJ; f += TPB / 32) {   // one warp per fiber; fibers past the end: zero
+    const TIN* src = U + (row0 + (int64_t)f * a.rs_in_v) * I;
+    for (int k = lane; k < I; k += 32) {
+      float2 x = make_float2(0.f, 0.f);
+      if (f < nf) {
+        const float d = sg[k];
+        if constexpr (sizeof(TIN) == 8) {
+          const float2 u = src[k];
+          x = make_float2(u.x * d, u.y * d);
+        } else {
+          x = make_float2(src[k] * d, 0.f);
+        }
+      }
+      Z[f * Ipad + k] = x;
+    }
+  }
+  __syncthreads();
+  const int nst = a.nst;
+  int st = 0;
+  cfft_stages_of<0, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  cfft_stages_of<1, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  cfft_stages_of<2, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  cfft_stages_of<3, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  cfft_stages_of<4, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  cfft_stages_of<5, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  cfft_stages_of<6, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  cfft_stages_of<7, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  cfft_stages_of<8, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  cfft_stages_of<9, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  cfft_stages_of<10, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  cfft_stages_of<11, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  cfft_stages_of<12, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  cfft_stages_of<13, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw);
+  if (st != nst && tid == 0) atomicExch(a.err, 1);   // a stage order the host never produces
+  const float c = a.cscale;
+  {
+    float2* yv = static_cast<float2*>(a.yv);
+    const int FW = BJ < 8 ? BJ : 8, KW = 32 / FW;
+    constexpr int NW = TPB / 32;
+    const int ngf = BJ / FW, G8 = ngf < NW ? ngf : NW, wpg = NW / G8;
+    const int kstep = wpg * KW;
+    for (int gf = warp % G8; gf < ngf; gf += G8) {
+      const int f = gf * FW + lane % FW;
+      int k = (warp / G8) * KW + lane / FW;
+      if (f >= nf) continue;
+      float2* dst = yv + out0 + f + (int64_t)k * a.out_k;
+      const int64_t dstep = (int64_t)kstep * a.out_k;
+      for (; k < I; k += kstep, dst += dstep) {
+        const float2 z = Z[f * Ipad + k];
+        *dst = make_float2(z.x * c, z.y * c);
+      }
+    }
+  }
+  if (a.ysame) {
+    float2* ys = static_cast<float2*>(a.ysame);
+    for (int f = warp; f < nf; f += TPB / 32) {
+      float2* dst = ys + (row0 + (int64_t)f * a.rs_in_v) * I;
+      for (int k = lane; k < I; k += 32) {
+        const float2 z = Z[f * Ipad + k];
+        dst[k] = make_float2(z.x * c, z.y * c);
+      }
+    }
+  }
+}
+
 // twiddles exp(-2 pi i t / I), post-scales c_k (cos, sin)(pi k / (2I)) / 2 and the signs d_k;
 // computed in FP64, rounded once
 __global__ void k_fft_tables(int I, const double* __restrict__ signs, float* __restrict__ tab) {
@@ -449,32 +548,36 @@ struct FftPlan {
   size_t smem;
 };
 
-size_t fft_smem_bytes(int BJ, int Ipad, int I) { return (size_t)(BJ * Ipad + 5 * I + 4) * sizeof(float) + 16; }
+// the fiber block (complex: two floats per entry), the tables, the mbarrier
+size_t fft_smem_bytes(int BJ, int Ipad, int I, bool cplx = false) {
+  return (size_t)((cplx ? 2 : 1) * BJ * Ipad + 5 * I + 4) * sizeof(float) + 16;
+}
 
 // the widest block (a power of two up to 128 fibers, not wider than mode v needs) whose stages fit
 // the threads' register slots, within the shared memory that lets 512 / tpb CTAs share an SM
-int fft_block_width(int I, int64_t Iv, int Ipad, const int* rix, int nst, int tpb) {
+int fft_block_width(int I, int64_t Iv, int Ipad, const int* rix, int nst, int tpb, bool cplx) {
   int64_t cap = 2;
   while (cap < Iv && cap < 128) cap *= 2;
   const size_t smem_cap = (size_t)kFftMaxSmem / (512 / tpb);
   for (int BJ = 128; BJ >= 2; BJ /= 2) {
     if (BJ > cap) continue;
-    const int S = BJ / 2;
+    const int S = cplx ? BJ : BJ / 2;   // complex: every fiber its own sequence
     bool ok = true;
     for (int s = 0; s < nst && ok; ++s) {
       const int R = kRadR1[rix[s]] * kRadR2[rix[s]];
       ok = ((int64_t)S * (I / R) + tpb - 1) / tpb <= kSlots / R;
     }
-    const size_t sm = fft_smem_bytes(BJ, Ipad, I);
+    const size_t sm = fft_smem_bytes(BJ, Ipad, I, cplx);
     if (ok && sm <= (size_t)kFftMaxSmem && (BJ <= 8 || sm <= smem_cap)) return BJ;
   }
   return 0;
 }
 
-void fft_search(int m, int from, int* cur, int depth, int I, int64_t Iv, int Ipad, int tpb, FftPlan* best) {
+void fft_search(int m, int from, int* cur, int depth, int I, int64_t Iv, int Ipad, int tpb, bool cplx,
+                FftPlan* best) {
   if (m == 1) {
     if (depth == 0) return;
-    const int BJ = fft_block_width(I, Iv, Ipad, cur, depth, tpb);
+    const int BJ = fft_block_width(I, Iv, Ipad, cur, depth, tpb, cplx);
     if (BJ > best->BJ || (BJ == best->BJ && BJ > 0 && depth < best->nst)) {
       best->BJ = BJ;
       best->nst = depth;
@@ -487,11 +590,11 @@ void fft_search(int m, int from, int* cur, int depth, int I, int64_t Iv, int Ipa
     const int R = kRadR1[r] * kRadR2[r];
     if (m % R) continue;
     cur[depth] = r;
-    fft_search(m / R, r, cur, depth + 1, I, Iv, Ipad, tpb, best);
+    fft_search(m / R, r, cur, depth + 1, I, Iv, Ipad, tpb, cplx, best);
   }
 }
 
-bool fft_plan(int I, int64_t Iv, FftPlan* pl) {
+bool fft_plan(int I, int64_t Iv, FftPlan* pl, bool cplx = false) {
   if (I < 2 || I > kMaxFftLen) return false;
   int m = I;
   for (int p : {2, 3, 5, 7})
@@ -504,7 +607,7 @@ bool fft_plan(int I, int64_t Iv, FftPlan* pl) {
   for (int t = 0; t < 2; ++t) {
     memset(&best[t], 0, sizeof(FftPlan));
     int cur[kMaxStages];
-    fft_search(I, 0, cur, 0, I, Iv, Ipad, tpbs[t], &best[t]);
+    fft_search(I, 0, cur, 0, I, Iv, Ipad, tpbs[t], cplx, &best[t]);
     best[t].tpb = tpbs[t];
   }
   const int want = (int)std::min<int64_t>(8, Iv);
@@ -512,7 +615,7 @@ bool fft_plan(int I, int64_t Iv, FftPlan* pl) {
   if (best[pick].BJ == 0) return false;
   *pl = best[pick];
   pl->Ipad = Ipad;
-  pl->smem = fft_smem_bytes(pl->BJ, Ipad, I);
+  pl->smem = fft_smem_bytes(pl->BJ, Ipad, I, cplx);
   return true;
 }
 
@@ -527,6 +630,20 @@ cudaError_t launch_fft_kernel(const FftArgs& a, size_t smem, cudaStream_t s) {
   }
   if (a.nblocks > INT32_MAX) return cudaErrorInvalidValue;
   k_mix_fft<T, TPB><<<(unsigned)a.nblocks, TPB, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename TIN, int TPB>
+cudaError_t launch_cfft_kernel(const FftArgs& a, size_t smem, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_mix_cfft<TIN, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftMaxSmem + 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (a.nblocks > INT32_MAX) return cudaErrorInvalidValue;
+  k_mix_cfft<TIN, TPB><<<(unsigned)a.nblocks, TPB, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -550,15 +667,15 @@ cudaError_t launch_fft_tables(int I, const double* signs, float* tab, cudaStream
   return cudaGetLastError();
 }
 
-cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* tab, int dtype, int N,
-                           const int64_t* dims, int n, int* err, cudaStream_t s) {
-  if (N < 2 || n < 0 || n >= N) return cudaErrorInvalidValue;
+namespace {
+// the kernel arguments of one pass (mode n read, mode v = n + 1 mod N written); false without a plan
+bool fft_args(FftArgs& a, FftPlan& pl, const void* U, void* yv, void* ysame, const float* tab, int N,
+              const int64_t* dims, int n, int* err, bool cplx) {
+  if (N < 2 || n < 0 || n >= N) return false;
   const int v = (n + 1) % N;
-  FftArgs a;
   memset(&a, 0, sizeof(a));
   const int I = (int)dims[n];
-  FftPlan pl;
-  if (!fft_plan(I, dims[v], &pl)) return cudaErrorInvalidValue;
+  if (!fft_plan(I, dims[v], &pl, cplx)) return false;
   a.U = U;
   a.yv = yv;
   a.ysame = ysame;
@@ -566,9 +683,10 @@ cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* ta
   a.I = I;
   a.Ipad = pl.Ipad;
   a.BJ = pl.BJ;
-  a.S = pl.BJ / 2;
+  a.S = cplx ? pl.BJ : pl.BJ / 2;
   a.nst = pl.nst;
   a.mH2 = magic(I / 2 + 1);
+  a.cscale = (float)(1.0 / sqrt((double)I));
   int Ns = 1;
   for (int st = 0; st < pl.nst; ++st) {
     const int R = kRadR1[pl.rix[st]] * kRadR2[pl.rix[st]];
@@ -604,7 +722,16 @@ cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* ta
   }
   a.nchunks = (a.Iv + a.BJ - 1) / a.BJ;
   a.nblocks = a.nchunks * (P / ((int64_t)I * a.Iv));
-  if (a.nblocks <= 0) return cudaErrorInvalidValue;
+  return a.nblocks > 0;
+}
+}  // namespace
+
+cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* tab, int dtype, int N,
+                           const int64_t* dims, int n, int* err, cudaStream_t s) {
+  FftArgs a;
+  FftPlan pl;
+  if (!fft_args(a, pl, U, yv, ysame, tab, N, dims, n, err, false)) return cudaErrorInvalidValue;
+  const int I = a.I;
   const size_t es = dtype == CPR_F32 ? 4 : 2;
   a.bulk = dtype == CPR_F32 && (I * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(U) & 15) == 0;
   if (dtype == CPR_F32)
@@ -613,6 +740,26 @@ cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* ta
     return pl.tpb == 128 ? launch_fft_kernel<__nv_bfloat16, 128>(a, pl.smem, s)
                          : launch_fft_kernel<__nv_bfloat16, 256>(a, pl.smem, s);
   return cudaErrorInvalidValue;
+}
+
+bool mix_cfft_supported(int N, const int64_t* dims) {
+  if (N < 2) return false;
+  for (int n = 0; n < N; ++n) {
+    if (dims[n] < 5) return false;
+    FftPlan pl;
+    if (!fft_plan((int)dims[n], dims[(n + 1) % N], &pl, true)) return false;
+  }
+  return true;
+}
+
+cudaError_t launch_mix_cfft(const void* U, bool real_in, void* yv, void* ysame, const float* tab, int N,
+                            const int64_t* dims, int n, int* err, cudaStream_t s) {
+  FftArgs a;
+  FftPlan pl;
+  if (!fft_args(a, pl, U, yv, ysame, tab, N, dims, n, err, true)) return cudaErrorInvalidValue;
+  if (real_in)
+    return pl.tpb == 128 ? launch_cfft_kernel<float, 128>(a, pl.smem, s) : launch_cfft_kernel<float, 256>(a, pl.smem, s);
+  return pl.tpb == 128 ? launch_cfft_kernel<float2, 128>(a, pl.smem, s) : launch_cfft_kernel<float2, 256>(a, pl.smem, s);
 }
 
 }  // namespace cpr
