@@ -163,6 +163,21 @@ def algorithmic(cls, w, P, b, iters_per_launch=None):
     return None
 
 
+def complex_form_rate(cb, X, dims, w, iters=10):
+    """The complex-transform form of CPRAND-MIX (Alg. 4) on the same tensor: setup (norm, unitary-DFT
+    mixing, copies) and device time per outer iteration over a fixed number of iterations, after one
+    warm-up call; its host loop synchronizes once per iteration."""
+    opts = cb.cpr_default_opts(seed=w["philox_seed"], fixed_iters=1, fit_samples=w["P_hat"])
+    warm = cb.cpr_cprand_mix_fft(X, dims, w["R"], w["S"], opts=opts)
+    opts = cb.cpr_default_opts(seed=w["philox_seed"], fixed_iters=iters, fit_samples=w["P_hat"])
+    out = cb.cpr_cprand_mix_fft(X, dims, w["R"], w["S"], opts=opts, ws=warm["ws"])
+    del warm
+    return {"what": "CPRAND-MIX with the unitary DFT (Alg. 4): complex mixed tensor, real factors, stacked "
+                    "real least squares; host loop, one synchronization per outer iteration",
+            "iters": out["iters"], "ms_setup": out["ms_setup"], "us_per_iter": 1e3 * out["ms_iterate"] / out["iters"],
+            "fit_est_last": out["fit_est"]}
+
+
 def true_fit_gpu(X, dims, lam, factors):
     """Exact fit 1 - ||X - X~|| / ||X|| (Sec. 4.2) of a CP model on the stored tensor, FP64 on the
     GPU (out of every timed region)."""
@@ -412,7 +427,7 @@ def run_ours(args, rank, world, local_rank):
     # time to fit: true fit within 1e-3 of the FP64 oracle's final fit (the oracle runs on this host's
     # cores), for the library and for the plain FP64 GPU form on the same GPU
     cpu = None
-    ttf = plain_out = gather = None
+    ttf = plain_out = gather = complex_form = None
     if rank == 0 and world == 1 and not args.skip_extras:
         if not args.no_cpu_baseline:
             cpu = cpu_baseline(X, dims, seconds=60.0)
@@ -445,6 +460,7 @@ def run_ours(args, rank, world, local_rank):
                      "what": "CPRAND-MIX in stock PyTorch FP64 ops (tensordot mixing, index gathers, "
                              "Cholesky solves), host-side loop and stopping test"}
         gather = gather_bandwidth(cb, X, dims)
+        complex_form = complex_form_rate(cb, X, dims, w)
 
     pk, pk_src = peaks()
     roof = None
@@ -495,6 +511,8 @@ def run_ours(args, rank, world, local_rank):
     if ttf is not None:
         out["time_to_fit"] = ttf
         out["plain_fp64_gpu"] = plain_out
+    if complex_form is not None:
+        out["complex_form"] = complex_form
     if gather is not None:
         for g in gather.values():
             g["frac_of_hbm_peak"] = g["read_write_GBs"] / pk["hbm_gbs"]

@@ -271,7 +271,7 @@ CPR_API int cpr_unmix_factors(const cpr_ktensor* Khat, cpr_ktensor* out, uint64_
  * parts (eq. (rcLS)); then normalizes and mixes the new factor.  Samples, initial factors and fit
  * entries use the Philox streams of cpr_cprand_mix; the stopping rules of Sec. 4.2 are checked on the
  * host after each outer iteration (the sampled fit on X with the real factors).
- *   X: FP32, every I_n in [5, 1600] a product of 2, 3, 5 and 7; R <= CPR_MAX_RANK; S >= R.
+ *   X: FP32, every I_n in [5, 6000] a product of 2, 3, 5 and 7; R <= CPR_MAX_RANK; S >= R.
  *   out: caller-owned real factors (I_n x R, FP64) and lambda, returned normalized in the original
  *   basis (no unmixing step).  opts->init_from_out must be 0.  ws: at least
  *   cpr_cprand_mix_fft_workspace_size(...) bytes (about (N + 1) complex copies of the tensor).

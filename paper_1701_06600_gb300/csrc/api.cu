@@ -1013,7 +1013,7 @@ size_t cf_layout(Carver& c, const cpr_tensor* X, int R, int64_t S, int64_t P_hat
   for (int n = 1; n < N; ++n) L.rep[n] = c.take<float2>((size_t)P);
   L.idx = c.take<uint32_t>((size_t)S * N);
   L.Xr = c.take<float>((size_t)imax * 2 * S);
-  L.Zr = c.take<double>((size_t)2 * S * R);
+  L.Zr = c.take<double>((size_t)3 * S * R);   // FP64 rows (2S x R), then their FP32 copy
   L.G = c.take<double>((size_t)R * R);
   L.Gi = c.take<double>((size_t)R * R);
   L.M = c.take<double>((size_t)imax * R);
@@ -1030,7 +1030,7 @@ int cf_check(const cpr_tensor* X, int R, int64_t S, const cpr_opts& o) {
   if (X->dtype != CPR_F32 || check_rank_samples(R, S)) return CPR_EINVAL;
   if (!mix_cfft_supported(X->order, X->dims)) return CPR_EINVAL;
   for (int n = 0; n < X->order; ++n)
-    if (X->dims[n] > 1600) return CPR_EINVAL;   // the unmixing kernel stages 16 fibers in shared memory
+    if (X->dims[n] > 6000) return CPR_EINVAL;   // the unmixing kernel stages 4 fibers in shared memory
   if (o.fit_samples < 1 || o.fit_samples > INT32_MAX || S > INT32_MAX / 2) return CPR_EINVAL;
   return CPR_OK;
 }

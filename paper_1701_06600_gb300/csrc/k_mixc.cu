@@ -19,7 +19,7 @@
 namespace cpr {
 namespace {
 
-constexpr int kSB = 16;   // sampled fibers per block of the unmixing kernel
+constexpr int kSB = 4;    // sampled fibers per block of the unmixing kernel
 
 __device__ __forceinline__ double2 cmul64(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -48,25 +48,27 @@ __global__ void k_cf_init(int I, int R, int m, uint64_t seed, uint32_t b, double
   A[e] = (double)(word_of(w, r % 4) >> 8) * (1.0 / 16777216.0);
 }
 
-// A^^ = W A (I x R complex, FP32 products accumulated in FP32 per 32-term chunk, chunks in FP64)
+// A^^ = W A (I x R complex): one warp per entry, the lanes split the sum over i (FP32 products and
+// per-lane sums, a fixed-order shuffle tree in FP64)
 __global__ void k_cf_mix_factor(int I, int R, const float2* __restrict__ W, const double* __restrict__ A,
                                 float2* __restrict__ Ah) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)I * R) return;
-  const int k = (int)(e / R), r = (int)(e - (int64_t)(e / R) * R);
+  const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (e >= (int64_t)I * R) return;   // whole warps
+  const int k = (int)(e / R), r = (int)(e - (int64_t)k * R);
   const float2* w = W + (int64_t)k * I;
-  double re = 0.0, im = 0.0;
-  for (int i0 = 0; i0 < I; i0 += 32) {
-    float pr = 0.f, pi = 0.f;
-    for (int i = i0; i < min(I, i0 + 32); ++i) {
-      const float a = (float)A[(int64_t)i * R + r];
-      pr = fmaf(w[i].x, a, pr);
-      pi = fmaf(w[i].y, a, pi);
-    }
-    re += pr;
-    im += pi;
+  float pr = 0.f, pi = 0.f;
+  for (int i = lane; i < I; i += 32) {
+    const float av = (float)A[(int64_t)i * R + r];
+    pr = fmaf(w[i].x, av, pr);
+    pi = fmaf(w[i].y, av, pi);
   }
-  Ah[e] = make_float2((float)re, (float)im);
+  double re = pr, im = pi;
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) Ah[e] = make_float2((float)re, (float)im);
 }
 
 struct CfArgs {
@@ -78,64 +80,54 @@ struct CfArgs {
   int N, n, S, R;
 };
 
-// 1. X_r = [Re, Im](W_n^H X^_S): a block unmixes kSB sampled fibers (staged in shared memory) for a
-// range of rows i; each thread accumulates kSB complex outputs over k (FP32 per 32-term chunk).
+// 1. X_r = [Re, Im](W_n^H X^_S): a block of 32 x kSB threads unmixes kSB sampled fibers (staged in
+// shared memory) for 32 consecutive rows i, one output per thread (FP32 products over 32-term chunks,
+// the chunks summed in FP64)
 __global__ void k_cf_unmix_fibers(CfArgs a, float* __restrict__ Xr) {
   extern __shared__ float2 xs[];   // kSB x I
   __shared__ int64_t col[kSB];
   const int I = (int)a.dims[a.n], S = a.S;
   const int j0 = blockIdx.x * kSB, nj = min(kSB, S - j0);
-  if (threadIdx.x < nj) {   // column of the mode-n unfolding holding fiber j0 + t (index map of §2.1)
-    const uint32_t* id = a.idx + (int64_t)(j0 + threadIdx.x) * a.N;
+  const int t = threadIdx.y * 32 + threadIdx.x, nt = 32 * kSB;
+  if (t < nj) {   // column of the mode-n unfolding holding fiber j0 + t (index map of §2.1)
+    const uint32_t* id = a.idx + (int64_t)(j0 + t) * a.N;
     int64_t c = 0, J = 1;
     for (int m = 0; m < a.N; ++m) {
       if (m == a.n) continue;
       c += (int64_t)id[m] * J;
       J *= a.dims[m];
     }
-    col[threadIdx.x] = c;
+    col[t] = c;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < nj * I; e += blockDim.x) {
+  for (int e = t; e < nj * I; e += nt) {
     const int jj = e / I, k = e - jj * I;
     xs[e] = a.Xn[col[jj] * I + k];
   }
   __syncthreads();
-  for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < I; i += gridDim.y * blockDim.x) {
-    double re[kSB], im[kSB];
-#pragma unroll
-    for (int jj = 0; jj < kSB; ++jj) re[jj] = im[jj] = 0.0;
-    for (int k0 = 0; k0 < I; k0 += 32) {
-      float pr[kSB], pi[kSB];
-#pragma unroll
-      for (int jj = 0; jj < kSB; ++jj) pr[jj] = pi[jj] = 0.f;
-      for (int k = k0; k < min(I, k0 + 32); ++k) {
-        const float2 w = a.W[(int64_t)k * I + i];   // conj(W[k][i]) = (w.x, -w.y)
-#pragma unroll
-        for (int jj = 0; jj < kSB; ++jj) {
-          const float2 x = xs[jj * I + k];
-          pr[jj] = fmaf(w.x, x.x, fmaf(w.y, x.y, pr[jj]));
-          pi[jj] = fmaf(w.x, x.y, fmaf(-w.y, x.x, pi[jj]));
-        }
-      }
-#pragma unroll
-      for (int jj = 0; jj < kSB; ++jj) {
-        re[jj] += pr[jj];
-        im[jj] += pi[jj];
-      }
+  const int i = blockIdx.y * 32 + threadIdx.x, jj = threadIdx.y;
+  if (i >= I || jj >= nj) return;
+  const float2* x = xs + jj * I;
+  double re = 0.0, im = 0.0;
+  for (int k0 = 0; k0 < I; k0 += 32) {
+    float pr = 0.f, pi = 0.f;
+    for (int k = k0; k < min(I, k0 + 32); ++k) {
+      const float2 w = a.W[(int64_t)k * I + i];   // conj(W[k][i]) = (w.x, -w.y)
+      const float2 v = x[k];
+      pr = fmaf(w.x, v.x, fmaf(w.y, v.y, pr));
+      pi = fmaf(w.x, v.y, fmaf(-w.y, v.x, pi));
     }
-    float* row = Xr + (int64_t)i * 2 * S;
-#pragma unroll
-    for (int jj = 0; jj < kSB; ++jj)
-      if (jj < nj) {
-        row[j0 + jj] = (float)re[jj];
-        row[S + j0 + jj] = (float)im[jj];
-      }
+    re += pr;
+    im += pi;
   }
+  float* row = Xr + (int64_t)i * 2 * S;
+  row[j0 + jj] = (float)re;
+  row[S + j0 + jj] = (float)im;
 }
 
-// 2. Z_r = [Re; Im] of the sampled rows of the mixed Khatri-Rao product (FP64 products)
-__global__ void k_cf_skr(CfArgs a, double* __restrict__ Zr) {
+// 2. Z_r = [Re; Im] of the sampled rows of the mixed Khatri-Rao product (FP64 products; an FP32 copy
+// for the contraction)
+__global__ void k_cf_skr(CfArgs a, double* __restrict__ Zr, float* __restrict__ Zf) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int S = a.S, R = a.R;
   if (e >= (int64_t)S * R) return;
@@ -148,40 +140,45 @@ __global__ void k_cf_skr(CfArgs a, double* __restrict__ Zr) {
   }
   Zr[(int64_t)j * R + r] = z.x;
   Zr[(int64_t)(S + j) * R + r] = z.y;
+  Zf[(int64_t)j * R + r] = (float)z.x;
+  Zf[(int64_t)(S + j) * R + r] = (float)z.y;
 }
 
-// 3a. G = Z_r^T Z_r (R x R, FP64): one thread per entry of the upper triangle, mirrored
+// 3a. G = Z_r^T Z_r (R x R, FP64): one block per entry of the upper triangle (its 2S products split
+// over the threads, then a fixed-order tree), mirrored
 __global__ void k_cf_gram(const double* __restrict__ Zr, int rows, int R, double* __restrict__ G) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < R * R; e += gridDim.x * blockDim.x) {
-    const int r = e / R, c = e - r * R;
-    if (c < r) continue;
-    double s0 = 0.0, s1 = 0.0;
-    int j = 0;
-    for (; j + 1 < rows; j += 2) {
-      s0 = fma(Zr[(int64_t)j * R + r], Zr[(int64_t)j * R + c], s0);
-      s1 = fma(Zr[(int64_t)(j + 1) * R + r], Zr[(int64_t)(j + 1) * R + c], s1);
-    }
-    if (j < rows) s0 = fma(Zr[(int64_t)j * R + r], Zr[(int64_t)j * R + c], s0);
-    G[r * R + c] = s0 + s1;
-    G[c * R + r] = s0 + s1;
+  __shared__ double red[128];
+  const int e = blockIdx.x, r = e / R, c = e - r * R;
+  if (c < r) return;
+  double a = 0.0;
+  for (int j = threadIdx.x; j < rows; j += blockDim.x) a = fma(Zr[(int64_t)j * R + r], Zr[(int64_t)j * R + c], a);
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 64; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    G[r * R + c] = red[0];
+    G[c * R + r] = red[0];
   }
 }
 
-// 3b. M = X_r Z_r (I x R, FP64 accumulation): one thread per entry
-__global__ void k_cf_contract(const float* __restrict__ Xr, const double* __restrict__ Zr, int I, int cols, int R,
+// 3b. M = X_r Z_r (I x R): one warp per entry, the lanes split the sum over the 2S rows (FP32
+// products and per-lane sums, the contraction's accumulation type as in the real form; a fixed-order
+// shuffle tree in FP64)
+__global__ void k_cf_contract(const float* __restrict__ Xr, const float* __restrict__ Zf, int I, int cols, int R,
                               double* __restrict__ M) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)I * R) return;
+  const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (e >= (int64_t)I * R) return;   // whole warps
   const int i = (int)(e / R), r = (int)(e - (int64_t)i * R);
   const float* x = Xr + (int64_t)i * cols;
-  double s0 = 0.0, s1 = 0.0;
-  int j = 0;
-  for (; j + 1 < cols; j += 2) {
-    s0 = fma((double)x[j], Zr[(int64_t)j * R + r], s0);
-    s1 = fma((double)x[j + 1], Zr[(int64_t)(j + 1) * R + r], s1);
-  }
-  if (j < cols) s0 = fma((double)x[j], Zr[(int64_t)j * R + r], s0);
-  M[e] = s0 + s1;
+  float s0 = 0.f;
+  for (int j = lane; j < cols; j += 32) s0 = fmaf(x[j], Zf[(int64_t)j * R + r], s0);
+  double a = s0;
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (lane == 0) M[e] = a;
 }
 
 // 4a. G^-1 (FP64 Cholesky inverse, one block); a singular Gram sets *bad
@@ -218,19 +215,23 @@ __global__ void k_cf_apply(const double* __restrict__ M, const double* __restric
   A[e] = s0 + s1;
 }
 
-// 4c. column norms (fixed order over rows, one thread per column) and normalization: lam_r = ||a_r||,
-// a zero column keeps weight 0 and stays as it is
+// 4c. column norms and normalization, one block per column (fixed-order tree over the rows):
+// lam_r = ||a_r||; a zero column keeps weight 0 and stays as it is
 __global__ void k_cf_normalize(double* __restrict__ A, int I, int R, double* __restrict__ lam) {
-  __shared__ double s_inv[64];
-  for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    double s = 0.0;
-    for (int i = 0; i < I; ++i) s = fma(A[(int64_t)i * R + r], A[(int64_t)i * R + r], s);
-    const double nrm = sqrt(s);
-    lam[r] = nrm;
-    s_inv[r] = nrm > 0.0 ? 1.0 / nrm : 1.0;
-  }
+  __shared__ double red[256];
+  const int r = blockIdx.x;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < I; i += blockDim.x) a = fma(A[(int64_t)i * R + r], A[(int64_t)i * R + r], a);
+  red[threadIdx.x] = a;
   __syncthreads();
-  for (int64_t e = threadIdx.x; e < (int64_t)I * R; e += blockDim.x) A[e] *= s_inv[e % R];
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double nrm = sqrt(red[0]);
+  if (threadIdx.x == 0) lam[r] = nrm;
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 1.0;
+  for (int i = threadIdx.x; i < I; i += blockDim.x) A[(int64_t)i * R + r] *= inv;
 }
 
 struct CfFit {
@@ -302,7 +303,7 @@ cudaError_t launch_cf_init(int I, int R, int m, uint64_t seed, uint32_t b, doubl
 
 cudaError_t launch_cf_mix_factor(int I, int R, const float2* W, const double* A, float2* Ah, cudaStream_t s) {
   const int64_t n = (int64_t)I * R;
-  k_cf_mix_factor<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(I, R, W, A, Ah);
+  k_cf_mix_factor<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(I, R, W, A, Ah);
   return cudaGetLastError();
 }
 
@@ -331,11 +332,12 @@ cudaError_t launch_cf_update(const float2* Xn, const uint32_t* idx, const float2
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const unsigned gy = (unsigned)((I + 127) / 128);
-  k_cf_unmix_fibers<<<dim3((unsigned)((S + kSB - 1) / kSB), gy), 128, xs_bytes, s>>>(a, Xr);
-  k_cf_skr<<<(unsigned)(((int64_t)S * R + 255) / 256), 256, 0, s>>>(a, Zr);
-  k_cf_gram<<<(unsigned)((R * R + 127) / 128), 128, 0, s>>>(Zr, 2 * S, R, G);
-  k_cf_contract<<<(unsigned)(((int64_t)I * R + 127) / 128), 128, 0, s>>>(Xr, Zr, I, 2 * S, R, M);
+  k_cf_unmix_fibers<<<dim3((unsigned)((S + kSB - 1) / kSB), (unsigned)((I + 31) / 32)), dim3(32, kSB), xs_bytes, s>>>(
+      a, Xr);
+  float* Zf = reinterpret_cast<float*>(Zr + (int64_t)2 * S * R);   // the FP32 copy after the FP64 one
+  k_cf_skr<<<(unsigned)(((int64_t)S * R + 255) / 256), 256, 0, s>>>(a, Zr, Zf);
+  k_cf_gram<<<(unsigned)(R * R), 128, 0, s>>>(Zr, 2 * S, R, G);
+  k_cf_contract<<<(unsigned)(((int64_t)I * R * 32 + 255) / 256), 256, 0, s>>>(Xr, Zf, I, 2 * S, R, M);
   const size_t inv_bytes = (size_t)(4 * R * R + R) * sizeof(double);
   static bool attr2 = false;
   if (!attr2) {
@@ -345,7 +347,7 @@ cudaError_t launch_cf_update(const float2* Xn, const uint32_t* idx, const float2
   }
   k_cf_inverse<<<1, 256, inv_bytes, s>>>(G, R, Gi, bad);
   k_cf_apply<<<(unsigned)(((int64_t)I * R + 127) / 128), 128, 0, s>>>(M, Gi, I, R, A);
-  k_cf_normalize<<<1, 256, 0, s>>>(A, I, R, lam);
+  k_cf_normalize<<<(unsigned)R, 256, 0, s>>>(A, I, R, lam);
   return cudaGetLastError();
 }
 
