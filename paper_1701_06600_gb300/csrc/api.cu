@@ -399,19 +399,23 @@ cpr_opts defaults() {
 // mode-n unfolding of the previous result (t2), results alternate through t1 and the last lands in
 // `final`; the last pass also writes its unfolding into rep_last when given (*wrote_rep_last).
 // Otherwise SIMT passes ping-pong between final and t1 so that the last lands in final.
+// the factored transform mixes this tensor (its tables are then built with the operators, in the
+// buffer of the dense FP32 operator, which is not needed)
+bool fft_mixing(int dtype, int N, const int64_t* dims) {
+  return mix_engine() != CPR_MIX_DENSE && mix_fft_supported(dtype, N, dims);
+}
+
 int enqueue_mixing(const void* src, void* final, void* t1, void* t2, void* rep_last, int dtype, int N,
                    const int64_t* dims, float* const* W32, float* const* Wlo, double* const* W64,
                    double* const* SG, int* err, unsigned* amax, bool amax0_ready, cudaStream_t s, int64_t& launches,
                    bool* wrote_rep_last) {
   *wrote_rep_last = false;
-  bool fft = mix_engine() != CPR_MIX_DENSE && t1 != nullptr && mix_fft_supported(dtype, N, dims);
+  bool fft = t1 != nullptr && fft_mixing(dtype, N, dims);
   for (int n = 0; n < N && fft; ++n) fft = W32[n] != nullptr && SG[n] != nullptr;
   if (fft) {
-    // factored DCT passes: the FFT tables replace the dense operator in its buffer (5 I <= I^2
-    // floats); pass n writes the layout pass n + 1 reads, the outputs alternate between final and
-    // t1 so that the last pass writes final
-    for (int n = 0; n < N; ++n)
-      CPR_LAUNCH(CPR_KERNEL_OTHER, launch_fft_tables((int)dims[n], SG[n], W32[n], s));
+    // factored DCT passes (the tables are in the dense operator's buffer, 5 I <= I^2 floats, built
+    // with the operators); pass n writes the layout pass n + 1 reads, the outputs alternate between
+    // final and t1 so that the last pass writes final
     void* bufs[2] = {final, t1};
     const void* U = src;
     for (int n = 0; n < N; ++n) {
@@ -610,9 +614,11 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
     CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq_finish(pl.d_normpart, pl.normblk, nullptr, pl.d_states + b, 1, s));
     if (mix) {
       const MixBufs& mb = pl.mixb[b];
+      const bool fftm = pl.d_tmp != nullptr && fft_mixing(p.dtype, p.N, p.dims) && mb.W32[0] != nullptr;
       for (int n = 0; n < p.N; ++n)
-        CPR_LAUNCH(CPR_KERNEL_OTHER, launch_build_mix_ops((int)p.dims[n], p.seed, p.b, n, mb.table, mb.W32[n], mb.W64[n],
-                                                         mb.F64[n], mb.sg[n], s));
+        CPR_LAUNCH(CPR_KERNEL_OTHER,
+                   launch_build_mix_ops((int)p.dims[n], p.seed, p.b, n, mb.table, fftm ? nullptr : mb.W32[n], mb.W64[n],
+                                        mb.F64[n], mb.sg[n], s, fftm ? mb.W32[n] : nullptr));
       if (int st = enqueue_mixing(Xs[b].data, mb.xhat, pl.d_tmp, pl.d_tmp2,
                                   p.use_rep ? const_cast<void*>(p.Xrep[p.N - 1]) : nullptr, p.dtype, p.N, p.dims,
                                   mb.W32, mb.Wlo, mb.W64, mb.sg, pl.d_counter + 2, amax, true, s, launches,
@@ -1071,8 +1077,7 @@ int cpr_cprand_mix_fft(const cpr_tensor* X, int R, int64_t S, const cpr_opts* op
   for (int n = 0; n < N; ++n) {
     const int I = (int)X->dims[n];
     CPR_LAUNCH(CPR_KERNEL_OTHER, launch_build_mix_ops(I, o.seed, o.batch_index, n, L.table, nullptr, nullptr, nullptr,
-                                                      L.signs[n], s));
-    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_fft_tables(I, L.signs[n], L.tab[n], s));
+                                                      L.signs[n], s, L.tab[n]));
     CPR_LAUNCH(CPR_KERNEL_OTHER, launch_cf_ops(I, L.signs[n], L.W[n], s));
   }
   {
@@ -1345,9 +1350,10 @@ int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, uint32_t b
   lay(cw, W32, Wlo, W64, F64, sg, &table, &tmp, &tmp2, &derr);
   CPR_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), s));
   int64_t launches = 0;
+  const bool fftm = fft_mixing(dt, N, X->dims) && W32[0] != nullptr;
   for (int n = 0; n < N; ++n)
-    CPR_LAUNCH(CPR_KERNEL_OTHER,
-               launch_build_mix_ops((int)X->dims[n], seed, b, n, table, W32[n], W64[n], F64[n], sg[n], s));
+    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_build_mix_ops((int)X->dims[n], seed, b, n, table, fftm ? nullptr : W32[n],
+                                                      W64[n], F64[n], sg[n], s, fftm ? W32[n] : nullptr));
   bool unused = false;
   if (int st = enqueue_mixing(X->data, out_dev, tmp, tmp2, nullptr, dt, N, X->dims, W32, Wlo, W64, sg, derr,
                               reinterpret_cast<unsigned*>(derr + 4), false, s, launches, &unused))

@@ -320,10 +320,9 @@ cudaError_t launch_mix_tc16(const float* U, float* ystd, float* yunf, float* yne
 
 // mixing by the factored DCT-II (FP32 / BF16 tensors whose every I_n factors into 2, 3, 5, 7):
 // pass n reads the mode-n unfolding and writes the mode-(n+1 mod N) unfolding (the last pass: the
-// standard layout, and its own layout into ysame when given); tab = 5 I floats from
-// launch_fft_tables (signs: D_n as FP64 +-1)
+// standard layout, and its own layout into ysame when given); tab = 5 I floats (twiddles,
+// post-scales, signs) from launch_build_mix_ops
 bool mix_fft_supported(int dtype, int N, const int64_t* dims);
-cudaError_t launch_fft_tables(int I, const double* signs, float* tab, cudaStream_t s);
 cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* tab, int dtype, int N,
                            const int64_t* dims, int n, int* err, cudaStream_t s);
 int mix_engine();   // CPR_MIX_* (process-wide, cpr_set_mix_engine)
@@ -348,7 +347,7 @@ cudaError_t launch_cf_fit(const double* const* A, const double* lam, int N, cons
 
 // mixing (Alg. 5)
 cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, double* table, float* W32,
-                                 double* W64, double* F64, double* signs, cudaStream_t s);
+                                 double* W64, double* F64, double* signs, cudaStream_t s, float* fft_tab = nullptr);
 cudaError_t launch_mix_mode(const void* X, void* Y, int dtype, int N, const int64_t* dims, int n,
                             const float* W32, const double* W64, cudaStream_t s);
 cudaError_t launch_unmix(const double* Ahat, double* A, const double* F64, const double* signs,

@@ -171,6 +171,9 @@ __global__ void __launch_bounds__(256) k_sumsq(const T* __restrict__ X, int64_t 
     uint4 q[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) q[u] = __ldcs(&Xv[v + u * nthr]);
+    // FP32 tensors: the eight per-vector FP32 sums are added with Kahan compensation in FP32 and folded
+    // into FP64 once (two FP64 additions per 8 vectors, not one per vector: the FP64 pipe bounded this)
+    float ks = 0.f, kc = 0.f;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const T* e = reinterpret_cast<const T*>(&q[u]);
@@ -188,9 +191,13 @@ __global__ void __launch_bounds__(256) k_sumsq(const T* __restrict__ X, int64_t 
           f = fmaf(x, x, f);
           mx = fmaxf(mx, fabsf(x));
         }
-        acc += (double)f;
+        const float y = f - kc;
+        const float t = ks + y;
+        kc = (t - ks) - y;
+        ks = t;
       }
     }
+    if constexpr (sizeof(T) != 8) acc += (double)ks - (double)kc;
   }
   for (; v < nvec; v += nthr) {
     const uint4 q = __ldcs(&Xv[v]);

@@ -23,8 +23,11 @@ __global__ void k_cos_table(int I, double* table) {
   if (q < 4 * I) table[q] = cospi((double)q / (2.0 * I));
 }
 
+// fft_tab (5 I floats, or null): the tables of the factored transform, from the same cosine table:
+// twiddles exp(-2 pi i t / I) = (cos, -sin)(2 pi t / I), post-scales c_k (cos, sin)(pi k / (2I)) / 2,
+// the signs; sin(pi x / (2I)) is read as cos(pi (I - x) / (2I)) (cosine even for negative I - x)
 __global__ void k_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, const double* __restrict__ table,
-                                float* W32, double* W64, double* F64, double* signs) {
+                                float* W32, double* W64, double* F64, double* signs, float* fft_tab) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)I * I) return;
   const int i = (int)(e / I), k = (int)(e % I);
@@ -38,13 +41,22 @@ __global__ void k_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, const d
   if (W64) W64[e] = f * d;
   if (W32) W32[e] = (float)(f * d);
   if (signs && i == 0) signs[k] = d;
+  if (fft_tab && i == 0) {   // entry t = k of the tables
+    const int t = k;
+    fft_tab[2 * t] = (float)table[4 * t];
+    fft_tab[2 * t + 1] = (float)(-table[abs(I - 4 * t)]);
+    const double ck = t == 0 ? sqrt(1.0 / I) : sqrt(2.0 / I);
+    fft_tab[2 * I + 2 * t] = (float)(0.5 * ck * table[t]);
+    fft_tab[2 * I + 2 * t + 1] = (float)(0.5 * ck * table[I - t]);
+    fft_tab[4 * I + t] = (float)d;
+  }
 }
 
 cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, double* table, float* W32, double* W64,
-                                 double* F64, double* signs, cudaStream_t s) {
+                                 double* F64, double* signs, cudaStream_t s, float* fft_tab) {
   k_cos_table<<<(4 * I + 255) / 256, 256, 0, s>>>(I, table);
   const int64_t total = (int64_t)I * I;
-  k_build_mix_ops<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(I, seed, b, n, table, W32, W64, F64, signs);
+  k_build_mix_ops<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(I, seed, b, n, table, W32, W64, F64, signs, fft_tab);
   return cudaGetLastError();
 }
 

@@ -522,21 +522,6 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_cfft(const __grid_consta
   }
 }
 
-// twiddles exp(-2 pi i t / I), post-scales c_k (cos, sin)(pi k / (2I)) / 2 and the signs d_k;
-// computed in FP64, rounded once
-__global__ void k_fft_tables(int I, const double* __restrict__ signs, float* __restrict__ tab) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= I) return;
-  double s, c;
-  sincospi(2.0 * t / I, &s, &c);
-  tab[2 * t] = (float)c;
-  tab[2 * t + 1] = (float)(-s);
-  sincospi((double)t / (2.0 * I), &s, &c);
-  const double ck = t == 0 ? sqrt(1.0 / I) : sqrt(2.0 / I);
-  tab[2 * I + 2 * t] = (float)(0.5 * ck * c);
-  tab[2 * I + 2 * t + 1] = (float)(0.5 * ck * s);
-  tab[4 * I + t] = (float)signs[t];
-}
 
 // the stage radices of I (every prime factor 2, 3, 5 or 7), grouped into the radices of kRadR1 x
 // kRadR2, listed in radix-index order; among the groupings, the one that admits the widest fiber block
@@ -662,10 +647,6 @@ bool mix_fft_supported(int dtype, int N, const int64_t* dims) {
   return true;
 }
 
-cudaError_t launch_fft_tables(int I, const double* signs, float* tab, cudaStream_t s) {
-  k_fft_tables<<<(I + 255) / 256, 256, 0, s>>>(I, signs, tab);
-  return cudaGetLastError();
-}
 
 namespace {
 // the kernel arguments of one pass (mode n read, mode v = n + 1 mod N written); false without a plan
