@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the studies that run after the timed regions (time to fit, the plain FP64 "
                          "GPU form, the gather bandwidth); used for profiler runs")
+    ap.add_argument("--quality-sweep", action="store_true",
+                    help="instead of the benchmark: the recovery study of Sec. 4.2 (Table 1 parameters), fit and "
+                         "score of CPRAND-MIX and CPRAND over synthetic tensors, three starts per rank")
+    ap.add_argument("--sweep-tensors", type=int, default=50, help="tensors per (size, C, eta) cell")
+    ap.add_argument("--sweep-sizes", default="3x400,4x90", help="order x dimension of the sweep's tensors")
     return ap.parse_args()
 
 
@@ -595,9 +600,92 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def score_assignment(true_factors, est_factors):
+    """Score of eq. (score) (Sec. 4.2): mean over the true components of the product over the modes of
+    the cosines with the matched estimated component, maximized over matchings; the best matching of
+    the pair-score matrix by linear assignment."""
+    import numpy as np
+    from scipy.optimize import linear_sum_assignment
+    S = None
+    for A, B in zip(true_factors, est_factors):
+        An = A / np.linalg.norm(A, axis=0, keepdims=True)
+        Bn = B / np.linalg.norm(B, axis=0, keepdims=True)
+        C = An.T @ Bn
+        S = C if S is None else S * C
+    rows, cols = linear_sum_assignment(-S)
+    return float(np.mean(S[rows, cols]))
+
+
+def exact_fit_device(X, dims, lam, factors):
+    """1 - ||X - X~|| / ||X|| in FP64 on the device (X flat column-major, any order N <= 5)."""
+    import torch
+    N = len(dims)
+    letters = "abcde"[:N]
+    spec = "r," + ",".join("%sr" % c for c in letters) + "->" + letters[::-1]
+    Xt = torch.einsum(spec, lam.double(), *[A.double() for A in factors]).reshape(-1)
+    Xd = X.double()
+    return 1.0 - torch.linalg.vector_norm(Xd - Xt).item() / torch.linalg.vector_norm(Xd).item()
+
+
+def run_quality_sweep(args):
+    """The recovery study of Sec. 4.2 with the parameters of its Table 1: tensors of order 3 (400^3) and
+    order 4 (90^4) with R_true = 5 collinear components (C in {0.5, 0.9}) and noise eta in {0.01, 0.1};
+    CPRAND-MIX and CPRAND with R in {5, 6} (S = 80, 108), three random starts each, the stopping rules
+    of Sec. 4.2 (P_hat = 2^14); per cell the median and quartiles of the exact fit and of the score, the
+    iterations, and the decompositions per second of the batched calls (the 6 starts of a tensor and
+    method in one call)."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1701_06600_gb300 import binding as cb
+    from synth import make_problem
+    torch.cuda.set_device(0)
+    sizes = [tuple(int(v) for v in z.split("x")) for z in args.sweep_sizes.split(",")]
+    cells, t_calls, n_dec = [], 0.0, 0
+    for si, (N, I) in enumerate(sizes):
+        dims = (I,) * N
+        for ci, (C, eta) in enumerate([(0.5, 0.01), (0.5, 0.1), (0.9, 0.01), (0.9, 0.1)]):
+            res = {(m, R): {"fit": [], "score": [], "iters": []} for m in ("cprand_mix", "cprand") for R in (5, 6)}
+            for t in range(args.sweep_tensors):
+                prob = make_problem(dims, 5, C=C, eta=eta, seed=100000 + 10000 * si + 1000 * ci + t,
+                                    dtype=torch.float32, device="cuda")
+                Rs = [5, 5, 5, 6, 6, 6]
+                Ss = [80, 80, 80, 108, 108, 108]
+                opts = [cb.cpr_default_opts(seed=7000 + t, batch_index=q, noise_eta=eta) for q in range(6)]
+                for m, mix in (("cprand_mix", True), ("cprand", False)):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    outs, _ = cb.cpr_cprand_batched([prob.X] * 6, [dims] * 6, Rs, Ss, opts, mix=mix)
+                    torch.cuda.synchronize()
+                    t_calls += time.perf_counter() - t0
+                    n_dec += 6
+                    for q, o in enumerate(outs):
+                        est = [A.cpu().numpy() for A in o["factors"]]
+                        r = res[(m, Rs[q])]
+                        r["fit"].append(exact_fit_device(prob.X, dims, o["lam"], o["factors"]))
+                        r["score"].append(score_assignment(prob.factors, est))
+                        r["iters"].append(o["iters"])
+                del prob
+            for (m, R), r in res.items():
+                q = lambda v, p: float(np.percentile(v, p))
+                cells.append({"order": N, "dim": I, "C": C, "eta": eta, "method": m, "R": R, "runs": len(r["fit"]),
+                              "fit_q25_med_q75": [q(r["fit"], 25), q(r["fit"], 50), q(r["fit"], 75)],
+                              "score_q25_med_q75": [q(r["score"], 25), q(r["score"], 50), q(r["score"], 75)],
+                              "iters_median": q(r["iters"], 50)})
+    return {"study": "recovery of Sec. 4.2 (Table 1 parameters): exact fit and score at termination",
+            "tensors_per_cell": args.sweep_tensors, "decompositions": n_dec,
+            "decompositions_per_s": n_dec / t_calls if t_calls > 0 else None,
+            "seconds_in_calls": t_calls, "data": "synthetic (Sec. 4.2 recipe, seeded)", "cells": cells}
+
+
 def main():
     args = parse()
     rank, world, local_rank = dist_env()
+    if args.quality_sweep:
+        if rank == 0:
+            print(json.dumps(run_quality_sweep(args)))
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
