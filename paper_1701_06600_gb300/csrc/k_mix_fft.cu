@@ -35,6 +35,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "internal.cuh"
 
@@ -72,6 +73,7 @@ struct FftArgs {
   int64_t nblocks;      // fiber blocks of the pass (nchunks x the remaining modes' extents)
   int no;               // number of remaining modes (not n, not v)
   int64_t oext[kMaxOrder], o_in[kMaxOrder], o_out[kMaxOrder];
+  int vec_v;            // the mode-v output admits 16-byte stores of 4 adjacent fibers
   int* err;
 };
 
@@ -523,6 +525,405 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_cfft(const __grid_consta
 }
 
 
+// ---- the same pass with the transform length and its plan fixed at compile time ----
+// For a length with a compiled plan every stage constant (L, Ns, the twiddle steps) is known to the
+// compiler, so shared-memory addresses take immediate offsets and the butterflies' roots of unity
+// are FMA immediates.  Each later stage reads its twiddles from its own table, laid out
+// T[(r - 1) Ns + k] = w_I^(r k I / (Ns R)), so that the lanes of a warp (consecutive k) read
+// consecutive entries.  The separation of the two real fibers of a sequence and the post-rotation
+// are done by the stores, each from the two entries k and I - k it needs (no extra pass over shared
+// memory), and the stores write 16 bytes per lane.
+
+// (cos, sin)(2 pi a / b) in double, evaluated by the compiler: the angle is split, in integers, into
+// a multiple of pi / 4 and a rest in [0, pi / 4) whose sine and cosine are Taylor sums
+struct CxPair {
+  double c, s;
+};
+constexpr double cx_sin_series(double x) {
+  double t = x, sum = x;
+  for (int n = 1; n < 14; ++n) {
+    t *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+    sum += t;
+  }
+  return sum;
+}
+constexpr double cx_cos_series(double x) {
+  double t = 1.0, sum = 1.0;
+  for (int n = 1; n < 14; ++n) {
+    t *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+    sum += t;
+  }
+  return sum;
+}
+constexpr CxPair cx_quarter_turns(double c, double s, int q) {   // (c, s) rotated by q quarter turns
+  return (q & 3) == 0 ? CxPair{c, s} : (q & 3) == 1 ? CxPair{-s, c} : (q & 3) == 2 ? CxPair{-c, -s} : CxPair{s, -c};
+}
+constexpr CxPair cx_cis_2pi(long a, long b) {
+  constexpr double kQuarterPi = 0.78539816339744830961566084581988;
+  const long t = 8 * (a % b);   // angle = (t / b) pi / 4
+  const int o = (int)(t / b);
+  const long rem = t - o * b;
+  if (o % 2 == 0) {   // o pi / 4 + phi, phi = (pi / 4) rem / b
+    const double phi = kQuarterPi * (double)rem / (double)b;
+    return cx_quarter_turns(cx_cos_series(phi), cx_sin_series(phi), o / 2);
+  }
+  const double psi = kQuarterPi * (double)(b - rem) / (double)b;   // (o + 1) pi / 4 - psi
+  return cx_quarter_turns(cx_cos_series(psi), -cx_sin_series(psi), (o + 1) / 2);
+}
+template <int R, int M>
+struct CxRoot {   // exp(-2 pi i M / R) rounded to FP32
+  static constexpr float re = (float)cx_cis_2pi(M, R).c;
+  static constexpr float im = (float)-cx_cis_2pi(M, R).s;
+};
+template <int R, int... M>
+__device__ __forceinline__ void ct_roots(float2 (&w)[R], std::integer_sequence<int, M...>) {
+  ((w[M] = make_float2(CxRoot<R, M>::re, CxRoot<R, M>::im)), ...);
+}
+
+// dft_comp with the roots as constants: w[m] = exp(-2 pi i m / R)
+template <int R1, int R2>
+__device__ __forceinline__ void ct_dft_comp(float2 (&v)[R1 * R2]) {
+  constexpr int R = R1 * R2;
+  float2 w[R];
+  ct_roots<R>(w, std::make_integer_sequence<int, R>{});
+  float2 rc1[R1 / 2 + 1], rc2[R2 / 2 + 1];   // (cos, sin)(2 pi m / R1), (cos, sin)(2 pi m / R2)
+#pragma unroll
+  for (int m = 0; m <= R1 / 2; ++m) rc1[m] = make_float2(w[m * R2].x, -w[m * R2].y);
+#pragma unroll
+  for (int m = 0; m <= R2 / 2; ++m) rc2[m] = make_float2(w[m * R1].x, -w[m * R1].y);
+  if constexpr (R2 == 1) {
+    dft<R1>(v, rc1);
+  } else {
+#pragma unroll
+    for (int r2 = 0; r2 < R2; ++r2) {
+      float2 t[R1];
+#pragma unroll
+      for (int r1 = 0; r1 < R1; ++r1) t[r1] = v[R2 * r1 + r2];
+      dft<R1>(t, rc1);
+#pragma unroll
+      for (int q1 = 0; q1 < R1; ++q1) v[R2 * q1 + r2] = (r2 && q1) ? cmul(t[q1], w[r2 * q1]) : t[q1];
+    }
+    float2 o[R];
+#pragma unroll
+    for (int q1 = 0; q1 < R1; ++q1) {
+      float2 t[R2];
+#pragma unroll
+      for (int r2 = 0; r2 < R2; ++r2) t[r2] = v[R2 * q1 + r2];
+      dft<R2>(t, rc2);
+#pragma unroll
+      for (int q2 = 0; q2 < R2; ++q2) o[q1 + R1 * q2] = t[q2];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = o[r];
+  }
+}
+
+// table rows of a later stage of radix R1 R2: the twiddle of entry r = R2 r1 + r2 is the product
+// of the rows w^(r2 k t) (r2 = 1 .. R2 - 1) and w^(R2 r1 k t) (r1 = 1 .. R1 - 1), rounded twice at most
+constexpr int ct_twiddle_rows(int R1, int R2) { return R2 > 1 ? (R1 - 1) + (R2 - 1) : R1 - 1; }
+
+template <int R1_, int R2_>
+struct CtRadix {
+  static constexpr int R1 = R1_, R2 = R2_, R = R1_ * R2_;
+};
+
+// a compiled plan: length, CTA width, fibers per CTA, the stages in order
+template <int I_, int TPB_, int BJ_, int MINB_, class... Rs>
+struct CtPlan {
+  static constexpr int I = I_, TPB = TPB_, BJ = BJ_, S = BJ_ / 2, MINB = MINB_;
+  static constexpr int NST = sizeof...(Rs);
+  static constexpr int radix(int s) {
+    const int rs[] = {Rs::R...};
+    return rs[s];
+  }
+  // the first stage writes butterfly j's R0 outputs at j (R0 + 1) + r (stride R0 + 1, odd, instead
+  // of the even R0: no bank conflicts); the second stage's reads follow (they stay immediate offsets
+  // when R0 divides its L)
+  static constexpr bool SKEW = NST >= 2 && radix(0) % 2 == 0 && (I_ / radix(1)) % radix(0) == 0;
+  static constexpr int LEN = I_ + (SKEW ? I_ / radix(0) : 0);   // complex entries of a sequence
+  // a sequence spans two fiber rows of IPAD floats: IPAD >= LEN, a multiple of 4 (16-byte rows for the
+  // bulk copies) with IPAD / 4 odd (conflict-free column reads by the stores)
+  static constexpr int IPAD = ((LEN + 3) / 4 * 4) % 8 == 0 ? (LEN + 3) / 4 * 4 + 4 : (LEN + 3) / 4 * 4;
+  static constexpr int twiddles() {   // entries of the later stages' tables
+    int ns = 1, n = 0;
+    const int rs[] = {Rs::R...}, r1s[] = {Rs::R1...}, r2s[] = {Rs::R2...};
+    for (int s = 0; s < NST; ++s) {
+      if (s > 0) n += ct_twiddle_rows(r1s[s], r2s[s]) * ns;
+      ns *= rs[s];
+    }
+    return n;
+  }
+  static constexpr int product() {
+    int p = 1;
+    const int rs[] = {Rs::R...};
+    for (int s = 0; s < NST; ++s) p *= rs[s];
+    return p;
+  }
+  // shared memory, in floats: the fiber rows, post-scales (2I), the first stage's sign masks (one word
+  // per butterfly of a sequence, rounded up to even), the stage tables, then the mbarrier
+  static constexpr int L0 = I_ / radix(0);
+  static constexpr int OFF_POST = BJ_ * IPAD, OFF_SG = OFF_POST + 2 * I_, OFF_T = OFF_SG + (L0 + 1) / 2 * 2,
+                       OFF_BAR = OFF_T + 2 * twiddles();
+  static constexpr size_t SMEM = (size_t)OFF_BAR * sizeof(float) + 16;
+};
+
+// one stage of the compiled plan (the Stockham stage of fft_stage with constant parameters).  smask:
+// for butterfly j of the first stage, bit r set when the sign of its entry r (reorder order) is -1
+template <class PL, int R1, int R2, int NS, bool FIRST>
+__device__ __forceinline__ void ct_stage(float2* Z, const float2* T, const uint32_t* smask, int tid) {
+  constexpr int I = PL::I, IPAD = PL::IPAD, TPB = PL::TPB, R = R1 * R2, L = I / R, NB = PL::S * L;
+  constexpr int NQ = (NB + TPB - 1) / TPB;
+  constexpr bool SKW = FIRST && PL::SKEW, SKR = !FIRST && NS == PL::radix(0) && PL::SKEW;
+  constexpr int R0 = PL::radix(0);
+  float2 v[NQ][R];
+  int dst[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int b = tid + q * TPB;
+    dst[q] = -1;
+    if (NB % TPB == 0 || b < NB) {
+      const int p = b / L, j = b - p * L;
+      if constexpr (FIRST) {   // v_p[m] = d[s] (x_{2p}[s], x_{2p+1}[s]), s = 2m or 2(I - 1 - m) + 1
+        static_assert(R <= 32, "one sign mask word per butterfly");
+        const float* row = reinterpret_cast<const float*>(Z + p * IPAD);
+        const uint32_t msk = smask[j];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          int src;
+          if (2 * (r + 1) * L <= I) src = 2 * j + 2 * r * L;                 // every m of this r even-placed
+          else if (2 * r * L >= I) src = (2 * I - 1 - 2 * r * L) - 2 * j;   // every m odd-placed
+          else {
+            const int m = j + r * L;
+            src = 2 * m < I ? 2 * m : 2 * I - 1 - 2 * m;
+          }
+          const uint32_t flip = (msk << (31 - r)) & 0x80000000u;   // the sign bit of d
+          v[q][r] = make_float2(__uint_as_float(__float_as_uint(row[src]) ^ flip),
+                                __uint_as_float(__float_as_uint(row[IPAD + src]) ^ flip));
+        }
+      } else {
+        const int k = j % NS;
+        // entry m of the first stage's output sits at m + m / R0 when skewed (R0 divides L)
+        const float2* z = Z + p * IPAD + j + (SKR ? j / R0 : 0);
+        constexpr int LS = SKR ? L + L / R0 : L;
+        const float2* t = T + k;
+        v[q][0] = z[0];
+        if constexpr (R2 > 1) {   // twiddle of r = R2 r1 + r2: the table rows' product
+          float2 wa[R2], wb[R1];
+#pragma unroll
+          for (int r2 = 1; r2 < R2; ++r2) wa[r2] = t[(r2 - 1) * NS];
+#pragma unroll
+          for (int r1 = 1; r1 < R1; ++r1) wb[r1] = t[(R2 - 1 + r1 - 1) * NS];
+#pragma unroll
+          for (int r = 1; r < R; ++r) {
+            const int r1 = r / R2, r2 = r % R2;
+            const float2 w = r1 == 0 ? wa[r2] : (r2 == 0 ? wb[r1] : cmul(wb[r1], wa[r2]));
+            v[q][r] = cmul(z[r * LS], w);
+          }
+        } else {
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[q][r] = cmul(z[r * LS], t[(r - 1) * NS]);
+        }
+      }
+      ct_dft_comp<R1, R2>(v[q]);
+      dst[q] = p * IPAD + (SKW ? j * (R + 1) : (j / NS) * NS * R + j % NS);
+    }
+    asm volatile("" ::: "memory");
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+    if (NB % TPB == 0 || dst[q] >= 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) Z[dst[q] + r * NS] = v[q][r];
+    }
+  __syncthreads();
+}
+
+template <class PL, int NS, bool FIRST, class R0, class... Rest>
+__device__ __forceinline__ void ct_stages(float2* Z, const float2* T, const uint32_t* smask, int tid) {
+  ct_stage<PL, R0::R1, R0::R2, NS, FIRST>(Z, T, smask, tid);
+  if constexpr (sizeof...(Rest) > 0)
+    ct_stages<PL, NS * R0::R, false, Rest...>(Z, FIRST ? T : T + ct_twiddle_rows(R0::R1, R0::R2) * NS, smask, tid);
+}
+
+// the stage tables from the length-I twiddles in global memory (L2-resident): row e of a stage of
+// radix R1 R2 (R2 > 1) holds w^(r2 k t) for e = r2 - 1 < R2 - 1, else w^(R2 r1 k t) for e = R2 - 2 + r1;
+// a plain radix R1 holds w^(r k t) in row r - 1 (t = I / (NS R), k < NS)
+template <class PL, int NS, bool FIRST, class R0, class... Rest>
+__device__ __forceinline__ void ct_tables(float2* T, const float2* twg, int tid) {
+  constexpr int ROWS = ct_twiddle_rows(R0::R1, R0::R2);
+  if constexpr (!FIRST) {
+    constexpr int CNT = ROWS * NS, TSTEP = PL::I / (NS * R0::R);
+    for (int e = tid; e < CNT; e += PL::TPB) {
+      const int row = e / NS, k = e - row * NS;
+      const int mult = R0::R2 > 1 ? (row < R0::R2 - 1 ? row + 1 : R0::R2 * (row - (R0::R2 - 1) + 1)) : row + 1;
+      T[e] = twg[mult * k * TSTEP];
+    }
+  }
+  if constexpr (sizeof...(Rest) > 0)
+    ct_tables<PL, NS * R0::R, false, Rest...>(FIRST ? T : T + ROWS * NS, twg, tid);
+}
+
+// y_{2p}[k], y_{2p+1}[k] from the transformed sequence p: A = Z_p[k], B = Z_p[(I - k) mod I]
+__device__ __forceinline__ float2 ct_separate(float2 A, float2 B, float2 pk) {
+  return make_float2(pk.x * (A.x + B.x) + pk.y * (A.y - B.y), pk.x * (A.y + B.y) - pk.y * (A.x - B.x));
+}
+
+template <typename T> __device__ __forceinline__ void st4(T* dst, float a, float b, float c, float d);
+template <> __device__ __forceinline__ void st4<float>(float* dst, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(dst) = make_float4(a, b, c, d);
+}
+template <> __device__ __forceinline__ void st4<__nv_bfloat16>(__nv_bfloat16* dst, float a, float b, float c, float d) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  uint2 u;
+  u.x = *reinterpret_cast<const uint32_t*>(&lo);
+  u.y = *reinterpret_cast<const uint32_t*>(&hi);
+  *reinterpret_cast<uint2*>(dst) = u;
+}
+
+template <class PL> struct CtStages;
+template <int I_, int TPB_, int BJ_, int MINB_, class... Rs>
+struct CtStages<CtPlan<I_, TPB_, BJ_, MINB_, Rs...>> {
+  using P = CtPlan<I_, TPB_, BJ_, MINB_, Rs...>;
+  static __device__ __forceinline__ void run(float2* Z, const float2* T, const uint32_t* smask, int tid) {
+    ct_stages<P, 1, true, Rs...>(Z, T, smask, tid);
+  }
+  static __device__ __forceinline__ void tables(float2* T, const float2* twg, int tid) {
+    ct_tables<P, 1, true, Rs...>(T, twg, tid);
+  }
+};
+
+template <typename T, class PL>
+__global__ void __launch_bounds__(PL::TPB, PL::MINB) k_mix_fft_ct(const __grid_constant__ FftArgs a) {
+  constexpr int I = PL::I, IPAD = PL::IPAD, BJ = PL::BJ, S = PL::S, TPB = PL::TPB, NW = TPB / 32;
+  static_assert(PL::product() == PL::I, "the plan's radices multiply to the length");
+  static_assert(BJ % 16 == 0 && TPB % 32 == 0, "4-fiber groups, whole warps");
+  extern __shared__ float4 fft_smem4[];
+  float* Y = reinterpret_cast<float*>(fft_smem4);
+  float2* Z = reinterpret_cast<float2*>(Y);
+  float2* post = reinterpret_cast<float2*>(Y + PL::OFF_POST);
+  uint32_t* smask = reinterpret_cast<uint32_t*>(Y + PL::OFF_SG);
+  float2* Tt = reinterpret_cast<float2*>(Y + PL::OFF_T);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Y + PL::OFF_BAR);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const T* U = static_cast<const T*>(a.U);
+  if (a.I != I) {   // the host launches a compiled plan for its own length only
+    if (tid == 0) atomicExch(a.err, 1);
+    return;
+  }
+  __shared__ longlong4 s_blk;
+  if (tid == 0) {
+    int64_t r0, o0;
+    const int n = fft_block(a, blockIdx.x, r0, o0);
+    s_blk = make_longlong4(r0, o0, n, 0);
+    if (a.bulk) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  __syncthreads();
+  const int64_t row0 = s_blk.x, out0 = s_blk.y;
+  const int nf = (int)s_blk.z;
+  if (a.bulk) {
+    if (tid == 0)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                   "r"((uint32_t)(nf * I * sizeof(float)))
+                   : "memory");
+    if (tid < nf)
+      fft_bulk_copy(Y + tid * IPAD, U + (row0 + (int64_t)tid * a.rs_in_v) * I, (uint32_t)(I * sizeof(float)), bar);
+  } else {
+    for (int f = warp; f < nf; f += NW) {
+      const T* src = U + (row0 + (int64_t)f * a.rs_in_v) * I;
+      for (int k = lane; k < I; k += 32) Y[f * IPAD + k] = ld_as_float<T>(src + k);
+    }
+  }
+  for (int e = tid; e < 2 * I; e += TPB) Y[PL::OFF_POST + e] = a.tab[2 * I + e];   // post-scales
+  for (int j = tid; j < PL::L0; j += TPB) {   // the signs of butterfly j's entries m = j + r L0
+    uint32_t msk = 0;
+    for (int r = 0; r < PL::radix(0); ++r) {
+      const int m = j + r * PL::L0;
+      msk |= (a.tab[4 * I + (2 * m < I ? 2 * m : 2 * I - 1 - 2 * m)] < 0.f ? 1u : 0u) << r;
+    }
+    smask[j] = msk;
+  }
+  CtStages<PL>::tables(Tt, reinterpret_cast<const float2*>(a.tab), tid);
+  for (int e = tid; e < (BJ - nf) * IPAD; e += TPB) Y[nf * IPAD + e] = 0.f;
+  bool ok = true;
+  if (a.bulk && tid == 0) {
+    ok = false;
+    for (uint32_t it = 0; it < kFftWaitLimit && !ok; ++it) ok = fft_mbar_try(bar, 0);
+  }
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicExch(a.err, 1);
+    return;
+  }
+  if (a.bulk && tid != 0) (void)fft_mbar_try(bar, 0);
+
+  CtStages<PL>::run(Z, Tt, smask, tid);
+
+  T* yv = static_cast<T*>(a.yv);
+  constexpr int KH = I / 2;   // entries k <= KH and their partners I - k cover 0 .. I - 1
+  if (a.vec_v && nf == BJ) {
+    // lane (k = k0 + lane % 8 <= KH, 4-fiber group g = 4 gq + lane / 8): y_{4g .. 4g+3} at k and at
+    // I - k from sequences 2g and 2g + 1 (each value read once), two 16-byte stores; a half warp reads
+    // 32 distinct banks (IPAD / 4 odd)
+    constexpr int NGQ = BJ / 16, NKO = (KH + 1 + 7) / 8;
+    for (int w = warp; w < NGQ * NKO; w += NW) {
+      const int k = (w / NGQ) * 8 + (lane & 7), g = (w % NGQ) * 4 + (lane >> 3);
+      if (k <= KH) {
+        const int kk = k == 0 ? 0 : I - k;
+        const float2* z0 = Z + 2 * g * IPAD;
+        const float2 A0 = z0[k], B0 = z0[kk], A1 = z0[IPAD + k], B1 = z0[IPAD + kk];
+        const float2 pk = post[k];
+        const float2 y0 = ct_separate(A0, B0, pk), y1 = ct_separate(A1, B1, pk);
+        st4<T>(yv + out0 + 4 * g + (int64_t)k * a.out_k, y0.x, y0.y, y1.x, y1.y);
+        if (kk != k) {
+          const float2 pq = post[kk];
+          const float2 q0 = ct_separate(B0, A0, pq), q1 = ct_separate(B1, A1, pq);
+          st4<T>(yv + out0 + 4 * g + (int64_t)kk * a.out_k, q0.x, q0.y, q1.x, q1.y);
+        }
+      }
+    }
+  } else {
+    for (int e = tid; e < BJ * I; e += TPB) {
+      const int f = e % BJ, k = e / BJ;
+      if (f < nf) {
+        const float2* z = Z + (f >> 1) * IPAD;
+        const float2 y = ct_separate(z[k], z[k == 0 ? 0 : I - k], post[k]);
+        yv[out0 + f + (int64_t)k * a.out_k] = from_float<T>((f & 1) ? y.y : y.x);
+      }
+    }
+  }
+  if (a.ysame) {   // each fiber a row of the input's layout
+    T* ys = static_cast<T*>(a.ysame);
+    // a warp: sequence p, 32 consecutive k <= KH and their partners I - k (conflict-free reads of
+    // Z_p[k], Z_p[I - k], post[k], post[I - k]); coalesced row segments of fibers 2p and 2p + 1
+    constexpr int KC = (KH + 1 + 31) / 32;
+    for (int w = warp; w < S * KC; w += NW) {
+      const int p = w / KC, k = (w - p * KC) * 32 + lane;
+      if (2 * p >= nf || k > KH) continue;
+      const int kk = k == 0 ? 0 : I - k;
+      const float2* z = Z + p * IPAD;
+      const float2 A = z[k], B = z[kk];
+      const float2 y = ct_separate(A, B, post[k]);
+      T* r0p = ys + (row0 + (int64_t)(2 * p) * a.rs_in_v) * I;
+      T* r1p = ys + (row0 + (int64_t)(2 * p + 1) * a.rs_in_v) * I;
+      const bool two = 2 * p + 1 < nf;
+      r0p[k] = from_float<T>(y.x);
+      if (two) r1p[k] = from_float<T>(y.y);
+      if (kk != k) {
+        const float2 q = ct_separate(B, A, post[kk]);
+        r0p[kk] = from_float<T>(q.x);
+        if (two) r1p[kk] = from_float<T>(q.y);
+      }
+    }
+  }
+}
+
+// the compiled plans: I = 400 = 20 x 20 (radix 20 = 5 x 4), 16 fibers per CTA, one butterfly per
+// thread in both stages, six CTAs per SM (64 registers, 34 KB of shared memory each)
+using CtPlan400 = CtPlan<400, 160, 16, 6, CtRadix<5, 4>, CtRadix<5, 4>>;
+
 // the stage radices of I (every prime factor 2, 3, 5 or 7), grouped into the radices of kRadR1 x
 // kRadR2, listed in radix-index order; among the groupings, the one that admits the widest fiber block
 // (then the fewest stages).  CTAs of 128 threads (four per SM) unless that narrows the block below 8
@@ -618,6 +1019,35 @@ cudaError_t launch_fft_kernel(const FftArgs& a, size_t smem, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T, class PL>
+cudaError_t launch_fft_ct_kernel(const FftArgs& a, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_mix_fft_ct<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (a.nblocks > INT32_MAX) return cudaErrorInvalidValue;
+  k_mix_fft_ct<T, PL><<<(unsigned)a.nblocks, PL::TPB, PL::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+// the compiled plan of a pass, when there is one: the length matches and mode v is at least one
+// CTA's block of fibers wide
+template <class PL>
+bool ct_plan_of(FftPlan* pl) {
+  memset(pl, 0, sizeof(*pl));
+  pl->tpb = PL::TPB;
+  pl->BJ = PL::BJ;
+  pl->Ipad = PL::IPAD;
+  pl->smem = PL::SMEM;
+  return true;
+}
+int ct_plan_id(int I, int64_t Iv) {
+  if (I == CtPlan400::I && Iv >= CtPlan400::BJ) return 1;
+  return 0;
+}
+
 template <typename TIN, int TPB>
 cudaError_t launch_cfft_kernel(const FftArgs& a, size_t smem, cudaStream_t s) {
   static bool attr = false;
@@ -650,13 +1080,18 @@ bool mix_fft_supported(int dtype, int N, const int64_t* dims) {
 
 namespace {
 // the kernel arguments of one pass (mode n read, mode v = n + 1 mod N written); false without a plan
+// (a compiled plan's kernel ignores the stage list; it is filled from the generic planner only)
 bool fft_args(FftArgs& a, FftPlan& pl, const void* U, void* yv, void* ysame, const float* tab, int N,
-              const int64_t* dims, int n, int* err, bool cplx) {
+              const int64_t* dims, int n, int* err, bool cplx, int ct = 0) {
   if (N < 2 || n < 0 || n >= N) return false;
   const int v = (n + 1) % N;
   memset(&a, 0, sizeof(a));
   const int I = (int)dims[n];
-  if (!fft_plan(I, dims[v], &pl, cplx)) return false;
+  if (ct == 1) {
+    if (!ct_plan_of<CtPlan400>(&pl)) return false;
+  } else if (!fft_plan(I, dims[v], &pl, cplx)) {
+    return false;
+  }
   a.U = U;
   a.yv = yv;
   a.ysame = ysame;
@@ -711,10 +1146,17 @@ cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* ta
                            const int64_t* dims, int n, int* err, cudaStream_t s) {
   FftArgs a;
   FftPlan pl;
-  if (!fft_args(a, pl, U, yv, ysame, tab, N, dims, n, err, false)) return cudaErrorInvalidValue;
+  if (N < 2 || n < 0 || n >= N) return cudaErrorInvalidValue;
+  const int ct = ct_plan_id((int)dims[n], dims[(n + 1) % N]);
+  if (!fft_args(a, pl, U, yv, ysame, tab, N, dims, n, err, false, ct)) return cudaErrorInvalidValue;
   const int I = a.I;
   const size_t es = dtype == CPR_F32 ? 4 : 2;
   a.bulk = dtype == CPR_F32 && (I * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(U) & 15) == 0;
+  const uintptr_t vmask = 4 * es - 1;   // 4 entries per vector store
+  a.vec_v = a.Iv % 4 == 0 && (reinterpret_cast<uintptr_t>(yv) & vmask) == 0;
+  if (ct == 1)
+    return dtype == CPR_F32 ? launch_fft_ct_kernel<float, CtPlan400>(a, s)
+                            : launch_fft_ct_kernel<__nv_bfloat16, CtPlan400>(a, s);
   if (dtype == CPR_F32)
     return pl.tpb == 128 ? launch_fft_kernel<float, 128>(a, pl.smem, s) : launch_fft_kernel<float, 256>(a, pl.smem, s);
   if (dtype == CPR_BF16)
