@@ -59,6 +59,10 @@ def parse():
                          "score of CPRAND-MIX and CPRAND over synthetic tensors, three starts per rank")
     ap.add_argument("--sweep-tensors", type=int, default=50, help="tensors per (size, C, eta) cell")
     ap.add_argument("--sweep-sizes", default="3x400,4x90", help="order x dimension of the sweep's tensors")
+    ap.add_argument("--mix-shape", action="append", default=None, metavar="I1xI2x...:dtype",
+                    help="instead of the benchmark: time the mixing call alone on this tensor shape "
+                         "(float32 or bfloat16; repeatable), as the benchmark's extras do for other workloads")
+    ap.add_argument("--mix-reps", type=int, default=4)
     return ap.parse_args()
 
 
@@ -142,8 +146,12 @@ def kernel_traffic(cls):
     return None
 
 
-MIX_KERNEL = ("k_mix_fft (factored DCT-II: mixed-radix Stockham FFT of BJ fibers in shared memory, "
-              "writes the next pass's unfolding layout)")
+MIX_KERNEL = ("k_mix_fft_ct (factored DCT-II, stage plan compiled for I_n = 400: two radix-20 Stockham "
+              "stages of 16 fibers in shared memory, DCT separation fused into the stores; writes the next "
+              "pass's unfolding layout)")
+MIX_SHAPES = [((1500, 1500, 1500), "float32"), ((1500, 1500, 1500), "bfloat16"),
+              ((100, 100, 100, 100), "bfloat16"), ((100, 100, 100, 100), "float32"),
+              ((1500, 1500, 200), "float32")]
 
 
 def algorithmic(cls, w, P, b, iters_per_launch=None):
@@ -181,6 +189,38 @@ def complex_form_rate(cb, X, dims, w, iters=10):
                     "real least squares; host loop, one synchronization per outer iteration",
             "iters": out["iters"], "ms_setup": out["ms_setup"], "us_per_iter": 1e3 * out["ms_iterate"] / out["iters"],
             "fit_est_last": out["fit_est"]}
+
+
+def mixing_shapes(cb, reps=4, shapes=None):
+    """The mixing preprocess alone (cpr_mix_tensor: the operator tables, then one factored-DCT pass per
+    mode) on the other workloads' tensors: device time per call by CUDA events over `reps` calls after
+    one warm-up call, against N passes x (P b read + P b written)."""
+    import torch
+    pk, pk_src = peaks()
+    res = []
+    for dims, dt in (shapes or MIX_SHAPES):
+        P = 1
+        for d in dims:
+            P *= d
+        X = torch.randn(P, device="cuda", dtype=getattr(torch, dt))
+        cb.cpr_mix_tensor(X, dims, seed=7)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            Y = cb.cpr_mix_tensor(X, dims, seed=7)
+            del Y
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        nbytes = len(dims) * 2 * P * X.element_size()
+        res.append({"dims": list(dims), "dtype": dt, "ms_per_call": ms,
+                    "passes": len(dims), "GBs": nbytes / (ms / 1e3) / 1e9,
+                    "frac_of_hbm_peak": nbytes / (ms / 1e3) / 1e9 / pk["hbm_gbs"]})
+        del X
+        torch.cuda.empty_cache()
+    return {"what": "cpr_mix_tensor per call (operator tables + N passes), algorithmic bytes N x 2 P b",
+            "peak_GBs": pk["hbm_gbs"], "peak_source": pk_src, "shapes": res}
 
 
 def true_fit_gpu(X, dims, lam, factors):
@@ -434,7 +474,7 @@ def run_ours(args, rank, world, local_rank):
     # time to fit: true fit within 1e-3 of the FP64 oracle's final fit (the oracle runs on this host's
     # cores), for the library and for the plain FP64 GPU form on the same GPU
     cpu = None
-    ttf = plain_out = gather = complex_form = None
+    ttf = plain_out = gather = complex_form = mix_other = None
     if rank == 0 and world == 1 and not args.skip_extras:
         if not args.no_cpu_baseline:
             cpu = cpu_baseline(X, dims, seconds=60.0)
@@ -468,6 +508,7 @@ def run_ours(args, rank, world, local_rank):
                              "Cholesky solves), host-side loop and stopping test"}
         gather = gather_bandwidth(cb, X, dims)
         complex_form = complex_form_rate(cb, X, dims, w)
+        mix_other = mixing_shapes(cb)
 
     pk, pk_src = peaks()
     roof = None
@@ -520,6 +561,8 @@ def run_ours(args, rank, world, local_rank):
         out["plain_fp64_gpu"] = plain_out
     if complex_form is not None:
         out["complex_form"] = complex_form
+    if mix_other is not None:
+        out["mixing_other_shapes"] = mix_other
     if gather is not None:
         for g in gather.values():
             g["frac_of_hbm_peak"] = g["read_write_GBs"] / pk["hbm_gbs"]
@@ -685,6 +728,17 @@ def main():
     if args.quality_sweep:
         if rank == 0:
             print(json.dumps(run_quality_sweep(args)))
+        return
+    if args.mix_shape:
+        if rank == 0:
+            import __graft_entry__
+            __graft_entry__.build()
+            from paper_1701_06600_gb300 import binding as cb
+            shapes = []
+            for spec in args.mix_shape:
+                dims, _, dt = spec.partition(":")
+                shapes.append((tuple(int(v) for v in dims.split("x")), dt or "float32"))
+            print(json.dumps({"mixing_shapes": mixing_shapes(cb, reps=args.mix_reps, shapes=shapes)}))
         return
     if args.impl == "reference":
         out = run_reference(args, rank, world)

@@ -74,6 +74,7 @@ struct FftArgs {
   int no;               // number of remaining modes (not n, not v)
   int64_t oext[kMaxOrder], o_in[kMaxOrder], o_out[kMaxOrder];
   int vec_v;            // the mode-v output admits 16-byte stores of 4 adjacent fibers
+  int vec_in;           // BF16 input rows admit 8-byte loads of 4 entries
   int* err;
 };
 
@@ -797,7 +798,9 @@ template <typename T, class PL>
 __global__ void __launch_bounds__(PL::TPB, PL::MINB) k_mix_fft_ct(const __grid_constant__ FftArgs a) {
   constexpr int I = PL::I, IPAD = PL::IPAD, BJ = PL::BJ, S = PL::S, TPB = PL::TPB, NW = TPB / 32;
   static_assert(PL::product() == PL::I, "the plan's radices multiply to the length");
-  static_assert(BJ % 16 == 0 && TPB % 32 == 0, "4-fiber groups, whole warps");
+  // 4-fiber groups; a warp's lanes cover GW of them (GW <= 4 keeps the column reads conflict-free)
+  constexpr int G4 = BJ / 4, GW = G4 < 4 ? G4 : 4, KPW = 32 / GW;
+  static_assert(BJ % 4 == 0 && G4 % GW == 0 && TPB % 32 == 0, "4-fiber groups, whole warps");
   extern __shared__ float4 fft_smem4[];
   float* Y = reinterpret_cast<float*>(fft_smem4);
   float2* Z = reinterpret_cast<float2*>(Y);
@@ -831,6 +834,29 @@ __global__ void __launch_bounds__(PL::TPB, PL::MINB) k_mix_fft_ct(const __grid_c
                    : "memory");
     if (tid < nf)
       fft_bulk_copy(Y + tid * IPAD, U + (row0 + (int64_t)tid * a.rs_in_v) * I, (uint32_t)(I * sizeof(float)), bar);
+  } else if (sizeof(T) == 2 && I % 4 == 0 && a.vec_in) {
+    // BF16 rows: 8-byte loads of 4 entries (widened exactly to FP32), four in flight per lane, 16-byte
+    // shared stores
+    constexpr int C4 = I / 4;
+    for (int f = warp; f < nf; f += NW) {
+      const uint2* src = reinterpret_cast<const uint2*>(U + (row0 + (int64_t)f * a.rs_in_v) * I);
+      float4* dst = reinterpret_cast<float4*>(Y + f * IPAD);
+      for (int c0 = 0; c0 < C4; c0 += 128) {
+        uint2 u[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = c0 + 32 * i + lane;
+          if (c < C4) u[i] = __ldg(src + c);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = c0 + 32 * i + lane;
+          if (c < C4)
+            dst[c] = make_float4(__uint_as_float(u[i].x << 16), __uint_as_float(u[i].x & 0xffff0000u),
+                                 __uint_as_float(u[i].y << 16), __uint_as_float(u[i].y & 0xffff0000u));
+        }
+      }
+    }
   } else {
     for (int f = warp; f < nf; f += NW) {
       const T* src = U + (row0 + (int64_t)f * a.rs_in_v) * I;
@@ -864,12 +890,12 @@ __global__ void __launch_bounds__(PL::TPB, PL::MINB) k_mix_fft_ct(const __grid_c
   T* yv = static_cast<T*>(a.yv);
   constexpr int KH = I / 2;   // entries k <= KH and their partners I - k cover 0 .. I - 1
   if (a.vec_v && nf == BJ) {
-    // lane (k = k0 + lane % 8 <= KH, 4-fiber group g = 4 gq + lane / 8): y_{4g .. 4g+3} at k and at
-    // I - k from sequences 2g and 2g + 1 (each value read once), two 16-byte stores; a half warp reads
-    // 32 distinct banks (IPAD / 4 odd)
-    constexpr int NGQ = BJ / 16, NKO = (KH + 1 + 7) / 8;
+    // lane (k = k0 + lane % KPW <= KH, 4-fiber group g = GW gq + lane / KPW): y_{4g .. 4g+3} at k and
+    // at I - k from sequences 2g and 2g + 1 (each value read once), two 16-byte stores; a half warp
+    // reads 32 distinct banks (IPAD / 4 odd)
+    constexpr int NGQ = G4 / GW, NKO = (KH + 1 + KPW - 1) / KPW;
     for (int w = warp; w < NGQ * NKO; w += NW) {
-      const int k = (w / NGQ) * 8 + (lane & 7), g = (w % NGQ) * 4 + (lane >> 3);
+      const int k = (w / NGQ) * KPW + lane % KPW, g = (w % NGQ) * GW + lane / KPW;
       if (k <= KH) {
         const int kk = k == 0 ? 0 : I - k;
         const float2* z0 = Z + 2 * g * IPAD;
@@ -920,9 +946,15 @@ __global__ void __launch_bounds__(PL::TPB, PL::MINB) k_mix_fft_ct(const __grid_c
   }
 }
 
-// the compiled plans: I = 400 = 20 x 20 (radix 20 = 5 x 4), 16 fibers per CTA, one butterfly per
-// thread in both stages, six CTAs per SM (64 registers, 34 KB of shared memory each)
+// the compiled plans:
+//  * I = 400 = 20 x 20 (radix 20 = 5 x 4), 16 fibers per CTA, one butterfly per thread in both
+//    stages, six CTAs per SM (64 registers, 34 KB of shared memory each);
+//  * I = 1500 = 25 x 12 x 5, 8 fibers per CTA, 256 threads (240, 500 and 1200 butterflies: one, two
+//    and five per thread), three CTAs per SM (71 KB each);
+//  * I = 100 = 10 x 10 (radix 10 = 5 x 2), 16 fibers per CTA, 96 threads (80 butterflies a stage).
 using CtPlan400 = CtPlan<400, 160, 16, 6, CtRadix<5, 4>, CtRadix<5, 4>>;
+using CtPlan1500 = CtPlan<1500, 256, 8, 3, CtRadix<5, 5>, CtRadix<4, 3>, CtRadix<5, 1>>;
+using CtPlan100 = CtPlan<100, 96, 16, 12, CtRadix<5, 2>, CtRadix<5, 2>>;
 
 // the stage radices of I (every prime factor 2, 3, 5 or 7), grouped into the radices of kRadR1 x
 // kRadR2, listed in radix-index order; among the groupings, the one that admits the widest fiber block
@@ -1045,6 +1077,8 @@ bool ct_plan_of(FftPlan* pl) {
 }
 int ct_plan_id(int I, int64_t Iv) {
   if (I == CtPlan400::I && Iv >= CtPlan400::BJ) return 1;
+  if (I == CtPlan1500::I && Iv >= CtPlan1500::BJ) return 2;
+  if (I == CtPlan100::I && Iv >= CtPlan100::BJ) return 3;
   return 0;
 }
 
@@ -1087,8 +1121,10 @@ bool fft_args(FftArgs& a, FftPlan& pl, const void* U, void* yv, void* ysame, con
   const int v = (n + 1) % N;
   memset(&a, 0, sizeof(a));
   const int I = (int)dims[n];
-  if (ct == 1) {
-    if (!ct_plan_of<CtPlan400>(&pl)) return false;
+  if (ct == 1 || ct == 2 || ct == 3) {
+    if (ct == 1) ct_plan_of<CtPlan400>(&pl);
+    if (ct == 2) ct_plan_of<CtPlan1500>(&pl);
+    if (ct == 3) ct_plan_of<CtPlan100>(&pl);
   } else if (!fft_plan(I, dims[v], &pl, cplx)) {
     return false;
   }
@@ -1154,9 +1190,16 @@ cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* ta
   a.bulk = dtype == CPR_F32 && (I * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(U) & 15) == 0;
   const uintptr_t vmask = 4 * es - 1;   // 4 entries per vector store
   a.vec_v = a.Iv % 4 == 0 && (reinterpret_cast<uintptr_t>(yv) & vmask) == 0;
+  a.vec_in = dtype == CPR_BF16 && I % 4 == 0 && (reinterpret_cast<uintptr_t>(U) & 7) == 0;
   if (ct == 1)
     return dtype == CPR_F32 ? launch_fft_ct_kernel<float, CtPlan400>(a, s)
                             : launch_fft_ct_kernel<__nv_bfloat16, CtPlan400>(a, s);
+  if (ct == 2)
+    return dtype == CPR_F32 ? launch_fft_ct_kernel<float, CtPlan1500>(a, s)
+                            : launch_fft_ct_kernel<__nv_bfloat16, CtPlan1500>(a, s);
+  if (ct == 3)
+    return dtype == CPR_F32 ? launch_fft_ct_kernel<float, CtPlan100>(a, s)
+                            : launch_fft_ct_kernel<__nv_bfloat16, CtPlan100>(a, s);
   if (dtype == CPR_F32)
     return pl.tpb == 128 ? launch_fft_kernel<float, 128>(a, pl.smem, s) : launch_fft_kernel<float, 256>(a, pl.smem, s);
   if (dtype == CPR_BF16)

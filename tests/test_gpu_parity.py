@@ -414,13 +414,14 @@ def test_tensor_core_mixing_matches_oracle(cb, engine, dims):
 # ------------------------------------------------------------------------------------------------
 # a0 by the factored DCT-II (mixed-radix FFT per fiber): stages of radix 2 to 25 (plain and
 # two-level), one to three stages, orders 2 to 4, fiber blocks that run past the end of a mode, blocks
-# of 2 to 32 fibers, the 400^3 and 1500 x ... sizes; the kernel compiled for I_n = 400 with full
-# blocks (vector stores), a partial last block, and a mode-v extent that is not a multiple of 4
-# (scalar stores); FP32 to 1e-6 relative (FP32 FFT rounding), BF16 to the BF16 bar
+# of 2 to 32 fibers, the 400^3 and 1500 x ... sizes; the kernels compiled for I_n = 400, 1500 and 100
+# with full blocks (vector stores), a partial last block, and a mode-v extent that is not a multiple
+# of 4 (scalar stores); FP32 to 1e-6 relative (FP32 FFT rounding), BF16 to the BF16 bar
 # ------------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("dims", [(64, 48, 40), (300, 12, 8), (16, 12, 20, 8), (40, 45, 21), (7, 10, 5), (20, 30),
                                   (50, 15, 12, 6), (14, 9, 35), (96, 20, 45), (35, 14, 21), (6000, 8, 5),
-                                  (400, 400, 400), (1500, 60, 20), (400, 20, 16), (30, 400, 18)])
+                                  (400, 400, 400), (1500, 60, 20), (400, 20, 16), (30, 400, 18), (100, 24, 30),
+                                  (24, 100, 17), (12, 1500, 9)])
 def test_fft_mixing_matches_oracle(cb, engine, dims):
     X = rand_tensor(dims, torch.float32, 12)
     T = to_oracle_array(X, dims)
@@ -434,7 +435,7 @@ def test_fft_mixing_matches_oracle(cb, engine, dims):
     assert rel(to_oracle_array(Yd, dims), ref) < 3e-5
 
 
-@pytest.mark.parametrize("dims", [(70, 30, 50), (100, 20, 12, 10), (400, 24, 10)])
+@pytest.mark.parametrize("dims", [(70, 30, 50), (100, 20, 12, 10), (400, 24, 10), (1500, 12, 9)])
 def test_fft_mixing_bf16_matches_oracle(cb, dims):
     # BF16 in and out, rounded to BF16 after every mode product (as the dense BF16 engine does)
     X = rand_tensor(dims, torch.bfloat16, 13)
