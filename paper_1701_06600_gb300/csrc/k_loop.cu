@@ -16,8 +16,9 @@
 //   4. Cluster barrier (the next update's samples are drawn and its fiber copies issued between
 //      the barrier's arrive and wait); every CTA sums the C partial Grams in one fixed order
 //      (identical G everywhere) and inverts it: Gauss-Jordan elimination in FP32 with one thread
-//      per entry of [G | I], then Newton-Schulz steps X <- X + X (I - G X) in FP64 (one for FP32
-//      tensors, two for FP64), each squaring the residual ||I - G X||; a residual above 1/4 or a
+//      per entry of [G | I], then Newton-Schulz steps X <- X + X (I - G X) (one for FP32 tensors,
+//      two for FP64) with the residual I - G X in FP64 and the small correction X (I - G X) in
+//      FP32, each squaring the residual ||I - G X||; a residual above 1/4 or a
 //      bad FP32 pivot falls back to an FP64 Cholesky inverse (which detects a singular Gram).
 //   5. The CTA's rows: M rows summed over the C partials (fixed order), A = M G^-1 in FP64, written
 //      to the FP64 result and stored into every CTA's copy of the factor; column sums of squares
@@ -498,7 +499,7 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
   const float* X0 = gj + (R & 1) * (R * W) + R;   // X0(i, c) = X0[i * W + c]
   double* X = reinterpret_cast<double*>(sm + L.X);
   {
-    // ---- Newton-Schulz refinement in FP64 (or the FP64 Cholesky inverse).  The first step writes
+    // ---- Newton-Schulz refinement (or the FP64 Cholesky inverse).  The first step writes
     // X directly (it reads the FP32 start); a second step (FP64 tensors) writes U, the result.
     double* U = reinterpret_cast<double*>(sm + L.U);
     double* E = reinterpret_cast<double*>(sm + L.E);
@@ -508,6 +509,9 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
     if (tid == 0) *s_em = 0u;
     __syncthreads();
     const int dbase = (RR + 31) / 32 * 32;   // first thread not computing an entry of E
+    // E in FP32 for the correction X E: |E| is small, so the FP32 product's rounding (about 1e-7 of
+    // |X E|) stays far below the FP64 residual of the step; it lives in the tableau half X0 is not in
+    float* Ef = gj + ((R + 1) & 1) * (R * W);
     bool drawn = false;
     for (int it = 0; fast && it < steps; ++it) {
       // E = I - G X  (X: the FP32 start in the first step)
@@ -532,6 +536,7 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
         }
         const double ev = (r == c ? 1.0 : 0.0) - (a0 + a1);
         E[e] = ev;
+        Ef[e] = (float)ev;
         em = fmaxf(em, fabsf((float)ev));
       }
       if (it == 0) {
@@ -549,30 +554,21 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
         fast = false;
         break;
       }
-      // X_new = X + X E
+      // X_new = X + X E, the correction in FP32 from the FP32 start X0 (which equals X to FP32
+      // accuracy) and E's FP32 copy
       double* Xout = it == 0 ? X : U;
       for (int e = tid; e < RR; e += kLT) {
         const int r = e / R, c = e - r * R;
-        double a0 = 0.0, a1 = 0.0, x;
+        const float* xr = X0 + r * W;
+        float a0 = 0.f, a1 = 0.f;
         int l = 0;
-        if (it == 0) {
-          const float* xr = X0 + r * W;
-          for (; l + 1 < R; l += 2) {
-            a0 = fma((double)xr[l], E[l * R + c], a0);
-            a1 = fma((double)xr[l + 1], E[(l + 1) * R + c], a1);
-          }
-          if (l < R) a0 = fma((double)xr[l], E[l * R + c], a0);
-          x = (double)xr[c];
-        } else {
-          const double* xr = X + r * R;
-          for (; l + 1 < R; l += 2) {
-            a0 = fma(xr[l], E[l * R + c], a0);
-            a1 = fma(xr[l + 1], E[(l + 1) * R + c], a1);
-          }
-          if (l < R) a0 = fma(xr[l], E[l * R + c], a0);
-          x = xr[c];
+        for (; l + 1 < R; l += 2) {
+          a0 = fmaf(xr[l], Ef[l * R + c], a0);
+          a1 = fmaf(xr[l + 1], Ef[(l + 1) * R + c], a1);
         }
-        Xout[e] = x + (a0 + a1);
+        if (l < R) a0 = fmaf(xr[l], Ef[l * R + c], a0);
+        const double x = it == 0 ? (double)xr[c] : X[r * R + c];
+        Xout[e] = x + (double)(a0 + a1);
       }
       __syncthreads();
       if (it == steps - 1 && steps == 2) X = U;   // the result of the second step
