@@ -283,6 +283,23 @@ def test_bf16_four_way_run_reaches_oracle_fit(cb):
     assert np.all(np.isfinite(err))
 
 
+@pytest.mark.parametrize("dims", [(24, 30, 100), (20, 12, 1500), (30, 20, 400), (16, 100, 36)])
+def test_mix_run_with_compiled_mixing_plans_tracks_oracle(cb, dims):
+    # decompositions whose mixing runs the kernels compiled for I_n = 100, 400, 1500 in the last pass
+    # (which also writes the mode-N unfolding copy the gathers read) or a middle one, with partial
+    # fiber blocks and mode-v extents that are not multiples of 4: sampled-fit trace and factors after
+    # a few outer iterations against the oracle
+    prob = make_problem(dims, 4, C=0.5, eta=0.01, seed=77, dtype=torch.float32, device=DEV)
+    T = to_oracle_array(prob.X, dims)
+    trace = torch.zeros(4, dtype=torch.float64, device=DEV)
+    opts = cb.cpr_default_opts(seed=43, fixed_iters=4, fit_trace_dev=trace.data_ptr())
+    out = cb.cpr_cprand_mix(prob.X, dims, 4, 60, opts=opts)
+    ref = mixing.cprand_mix(T, 4, 60, seed=43, rule=cp.StopRule(fixed_iters=4))
+    np.testing.assert_allclose(trace.cpu().numpy(), ref["fits"], rtol=0, atol=1e-4)
+    for A, Ar in zip(out["factors"], ref["factors"]):
+        assert rel(A.cpu().numpy(), Ar) < 1e-3
+
+
 def test_congruence_09_trace_tracks_oracle(cb):
     dims = (60, 50, 40)
     prob = make_problem(dims, 5, C=0.9, eta=0.01, seed=23, dtype=torch.float32, device=DEV)
