@@ -660,10 +660,11 @@ struct CtPlan {
     for (int s = 0; s < NST; ++s) p *= rs[s];
     return p;
   }
-  // shared memory, in floats: the fiber rows, post-scales (2I), the first stage's sign masks (one word
+  // shared memory, in floats: the fiber rows, post-scales of k <= I/2 (those of I - k are the same
+  // with swapped components), the first stage's sign masks (one word
   // per butterfly of a sequence, rounded up to even), the stage tables, then the mbarrier
   static constexpr int L0 = I_ / radix(0);
-  static constexpr int OFF_POST = BJ_ * IPAD, OFF_SG = OFF_POST + 2 * I_, OFF_T = OFF_SG + (L0 + 1) / 2 * 2,
+  static constexpr int OFF_POST = BJ_ * IPAD, OFF_SG = OFF_POST + 2 * (I_ / 2 + 1), OFF_T = OFF_SG + (L0 + 1) / 2 * 2,
                        OFF_BAR = OFF_T + 2 * twiddles();
   static constexpr size_t SMEM = (size_t)OFF_BAR * sizeof(float) + 16;
 };
@@ -863,7 +864,7 @@ __global__ void __launch_bounds__(PL::TPB, PL::MINB) k_mix_fft_ct(const __grid_c
       for (int k = lane; k < I; k += 32) Y[f * IPAD + k] = ld_as_float<T>(src + k);
     }
   }
-  for (int e = tid; e < 2 * I; e += TPB) Y[PL::OFF_POST + e] = a.tab[2 * I + e];   // post-scales
+  for (int e = tid; e < 2 * (I / 2 + 1); e += TPB) Y[PL::OFF_POST + e] = a.tab[2 * I + e];   // post-scales, k <= I/2
   for (int j = tid; j < PL::L0; j += TPB) {   // the signs of butterfly j's entries m = j + r L0
     uint32_t msk = 0;
     for (int r = 0; r < PL::radix(0); ++r) {
@@ -903,8 +904,8 @@ __global__ void __launch_bounds__(PL::TPB, PL::MINB) k_mix_fft_ct(const __grid_c
         const float2 pk = post[k];
         const float2 y0 = ct_separate(A0, B0, pk), y1 = ct_separate(A1, B1, pk);
         st4<T>(yv + out0 + 4 * g + (int64_t)k * a.out_k, y0.x, y0.y, y1.x, y1.y);
-        if (kk != k) {
-          const float2 pq = post[kk];
+        if (kk != k) {   // post(I - k) = post(k) with its components swapped (c_k = c_{I-k} for k >= 1)
+          const float2 pq = make_float2(pk.y, pk.x);
           const float2 q0 = ct_separate(B0, A0, pq), q1 = ct_separate(B1, A1, pq);
           st4<T>(yv + out0 + 4 * g + (int64_t)kk * a.out_k, q0.x, q0.y, q1.x, q1.y);
         }
@@ -915,7 +916,8 @@ __global__ void __launch_bounds__(PL::TPB, PL::MINB) k_mix_fft_ct(const __grid_c
       const int f = e % BJ, k = e / BJ;
       if (f < nf) {
         const float2* z = Z + (f >> 1) * IPAD;
-        const float2 y = ct_separate(z[k], z[k == 0 ? 0 : I - k], post[k]);
+        const float2 pk = k <= I / 2 ? post[k] : make_float2(post[I - k].y, post[I - k].x);
+        const float2 y = ct_separate(z[k], z[k == 0 ? 0 : I - k], pk);
         yv[out0 + f + (int64_t)k * a.out_k] = from_float<T>((f & 1) ? y.y : y.x);
       }
     }
@@ -923,7 +925,7 @@ __global__ void __launch_bounds__(PL::TPB, PL::MINB) k_mix_fft_ct(const __grid_c
   if (a.ysame) {   // each fiber a row of the input's layout
     T* ys = static_cast<T*>(a.ysame);
     // a warp: sequence p, 32 consecutive k <= KH and their partners I - k (conflict-free reads of
-    // Z_p[k], Z_p[I - k], post[k], post[I - k]); coalesced row segments of fibers 2p and 2p + 1
+    // Z_p[k], Z_p[I - k], post[k]); coalesced row segments of fibers 2p and 2p + 1
     constexpr int KC = (KH + 1 + 31) / 32;
     for (int w = warp; w < S * KC; w += NW) {
       const int p = w / KC, k = (w - p * KC) * 32 + lane;
@@ -931,14 +933,15 @@ __global__ void __launch_bounds__(PL::TPB, PL::MINB) k_mix_fft_ct(const __grid_c
       const int kk = k == 0 ? 0 : I - k;
       const float2* z = Z + p * IPAD;
       const float2 A = z[k], B = z[kk];
-      const float2 y = ct_separate(A, B, post[k]);
+      const float2 pk = post[k];
+      const float2 y = ct_separate(A, B, pk);
       T* r0p = ys + (row0 + (int64_t)(2 * p) * a.rs_in_v) * I;
       T* r1p = ys + (row0 + (int64_t)(2 * p + 1) * a.rs_in_v) * I;
       const bool two = 2 * p + 1 < nf;
       r0p[k] = from_float<T>(y.x);
       if (two) r1p[k] = from_float<T>(y.y);
       if (kk != k) {
-        const float2 q = ct_separate(B, A, post[kk]);
+        const float2 q = ct_separate(B, A, make_float2(pk.y, pk.x));
         r0p[kk] = from_float<T>(q.x);
         if (two) r1p[kk] = from_float<T>(q.y);
       }
