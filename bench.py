@@ -223,6 +223,44 @@ def mixing_shapes(cb, reps=4, shapes=None):
             "peak_GBs": pk["hbm_gbs"], "peak_source": pk_src, "shapes": res}
 
 
+def batch_rate(cb, B=64):
+    """The batching workload: B independent 3-way FP32 tensors (every dim uniform in [64, 512], rank
+    uniform in [4, 32], congruence uniform in [0, 0.9], 1% noise), CPRAND-MIX with S = round(10 R ln R)
+    (at least R) and the paper's stopping rules, all in one batched call.  Device time of the call by
+    CUDA events, after a warm-up call with the same workspace; decompositions and outer iterations
+    per second over the whole batch."""
+    import math
+    import torch
+    from synth import batch_problem_specs, make_problem
+    specs = batch_problem_specs(1004, B=B)
+    Xs, dims_l, Rs, Ss, opts = [], [], [], [], []
+    for b, sp in enumerate(specs):
+        prob = make_problem(sp["dims"], sp["R"], C=sp["C"], eta=0.01, seed=1000 * (b + 1) + 4,
+                            dtype=torch.float32, device="cuda")
+        Xs.append(prob.X)
+        dims_l.append(sp["dims"])
+        Rs.append(sp["R"])
+        Ss.append(max(sp["R"], int(math.floor(10.0 * sp["R"] * math.log(sp["R"]) + 0.5))))
+        opts.append(cb.cpr_default_opts(seed=2004, batch_index=b, noise_eta=0.01))
+    _, ws = cb.cpr_cprand_batched(Xs, dims_l, Rs, Ss, opts, mix=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    outs, ws = cb.cpr_cprand_batched(Xs, dims_l, Rs, Ss, opts, mix=True, ws=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    iters = sum(o["iters"] for o in outs)
+    nbytes = sum(int(np.prod(d)) * 4 for d in dims_l)
+    del Xs, ws
+    torch.cuda.empty_cache()
+    return {"what": "%d independent CPRAND-MIX decompositions in one batched call (dims U[64,512], R U[4,32], "
+                    "C U[0,0.9], 1%% noise, S = round(10 R ln R), paper stopping rules)" % B,
+            "tensor_GB": nbytes / 1e9, "ms_per_call": ms, "decompositions_per_s": B / (ms / 1e3),
+            "outer_iters_total": iters, "outer_iters_per_s": iters / (ms / 1e3),
+            "all_ok": all(o["status"] == cb.OK for o in outs)}
+
+
 def true_fit_gpu(X, dims, lam, factors):
     """Exact fit 1 - ||X - X~|| / ||X|| (Sec. 4.2) of a CP model on the stored tensor, FP64 on the
     GPU (out of every timed region)."""
@@ -474,7 +512,7 @@ def run_ours(args, rank, world, local_rank):
     # time to fit: true fit within 1e-3 of the FP64 oracle's final fit (the oracle runs on this host's
     # cores), for the library and for the plain FP64 GPU form on the same GPU
     cpu = None
-    ttf = plain_out = gather = complex_form = mix_other = None
+    ttf = plain_out = gather = complex_form = mix_other = batch = None
     if rank == 0 and world == 1 and not args.skip_extras:
         if not args.no_cpu_baseline:
             cpu = cpu_baseline(X, dims, seconds=60.0)
@@ -509,6 +547,7 @@ def run_ours(args, rank, world, local_rank):
         gather = gather_bandwidth(cb, X, dims)
         complex_form = complex_form_rate(cb, X, dims, w)
         mix_other = mixing_shapes(cb)
+        batch = batch_rate(cb)
 
     pk, pk_src = peaks()
     roof = None
@@ -563,6 +602,8 @@ def run_ours(args, rank, world, local_rank):
         out["complex_form"] = complex_form
     if mix_other is not None:
         out["mixing_other_shapes"] = mix_other
+    if batch is not None:
+        out["batch_64"] = batch
     if gather is not None:
         for g in gather.values():
             g["frac_of_hbm_peak"] = g["read_write_GBs"] / pk["hbm_gbs"]
