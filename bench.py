@@ -258,6 +258,8 @@ def batch_rate(cb, B=64):
                     "C U[0,0.9], 1%% noise, S = round(10 R ln R), paper stopping rules)" % B,
             "tensor_GB": nbytes / 1e9, "ms_per_call": ms, "decompositions_per_s": B / (ms / 1e3),
             "outer_iters_total": iters, "outer_iters_per_s": iters / (ms / 1e3),
+            "phase_ms": {"setup": outs[0]["ms_setup"], "iterate": outs[0]["ms_iterate"],
+                         "finish": outs[0]["ms_finish"]},
             "all_ok": all(o["status"] == cb.OK for o in outs)}
 
 

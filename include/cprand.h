@@ -100,8 +100,9 @@ typedef struct {
   uint32_t first_iter;   /* counter word 2 of the first outer iteration (resume) */
   double* fit_trace_dev; /* device, >= max(max_iters, fixed_iters) doubles, or NULL */
   int32_t loop_path;     /* how the outer iterations are launched: 0 automatic (a thread-block
-                            cluster per problem when every problem of the call fits one, else the
-                            captured graph); 1 clusters (every factor replicated in each CTA's
+                            cluster per problem when every problem of the call fits one with its
+                            factors replicated in each CTA, or, for a single problem, with them
+                            distributed over the CTAs; else the captured graph); 1 clusters (every factor replicated in each CTA's
                             shared memory when every problem fits that layout, else each factor's
                             rows distributed over the CTAs; CPR_EINVAL if a problem fits neither);
                             2 captured graph; 3 plain stream launches; 4 clusters with distributed
