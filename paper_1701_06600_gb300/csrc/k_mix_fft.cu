@@ -529,11 +529,11 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_cfft(const __grid_consta
 // ---- the same pass with the transform length and its plan fixed at compile time ----
 // For a length with a compiled plan every stage constant (L, Ns, the twiddle steps) is known to the
 // compiler, so shared-memory addresses take immediate offsets and the butterflies' roots of unity
-// are FMA immediates.  Each later stage reads its twiddles from its own table, laid out
-// T[(r - 1) Ns + k] = w_I^(r k I / (Ns R)), so that the lanes of a warp (consecutive k) read
-// consecutive entries.  The separation of the two real fibers of a sequence and the post-rotation
-// are done by the stores, each from the two entries k and I - k it needs (no extra pass over shared
-// memory), and the stores write 16 bytes per lane.
+// are FMA immediates.  Each later stage reads its twiddles from its own small table (rows indexed by
+// k, so that the lanes of a warp read consecutive entries), whose row products give the stage's
+// R - 1 twiddles.  The separation of the two real fibers of a sequence and the post-rotation are
+// done by the stores: a lane reads the entries k and I - k once and writes the results at both (no
+// extra pass over shared memory), 16 bytes per store.
 
 // (cos, sin)(2 pi a / b) in double, evaluated by the compiler: the angle is split, in integers, into
 // a multiple of pi / 4 and a rest in [0, pi / 4) whose sine and cosine are Taylor sums
@@ -951,9 +951,9 @@ __global__ void __launch_bounds__(PL::TPB, PL::MINB) k_mix_fft_ct(const __grid_c
 
 // the compiled plans:
 //  * I = 400 = 20 x 20 (radix 20 = 5 x 4), 16 fibers per CTA, one butterfly per thread in both
-//    stages, six CTAs per SM (64 registers, 34 KB of shared memory each);
+//    stages, six CTAs per SM (64 registers, 30 KB of shared memory each);
 //  * I = 1500 = 25 x 12 x 5, 8 fibers per CTA, 256 threads (240, 500 and 1200 butterflies: one, two
-//    and five per thread), three CTAs per SM (71 KB each);
+//    and five per thread), three CTAs per SM (65 KB each);
 //  * I = 100 = 10 x 10 (radix 10 = 5 x 2), 16 fibers per CTA, 96 threads (80 butterflies a stage).
 using CtPlan400 = CtPlan<400, 160, 16, 6, CtRadix<5, 4>, CtRadix<5, 4>>;
 using CtPlan1500 = CtPlan<1500, 256, 8, 3, CtRadix<5, 5>, CtRadix<4, 3>, CtRadix<5, 1>>;
