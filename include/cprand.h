@@ -250,7 +250,8 @@ CPR_API int cpr_fit_estimate(const cpr_tensor* X, const cpr_ktensor* K, int64_t 
 /* Mixing preprocess (Alg. 5, mixing step): out_dev = X x_1 F_1 D_1 ... x_N F_N D_N, mode 1
  * first, in X's dtype and layout.  FP32 and BF16 tensors whose every I_n (>= 5) factors into 2, 3,
  * 5 and 7: each mode product is a factored DCT-II (a mixed-radix FFT of the reordered fiber in
- * shared memory, FP32 arithmetic, twiddles rounded once from FP64; about 1e-7 relative).  Other
+ * shared memory, FP32 arithmetic, twiddles rounded from FP64 values, or products of two such values;
+ * about 1e-7 relative; stage plans compiled in for I_n = 100, 400 and 1500).  Other
  * FP32 tensors: tensor-core dense products with both operands split into two halves (FP16 halves
  * scaled by powers of two when every I_n is a multiple of 8, else TF32 halves; about 2^-21 relative
  * per product) accumulated in FP32; other BF16 tensors: FP32 SIMT products; FP64 tensors: FP64.
