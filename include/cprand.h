@@ -106,12 +106,33 @@ typedef struct {
                             shared memory when every problem fits that layout, else each factor's
                             rows distributed over the CTAs; CPR_EINVAL if a problem fits neither);
                             2 captured graph; 3 plain stream launches; 4 clusters with distributed
-                            factor rows only.  Read from the first problem's options in a batched
-                            call. */
+                            factor rows only; 5 the whole GPU (one cooperative launch of one CTA per
+                            SM, grid-wide barriers between the phases of a mode update; single
+                            FP32 / BF16 problems with every I_n <= 32 x the SM count, CPR_EINVAL
+                            otherwise).  Automatic choice for a single problem that does not fit
+                            the replicated-factor cluster: the whole GPU when it fits, else the
+                            distributed-factor cluster, else the graph.  Read from the first
+                            problem's options in a batched call. */
   int32_t layout;        /* 0: before iterating, also store every mode-n unfolding X_(n) as its own
                             column-major copy (N-1 extra copies of the tensor in the workspace) so
                             that every sampled fiber is read contiguously; 1: gather every mode
                             from the single tensor (fibers of modes 2..N are strided) */
+  const uint32_t* user_samples; /* test hook, device, or NULL: the sample multi-indices to use in
+                            place of the Philox draws, N x user_S x N uint32 (entry
+                            (n * user_S + j) * N + m is i_m of sample j of every mode-n update;
+                            the mode-n slot is ignored; every index must be below I_m).  Requires
+                            S == user_S; the iterations run on the captured graph (loop_path 0 or
+                            2; 3 and 5 are also accepted).  With every multi-index of the other
+                            modes listed once, the update is the exact ALS update of Alg. 1. */
+  int64_t user_S;
+  int64_t wait_budget;   /* polls of each wait at a grid-wide barrier of the whole-GPU loop
+                            (loop_path 5; a poll is one acquire load and a 32 ns sleep); 0: the
+                            library default (2^22 polls, on the order of a second).  A wait that
+                            runs out makes every CTA leave at its next barrier and the call return
+                            CPR_ETIMEOUT (that kernel issues no asynchronous copies).  The waits on
+                            TMA copies (cluster loops, mixing kernels) keep the library's fixed
+                            limits; after one runs out the kernel waits again, bounded, for its own
+                            copies before it returns, and the call reports CPR_ETIMEOUT. */
 } cpr_opts;
 
 typedef struct {
@@ -312,8 +333,10 @@ CPR_API int cpr_profile_end(double* ms, int64_t* launches);
  * before anything is enqueued.  norm_x < 0 computes ||X|| in the same array.  Every call on a
  * device shares the array (each call clears what must start at zero): calls whose work overlaps on
  * the GPU race and must be ordered by the caller.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current; make that first call
- * outside any stream capture.  Writes the estimate to *fit_host (synchronizes the stream). */
+ * array's device address (cudaGetSymbolAddress) with that device current.  Every call synchronizes
+ * the stream and copies the estimate into *fit_host, so it cannot be recorded into a graph: on a
+ * stream that is being captured it returns CPR_EINVAL and enqueues nothing.  Its launches are not
+ * counted or timed by the kernel profiler (cpr_profile_begin / cpr_profile_end). */
 #define CPR_NOALLOC_MAX_FIT_SAMPLES (1 << 20)
 CPR_API int cpr_fit_estimate_noalloc(const cpr_tensor* X, const cpr_ktensor* K, int64_t P_hat, uint64_t seed,
                                      uint32_t b, double norm_x, double* fit_host, void* stream);

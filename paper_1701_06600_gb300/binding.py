@@ -36,9 +36,10 @@ class CprOpts(ctypes.Structure):
                 ("noise_eta", ctypes.c_double), ("stall_iters", ctypes.c_int32),
                 ("init_from_out", ctypes.c_int32), ("fit_samples", ctypes.c_int64), ("seed", ctypes.c_uint64),
                 ("batch_index", ctypes.c_uint32), ("first_iter", ctypes.c_uint32),
-                ("fit_trace_dev", ctypes.c_void_p), ("loop_path", ctypes.c_int32), ("layout", ctypes.c_int32)]
+                ("fit_trace_dev", ctypes.c_void_p), ("loop_path", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("user_samples", ctypes.c_void_p), ("user_S", ctypes.c_int64), ("wait_budget", ctypes.c_int64)]
 
-LOOP_AUTO, LOOP_CLUSTER, LOOP_GRAPH, LOOP_STREAM, LOOP_CLUSTER_DIST = range(5)
+LOOP_AUTO, LOOP_CLUSTER, LOOP_GRAPH, LOOP_STREAM, LOOP_CLUSTER_DIST, LOOP_GRID = range(6)
 MIX_AUTO, MIX_FFT, MIX_DENSE = range(3)
 
 

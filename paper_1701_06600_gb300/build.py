@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcprand.so")
-SOURCES = ["api.cu", "k_update.cu", "k_fit.cu", "k_mix.cu", "k_mix_tc.cu", "k_mix_fft.cu", "k_mixc.cu", "k_cluster.cu", "k_loop.cu", "k_als.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "k_update.cu", "k_fit.cu", "k_mix.cu", "k_mix_tc.cu", "k_mix_fft.cu", "k_mixc.cu", "k_cluster.cu", "k_loop.cu", "k_als.cu", "noalloc.cu", "k_grid.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]

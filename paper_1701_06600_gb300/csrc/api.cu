@@ -205,6 +205,8 @@ struct Plan {
   void* d_tmp = nullptr;     // shared ping-pong buffer of the mixing passes
   void* d_tmp2 = nullptr;    // second pass buffer (tensor-core mixing reads unfoldings)
   int normblk = 0;
+  GridScratch gscr{};        // whole-GPU loop (single FP32 / BF16 problems)
+  bool has_grid = false;
   size_t bytes = 0;
 };
 
@@ -262,6 +264,21 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws, int als = 0, int
   for (int b = 0; b < B; ++b) maxP = std::max(maxP, prod_dims(specs[b].X));
   pl.normblk = sumsq_blocks(maxP);
   pl.d_normpart = cv.take<double>(pl.normblk);
+  if (B == 1 && specs[0].S > 0 && specs[0].X->dtype != CPR_F64 && !als) {
+    const int R = specs[0].R;
+    const int NE = R * (R + 1) / 2;
+    int64_t imax = 1;
+    for (int n = 0; n < specs[0].X->order; ++n) imax = std::max<int64_t>(imax, specs[0].X->dims[n]);
+    GridScratch& g = pl.gscr;
+    g.Gpart = cv.take<double>((size_t)kGridMaxCTAs * NE);
+    g.Gfull = cv.take<double>((size_t)NE);
+    g.Mpart = cv.take<float>((size_t)std::max<int64_t>((int64_t)kGridMaxCTAs * kGridTileRows, imax) * R);
+    g.Npart = cv.take<double>((size_t)kGridMaxCTAs * R);
+    g.fitpart = cv.take<double>((size_t)kGridMaxCTAs);
+    g.bar = cv.take<unsigned>(4);
+    g.err = reinterpret_cast<int*>(g.bar + 2);
+    pl.has_grid = true;
+  }
   if (mix) {
     pl.d_tmp = cv.take<unsigned char>((size_t)maxP * elem_size(pl.dtype));
     if (pl.dtype == CPR_F32) pl.d_tmp2 = cv.take<unsigned char>((size_t)maxP * elem_size(pl.dtype));
@@ -345,6 +362,7 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws, int als = 0, int
       p.b = o->batch_index;
       p.t0 = o->first_iter;
       p.trace = o->fit_trace_dev;
+      p.user_idx = o->user_samples;
     }
     p.state = pl.d_states + b;   // pointer arithmetic on a null base only measures
     if (mix) {
@@ -589,6 +607,8 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
     if (op[b].fit_samples < 1 || op[b].fit_samples > INT32_MAX) return CPR_EINVAL;
     if (op[b].max_iters < 1 && op[b].fixed_iters < 1) return CPR_EINVAL;
     if (op[b].init_from_out != op[0].init_from_out) return CPR_EINVAL;
+    if (op[b].user_samples && op[b].user_S != Ss[b]) return CPR_EINVAL;
+    if (op[b].wait_budget < 0) return CPR_EINVAL;
     specs[b] = ProbSpec{&Xs[b], Rs[b], Ss[b], op[b].fit_samples, &op[b], nullptr, nullptr};
     maxN = std::max(maxN, (int)Xs[b].order);
   }
@@ -651,14 +671,43 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
   const unsigned loop_classes = (1u << CPR_KERNEL_SAMPLE_SKR) | (1u << CPR_KERNEL_CONTRACT) | (1u << CPR_KERNEL_CHOL) |
                                 (1u << CPR_KERNEL_SOLVE) | (1u << CPR_KERNEL_NORMALIZE) | (1u << CPR_KERNEL_FIT);
   const int path = op[0].loop_path;
-  if (path < 0 || path > 4) return CPR_EINVAL;
+  if (path < 0 || path > 5) return CPR_EINVAL;
+  bool user_samples = false;
+  for (int b = 0; b < B; ++b) user_samples = user_samples || op[b].user_samples != nullptr;
+  // caller-given samples: the graph kernels, the plain stream launches and the whole-GPU loop read them
+  if (user_samples && (path == 1 || path == 4)) return CPR_EINVAL;
   const bool stream_only = path == 3 || (prof().on && (prof().mask & loop_classes));
+  // the whole GPU for one large FP32 / BF16 problem (explicitly, or automatically when the
+  // replicated-factor cluster cannot hold it)
+  int grid_G = 0;
+  bool use_grid = false;
+  if (!stream_only && pl.has_grid && (path == 5 || path == 0)) {
+    int maxR = pl.probs[0].R;
+    grid_G = grid_capacity(pl.dtype, maxR);
+    const bool fits = grid_G > 0 && grid_fits(pl.probs[0], grid_G);
+    if (path == 5) {
+      if (!fits) return CPR_EINVAL;
+      use_grid = true;
+    } else if (fits && !user_samples) {
+      const int rs = loop_rep_smem_bytes(pl.probs.data(), B);
+      use_grid = !(rs > 0 && loop_rep_capacity(pl.dtype, rs, maxR) > 0);
+    }
+  } else if (path == 5) {
+    return CPR_EINVAL;
+  }
   // small problems: the whole loop in thread-block clusters (one cluster per problem at a time);
   // first choice: every factor replicated in each CTA of the cluster; else factor rows
   // distributed over the CTAs
   int C = 16, csmem = -1, ncl = 0;
   bool rep = false;
-  if (!stream_only && path != 2) {
+  if (use_grid) {
+    GridScratch gsc = pl.gscr;
+    gsc.wait_limit = op[0].wait_budget > 0 ? (uint32_t)std::min<int64_t>(op[0].wait_budget, UINT32_MAX)
+                                           : kDefaultWaitPolls;
+    CPR_CUDA(cudaMemsetAsync(gsc.bar, 0, 4 * sizeof(unsigned), s));
+    CPR_LAUNCH(CPR_KERNEL_LOOP, launch_grid_run(pl.d_probs, B, gsc, pl.dtype, pl.probs[0].R, grid_G, s));
+    ncl = 1;   // the loop has run
+  } else if (!stream_only && path != 2 && !user_samples) {
     int maxR = 0;
     for (int b = 0; b < B; ++b) maxR = std::max(maxR, pl.probs[b].R);
     if (path != 4) {
@@ -749,10 +798,11 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
   int loop_iters = 0;
   CPR_CUDA(cudaMemcpyAsync(&loop_iters, pl.d_counter, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (int st = ph.mark(3, s)) return st;
-  int dev_err = 0;
+  int dev_err = 0, grid_err = 0;
   CPR_CUDA(cudaMemcpyAsync(&dev_err, pl.d_counter + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (use_grid) CPR_CUDA(cudaMemcpyAsync(&grid_err, pl.gscr.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CPR_CUDA(cudaStreamSynchronize(s));
-  if (dev_err) return CPR_ETIMEOUT;
+  if (dev_err || grid_err) return CPR_ETIMEOUT;
   launches += (int64_t)loop_iters * body_kernels;
   if (results) {
     for (int b = 0; b < B; ++b) {

@@ -95,6 +95,26 @@ struct Prob {
   int32_t als_nsplit[kMaxOrder];  // MTTKRP: splits per mode
   int32_t als_rg;          // MTTKRP: rank groups of 8 columns per thread tile (1, 2, 4 or 8)
   int32_t pad2;
+
+  // caller-given sample multi-indices (test hook): N x S x N uint32, entry ((n S + j) N + m) is
+  // i_m of sample j of every mode-n update (the mode-n slot is ignored); null: Philox draws
+  const uint32_t* user_idx;
+};
+
+// Global scratch and barrier words of the whole-GPU loop (k_grid.cu), carved from the workspace.
+constexpr int kGridMaxCTAs = 256;  // CTAs the scratch is sized for (one per SM)
+constexpr int kGridMaxRows = 32;   // factor rows a CTA solves per mode update (I_n <= 32 G)
+constexpr int kGridTileRows = 96;  // fiber rows of a contraction tile
+constexpr uint32_t kDefaultWaitPolls = 1u << 22;   // polls of a bounded wait unless opts say otherwise
+struct GridScratch {
+  double* Gpart;     // G x NE partial Grams (packed upper triangle)
+  double* Gfull;     // NE
+  float* Mpart;      // nsplit x R x I_n partial M (column-major per split)
+  double* Npart;     // G x R column sums of squares
+  double* fitpart;   // G partial fit sums
+  unsigned* bar;     // [0] arrivals, [1] generation (zeroed before each launch)
+  int* err;          // set when a barrier wait ran out
+  uint32_t wait_limit;  // polls per barrier wait
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -255,6 +275,12 @@ int cluster_smem_bytes(const Prob* probs_host, int B, int C);
 int cluster_capacity(int dtype, int C, int smem, int maxR);
 cudaError_t launch_cluster_run(const Prob* probs, int B, int* queue, int dtype, int C, int smem, int nclusters,
                                int maxR, cudaStream_t s);
+// the whole iteration loop over the whole GPU (cooperative launch, grid barriers), one problem at
+// a time: large FP32 / BF16 problems
+int grid_capacity(int dtype, int maxR);
+bool grid_fits(const Prob& p, int G);
+cudaError_t launch_grid_run(const Prob* probs, int B, const GridScratch& gs, int dtype, int maxR, int G,
+                            cudaStream_t s);
 // the whole iteration loop in 16-CTA clusters with every factor replicated in each CTA (the first
 // choice when every problem of the call fits)
 int loop_rep_smem_bytes(const Prob* probs_host, int B);
@@ -265,6 +291,9 @@ cudaError_t launch_sumsq(const void* X, int dtype, int64_t P, double* part, int 
                          unsigned* amax = nullptr);
 cudaError_t launch_sumsq_finish(const double* part, int nblk, double* out_norm, State* st,
                                 int nstates, cudaStream_t s);
+// ||X|| reduction: at most kSumsqMaxBlocks partial sums.  A fixed cap (not the device's SM count)
+// keeps the summation order, and so the result, the same on every device.
+constexpr int kSumsqMaxBlocks = 1216;
 int sumsq_blocks(int64_t P);
 
 // step hooks

@@ -148,7 +148,7 @@ cudaError_t launch_loop_cond(const Prob* probs, int B, int* loop_iter, int cap, 
 int sumsq_blocks(int64_t P) {
   int64_t b = (P + 256 * 64 - 1) / (256 * 64);
   if (b < 1) b = 1;
-  if (b > 152 * 8) b = 152 * 8;
+  if (b > kSumsqMaxBlocks) b = kSumsqMaxBlocks;
   return (int)b;
 }
 
@@ -244,7 +244,13 @@ __global__ void __launch_bounds__(256) k_sumsq_finish(const double* part, int nb
   if (threadIdx.x == 0) {
     const double nrm = sqrt(t);
     if (out_norm) *out_norm = nrm;
-    for (int q = 0; q < nstates; ++q) st[q].norm_x = nrm;
+    for (int q = 0; q < nstates; ++q) {
+      st[q].norm_x = nrm;
+      if (!isfinite(nrm)) {   // a NaN or Inf in X: no fit can be formed, the run does not start
+        st[q].status = CPR_ENONFINITE;
+        st[q].done = 1;
+      }
+    }
   }
 }
 

@@ -1,0 +1,1049 @@
+// The whole outer-iteration loop of CPRAND (Alg. 3 with Alg. 2, the sampled fit of Sec. 3.4 and
+// the stopping rules of Sec. 4.2) for one large problem at a time, spread over the whole GPU: a
+// cooperative launch of one 512-thread CTA per SM, phases separated by grid-wide barriers.
+//
+// This is the path for problems whose factors and sampled fibers are far too large for one
+// thread-block cluster (1500^3 with R = 50 and S = 2000: 12 MB of fibers and 2.5 million FP64 Gram
+// products per mode update).  On this GPU FP64 issues at about 1.7 operations per clock per SM
+// against 128 for FP32, so every FP64 step is spread evenly over all SMs and kept to a plain
+// product form with every lane busy.  Per mode update n of outer iteration t:
+//
+//   P1  (concurrently, in disjoint warps of every CTA)
+//       warps 0-3   partial FP64 Gram Z_S^T Z_S (packed upper triangle) of the CTA's ceil(S/G)
+//                   samples: the Z_S rows (Alg. 2) as FP64 products of the FP32 factor rows times
+//                   the lazy column scales.
+//       warps 4-15  contraction units (96 fiber rows x one split of the samples): the split's
+//                   Z_S rows in FP32, the sampled fibers (Sec. 3.2 index map) streamed through
+//                   shared memory in chunks of 32 samples (the next chunk's loads in flight while
+//                   the current one is multiplied), M_split = X_S Z_S with FP32 accumulation,
+//                   stored column-major to global scratch.  The next mode update's fiber
+//                   segments are prefetched into L2 (the draw depends on the Philox counter only).
+//   --- grid barrier
+//   P2  each CTA sums a slice of the packed Gram over the G partials (fixed order) and the split
+//       partials of its own ceil(I_n/G) factor rows (FP64).
+//   --- grid barrier
+//   P3  every CTA reads G and inverts its Jacobi-scaled copy in FP32 (the sweep operator, one
+//       block barrier per pivot; the same arithmetic in every CTA, so the same decisions), then
+//       solves its rows: A0 = M G^-1 with the FP32 inverse, then refinement steps
+//       A <- A + (M - A G) G^-1 with the residual M - A G in FP64 (a dense product, every lane
+//       busy) until the correction is below 1e-5 of the row block, which leaves an error near its
+//       square (at most three steps).  A
+//       non-positive sweep pivot falls back to an FP64 Cholesky inverse; a non-positive Cholesky
+//       pivot is a singular Gram (CPR_ESINGULAR).  The rows go to the FP64 factor and its FP32
+//       copy (unnormalized), their column sums of squares to global scratch.
+//   --- grid barrier
+//   P4  every CTA sums the column partials (fixed order): lambda_r and the lazy scale 1/lambda_r.
+// After the N modes: the CTA's share of the P_hat fixed fit entries (one warp per entry, FP32
+// model, FP64 squares), a grid barrier, and every CTA sums the G partials in the same order and
+// applies the stopping rules to its own copy of the loop state.
+//
+// Cross-CTA data is written before a barrier and read after it with L1-bypassing loads.  Every
+// barrier wait is bounded (opts->wait_budget polls, default about a second): a CTA whose wait runs
+// out sets the error flag and returns; CTAs that see the flag at a barrier return too, so the
+// kernel always ends, and the call reports CPR_ETIMEOUT.  This kernel issues no asynchronous
+// copies, so a CTA that returns early leaves nothing in flight.
+#include <math.h>
+
+#include "internal.cuh"
+#include "small_spd.cuh"
+
+namespace cpr {
+
+namespace {
+
+constexpr int kGT = 512;                 // threads per CTA
+constexpr int kGW = kGT / 32;            // warps per CTA
+constexpr int kGramT = 128;              // threads of the Gram partial (warps 0-3)
+constexpr int kCT = kGT - kGramT;        // contraction threads (warps 4-15)
+constexpr int kTI = 96;                  // fiber rows per contraction tile
+constexpr int kCG = kCT / kTI;           // column groups per tile row (4)
+constexpr int kSC = 256;                 // samples per super-chunk (Z_S rows staged in shared memory)
+constexpr int kXC = 32;                  // samples per fiber chunk
+constexpr int kXPT = kXC * kTI / kCT;    // fiber elements per contraction thread and chunk (8)
+constexpr int kGC = 32;                  // Gram samples per chunk
+constexpr int kNEMax = kMaxRank * (kMaxRank + 1) / 2;
+static_assert(kTI % 32 == 0 && kCT % kTI == 0 && (kXC * kTI) % kCT == 0, "tile shape");
+static_assert(kTI == kGridTileRows, "the workspace sizes Mpart for this tile height");
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// AND of v over the n threads of block barrier id (which all call it); also a barrier for them.
+__device__ __forceinline__ bool named_and(int id, int n, bool v) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.and.pred q, %2, %3, p;\n selp.s32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((int)v), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
+template <typename T> __device__ __forceinline__ float gf(T v);
+template <> __device__ __forceinline__ float gf<float>(float v) { return v; }
+template <> __device__ __forceinline__ float gf<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Shared-memory layout (byte offsets), computed identically on the host and the device.  The
+// solver region (G and the FP32 inverse) is written by warps 0-3 while warps 4-15 still use the P1
+// region, so the two do not overlap; the row-solve region (after the contraction) overlays P1.
+struct GridSmem {
+  int G, sw;               // solver: R x R FP64 Gram; two R x R FP32 sweep buffers (the FP64
+                           // fallback inverse reuses them as one R x R FP64 matrix)
+  int gids, Zd;            // P1, Gram warps
+  int cids, coffs, Zf, xs; // P1, contraction warps
+  int mrow, arow, m32;     // row solve (overlays P1)
+  int fL, fT, fd;          // FP64 fallback factor and triangular inverse (overlay P1, not m32's use)
+  int bytes;
+  int ZP;                  // Zf row pitch (MAXR)
+};
+
+__host__ __device__ inline int ga16(int x) { return (x + 15) / 16 * 16; }
+
+__host__ __device__ inline GridSmem grid_layout(int R, int MAXR, int tbytes) {
+  GridSmem L;
+  L.ZP = MAXR;
+  int o = 0;
+  L.G = o;     o = ga16(o + R * R * 8);
+  L.sw = o;    o = ga16(o + 2 * R * R * 4);
+  const int base = o;
+  L.gids = o;  o = ga16(o + kGC * kMaxOrder * 4);
+  L.Zd = o;    o = ga16(o + kGC * R * 8);
+  L.cids = o;  o = ga16(o + kSC * kMaxOrder * 4);
+  L.coffs = o; o = ga16(o + kSC * 8);
+  L.Zf = o;    o = ga16(o + kSC * MAXR * 4);
+  L.xs = o;    o = ga16(o + 2 * kXC * kTI * tbytes);
+  const int p1 = o;
+  o = base;
+  L.mrow = o;  o = ga16(o + kGridMaxRows * R * 8);
+  L.arow = o;  o = ga16(o + kGridMaxRows * R * 8);
+  const int u = o;
+  L.m32 = o;   o = ga16(o + kGridMaxRows * R * 4);
+  const int a = o;
+  o = u;
+  L.fL = o;    o = ga16(o + R * R * 8);
+  L.fT = o;    o = ga16(o + R * R * 8);
+  L.fd = o;    o = ga16(o + R * 8);
+  int p3 = o > a ? o : a;
+  L.bytes = p1 > p3 ? p1 : p3;
+  return L;
+}
+
+struct GridCtx {
+  unsigned gen;       // barrier generation this CTA has passed
+  int G, c;           // CTAs, this CTA
+};
+
+// Grid-wide barrier with a bounded wait.  Returns false (in every thread of the CTA) when the wait
+// ran out or another CTA reported an error; the caller then returns.
+// bar_id / nthr: the block barrier of the calling threads (0 / kGT: the whole CTA; thread 0 must be one
+// of them, and every CTA's thread 0 calls the same sequence of grid barriers).
+__device__ __forceinline__ bool grid_sync(const GridScratch& gs, GridCtx& x, int* s_flag, int bar_id = 0,
+                                          int nthr = kGT) {
+  named_sync(bar_id, nthr);
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned my = x.gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(gs.bar, 1u) + 1u;
+    if (arrived == (unsigned)x.G) {
+      *((volatile unsigned*)gs.bar) = 0u;
+      __threadfence();
+      st_release_u32(gs.bar + 1, my + 1u);
+    } else {
+      uint32_t it = 0;
+      while (ld_acquire_u32(gs.bar + 1) == my) {
+        if (++it > gs.wait_limit) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (ok && ld_relaxed_i32(gs.err) != 0) ok = 0;
+    if (!ok) atomicExch(gs.err, 1);
+    x.gen = my + 1u;
+    *s_flag = ok;
+  }
+  named_sync(bar_id, nthr);
+  return *s_flag != 0;
+}
+
+// out[j] = sum over i < rows of src[i * stride + j] for j < cols (cols <= 64), from global scratch
+// written by other CTAs: the rows are split into at most 32 chunks, each thread sums one (chunk,
+// column) pair with its loads in flight together, and the chunk partials are then added in chunk
+// order.  The order is fixed, so every CTA that sums the same data gets the same result.  part:
+// nthr doubles of shared memory.  Called by threads 0 .. nthr-1 (block barrier bar_id); ends with
+// that barrier.
+__device__ void sum_rows(const double* src, int rows, int cols, int64_t stride, double* out, double* part,
+                         int bar_id = 0, int nthr = kGT) {
+  const int tid = threadIdx.x;
+  int cp = 1;
+  while (cp < cols) cp <<= 1;
+  const int nch = min(nthr / cp, 32);
+  const int j = tid % cp, q = tid / cp;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  if (j < cols && q < nch) {
+    const int per = (rows + nch - 1) / nch;
+    const int r0 = q * per, r1 = min(rows, r0 + per);
+    int i = r0;
+    for (; i + 3 < r1; i += 4) {
+      a0 += __ldcg(src + (int64_t)i * stride + j);
+      a1 += __ldcg(src + (int64_t)(i + 1) * stride + j);
+      a2 += __ldcg(src + (int64_t)(i + 2) * stride + j);
+      a3 += __ldcg(src + (int64_t)(i + 3) * stride + j);
+    }
+    for (; i < r1; ++i) a0 += __ldcg(src + (int64_t)i * stride + j);
+  }
+  if (q < nch) part[q * cp + j] = (a0 + a1) + (a2 + a3);
+  named_sync(bar_id, nthr);
+  if (tid < cols) {
+    double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+    int qq = 0;
+    for (; qq + 3 < nch; qq += 4) {
+      b0 += part[qq * cp + tid];
+      b1 += part[(qq + 1) * cp + tid];
+      b2 += part[(qq + 2) * cp + tid];
+      b3 += part[(qq + 3) * cp + tid];
+    }
+    for (; qq < nch; ++qq) b0 += part[qq * cp + tid];
+    out[tid] = (b0 + b1) + (b2 + b3);
+  }
+  named_sync(bar_id, nthr);
+}
+
+// Sample j of mode update (n, t): indices by mode (mode-n slot 0) and the fiber's storage offset
+// in the copy mode n reads (Philox stream 0, counter (j, n, t, b); the k-th mode other than n takes
+// word k%4 of block k/4; i_m = floor(w I_m / 2^32)).  With a caller sample table (test hook), the
+// multi-index is read from it instead.
+__device__ __forceinline__ int64_t grid_draw(const Prob& p, int n, uint32_t t, uint32_t j, uint32_t* ids) {
+  if (p.user_idx) {
+    const uint32_t* u = p.user_idx + ((int64_t)n * p.S + j) * p.N;
+    for (int m = 0; m < p.N; ++m) ids[m] = m == n ? 0u : u[m];
+  } else {
+    const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
+    const uint4 w0 = philox10(make_uint4(j, counter_word1(kStreamSamples, 0, n), t, p.b), k0, k1);
+    uint4 w1 = make_uint4(0u, 0u, 0u, 0u);
+    if (p.N - 1 > 4) w1 = philox10(make_uint4(j, counter_word1(kStreamSamples, 1, n), t, p.b), k0, k1);
+    int k = 0;
+    for (int m = 0; m < p.N; ++m) {
+      uint32_t im = 0;
+      if (m != n) {
+        const uint32_t w = k < 4 ? word_of(w0, k) : word_of(w1, k - 4);
+        im = scale_index(w, (uint32_t)p.dims[m]);
+        ++k;
+      }
+      ids[m] = im;
+    }
+  }
+  int64_t stride;
+  return fiber_offset(p, n, ids, &stride);
+}
+
+// Rows jj < cnt of the sampled Khatri-Rao product (Alg. 2) for the modes other than n:
+// out[jj * pitch + r] = pre[r] * prod_{m != n} A32[m](ids[jj][m], r) for r < R (0 for R <= r < pitch),
+// by nthr threads (a multiple of 64; t = this thread's index among them): thread t takes column
+// t % 64 of every (nthr / 64)-th sample, and the factor-row loads of 8 samples of one mode are
+// issued together (L2-resident rows: the latency, not the bandwidth, is what these loads cost).
+template <typename OUT>
+__device__ __forceinline__ void build_rows(const Prob& p, int n, const uint32_t* ids, int cnt, const OUT* pre,
+                                           OUT* out, int pitch, int t, int nthr) {
+  const int R = p.R, N = p.N;
+  const int r = t & 63, lanes = nthr >> 6;
+  if (r >= pitch) return;
+  for (int b = t >> 6; b < cnt; b += 8 * lanes) {
+    OUT z[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) z[k] = r < R ? pre[r] : OUT(0);
+    for (int m = 0; m < N; ++m) {
+      if (m == n) continue;
+      const float* Am = p.A32[m];
+      float v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int jj = b + k * lanes;
+        v[k] = (jj < cnt && r < R) ? __ldcg(Am + (int64_t)ids[jj * kMaxOrder + m] * R + r) : 1.f;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) z[k] *= (OUT)v[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int jj = b + k * lanes;
+      if (jj < cnt) out[jj * pitch + r] = z[k];
+    }
+  }
+}
+
+// Work split of mode n over G CTAs.
+struct ModeSplit {
+  int I, ntile, nsplit, spl, units, rpc;
+};
+
+__device__ __forceinline__ ModeSplit mode_split(const Prob& p, int n, int G) {
+  ModeSplit s;
+  s.I = (int)p.dims[n];
+  s.ntile = (s.I + kTI - 1) / kTI;
+  int ns = G / s.ntile;
+  if (ns < 1) ns = 1;
+  const int most = (p.S + 15) / 16;   // at least 16 samples per split
+  if (ns > most) ns = most;
+  s.spl = (p.S + ns - 1) / ns;
+  s.nsplit = (p.S + s.spl - 1) / s.spl;
+  s.units = s.ntile * s.nsplit;
+  s.rpc = (s.I + G - 1) / G;
+  return s;
+}
+
+// ---- P1, Gram warps: partial Z_S^T Z_S over this CTA's samples (packed upper triangle), FP64.
+template <int MAXR>
+__device__ void gram_partial(const Prob& p, const GridSmem& L, unsigned char* sm, const GridScratch& gs,
+                             const GridCtx& x, int n, uint32_t t, const double* scomb, const unsigned char* ne_r,
+                             const unsigned char* ne_c) {
+  constexpr int EPT = (MAXR * (MAXR + 1) / 2 + kGramT - 1) / kGramT;   // packed entries per thread (at most)
+  const int tid = threadIdx.x, R = p.R, N = p.N, S = p.S;
+  const int NE = R * (R + 1) / 2;
+  const int gpc = (S + x.G - 1) / x.G;
+  const int j0 = x.c * gpc;
+  const int jn = min(S, j0 + gpc);
+  uint32_t* ids = reinterpret_cast<uint32_t*>(sm + L.gids);
+  double* Zd = reinterpret_cast<double*>(sm + L.Zd);
+  double acc[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) acc[q] = 0.0;
+  for (int c0 = j0; c0 < jn; c0 += kGC) {
+    const int cnt = min(kGC, jn - c0);
+    if (tid < cnt) grid_draw(p, n, t, (uint32_t)(c0 + tid), ids + tid * kMaxOrder);
+    named_sync(1, kGramT);
+    build_rows<double>(p, n, ids, cnt, scomb, Zd, R, tid, kGramT);
+    named_sync(1, kGramT);
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = tid + q * kGramT;
+      if (q * kGramT < NE && e < NE) {
+        const int r = ne_r[e], cc = ne_c[e];
+        double a0 = acc[q], a1 = 0.0;
+        int jj = 0;
+        for (; jj + 1 < cnt; jj += 2) {
+          a0 = fma(Zd[jj * R + r], Zd[jj * R + cc], a0);
+          a1 = fma(Zd[(jj + 1) * R + r], Zd[(jj + 1) * R + cc], a1);
+        }
+        if (jj < cnt) a0 = fma(Zd[jj * R + r], Zd[jj * R + cc], a0);
+        acc[q] = a0 + a1;
+      }
+    }
+    named_sync(1, kGramT);
+  }
+  double* dst = gs.Gpart + (int64_t)x.c * NE;
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * kGramT;
+    if (q * kGramT < NE && e < NE) dst[e] = acc[q];
+  }
+}
+
+// ---- P1, contraction warps: M_split(tile rows, :) = X_S Z_S over the unit's samples, FP32.
+template <typename T, int MAXR>
+__device__ void contract_units(const Prob& p, const GridSmem& L, unsigned char* sm, const GridScratch& gs,
+                               const GridCtx& x, int n, uint32_t t, const ModeSplit& ms, const float* scf) {
+  constexpr int CW = MAXR / kCG;           // columns per thread
+  static_assert(CW % 4 == 0, "float4 Z loads");
+  const int ct = threadIdx.x - kGramT;     // 0 .. kCT-1
+  const int ii = ct % kTI, g = ct / kTI;
+  const int R = p.R, N = p.N, ZP = L.ZP;
+  uint32_t* ids = reinterpret_cast<uint32_t*>(sm + L.cids);
+  int64_t* offs = reinterpret_cast<int64_t*>(sm + L.coffs);
+  float* Zf = reinterpret_cast<float*>(sm + L.Zf);
+  T* xs = reinterpret_cast<T*>(sm + L.xs);
+  const T* __restrict__ X = reinterpret_cast<const T*>(p.Xrep[n]);
+  const int64_t stride = p.use_rep ? 1 : p.st[n];
+  for (int u = x.c; u < ms.units; u += x.G) {
+    const int tile = u % ms.ntile, split = u / ms.ntile;
+    const int i0 = tile * kTI;
+    const int js = split * ms.spl;
+    const int cnt = min(ms.spl, p.S - js);
+    float acc[CW];
+#pragma unroll
+    for (int k = 0; k < CW; ++k) acc[k] = 0.f;
+    for (int s0 = 0; s0 < cnt; s0 += kSC) {
+      const int scn = min(kSC, cnt - s0);
+      named_sync(2, kCT);   // the previous super-chunk's Z rows and fibers are no longer read
+      for (int jj = ct; jj < scn; jj += kCT)
+        offs[jj] = grid_draw(p, n, t, (uint32_t)(js + s0 + jj), ids + jj * kMaxOrder);
+      named_sync(2, kCT);
+      // Z_S rows of the super-chunk in FP32 (zero-padded to the pitch)
+      build_rows<float>(p, n, ids, scn, scf, Zf, ZP, ct, kCT);
+      // fibers: chunks of kXC samples x kTI rows, the next chunk's loads in flight
+      const int nch = (scn + kXC - 1) / kXC;
+      T reg[kXPT];
+      auto load_chunk = [&](int k) {
+#pragma unroll
+        for (int q = 0; q < kXPT; ++q) {
+          const int e = ct + q * kCT;
+          const int jj = k * kXC + e / kTI, r = e % kTI;
+          T v = T(0.f);
+          if (jj < scn && i0 + r < ms.I) v = X[offs[jj] + (int64_t)(i0 + r) * stride];
+          reg[q] = v;
+        }
+      };
+      auto store_chunk = [&](int k) {
+        T* dst = xs + (k & 1) * (kXC * kTI);
+#pragma unroll
+        for (int q = 0; q < kXPT; ++q) dst[ct + q * kCT] = reg[q];
+      };
+      load_chunk(0);
+      store_chunk(0);
+      named_sync(2, kCT);
+      for (int k = 0; k < nch; ++k) {
+        if (k + 1 < nch) load_chunk(k + 1);
+        const T* xb = xs + (k & 1) * (kXC * kTI);
+        const int jn = min(kXC, scn - k * kXC);
+        const float* zb = Zf + (k * kXC) * ZP + g * CW;
+#pragma unroll 2
+        for (int jj = 0; jj < jn; ++jj) {
+          const float xv = gf<T>(xb[jj * kTI + ii]);
+          const float4* z4 = reinterpret_cast<const float4*>(zb + jj * ZP);
+#pragma unroll
+          for (int v = 0; v < CW / 4; ++v) {
+            const float4 zq = z4[v];
+            acc[4 * v + 0] = fmaf(xv, zq.x, acc[4 * v + 0]);
+            acc[4 * v + 1] = fmaf(xv, zq.y, acc[4 * v + 1]);
+            acc[4 * v + 2] = fmaf(xv, zq.z, acc[4 * v + 2]);
+            acc[4 * v + 3] = fmaf(xv, zq.w, acc[4 * v + 3]);
+          }
+        }
+        if (k + 1 < nch) store_chunk(k + 1);
+        named_sync(2, kCT);
+      }
+    }
+    // M_split stored column-major (lanes = consecutive rows)
+    const int i = i0 + ii;
+    if (i < ms.I) {
+      float* dst = gs.Mpart + (int64_t)split * R * ms.I + i;
+#pragma unroll
+      for (int k = 0; k < CW; ++k) {
+        const int r = g * CW + k;
+        if (r < R) dst[(int64_t)r * ms.I] = acc[k];
+      }
+    }
+  }
+}
+
+// Prefetch into L2 the fiber segments the contraction units of the next mode update will read.
+template <typename T>
+__device__ void prefetch_next(const Prob& p, const GridCtx& x, int n, uint32_t t, const ModeSplit& ms) {
+  const int ct = threadIdx.x - kGramT;
+  const T* X = reinterpret_cast<const T*>(p.Xrep[n]);
+  if (!(p.use_rep || n == 0)) return;   // strided fibers: nothing contiguous to prefetch
+  for (int u = x.c; u < ms.units; u += x.G) {
+    const int tile = u % ms.ntile, split = u / ms.ntile;
+    const int i0 = tile * kTI;
+    const int rows = min(kTI, ms.I - i0);
+    const int js = split * ms.spl;
+    const int cnt = min(ms.spl, p.S - js);
+    const int lines = rows * (int)sizeof(T) / 128 + 2;   // 128-byte lines a row segment can touch
+    for (int e = ct; e < cnt * lines; e += kCT) {
+      const int jj = e / lines, l = e - jj * lines;
+      uint32_t ids[kMaxOrder];
+      const int64_t off = grid_draw(p, n, t, (uint32_t)(js + jj), ids);
+      const uintptr_t a0 = reinterpret_cast<uintptr_t>(X + off + i0) & ~(uintptr_t)127;
+      const uintptr_t end = reinterpret_cast<uintptr_t>(X + off + i0 + rows);
+      const uintptr_t a = a0 + (uintptr_t)l * 128;
+      if (a < end) prefetch_l2(reinterpret_cast<const void*>(a));
+    }
+  }
+}
+
+// X0 ~ Gs^-1 in FP32 for the Jacobi-scaled Gram Gs (unit diagonal) by the sweep operator: pivot k
+// maps A to A' with A'_ij = A_ij - A_ik A_kj / A_kk (i, j != k), A'_ik = A_ik / A_kk, A'_kk = -1 / A_kk;
+// after every pivot A = -Gs^-1.  A stays symmetric, so each of the NT threads updates its fixed
+// entries of the packed upper triangle (row and column looked up once; all of a step's loads are
+// issued before its stores) and writes both mirror positions
+// of the next buffer; two R x R buffers alternate (one block barrier per pivot).  A pivot below 1e-6
+// (relative to the unit diagonal) or not finite returns false in every thread.  The result (negated
+// back) is left in buffer R & 1.
+template <int EPT, int NT>
+__device__ __forceinline__ void sweep_step(const float* o, float* w, int R, int k, float inv, const int* eij, int NE) {
+  const int tid = threadIdx.x;
+  const float* ok = o + k * R;     // row k (= column k)
+  // the entries in groups of eight: every operand of a group first, then its updates, so that the
+  // stores into w do not hold back the loads from o
+  constexpr int GQ = 8;
+#pragma unroll
+  for (int q0 = 0; q0 < EPT; q0 += GQ) {
+    float aik[GQ], akj[GQ], aij[GQ];
+#pragma unroll
+    for (int u = 0; u < GQ; ++u) {
+      const int q = q0 + u;
+      if (q < EPT) {
+        const int i = eij[q] >> 8, j = eij[q] & 255;
+        aik[u] = ok[i];
+        akj[u] = ok[j];
+        aij[u] = o[i * R + j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < GQ; ++u) {
+      const int q = q0 + u;
+      if (q < EPT && q * NT + tid < NE) {
+        const int i = eij[q] >> 8, j = eij[q] & 255;
+        float v;
+        if (i == k && j == k) v = -inv;
+        else if (i == k) v = akj[u] * inv;
+        else if (j == k) v = aik[u] * inv;
+        else v = fmaf(-aik[u] * inv, akj[u], aij[u]);
+        w[i * R + j] = v;
+        w[j * R + i] = v;
+      }
+    }
+  }
+}
+
+template <int MAXR, int NT>
+__device__ bool sweep_inverse(float* sw, int R, const unsigned char* ne_r, const unsigned char* ne_c, int bar_id) {
+  constexpr int EPT = (MAXR * (MAXR + 1) / 2 + NT - 1) / NT;
+  const int tid = threadIdx.x;
+  const int RR = R * R, NE = R * (R + 1) / 2;
+  int eij[EPT];   // (row << 8) | column of this thread's packed entries
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * NT;
+    eij[q] = e < NE ? ((int)ne_r[e] << 8) | ne_c[e] : 0;
+  }
+  bool bad = false;
+  for (int k = 0; k < R; ++k) {
+    const float d = sw[(k & 1) * RR + k * R + k];
+    bad = bad || !(d > 1e-6f) || !isfinite(d);
+    sweep_step<EPT, NT>(sw + (k & 1) * RR, sw + ((k + 1) & 1) * RR, R, k, __frcp_rn(d), eij, NE);
+    named_sync(bar_id, NT);
+  }
+  float* res = sw + (R & 1) * RR;
+  for (int e = tid; e < RR; e += NT) res[e] = -res[e];
+  named_sync(bar_id, NT);
+  return !bad;
+}
+
+// ---- solver warps (threads 0 .. kGramT-1), after the Gram is reduced: G from the packed triangle,
+// the Jacobi scales dsc_r = 1 / sqrt(G_rr), and the FP32 inverse X0 of the scaled Gram (G^-1 ~ D X0 D)
+// in buffer R & 1 of sw.  Returns whether the FP32 inverse is usable (identical in every CTA).
+template <int MAXR>
+__device__ bool solver_prepare(const Prob& p, const GridSmem& L, unsigned char* sm, const GridScratch& gs,
+                               double* dsc, const unsigned char* ne_r, const unsigned char* ne_c) {
+  const int tid = threadIdx.x, R = p.R, RR = R * R;
+  const int NE = R * (R + 1) / 2;
+  double* G = reinterpret_cast<double*>(sm + L.G);
+  float* sw = reinterpret_cast<float*>(sm + L.sw);
+  constexpr int GPT = (MAXR * (MAXR + 1) / 2 + kGramT - 1) / kGramT;
+  double gv[GPT];
+#pragma unroll
+  for (int q = 0; q < GPT; ++q) {       // every load in flight before the stores
+    const int e = tid + q * kGramT;
+    gv[q] = e < NE ? __ldcg(gs.Gfull + e) : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < GPT; ++q) {
+    const int e = tid + q * kGramT;
+    if (e < NE) {
+      const int r = ne_r[e], cc = ne_c[e];
+      G[r * R + cc] = gv[q];
+      G[cc * R + r] = gv[q];
+    }
+  }
+  named_sync(1, kGramT);
+  bool good = true;
+  for (int r = tid; r < R; r += kGramT) {
+    const double d = G[r * R + r];
+    good = good && d > 0.0 && isfinite(d);
+    dsc[r] = (d > 0.0 && isfinite(d)) ? rsqrt64(d) : 0.0;
+  }
+  const bool fast = named_and(1, kGramT, good);   // the same in every solver thread
+  // the scaled FP32 copy (the FP32 start only needs FP32 accuracy)
+  for (int e = tid; e < RR; e += kGramT) {
+    const int r = e / R, cc = e - r * R;
+    sw[e] = (float)G[e] * (float)dsc[r] * (float)dsc[cc];
+  }
+  named_sync(1, kGramT);
+  return fast && sweep_inverse<MAXR, kGramT>(sw, R, ne_r, ne_c, 1);
+}
+
+// ---- all threads, after the contraction: this CTA's rows of A^(n) = M G^-1 (Alg. 3 least-squares
+// step through the FP64 normal equations) from mrow (M rows, FP64).  fast: the FP32 inverse is usable
+// (refinement path); else the FP64 Cholesky inverse, which also decides singularity.  Returns false
+// if the Gram is singular.
+template <int MAXR>
+__device__ bool solve_rows(const Prob& p, const GridSmem& L, unsigned char* sm, const GridCtx& x,
+                           const ModeSplit& ms, const double* dsc, bool fast, int* s_flag, unsigned* s_umax) {
+  const int tid = threadIdx.x, R = p.R, RR = R * R;
+  const double* G = reinterpret_cast<const double*>(sm + L.G);
+  const double* mrow = reinterpret_cast<const double*>(sm + L.mrow);
+  double* arow = reinterpret_cast<double*>(sm + L.arow);
+  float* sw = reinterpret_cast<float*>(sm + L.sw);
+  float* m32 = reinterpret_cast<float*>(sm + L.m32);
+  const float* X0 = sw + (R & 1) * RR;   // X0(r, c), scaled: G^-1 ~ D X0 D
+  const int i0 = x.c * ms.rpc;
+  const int nrows = max(0, min(ms.I, i0 + ms.rpc) - i0);
+  const int NO = nrows * R;
+  if (!fast) {
+    // FP64 Cholesky inverse (also the singularity test) into the sweep buffers, then A = M G^-1
+    double* X = reinterpret_cast<double*>(sw);
+    if (tid == 0) *s_flag = 0;
+    __syncthreads();
+    spd_inverse_fp64(G, X, reinterpret_cast<double*>(sm + L.fL), reinterpret_cast<double*>(sm + L.fT),
+                     reinterpret_cast<double*>(sm + L.fd), R, s_flag);
+    const bool singular = *s_flag != 0;
+    for (int e = tid; e < NO; e += kGT) {
+      const int li = e / R, cc = e - li * R;
+      const double* m = mrow + li * R;
+      double a0 = 0.0, a1 = 0.0;
+      int l = 0;
+      for (; l + 1 < R; l += 2) {
+        a0 = fma(m[l], X[l * R + cc], a0);
+        a1 = fma(m[l + 1], X[(l + 1) * R + cc], a1);
+      }
+      if (l < R) a0 = fma(m[l], X[l * R + cc], a0);
+      arow[e] = a0 + a1;
+    }
+    __syncthreads();
+    return !singular;
+  }
+  // A0 = ((M D) X0) D in FP32
+  for (int e = tid; e < NO; e += kGT) {
+    const int r = e % R;
+    m32[e] = (float)(mrow[e] * dsc[r]);
+  }
+  __syncthreads();
+  for (int e = tid; e < NO; e += kGT) {
+    const int li = e / R, cc = e - li * R;
+    const float* m = m32 + li * R;
+    float a0 = 0.f, a1 = 0.f;
+    int l = 0;
+    for (; l + 1 < R; l += 2) {
+      a0 = fmaf(m[l], X0[l * R + cc], a0);
+      a1 = fmaf(m[l + 1], X0[(l + 1) * R + cc], a1);
+    }
+    if (l < R) a0 = fmaf(m[l], X0[l * R + cc], a0);
+    arow[e] = (double)(a0 + a1) * dsc[cc];
+  }
+  __syncthreads();
+  // refinement: residual M - A G in FP64, correction through the FP32 inverse
+  for (int it = 0; it < 3; ++it) {
+    if (tid == 0) s_umax[0] = s_umax[1] = 0u;
+    for (int e = tid; e < NO; e += kGT) {
+      const int li = e / R, cc = e - li * R;
+      const double* a = arow + li * R;
+      double s0 = 0.0, s1 = 0.0;
+      int l = 0;
+      for (; l + 1 < R; l += 2) {
+        s0 = fma(a[l], G[l * R + cc], s0);
+        s1 = fma(a[l + 1], G[(l + 1) * R + cc], s1);
+      }
+      if (l < R) s0 = fma(a[l], G[l * R + cc], s0);
+      m32[e] = (float)((mrow[e] - (s0 + s1)) * dsc[cc]);
+    }
+    __syncthreads();
+    float cm = 0.f, am = 0.f;
+    for (int e = tid; e < NO; e += kGT) {
+      const int li = e / R, cc = e - li * R;
+      const float* m = m32 + li * R;
+      float a0 = 0.f, a1 = 0.f;
+      int l = 0;
+      for (; l + 1 < R; l += 2) {
+        a0 = fmaf(m[l], X0[l * R + cc], a0);
+        a1 = fmaf(m[l + 1], X0[(l + 1) * R + cc], a1);
+      }
+      if (l < R) a0 = fmaf(m[l], X0[l * R + cc], a0);
+      const double corr = (double)(a0 + a1) * dsc[cc];
+      const double a = arow[e] + corr;
+      arow[e] = a;
+      cm = fmaxf(cm, fabsf((float)corr));
+      am = fmaxf(am, fabsf((float)a));
+    }
+    cm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(cm)));
+    am = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(am)));
+    if ((tid & 31) == 0) {
+      atomicMax(s_umax, __float_as_uint(cm));
+      atomicMax(s_umax + 1, __float_as_uint(am));
+    }
+    __syncthreads();
+    // the error left after a correction of relative size c is about c^2 (the FP32 inverse's error
+    // shrinks it by the same factor it shrank the previous one): stop once c < 1e-5
+    const bool done = !(__uint_as_float(s_umax[0]) > 1e-5f * __uint_as_float(s_umax[1]));
+    __syncthreads();
+    if (done) break;
+  }
+  return true;
+}
+
+template <typename T, int MAXR>
+__global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, GridScratch gs) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ Prob P;
+  __shared__ double sc[kMaxOrder * kMaxRank];
+  __shared__ double lam[kMaxRank], scomb[kMaxRank], dsc[kMaxRank];
+  __shared__ float scf[kMaxRank], wrf[kMaxRank];
+  __shared__ double red[kGW];
+  __shared__ double red64[kMaxRank], redp[kGT];
+  __shared__ unsigned char ne_r[kNEMax], ne_c[kNEMax];
+  __shared__ int s_flag, s_flag2, s_done, s_status, s_iter, s_stall, s_fast, s_abort;
+  __shared__ unsigned s_umax[2];
+  __shared__ double s_best, s_last;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  GridCtx x;
+  x.gen = 0u;
+  x.G = (int)gridDim.x;
+  x.c = (int)blockIdx.x;
+  for (int b = 0; b < B; ++b) {
+    {
+      const int words = (int)(sizeof(Prob) / 4);
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(probs + b);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&P);
+      for (int w = tid; w < words; w += kGT) dst[w] = src[w];
+    }
+    __syncthreads();
+    const Prob& p = P;
+    const int R = p.R, N = p.N;
+    const GridSmem L = grid_layout(R, MAXR, (int)sizeof(T));
+    State* st = p.state;
+    if (tid == 0) {
+      int e = 0;
+      for (int r = 0; r < R; ++r)
+        for (int cc = r; cc < R; ++cc, ++e) {
+          ne_r[e] = (unsigned char)r;
+          ne_c[e] = (unsigned char)cc;
+        }
+      s_done = st->done;
+      s_status = st->status;
+      s_iter = st->iter;
+      s_stall = st->stall;
+      s_best = st->best;
+      s_last = st->last_fit;
+    }
+    if (tid == 0) {
+      s_fast = 0;
+      s_abort = 0;
+    }
+    for (int e = tid; e < N * R; e += kGT) sc[e] = p.scale[e / R][e % R];
+    for (int r = tid; r < R; r += kGT) lam[r] = p.lambda[r];
+    __syncthreads();
+    const double inv_norm = 1.0 / st->norm_x;
+    const double fit_scale = (double)p.P / (double)p.P_hat;
+    const int cap = p.fixed_iters > 0 ? p.fixed_iters : p.max_iters;
+    bool alive = true;
+    while (alive && !s_done && s_iter < cap) {
+      const uint32_t t = p.t0 + (uint32_t)s_iter;
+      bool singular = false;
+      for (int n = 0; n < N; ++n) {
+        const ModeSplit ms = mode_split(p, n, x.G);
+        // combined lazy scale of the other modes
+        for (int r = tid; r < R; r += kGT) {
+          double cmb = 1.0;
+          for (int m = 0; m < N; ++m)
+            if (m != n) cmb *= sc[m * R + r];
+          scomb[r] = cmb;
+          scf[r] = (float)cmb;
+        }
+        __syncthreads();
+        // ---- P1: warps 0-3 Gram partial, grid barrier among themselves (A), their slice of the
+        // reduced Gram, grid barrier (B), G and its FP32 inverse; meanwhile warps 4-15 contract
+        if (tid < kGramT) {
+          gram_partial<MAXR>(p, L, sm, gs, x, n, t, scomb, ne_r, ne_c);
+          bool gok = grid_sync(gs, x, &s_flag, 1, kGramT);
+          if (gok) {
+            const int NE = R * (R + 1) / 2;
+            const int epc = (NE + x.G - 1) / x.G;      // at most 64 (NE <= 2080, G >= 33 on this path)
+            const int e0 = x.c * epc;
+            const int ne = max(0, min(NE, e0 + epc) - e0);
+            if (ne > 0) {
+              sum_rows(gs.Gpart + e0, x.G, ne, NE, red64, redp, 1, kGramT);
+              for (int e = tid; e < ne; e += kGramT) gs.Gfull[e0 + e] = red64[e];
+            }
+            gok = grid_sync(gs, x, &s_flag, 1, kGramT);
+          }
+          if (gok) {
+            const bool f = solver_prepare<MAXR>(p, L, sm, gs, dsc, ne_r, ne_c);
+            if (tid == 0) s_fast = f ? 1 : 0;
+          } else if (tid == 0) {
+            s_abort = 1;
+          }
+        } else {
+          contract_units<T, MAXR>(p, L, sm, gs, x, n, t, ms, scf);
+          const int nn = n + 1 < N ? n + 1 : 0;
+          const uint32_t nt = n + 1 < N ? t : t + 1;
+          prefetch_next<T>(p, x, nn, nt, mode_split(p, nn, x.G));
+        }
+        __syncthreads();
+        if (s_abort) {
+          alive = false;
+          break;
+        }
+        if (!(alive = grid_sync(gs, x, &s_flag))) break;   // (C) every split's partial M is stored
+        // ---- P3: the split partials of this CTA's rows, then A = M G^-1
+        {
+          double* mrow = reinterpret_cast<double*>(sm + L.mrow);
+          const int i0 = x.c * ms.rpc;
+          const int nrows = max(0, min(ms.I, i0 + ms.rpc) - i0);
+          for (int e = tid; e < nrows * R; e += kGT) {
+            const int li = e / R, r = e - li * R;
+            const float* src = gs.Mpart + (int64_t)r * ms.I + i0 + li;
+            const int64_t sstr = (int64_t)R * ms.I;
+            double a0 = 0.0, a1 = 0.0;
+            int q = 0;
+            for (; q + 7 < ms.nsplit; q += 8) {   // eight loads in flight
+              float v[8];
+#pragma unroll
+              for (int k = 0; k < 8; ++k) v[k] = __ldcg(src + (q + k) * sstr);
+#pragma unroll
+              for (int k = 0; k < 8; k += 2) {
+                a0 += (double)v[k];
+                a1 += (double)v[k + 1];
+              }
+            }
+            for (; q < ms.nsplit; ++q) a0 += (double)__ldcg(src + q * sstr);
+            mrow[e] = a0 + a1;
+          }
+        }
+        __syncthreads();
+        const bool ok = solve_rows<MAXR>(p, L, sm, x, ms, dsc, s_fast != 0, &s_flag2, s_umax);
+        {
+          const double* arow = reinterpret_cast<const double*>(sm + L.arow);
+          const int i0 = x.c * ms.rpc;
+          const int nrows = max(0, min(ms.I, i0 + ms.rpc) - i0);
+          double* A64 = p.A64[n] + (int64_t)i0 * R;
+          float* A32 = p.A32[n] + (int64_t)i0 * R;
+          for (int e = tid; e < nrows * R; e += kGT) {
+            const double a = arow[e];
+            A64[e] = a;
+            A32[e] = (float)a;
+          }
+          for (int r = tid; r < R; r += kGT) {
+            double s0 = 0.0;
+            for (int li = 0; li < nrows; ++li) s0 = fma(arow[li * R + r], arow[li * R + r], s0);
+            gs.Npart[(int64_t)x.c * R + r] = s0;
+          }
+        }
+        if (!ok) singular = true;   // identical in every CTA (same G, same arithmetic)
+        if (!(alive = grid_sync(gs, x, &s_flag))) break;   // (D) every row and column partial stored
+        if (singular) break;
+        // ---- P4: lambda and the lazy scales of mode n
+        sum_rows(gs.Npart, x.G, R, R, red64, redp);
+        for (int r = tid; r < R; r += kGT) {
+          const double a = red64[r];
+          const double y = a > 0.0 ? rsqrt64(a) : 0.0;
+          const double nrm = a * y;
+          lam[r] = nrm;
+          sc[n * R + r] = nrm > 0.0 ? y : 1.0;
+        }
+        __syncthreads();
+      }
+      if (!alive) break;
+      if (singular) {
+        if (tid == 0) {
+          s_status = CPR_ESINGULAR;
+          s_done = 1;
+        }
+        __syncthreads();
+        break;
+      }
+      // ---- sampled fit (Sec. 3.4): one warp per fixed entry
+      for (int r = tid; r < R; r += kGT) {
+        double w = lam[r];
+        for (int m = 0; m < N; ++m) w *= sc[m * R + r];
+        wrf[r] = (float)w;
+      }
+      __syncthreads();
+      {
+        const int fpc = (p.P_hat + x.G - 1) / x.G;
+        const int f0 = x.c * fpc;
+        const int f1 = min(p.P_hat, f0 + fpc);
+        double e2 = 0.0;
+        // the CTA's fit entries staged in shared memory (the P1 region is free here) in chunks; four
+        // entries per warp at a time, their factor-row loads issued together
+        uint32_t* fids = reinterpret_cast<uint32_t*>(sm + L.Zf);
+        double* fxs = reinterpret_cast<double*>(sm + L.cids);
+        const int fchunk = kSC;              // entries per chunk (ids: kSC * N <= kSC * MAXR words)
+        for (int c0 = f0; c0 < f1; c0 += fchunk) {
+          const int cn = min(fchunk, f1 - c0);
+          for (int e = tid; e < cn * N; e += kGT) fids[e] = p.fit_idx[(int64_t)c0 * N + e];
+          for (int e = tid; e < cn; e += kGT) fxs[e] = p.fit_x[c0 + e];
+          __syncthreads();
+          for (int j0 = 4 * warp; j0 < cn; j0 += 4 * kGW) {
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {          // R <= 64: two columns per lane
+              const int r = lane + 32 * h;
+              if (r < R) {
+                float tt[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) tt[u] = wrf[r];
+                for (int m = 0; m < N; ++m) {
+                  const float* Am = p.A32[m];
+                  float a[4];
+#pragma unroll
+                  for (int u = 0; u < 4; ++u)
+                    a[u] = j0 + u < cn ? __ldcg(Am + (int64_t)fids[(j0 + u) * N + m] * R + r) : 0.f;
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) tt[u] *= a[u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] += tt[u];
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              for (int o = 16; o > 0; o >>= 1) v[u] += __shfl_xor_sync(0xffffffffu, v[u], o);
+              if (j0 + u < cn) {
+                const double e = fxs[j0 + u] - (double)v[u];
+                e2 = fma(e, e, e2);
+              }
+            }
+          }
+          __syncthreads();
+        }
+        if (lane == 0) red[warp] = e2;
+        __syncthreads();
+        if (tid == 0) {
+          double a = 0.0;
+          for (int q = 0; q < kGW; ++q) a += red[q];
+          gs.fitpart[x.c] = a;
+        }
+      }
+      if (!(alive = grid_sync(gs, x, &s_flag))) break;
+      sum_rows(gs.fitpart, x.G, 1, 1, red64, redp);
+      if (warp == 0) {
+        const double a = red64[0];
+        if (lane == 0) {
+          const double v = fit_scale * a;
+          const double fit = v > 0.0 ? 1.0 - v * rsqrt64(v) * inv_norm : (v == 0.0 ? 1.0 : NAN);
+          const int t1 = s_iter + 1;
+          bool stop = false;
+          if (!isfinite(fit)) {
+            s_status = CPR_ENONFINITE;
+            stop = true;
+          } else if (p.fixed_iters > 0) {
+            stop = t1 >= p.fixed_iters;
+          } else {
+            if (fit > s_best) {
+              s_best = fit;
+              s_stall = 0;
+            } else {
+              s_stall += 1;
+            }
+            if (t1 >= p.max_iters) stop = true;
+            if (t1 >= 2 && fabs(fit - s_last) <= p.tol) stop = true;
+            if (p.eta >= 0.0 && fit >= 1.0 - 1.2 * p.eta) stop = true;
+            if (p.stall_iters > 0 && s_stall >= p.stall_iters) stop = true;
+          }
+          if (x.c == 0 && p.trace) p.trace[s_iter] = fit;
+          s_last = fit;
+          s_iter = t1;
+          if (stop) s_done = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!alive) return;   // a barrier wait ran out (the error flag is set); nothing is in flight
+    // publish the loop state, lambda and the lazy scales (CTA 0)
+    if (x.c == 0) {
+      for (int e = tid; e < N * R; e += kGT) p.scale[e / R][e % R] = sc[e];
+      for (int r = tid; r < R; r += kGT) p.lambda[r] = lam[r];
+      if (tid == 0) {
+        st->done = 1;
+        st->status = s_status;
+        st->iter = s_iter;
+        st->stall = s_stall;
+        st->best = s_best;
+        st->last_fit = s_last;
+      }
+    }
+    // the next problem reuses the scratch: every CTA leaves this one first
+    if (!grid_sync(gs, x, &s_flag)) return;
+  }
+}
+
+template <typename T, int MAXR>
+cudaError_t grid_launch(const Prob* probs, int B, const GridScratch& gs, int G, cudaStream_t s, int query,
+                        int* capacity, int maxR) {
+  auto kern = k_grid_run<T, MAXR>;
+  const GridSmem L = grid_layout(maxR, MAXR, (int)sizeof(T));
+  const int smem = L.bytes;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (query) {
+    int per_sm = 0, dev = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGT, smem)) != cudaSuccess) return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    *capacity = per_sm >= 1 ? sms : 0;
+    return cudaSuccess;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G, 1, 1);
+  cfg.blockDim = dim3(kGT, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, probs, B, gs);
+}
+
+template <typename T>
+cudaError_t grid_dispatch_r(int maxR, const Prob* probs, int B, const GridScratch& gs, int G, cudaStream_t s,
+                            int query, int* cap) {
+  if (maxR <= 16) return grid_launch<T, 16>(probs, B, gs, G, s, query, cap, maxR);
+  if (maxR <= 32) return grid_launch<T, 32>(probs, B, gs, G, s, query, cap, maxR);
+  if (maxR <= 48) return grid_launch<T, 48>(probs, B, gs, G, s, query, cap, maxR);
+  return grid_launch<T, 64>(probs, B, gs, G, s, query, cap, maxR);
+}
+
+}  // namespace
+
+// CTAs of the grid loop on this device (one per SM), or 0 if it cannot be launched for this dtype
+// and rank.
+int grid_capacity(int dtype, int maxR) {
+  int cap = 0;
+  cudaError_t e = cudaSuccess;
+  if (dtype == CPR_F32) e = grid_dispatch_r<float>(maxR, nullptr, 0, GridScratch{}, 0, nullptr, 1, &cap);
+  else if (dtype == CPR_BF16) e = grid_dispatch_r<__nv_bfloat16>(maxR, nullptr, 0, GridScratch{}, 0, nullptr, 1, &cap);
+  else return 0;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return cap > kGridMaxCTAs ? kGridMaxCTAs : cap;
+}
+
+// Whether a problem fits the grid loop's fixed limits (every mode's factor rows per CTA).
+bool grid_fits(const Prob& p, int G) {
+  if (p.dtype == CPR_F64 || p.R > kMaxRank || G < 33) return false;   // G >= 33: a CTA's Gram slice <= 64
+  for (int n = 0; n < p.N; ++n)
+    if ((p.dims[n] + G - 1) / G > kGridMaxRows) return false;
+  return true;
+}
+
+cudaError_t launch_grid_run(const Prob* probs, int B, const GridScratch& gs, int dtype, int maxR, int G,
+                            cudaStream_t s) {
+  if (dtype == CPR_F32) return grid_dispatch_r<float>(maxR, probs, B, gs, G, s, 0, nullptr);
+  return grid_dispatch_r<__nv_bfloat16>(maxR, probs, B, gs, G, s, 0, nullptr);
+}
+
+}  // namespace cpr

@@ -499,29 +499,39 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
   const float* X0 = gj + (R & 1) * (R * W) + R;   // X0(i, c) = X0[i * W + c]
   double* X = reinterpret_cast<double*>(sm + L.X);
   {
-    // ---- Newton-Schulz refinement (or the FP64 Cholesky inverse).  The first step writes
-    // X directly (it reads the FP32 start); a second step (FP64 tensors) writes U, the result.
+    // ---- Newton-Schulz refinement (or the FP64 Cholesky inverse).  Step k: E = I - G X_k with the
+    // residual in FP64, X_{k+1} = X_k + X0 E (the small correction in FP32 from the FP32 start X0,
+    // which equals X_k to FP32 accuracy).  b = R max|E_ij| bounds ||E||_inf, and the step leaves a
+    // residual of at most b^2 (plus the FP32 correction's rounding, about 1e-7 of b), so the steps stop
+    // once b^2 is below the target (1e-7 for FP32 / BF16 tensors, 1e-13 for FP64); a start with
+    // b >= 1/2, or no convergence within six steps, takes the FP64 Cholesky inverse instead (which
+    // also reports a singular Gram).  Iterates alternate between X and U.
     double* U = reinterpret_cast<double*>(sm + L.U);
     double* E = reinterpret_cast<double*>(sm + L.E);
     const int RR = R * R;
     bool fast = ok;
-    const int steps = sizeof(ACC) == 8 ? 2 : 1;
-    if (tid == 0) *s_em = 0u;
+    const double target = sizeof(ACC) == 8 ? 1e-13 : 1e-7;
+    if (tid == 0) {
+      s_em[1] = 0u;
+      s_em[2] = 0u;
+    }
     __syncthreads();
     const int dbase = (RR + 31) / 32 * 32;   // first thread not computing an entry of E
     // E in FP32 for the correction X E: |E| is small, so the FP32 product's rounding (about 1e-7 of
     // |X E|) stays far below the FP64 residual of the step; it lives in the tableau half X0 is not in
     float* Ef = gj + ((R + 1) & 1) * (R * W);
     bool drawn = false;
-    for (int it = 0; fast && it < steps; ++it) {
-      // E = I - G X  (X: the FP32 start in the first step)
+    const double* cur = nullptr;   // the current iterate (null: the FP32 start X0)
+    for (int it = 0; fast; ++it) {
+      unsigned* slot = s_em + 1 + (it & 1);
+      if (tid == 0) s_em[1 + ((it + 1) & 1)] = 0u;   // the next step's slot (read two barriers ago)
       float em = 0.f;
       for (int e = tid; e < RR; e += kLT) {
         const int r = e / R, c = e - r * R;
         const double* g = G + r * R;
         double a0 = 0.0, a1 = 0.0;
         int l = 0;
-        if (it == 0) {
+        if (!cur) {
           for (; l + 1 < R; l += 2) {
             a0 = fma(g[l], (double)X0[l * W + c], a0);
             a1 = fma(g[l + 1], (double)X0[(l + 1) * W + c], a1);
@@ -529,19 +539,19 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
           if (l < R) a0 = fma(g[l], (double)X0[l * W + c], a0);
         } else {
           for (; l + 1 < R; l += 2) {
-            a0 = fma(g[l], X[l * R + c], a0);
-            a1 = fma(g[l + 1], X[(l + 1) * R + c], a1);
+            a0 = fma(g[l], cur[l * R + c], a0);
+            a1 = fma(g[l + 1], cur[(l + 1) * R + c], a1);
           }
-          if (l < R) a0 = fma(g[l], X[l * R + c], a0);
+          if (l < R) a0 = fma(g[l], cur[l * R + c], a0);
         }
         const double ev = (r == c ? 1.0 : 0.0) - (a0 + a1);
         E[e] = ev;
         Ef[e] = (float)ev;
         em = fmaxf(em, fabsf((float)ev));
       }
+      const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(em));
+      if ((tid & 31) == 0 && wm) atomicMax(slot, wm);
       if (it == 0) {
-        const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(em));
-        if ((tid & 31) == 0 && wm) atomicMax(s_em, wm);
         if (K.draw_late && tid >= dbase) {
           draw_and_copy<T>(K, nn, nt, rank * spc, cnt, reinterpret_cast<uint32_t*>(sm + L.ids[cb ^ 1]),
                            reinterpret_cast<int64_t*>(sm + L.offs[cb ^ 1]), reinterpret_cast<T*>(sm + L.fib[cb ^ 1]),
@@ -550,13 +560,17 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
         drawn = true;
       }
       __syncthreads();
-      if (it == 0 && !(__uint_as_float(*s_em) < 0.25f)) {
+      const float b = (float)R * __uint_as_float(*slot);
+      if (!(b < 0.5f)) {
         fast = false;
         break;
       }
-      // X_new = X + X E, the correction in FP32 from the FP32 start X0 (which equals X to FP32
-      // accuracy) and E's FP32 copy
-      double* Xout = it == 0 ? X : U;
+      const bool last = (double)b * (double)b < target;
+      if (!last && it >= 6) {
+        fast = false;
+        break;
+      }
+      double* Xout = (it & 1) ? U : X;
       for (int e = tid; e < RR; e += kLT) {
         const int r = e / R, c = e - r * R;
         const float* xr = X0 + r * W;
@@ -567,12 +581,14 @@ __device__ void loop_mode_update(const LoopConst& K, unsigned char* sm, cg::clus
           a1 = fmaf(xr[l + 1], Ef[(l + 1) * R + c], a1);
         }
         if (l < R) a0 = fmaf(xr[l], Ef[l * R + c], a0);
-        const double x = it == 0 ? (double)xr[c] : X[r * R + c];
+        const double x = cur ? cur[e] : (double)xr[c];
         Xout[e] = x + (double)(a0 + a1);
       }
       __syncthreads();
-      if (it == steps - 1 && steps == 2) X = U;   // the result of the second step
+      cur = Xout;
+      if (last) break;
     }
+    if (fast) X = const_cast<double*>(cur);
     if (K.draw_late && !drawn) {   // the refinement did not run: draw with every thread
       draw_and_copy<T>(K, nn, nt, rank * spc, cnt, reinterpret_cast<uint32_t*>(sm + L.ids[cb ^ 1]),
                        reinterpret_cast<int64_t*>(sm + L.offs[cb ^ 1]), reinterpret_cast<T*>(sm + L.fib[cb ^ 1]),
@@ -672,7 +688,7 @@ __global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, i
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ LoopConst K;
   __shared__ int s_prob, s_bad, s_done, s_status, s_iter, s_stall;
-  __shared__ unsigned s_em;
+  __shared__ unsigned s_em[3];   // [0] diagonal maximum; [1], [2] refinement residuals
   __shared__ int s_tout;
   __shared__ double s_best, s_last;
   __shared__ double fitpart[4];
@@ -821,7 +837,7 @@ __global__ void __launch_bounds__(kLT, 1) k_loop_rep(const Prob* probs, int B, i
         // the next mode update (its samples and fiber copies are issued during this one)
         const int nn = n + 1 < N ? n + 1 : 0;
         const uint32_t nt = n + 1 < N ? t : t + 1;
-        loop_mode_update<T, ACC, MAXR>(K, sm, cl, n, cb, nn, nt, &s_bad, &s_em, fbar, fpar, fblk, &s_tout);
+        loop_mode_update<T, ACC, MAXR>(K, sm, cl, n, cb, nn, nt, &s_bad, s_em, fbar, fpar, fblk, &s_tout);
         ++u;
         if (s_bad) break;   // identical in every CTA (same G, same factorization)
       }

@@ -43,6 +43,7 @@ namespace cpr {
 namespace {
 
 constexpr uint32_t kFftWaitLimit = 1u << 24;
+constexpr uint32_t kFftDrainLimit = 1u << 26;   // second wait after an expiry, before the CTA leaves
 constexpr int kSlots = 32;          // complex values a thread holds in a stage
 constexpr int kMaxStages = 16;
 constexpr int kFftMaxSmem = 200 * 1024;
@@ -269,6 +270,17 @@ __device__ __forceinline__ void fft_bulk_copy(void* dst, const void* src, uint32
                : "memory");
 }
 
+// After a copy wait ran out: report it, then let the CTA's bulk copies land (a second bounded wait
+// on the same mbarrier phase) before the CTA leaves, so that no copy targets the shared memory of a
+// CTA that has exited.
+__device__ __forceinline__ void fft_drain(uint64_t* bar, int* err, int tid) {
+  if (tid == 0) {
+    atomicExch(err, 1);
+    for (uint32_t it = 0; it < kFftDrainLimit && !fft_mbar_try(bar, 0); ++it) __nanosleep(64);
+  }
+  __syncthreads();
+}
+
 // block blk of the pass: its fibers run along mode v from i_v = iv0; returns the fiber count and the
 // first fiber's input row and output offset
 __device__ __forceinline__ int fft_block(const FftArgs& a, int64_t blk, int64_t& row0, int64_t& out0) {
@@ -353,7 +365,7 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_fft(const __grid_constan
     for (uint32_t it = 0; it < kFftWaitLimit && !ok; ++it) ok = fft_mbar_try(bar, 0);
   }
   if (__syncthreads_or(!ok)) {   // the whole CTA leaves together if the wait ran out
-    if (tid == 0) atomicExch(a.err, 1);
+    fft_drain(bar, a.err, tid);
     return;
   }
   if (a.bulk && tid != 0) (void)fft_mbar_try(bar, 0);   // completed: returns at once
@@ -881,7 +893,7 @@ __global__ void __launch_bounds__(PL::TPB, PL::MINB) k_mix_fft_ct(const __grid_c
     for (uint32_t it = 0; it < kFftWaitLimit && !ok; ++it) ok = fft_mbar_try(bar, 0);
   }
   if (__syncthreads_or(!ok)) {
-    if (tid == 0) atomicExch(a.err, 1);
+    fft_drain(bar, a.err, tid);
     return;
   }
   if (a.bulk && tid != 0) (void)fft_mbar_try(bar, 0);

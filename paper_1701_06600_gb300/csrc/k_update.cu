@@ -119,7 +119,12 @@ __global__ void __launch_bounds__(kP1Rows) k_sample_contract(const Prob* probs, 
   ACC* Zs = reinterpret_cast<ACC*>(Zd + (p.spl > R ? p.spl : R) * R);
   const int tid = threadIdx.x;
   const uint32_t t = p.t0 + (uint32_t)p.state->iter;
-  if (tid < cnt) {
+  if (tid < cnt && p.user_idx) {   // caller-given multi-indices (test hook)
+    const uint32_t* u = p.user_idx + ((int64_t)n * S + js + tid) * N;
+    for (int m = 0; m < N; ++m) ids[tid * kMaxOrder + m] = m == n ? 0u : u[m];
+    int64_t stride;
+    offs[tid] = fiber_offset(p, n, ids + tid * kMaxOrder, &stride);
+  } else if (tid < cnt) {
     const uint32_t j = (uint32_t)(js + tid);
     const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
     const uint4 w0 = philox10(make_uint4(j, counter_word1(kStreamSamples, 0, n), t, p.b), k0, k1);

@@ -29,7 +29,7 @@ namespace {
 constexpr int kNaThreads = 256;
 constexpr int64_t kNaMaxFit = CPR_NOALLOC_MAX_FIT_SAMPLES;
 constexpr int kNaMaxFitBlocks = (int)(kNaMaxFit / kNaThreads);
-constexpr int kNaNormBlocks = 152 * 8;  // the most blocks the ||X|| reduction uses
+constexpr int kNaNormBlocks = kSumsqMaxBlocks;  // the most blocks the ||X|| reduction uses
 // scratch layout, in doubles
 constexpr int kNaFitPart = 0;
 constexpr int kNaNormPart = kNaFitPart + kNaMaxFitBlocks;
@@ -157,6 +157,9 @@ extern "C" int cpr_fit_estimate_noalloc(const cpr_tensor* X, const cpr_ktensor* 
   memset(&a, 0, sizeof(a));
   int64_t st = 1;
   double P = 1.0;
+  double Pd = 1.0;
+  for (int n = 0; n < X->order; ++n) Pd *= (double)X->dims[n];
+  if (Pd > 4.0e18) return CPR_EINVAL;   // the same bound on the entry count as cpr_fit_estimate
   for (int n = 0; n < X->order; ++n) {
     if (X->dims[n] < 1 || X->dims[n] >= (int64_t(1) << 31) || K->dims[n] != X->dims[n] || !K->factors[n])
       return CPR_EINVAL;
@@ -179,9 +182,15 @@ extern "C" int cpr_fit_estimate_noalloc(const cpr_tensor* X, const cpr_ktensor* 
   double* scratch = scratch_for_current_device(&err);
   if (!scratch) return CPR_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
+  // the call ends with a synchronization and a copy into pageable host memory, which a captured
+  // stream cannot take: refuse before anything is enqueued
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cst) != cudaSuccess) return CPR_ECUDA;
+  if (cst != cudaStreamCaptureStatusNone) return CPR_EINVAL;
+  const int nblk = a.use_scratch_norm ? sumsq_blocks(st) : 0;
+  if (nblk > kNaNormBlocks) return CPR_EINVAL;   // cannot happen while both use kSumsqMaxBlocks
   if (cudaMemsetAsync(scratch + kNaCounter, 0, sizeof(double), s) != cudaSuccess) return CPR_ECUDA;
   if (a.use_scratch_norm) {
-    const int nblk = sumsq_blocks(st);   // at most kNaNormBlocks
     if (launch_sumsq(X->data, X->dtype, st, scratch + kNaNormPart, nblk, s) != cudaSuccess) return CPR_ECUDA;
     if (launch_sumsq_finish(scratch + kNaNormPart, nblk, scratch + kNaNorm, nullptr, 0, s) != cudaSuccess)
       return CPR_ECUDA;

@@ -75,6 +75,16 @@ def test_bf16_100x4_reaches_fp64_oracle_fit(cb):
     print("100^4 BF16: iterations gpu %d oracle %d, final fit gpu %.6f oracle %.6f, per-iteration |dF^|: %s"
           % (out["iters"], ref["iters"], f_gpu, f_ref, " ".join("%.1e" % v for v in err)))
     assert np.all(np.isfinite(err))
+    # per iteration against the oracle's CPRAND on the mixed tensor the GPU stored: the same BF16
+    # data and the same draws, so the traces differ only by the FP32 contraction / FP64 solve
+    # arithmetic (the divergence above is the BF16 rounding of the mixed tensor moving the trajectory)
+    k = min(out["iters"], 10)
+    Th = to_oracle_array(cb.cpr_mix_tensor(prob.X, dims, seed=2003), dims)
+    ref_h = cp.cprand(Th, R, S, seed=2003, rule=cp.StopRule(fixed_iters=k))
+    err_h = np.abs(trace.cpu().numpy()[:k] - ref_h["fits"])
+    print("100^4 BF16 vs the oracle on the stored mixed tensor, per iteration: %s"
+          % " ".join("%.1e" % v for v in err_h))
+    assert np.all(err_h < 1e-4), err_h
 
 
 # ------------------------------------------------------------------------------------------------
@@ -177,3 +187,63 @@ def test_1500_cubed_cp_als_exact_fit_matches_direct_evaluation(cb, big):
           "CPRAND-MIX setup %.1f ms, iterations %.1f ms"
           % (out["ms_setup"], out["ms_iterate"], out["fit_est"], mix["ms_setup"], mix["ms_iterate"]))
     assert abs(out["fit_est"] - f_direct) < 1e-6, (out["fit_est"], f_direct)
+
+
+def test_1500_cubed_run_to_stopping_rule_reaches_cp_als_fit(cb, big):
+    # the headline workload to its stopping rule (best-fit stall of 10 iterations, at most 200) on the
+    # whole-GPU loop: its exact final fit is within 1e-3 of the converged fit of the exact FP64 CP-ALS
+    # (Alg. 1) on the same tensor; the host oracle cannot converge at 13.5 GB, so the library's exact
+    # CP-ALS, itself checked against direct evaluation above, is the reference
+    dims, X = big
+    R, S = 50, 2000
+    out = cb.cpr_cprand_mix(X, dims, R, S, opts=cb.cpr_default_opts(seed=2005, stall_iters=10, fit_tol=-1.0))
+    assert out["status"] == cb.OK
+    f_mix = true_fit_device(X, dims, out["lam"], out["factors"])
+    del out
+    torch.cuda.empty_cache()
+    als = cb.cpr_cp_als(X, dims, R, opts=cb.cpr_default_opts(seed=2005, fit_tol=1e-6))
+    assert als["status"] == cb.OK
+    f_als = true_fit_device(X, dims, als["lam"], als["factors"])
+    print("1500^3 to the rule: CPRAND-MIX exact fit %.6f, CP-ALS (%d iterations) %.6f" % (f_mix, als["iters"], f_als))
+    assert f_mix > f_als - 1e-3, (f_mix, f_als)
+
+
+@pytest.fixture(scope="module")
+def big_bf16(cb):
+    dims = (1500, 1500, 1500)
+    prob = make_problem(dims, 50, C=0.5, eta=0.001, seed=1005, dtype=torch.bfloat16, device=DEV)
+    yield dims, prob.X
+    del prob
+    torch.cuda.empty_cache()
+
+
+def test_1500_cubed_bf16_update_matches_oracle_on_gathered_fibers(cb, big_bf16):
+    # the same per-mode check on the BF16-stored tensor (6.75 GB): the gathered BF16 values are exact
+    # in the oracle's FP64, the contraction accumulates in FP32, the solve is FP64
+    dims, X = big_bf16
+    R, S = 50, 2000
+    rng = np.random.default_rng(7)
+    f0 = [rng.random((d, R)).astype(np.float32).astype(np.float64) for d in dims]
+    Xv = X.view(*dims[::-1]).permute(2, 1, 0)
+    for n in range(3):
+        facs = [torch.tensor(f, device=DEV) for f in f0]
+        lam = torch.empty(R, dtype=torch.float64, device=DEV)
+        assert cb.cpr_sampled_update(X, dims, lam, facs, n, S, seed=2005, b=0, t=n) == cb.OK
+        idx = streams.ls_sample_indices(2005, 0, n, n, S, dims)
+        sel = tuple(torch.as_tensor(idx[:, m], device=DEV) for m in range(3) if m != n)
+        X_S = torch.movedim(Xv, n, -1)[sel].T.double().cpu().numpy()
+        A_ref, lam_ref = cp.normalize_columns(cp.sampled_ls(cp.skr(f0, idx, n), X_S))
+        assert rel(facs[n].cpu().numpy(), A_ref) < 1e-4, n
+        assert rel(lam.cpu().numpy(), lam_ref) < 1e-4, n
+
+
+def test_1500_cubed_bf16_mix_run_fit_estimate_matches_exact_fit(cb, big_bf16):
+    dims, X = big_bf16
+    trace = torch.zeros(3, dtype=torch.float64, device=DEV)
+    out = cb.cpr_cprand_mix(X, dims, 50, 2000, opts=cb.cpr_default_opts(seed=2005, fixed_iters=3,
+                                                                         fit_trace_dev=trace.data_ptr()))
+    assert out["status"] == cb.OK and out["iters"] == 3
+    tr = trace.cpu().numpy()
+    f_true = true_fit_device(X, dims, out["lam"], out["factors"])
+    print("1500^3 BF16: sampled fit %s, exact fit %.6f" % (tr, f_true))
+    assert np.all(np.isfinite(tr)) and abs(tr[-1] - f_true) < 2e-3, (tr, f_true)
