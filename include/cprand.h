@@ -146,6 +146,24 @@ typedef struct {
   double ms_finish;      /* device time of unmixing and output copies */
 } cpr_result;
 
+/* Contraction engine of the whole-GPU loop (loop_path 5; process-wide, applies to calls enqueued
+ * afterwards): CPR_CONTRACT_AUTO and CPR_CONTRACT_TC compute M = X_S Z_S (Alg. 3) on the tensor cores
+ * (tcgen05, kind::tf32, each FP32 operand split into TF32 halves: hi*hi + hi*lo + lo*hi accumulated
+ * in FP32 in TMEM, about 2^-20 relative per product; BF16 tensor values are exact TF32 values, so
+ * their lo*hi term is zero and is skipped); CPR_CONTRACT_FMA by FP32 FMA.  Returns the previous
+ * engine, or -1 (nothing changed) for an unknown value. */
+enum { CPR_CONTRACT_AUTO = 0, CPR_CONTRACT_TC = 1, CPR_CONTRACT_FMA = 2 };
+CPR_API int cpr_set_contract_engine(int engine);
+
+/* A schedule of the iteration loop, as chosen by the autotuner. */
+typedef struct {
+  int32_t loop_path;      /* cpr_opts.loop_path value of the chosen engine (1, 2, 4 or 5) */
+  int32_t split_per_sm;   /* graph engine: (fiber tile, sample split) blocks per SM per mode update */
+  int32_t grid_min_split; /* whole-GPU engine: fewest samples per contraction split */
+  int32_t pad;
+  double ms_per_iter;     /* device time per outer iteration when it was tuned */
+} cpr_schedule;
+
 /* Kernel classes of the profiler. */
 enum {
   CPR_KERNEL_MIX = 0,        /* mode-n mixing product (Alg. 5 mixing step) */
@@ -224,6 +242,10 @@ CPR_API size_t cpr_batched_workspace_size(int B, const cpr_tensor* Xs, const int
 CPR_API int cpr_cprand_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss,
                        const cpr_opts* opts, int mix, cpr_ktensor* outs, cpr_result* results,
                        void* ws, size_t ws_bytes, void* stream);
+/* cpr_cprand_batched with mix = 1: B independent CPRAND-MIX decompositions (Alg. 5) at once. */
+CPR_API int cpr_cprand_mix_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss,
+                                   const cpr_opts* opts, cpr_ktensor* outs, cpr_result* results, void* ws,
+                                   size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------------
  * Steps of the hot path (each is also a parity-test hook)
@@ -340,6 +362,32 @@ CPR_API int cpr_profile_end(double* ms, int64_t* launches);
 #define CPR_NOALLOC_MAX_FIT_SAMPLES (1 << 20)
 CPR_API int cpr_fit_estimate_noalloc(const cpr_tensor* X, const cpr_ktensor* K, int64_t P_hat, uint64_t seed,
                                      uint32_t b, double norm_x, double* fit_host, void* stream);
+
+/* Schedule autotuner (no counterpart in the paper; an implementation aid for the batched starts of
+ * Sec. 4.2 and the large single problems).  cpr_autotune runs the given batch (arguments as for
+ * cpr_cprand_batched, every problem with fixed_iters = trial_iters, no trace, no caller samples) once
+ * with the default schedule (warm-up) and once per candidate: the replicated- and distributed-factor
+ * clusters, the whole-GPU loop with 16, 32 and 64 samples at least per contraction split, and the
+ * captured graph with 1, 2 and 4 blocks per SM per mode update; candidates that do not apply to the
+ * batch are skipped.  The schedule with the least device time per outer iteration is recorded for the
+ * batch's bucket -- dtype, order, batch size, mixing, and per mode the largest extent, the rank and
+ * the sample count, each rounded (extents and S to the next power of two, R to the next multiple
+ * of 8) -- and returned in *best.  Every later call in this process whose loop_path is 0 and whose
+ * batch falls in a recorded bucket runs with the recorded schedule.  The outputs and the workspace
+ * are those of cpr_cprand_batched (they hold the last candidate's result afterwards).  Synchronizes
+ * the stream after every candidate.
+ * cpr_tune_lookup: the recorded schedule of a batch's bucket (CPR_EINVAL when there is none).
+ * cpr_tune_save / cpr_tune_load: write the table to a text file (one bucket per line) / add a file's
+ * buckets to it; the file named by the environment variable CPRAND_TUNE_CACHE is loaded on the
+ * first lookup.  cpr_tune_clear: empty the table.  Host-side only; not thread-safe against
+ * concurrent tuning of the same bucket. */
+CPR_API int cpr_autotune(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, const cpr_opts* opts, int mix,
+                         cpr_ktensor* outs, void* ws, size_t ws_bytes, void* stream, int trial_iters,
+                         cpr_schedule* best);
+CPR_API int cpr_tune_lookup(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, int mix, cpr_schedule* out);
+CPR_API int cpr_tune_save(const char* path);
+CPR_API int cpr_tune_load(const char* path);
+CPR_API void cpr_tune_clear(void);
 
 /* ||X||_F (FP64 accumulation) written to *norm_host (synchronizes the stream). */
 CPR_API int cpr_tensor_norm(const cpr_tensor* X, double* norm_host, void* ws, size_t ws_bytes,

@@ -41,12 +41,18 @@ class CprOpts(ctypes.Structure):
 
 LOOP_AUTO, LOOP_CLUSTER, LOOP_GRAPH, LOOP_STREAM, LOOP_CLUSTER_DIST, LOOP_GRID = range(6)
 MIX_AUTO, MIX_FFT, MIX_DENSE = range(3)
+CONTRACT_AUTO, CONTRACT_TC, CONTRACT_FMA = range(3)
 
 
 class CprResult(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("fit_est", ctypes.c_double),
                 ("norm_x", ctypes.c_double), ("kernel_launches", ctypes.c_int64), ("ms_setup", ctypes.c_double),
                 ("ms_iterate", ctypes.c_double), ("ms_finish", ctypes.c_double)]
+
+
+class CprSchedule(ctypes.Structure):
+    _fields_ = [("loop_path", ctypes.c_int32), ("split_per_sm", ctypes.c_int32), ("grid_min_split", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("ms_per_iter", ctypes.c_double)]
 
 
 class CprError(RuntimeError):
@@ -88,6 +94,10 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(CprOpts), ctypes.c_int,
                                           ctypes.POINTER(CprKtensor), ctypes.POINTER(CprResult),
                                           ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "cpr_cprand_mix_batched": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(CprTensor), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(CprOpts),
+                                              ctypes.POINTER(CprKtensor), ctypes.POINTER(CprResult),
+                                              ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "cpr_sample_indices": (ctypes.c_int, [ctypes.POINTER(CprTensor), ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
                                           ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p]),
@@ -111,6 +121,16 @@ _SIGS = {
                                                 ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double,
                                                 ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "cpr_set_mix_engine": (ctypes.c_int, [ctypes.c_int]),
+    "cpr_set_contract_engine": (ctypes.c_int, [ctypes.c_int]),
+    "cpr_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(CprTensor), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(CprOpts), ctypes.c_int,
+                                    ctypes.POINTER(CprKtensor), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                    ctypes.c_int, ctypes.POINTER(CprSchedule)]),
+    "cpr_tune_lookup": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(CprTensor), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.POINTER(CprSchedule)]),
+    "cpr_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "cpr_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "cpr_tune_clear": (None, []),
     "cpr_profile_begin": (ctypes.c_int, [ctypes.c_uint]),
     "cpr_profile_end": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }
@@ -279,6 +299,15 @@ def cpr_set_mix_engine(engine):
     prev = lib().cpr_set_mix_engine(int(engine))
     if prev < 0:
         raise ValueError("unknown mixing engine %r" % (engine,))
+    return prev
+
+
+def cpr_set_contract_engine(engine):
+    """Select the contraction engine of the whole-GPU loop (CONTRACT_AUTO, CONTRACT_TC, CONTRACT_FMA);
+    returns the previous one."""
+    prev = lib().cpr_set_contract_engine(int(engine))
+    if prev < 0:
+        raise ValueError("unknown contraction engine %r" % (engine,))
     return prev
 
 
@@ -499,3 +528,65 @@ def cpr_tensor_norm(X, dims, stream=None):
                                ctypes.c_size_t(ws.numel()), _stream(stream))
     _check(st, "cpr_tensor_norm")
     return out.value
+
+
+def _schedule_dict(sc):
+    return {"loop_path": sc.loop_path, "split_per_sm": sc.split_per_sm, "grid_min_split": sc.grid_min_split,
+            "ms_per_iter": sc.ms_per_iter}
+
+
+def _batch_descs(Xs, dims_list, Rs, Ss):
+    B = len(Xs)
+    descs = (CprTensor * B)(*[tensor_desc(X, d) for X, d in zip(Xs, dims_list)])
+    Rarr = (ctypes.c_int * B)(*[int(r) for r in Rs])
+    Sarr = (ctypes.c_int64 * B)(*[int(s) for s in Ss])
+    return B, descs, Rarr, Sarr
+
+
+def cpr_autotune(Xs, dims_list, Rs, Ss, opts_list=None, mix=False, trial_iters=3, ws=None, stream=None):
+    """Time the candidate schedules on this batch and record the fastest for its bucket; returns the
+    chosen schedule (dict) and the workspace."""
+    B, descs, Rarr, Sarr = _batch_descs(Xs, dims_list, Rs, Ss)
+    if opts_list is None:
+        opts_list = [cpr_default_opts(batch_index=b) for b in range(B)]
+    oarr = (CprOpts * B)(*opts_list)
+    outs = [alloc_ktensor(d, r, Xs[0].device) for d, r in zip(dims_list, Rs)]
+    karr = (CprKtensor * B)(*[ktensor_desc(l, f) for l, f in outs])
+    need = lib().cpr_batched_workspace_size(B, descs, Rarr, Sarr, oarr, int(bool(mix)))
+    if need == 0:
+        raise CprError(EINVAL, "cpr_batched_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, Xs[0].device)
+    sc = CprSchedule()
+    st = lib().cpr_autotune(B, descs, Rarr, Sarr, oarr, int(bool(mix)), karr, ctypes.c_void_p(ws.data_ptr()),
+                            ctypes.c_size_t(ws.numel()), _stream(stream), int(trial_iters), ctypes.byref(sc))
+    _check(st, "cpr_autotune")
+    return _schedule_dict(sc), ws
+
+
+def cpr_tune_lookup(dims_list, Rs, Ss, dtype=F32, mix=False):
+    """The recorded schedule of a batch's bucket (dict), or None.  Host-side only."""
+    B = len(dims_list)
+    descs = (CprTensor * B)()
+    for b, dims in enumerate(dims_list):
+        descs[b].order = len(dims)
+        descs[b].dtype = dtype
+        for n, v in enumerate(dims):
+            descs[b].dims[n] = int(v)
+    Rarr = (ctypes.c_int * B)(*[int(r) for r in Rs])
+    Sarr = (ctypes.c_int64 * B)(*[int(s) for s in Ss])
+    sc = CprSchedule()
+    st = lib().cpr_tune_lookup(B, descs, Rarr, Sarr, int(bool(mix)), ctypes.byref(sc))
+    return _schedule_dict(sc) if st == OK else None
+
+
+def cpr_tune_save(path):
+    _check(lib().cpr_tune_save(str(path).encode()), "cpr_tune_save")
+
+
+def cpr_tune_load(path):
+    _check(lib().cpr_tune_load(str(path).encode()), "cpr_tune_load")
+
+
+def cpr_tune_clear():
+    lib().cpr_tune_clear()

@@ -2,12 +2,16 @@
 // layout, and the order of kernel launches.  No device memory is allocated here; every buffer is
 // carved out of the caller's workspace.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
 #include <cmath>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "internal.cuh"
@@ -16,6 +20,7 @@ using namespace cpr;
 
 namespace {
 std::atomic<int> g_mix_engine{CPR_MIX_AUTO};
+std::atomic<int> g_contract_engine{CPR_CONTRACT_AUTO};
 }
 int cpr::mix_engine() { return g_mix_engine.load(); }
 
@@ -220,10 +225,31 @@ struct ProbSpec {
   double* user_lambda;
 };
 
-// Pick the sample split: enough (tile, split) blocks per mode update to give the GPU about two
+// SMs of the current device (queried once per device).
+int device_sms() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (!cache[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 148;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+// A schedule: how the iteration loop is launched and the tile parameters the autotuner chooses.
+struct Schedule {
+  int loop_path = 0;        // cpr_opts.loop_path values; 0: the automatic rule
+  int split_per_sm = 2;     // graph path: (tile, split) blocks per SM per mode update across the batch
+  int grid_min_split = 16;  // whole-GPU loop: fewest samples per contraction split
+};
+constexpr int kMaxSplitPerSM = 4;   // the workspace is sized for the finest split a schedule may use
+
+// Pick the sample split: enough (tile, split) blocks per mode update to give the GPU about per_sm
 // blocks per SM across the batch, between 16 and kMaxSplit samples per block.
-void choose_split(int B, int64_t imax_mean, int S, int* spl, int* nsplit) {
-  const int64_t target = std::max<int64_t>(1, (2 * 152) / std::max(1, B));
+void choose_split(int B, int64_t imax_mean, int S, int per_sm, int* spl, int* nsplit) {
+  const int64_t target = std::max<int64_t>(1, ((int64_t)per_sm * device_sms()) / std::max(1, B));
   const int64_t ntile = std::max<int64_t>(1, (imax_mean + kP1Rows - 1) / kP1Rows);
   const int64_t ns0 = (target + ntile - 1) / ntile;
   int64_t sp = (S + ns0 - 1) / ns0;
@@ -239,7 +265,7 @@ void choose_als_split(Prob& p, int n) {
   const int TI = mttkrp_tile_rows(p.als_rg, p.dtype), JT = mttkrp_tile_cols(p.als_rg, p.dtype);
   const int64_t I = p.dims[n], J = p.P / I;
   const int64_t rowtiles = (I + TI - 1) / TI;
-  int64_t ns = (152 * 8 + rowtiles - 1) / rowtiles;
+  int64_t ns = ((int64_t)device_sms() * 8 + rowtiles - 1) / rowtiles;
   const int64_t tiles = (J + JT - 1) / JT;
   ns = std::max<int64_t>(1, std::min(ns, tiles / 8));
   int64_t js = (J + ns - 1) / ns;
@@ -251,7 +277,10 @@ void choose_als_split(Prob& p, int n) {
 // Lays out (ws == nullptr: measures) the buffers of B problems.  mix: also the mixing buffers.
 // als: CP-ALS buffers (Grams, MTTKRP partials, unfolding copies of every mode when als_mode < 0,
 // else one copy buffer used for mode als_mode).
-Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws, int als = 0, int als_mode = -1) {
+Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws, int als = 0, int als_mode = -1,
+               const Schedule* sch = nullptr) {
+  const Schedule dflt;
+  if (!sch) sch = &dflt;
   Plan pl;
   pl.B = B;
   pl.mix = mix;
@@ -322,10 +351,14 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws, int als = 0, int
     }
     p.lambda = sp.user_lambda ? sp.user_lambda : cv.take<double>(R);
     if (S > 0) {
-      choose_split(B, isum / N, S, &p.spl, &p.nsplit);
-      p.Gpart = cv.take<double>((size_t)p.nsplit * R * R);
+      choose_split(B, isum / N, S, sch->split_per_sm, &p.spl, &p.nsplit);
+      int spl_most = 0, ns_most = 0;   // the finest split any schedule may pick sizes the buffers
+      choose_split(B, isum / N, S, kMaxSplitPerSM, &spl_most, &ns_most);
+      ns_most = std::max(ns_most, p.nsplit);
+      p.grid_min_split = sch->grid_min_split;
+      p.Gpart = cv.take<double>((size_t)ns_most * R * R);
       p.L = cv.take<double>((size_t)R * R);
-      p.Mpart = cv.take<unsigned char>((size_t)p.nsplit * imax * R * (f64 ? 8 : 4));
+      p.Mpart = cv.take<unsigned char>((size_t)ns_most * imax * R * (f64 ? 8 : 4));
       p.Npart = cv.take<double>((size_t)((imax + kP2Rows - 1) / kP2Rows) * R);
     }
     if (als) {
@@ -591,8 +624,88 @@ int enqueue_finalize(const Plan& pl, int maxN, cudaStream_t s, int64_t& launches
   return CPR_OK;
 }
 
+// ------------------------------------------------------------------------------------------------
+// Schedule autotuner: the tuned schedule of a problem bucket (dtype, order, batch size, mixing, and
+// per mode the largest extent, the largest rank and sample count of the batch, each bucketed) is
+// kept in a process-wide table, applied by every call with loop_path 0, and can be saved to and
+// loaded from a text file (one line per bucket: key, loop path, split per SM, grid minimum split,
+// milliseconds per outer iteration when it was tuned).  The environment variable CPRAND_TUNE_CACHE
+// names a file loaded on the first lookup.
+// ------------------------------------------------------------------------------------------------
+int ceil_log2(int64_t v) {
+  int k = 0;
+  while (((int64_t)1 << k) < v) ++k;
+  return k;
+}
+
+std::string tune_key(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, int mix) {
+  int64_t mx[CPR_MAX_ORDER] = {};
+  int R = 0;
+  int64_t S = 0;
+  for (int b = 0; b < B; ++b) {
+    for (int n = 0; n < Xs[b].order; ++n) mx[n] = std::max(mx[n], Xs[b].dims[n]);
+    R = std::max(R, Rs[b]);
+    S = std::max(S, Ss[b]);
+  }
+  std::string k = "d" + std::to_string(Xs[0].dtype) + ":N" + std::to_string(Xs[0].order) + ":B" +
+                  std::to_string(ceil_log2(B)) + ":m" + std::to_string(mix ? 1 : 0) + ":I";
+  for (int n = 0; n < Xs[0].order; ++n) k += (n ? "," : "") + std::to_string(ceil_log2(mx[n]));
+  k += ":R" + std::to_string((R + 7) / 8) + ":S" + std::to_string(ceil_log2(S));
+  return k;
+}
+
+struct TuneEntry {
+  Schedule sch;
+  double ms_per_iter;
+};
+
+struct TuneTable {
+  std::mutex mu;
+  std::map<std::string, TuneEntry> map;
+  bool env_loaded = false;
+};
+
+TuneTable& tune_table() {
+  static TuneTable t;
+  return t;
+}
+
+int tune_load_locked(TuneTable& t, const char* path) {
+  FILE* f = fopen(path, "r");
+  if (!f) return CPR_EINVAL;
+  char key[512];
+  int lp, sp, gm;
+  double ms;
+  while (fscanf(f, "%511s %d %d %d %lf", key, &lp, &sp, &gm, &ms) == 5) {
+    if (lp < 0 || lp > 5 || sp < 1 || sp > kMaxSplitPerSM || gm < 1 || gm > 1024) continue;
+    Schedule sc;
+    sc.loop_path = lp;
+    sc.split_per_sm = sp;
+    sc.grid_min_split = gm;
+    t.map[key] = TuneEntry{sc, ms};
+  }
+  fclose(f);
+  return CPR_OK;
+}
+
+bool tune_lookup(const std::string& key, Schedule* out, double* ms = nullptr) {
+  TuneTable& t = tune_table();
+  std::lock_guard<std::mutex> lk(t.mu);
+  if (!t.env_loaded) {
+    t.env_loaded = true;
+    const char* path = getenv("CPRAND_TUNE_CACHE");
+    if (path && *path) tune_load_locked(t, path);
+  }
+  auto it = t.map.find(key);
+  if (it == t.map.end()) return false;
+  *out = it->second.sch;
+  if (ms) *ms = it->second.ms_per_iter;
+  return true;
+}
+
 int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, const cpr_opts* opts, int mix,
-                cpr_ktensor* outs, cpr_result* results, void* ws, size_t ws_bytes, cudaStream_t s) {
+                cpr_ktensor* outs, cpr_result* results, void* ws, size_t ws_bytes, cudaStream_t s,
+                const Schedule* forced = nullptr) {
   if (B < 1 || !Xs || !Rs || !Ss || !outs) return CPR_EINVAL;
   std::vector<cpr_opts> op(B);
   std::vector<ProbSpec> specs(B);
@@ -612,9 +725,16 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
     specs[b] = ProbSpec{&Xs[b], Rs[b], Ss[b], op[b].fit_samples, &op[b], nullptr, nullptr};
     maxN = std::max(maxN, (int)Xs[b].order);
   }
-  const Plan measure = make_plan(B, specs.data(), mix, nullptr);
+  // the schedule: forced (autotuner trials), tuned for this bucket (loop_path 0), or the defaults
+  bool any_user = false;
+  for (int b = 0; b < B; ++b) any_user = any_user || op[b].user_samples != nullptr;
+  Schedule sch;
+  if (forced) sch = *forced;
+  else if (op[0].loop_path == 0 && !any_user && tune_lookup(tune_key(B, Xs, Rs, Ss, mix), &sch)) {}
+  else sch = Schedule{};
+  const Plan measure = make_plan(B, specs.data(), mix, nullptr, 0, -1, &sch);
   if (int st = check_ws(ws, ws_bytes, measure.bytes)) return st;
-  Plan pl = make_plan(B, specs.data(), mix, ws);
+  Plan pl = make_plan(B, specs.data(), mix, ws, 0, -1, &sch);
   CPR_CUDA(prepare_kernel_attributes());
   int64_t launches = 0;
   PhaseEvents ph;
@@ -670,8 +790,8 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
   // lives inside the loop (events need plain stream launches)
   const unsigned loop_classes = (1u << CPR_KERNEL_SAMPLE_SKR) | (1u << CPR_KERNEL_CONTRACT) | (1u << CPR_KERNEL_CHOL) |
                                 (1u << CPR_KERNEL_SOLVE) | (1u << CPR_KERNEL_NORMALIZE) | (1u << CPR_KERNEL_FIT);
-  const int path = op[0].loop_path;
-  if (path < 0 || path > 5) return CPR_EINVAL;
+  if (op[0].loop_path < 0 || op[0].loop_path > 5) return CPR_EINVAL;
+  const int path = (forced || op[0].loop_path == 0) ? sch.loop_path : op[0].loop_path;
   bool user_samples = false;
   for (int b = 0; b < B; ++b) user_samples = user_samples || op[b].user_samples != nullptr;
   // caller-given samples: the graph kernels, the plain stream launches and the whole-GPU loop read them
@@ -704,6 +824,7 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
     GridScratch gsc = pl.gscr;
     gsc.wait_limit = op[0].wait_budget > 0 ? (uint32_t)std::min<int64_t>(op[0].wait_budget, UINT32_MAX)
                                            : kDefaultWaitPolls;
+    gsc.use_tc = g_contract_engine.load() == CPR_CONTRACT_FMA ? 0 : 1;
     CPR_CUDA(cudaMemsetAsync(gsc.bar, 0, 4 * sizeof(unsigned), s));
     CPR_LAUNCH(CPR_KERNEL_LOOP, launch_grid_run(pl.d_probs, B, gsc, pl.dtype, pl.probs[0].R, grid_G, s));
     ncl = 1;   // the loop has run
@@ -1446,6 +1567,120 @@ int cpr_unmix_factors(const cpr_ktensor* Khat, cpr_ktensor* out, uint64_t seed, 
   if (Khat->lambda && out->lambda && Khat->lambda != out->lambda)
     CPR_CUDA(cudaMemcpyAsync(out->lambda, Khat->lambda, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
   return CPR_OK;
+}
+
+int cpr_cprand_mix_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, const cpr_opts* opts,
+                           cpr_ktensor* outs, cpr_result* results, void* ws, size_t ws_bytes, void* stream) {
+  return run_batched(B, Xs, Rs, Ss, opts, 1, outs, results, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int cpr_autotune(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, const cpr_opts* opts, int mix,
+                 cpr_ktensor* outs, void* ws, size_t ws_bytes, void* stream, int trial_iters, cpr_schedule* best) {
+  if (B < 1 || !Xs || !Rs || !Ss || !outs || trial_iters < 1) return CPR_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<cpr_opts> op(B);
+  for (int b = 0; b < B; ++b) {
+    op[b] = opts ? opts[b] : defaults();
+    if (!opts) op[b].batch_index = (uint32_t)b;
+    op[b].fixed_iters = trial_iters;     // the same iterations for every candidate
+    op[b].fit_trace_dev = nullptr;
+    op[b].user_samples = nullptr;
+    op[b].user_S = 0;
+  }
+  std::vector<cpr_result> res(B);
+  // candidates: the replicated / distributed clusters, the whole GPU with three split widths, the
+  // graph with three split densities (those that do not apply return CPR_EINVAL and are skipped)
+  std::vector<Schedule> cand;
+  Schedule c;
+  c.loop_path = 1; cand.push_back(c);
+  c.loop_path = 4; cand.push_back(c);
+  for (int gm : {16, 32, 64}) { c = Schedule{}; c.loop_path = 5; c.grid_min_split = gm; cand.push_back(c); }
+  for (int sp : {1, 2, 4}) { c = Schedule{}; c.loop_path = 2; c.split_per_sm = sp; cand.push_back(c); }
+  // warm-up (kernel loading), the default schedule
+  Schedule d;
+  if (int st = run_batched(B, Xs, Rs, Ss, op.data(), mix, outs, res.data(), ws, ws_bytes, s, &d)) return st;
+  double best_ms = INFINITY;
+  Schedule win;
+  for (const Schedule& sc : cand) {
+    const int st = run_batched(B, Xs, Rs, Ss, op.data(), mix, outs, res.data(), ws, ws_bytes, s, &sc);
+    if (st == CPR_EINVAL) continue;   // this engine does not take the batch
+    if (st != CPR_OK) return st;
+    bool ok = true;
+    int iters = 0;
+    for (int b = 0; b < B; ++b) {
+      ok = ok && res[b].status == CPR_OK;
+      iters = std::max(iters, (int)res[b].iters);
+    }
+    if (!ok || iters < 1) continue;
+    const double ms = res[0].ms_iterate / iters;
+    if (ms < best_ms) {
+      best_ms = ms;
+      win = sc;
+    }
+  }
+  if (!(best_ms < INFINITY)) return CPR_EINVAL;
+  {
+    TuneTable& t = tune_table();
+    std::lock_guard<std::mutex> lk(t.mu);
+    t.map[tune_key(B, Xs, Rs, Ss, mix)] = TuneEntry{win, best_ms};
+  }
+  if (best) {
+    best->loop_path = win.loop_path;
+    best->split_per_sm = win.split_per_sm;
+    best->grid_min_split = win.grid_min_split;
+    best->pad = 0;
+    best->ms_per_iter = best_ms;
+  }
+  return CPR_OK;
+}
+
+int cpr_tune_lookup(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, int mix, cpr_schedule* out) {
+  if (B < 1 || !Xs || !Rs || !Ss || !out) return CPR_EINVAL;
+  for (int b = 0; b < B; ++b)
+    if (check_tensor(&Xs[b], false)) return CPR_EINVAL;
+  Schedule sc;
+  double ms = 0.0;
+  if (!tune_lookup(tune_key(B, Xs, Rs, Ss, mix), &sc, &ms)) {
+    memset(out, 0, sizeof(*out));
+    return CPR_EINVAL;
+  }
+  out->loop_path = sc.loop_path;
+  out->split_per_sm = sc.split_per_sm;
+  out->grid_min_split = sc.grid_min_split;
+  out->pad = 0;
+  out->ms_per_iter = ms;
+  return CPR_OK;
+}
+
+int cpr_tune_save(const char* path) {
+  if (!path) return CPR_EINVAL;
+  TuneTable& t = tune_table();
+  std::lock_guard<std::mutex> lk(t.mu);
+  FILE* f = fopen(path, "w");
+  if (!f) return CPR_EINVAL;
+  for (const auto& kv : t.map)
+    fprintf(f, "%s %d %d %d %.17g\n", kv.first.c_str(), kv.second.sch.loop_path, kv.second.sch.split_per_sm,
+            kv.second.sch.grid_min_split, kv.second.ms_per_iter);
+  return fclose(f) == 0 ? CPR_OK : CPR_EINVAL;
+}
+
+int cpr_tune_load(const char* path) {
+  if (!path) return CPR_EINVAL;
+  TuneTable& t = tune_table();
+  std::lock_guard<std::mutex> lk(t.mu);
+  return tune_load_locked(t, path);
+}
+
+void cpr_tune_clear(void) {
+  TuneTable& t = tune_table();
+  std::lock_guard<std::mutex> lk(t.mu);
+  t.map.clear();
+  t.env_loaded = true;   // a cleared table stays empty until a load or a tuning run
+}
+
+int cpr_set_contract_engine(int engine) {
+  if (engine < CPR_CONTRACT_AUTO || engine > CPR_CONTRACT_FMA) return -1;
+  return g_contract_engine.exchange(engine);
 }
 
 int cpr_set_mix_engine(int engine) {

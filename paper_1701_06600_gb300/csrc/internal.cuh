@@ -99,12 +99,14 @@ struct Prob {
   // caller-given sample multi-indices (test hook): N x S x N uint32, entry ((n S + j) N + m) is
   // i_m of sample j of every mode-n update (the mode-n slot is ignored); null: Philox draws
   const uint32_t* user_idx;
+  int32_t grid_min_split;  // whole-GPU loop: fewest samples per contraction split (0: 16)
+  int32_t pad3;
 };
 
 // Global scratch and barrier words of the whole-GPU loop (k_grid.cu), carved from the workspace.
 constexpr int kGridMaxCTAs = 256;  // CTAs the scratch is sized for (one per SM)
 constexpr int kGridMaxRows = 32;   // factor rows a CTA solves per mode update (I_n <= 32 G)
-constexpr int kGridTileRows = 96;  // fiber rows of a contraction tile
+constexpr int kGridTileRows = 128; // most fiber rows of a contraction tile (sizes the partial M)
 constexpr uint32_t kDefaultWaitPolls = 1u << 22;   // polls of a bounded wait unless opts say otherwise
 struct GridScratch {
   double* Gpart;     // G x NE partial Grams (packed upper triangle)
@@ -115,6 +117,7 @@ struct GridScratch {
   unsigned* bar;     // [0] arrivals, [1] generation (zeroed before each launch)
   int* err;          // set when a barrier wait ran out
   uint32_t wait_limit;  // polls per barrier wait
+  int32_t use_tc;       // contraction on the tensor cores (1) or by FP32 FMA (0)
 };
 
 // ------------------------------------------------------------------------------------------------

@@ -46,6 +46,7 @@
 
 #include "internal.cuh"
 #include "small_spd.cuh"
+#include "tc_util.cuh"
 
 namespace cpr {
 
@@ -57,13 +58,15 @@ constexpr int kGramT = 128;              // threads of the Gram partial (warps 0
 constexpr int kCT = kGT - kGramT;        // contraction threads (warps 4-15)
 constexpr int kTI = 96;                  // fiber rows per contraction tile
 constexpr int kCG = kCT / kTI;           // column groups per tile row (4)
-constexpr int kSC = 256;                 // samples per super-chunk (Z_S rows staged in shared memory)
+constexpr int kSC = 128;                 // samples per super-chunk (Z_S rows staged in shared memory)
 constexpr int kXC = 32;                  // samples per fiber chunk
 constexpr int kXPT = kXC * kTI / kCT;    // fiber elements per contraction thread and chunk (8)
 constexpr int kGC = 32;                  // Gram samples per chunk
+constexpr int kTM = 128;                 // tensor-core contraction: fiber rows per unit (MMA M)
+constexpr int kTK = 32;                  // tensor-core contraction: samples per stage (128 bytes of FP32)
 constexpr int kNEMax = kMaxRank * (kMaxRank + 1) / 2;
 static_assert(kTI % 32 == 0 && kCT % kTI == 0 && (kXC * kTI) % kCT == 0, "tile shape");
-static_assert(kTI == kGridTileRows, "the workspace sizes Mpart for this tile height");
+static_assert(kTI <= kGridTileRows && kTM <= kGridTileRows, "the workspace sizes Mpart for the tile height");
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
@@ -100,14 +103,14 @@ template <typename T> __device__ __forceinline__ float gf(T v);
 template <> __device__ __forceinline__ float gf<float>(float v) { return v; }
 template <> __device__ __forceinline__ float gf<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// Shared-memory layout (byte offsets), computed identically on the host and the device.  The
-// solver region (G and the FP32 inverse) is written by warps 0-3 while warps 4-15 still use the P1
-// region, so the two do not overlap; the row-solve region (after the contraction) overlays P1.
+// Shared-memory layout (byte offsets), computed identically on the host and the device.  What is
+// used after the contraction (G, its FP32 inverse, the row solve) overlays the P1 region.
 struct GridSmem {
-  int G, sw;               // solver: R x R FP64 Gram; two R x R FP32 sweep buffers (the FP64
-                           // fallback inverse reuses them as one R x R FP64 matrix)
+  int G, sw;               // R x R FP64 Gram; two R x R FP32 sweep buffers (the FP64 fallback
+                           // inverse reuses them as one R x R FP64 matrix)
   int gids, Zd;            // P1, Gram warps
-  int cids, coffs, Zf, xs; // P1, contraction warps
+  int cids, coffs, Zf, xs; // P1, contraction warps (xs: SIMT fiber chunks)
+  int stage;               // P1, tensor-core stages (aligned to 1024 bytes at run time)
   int mrow, arow, m32;     // row solve (overlays P1)
   int fL, fT, fd;          // FP64 fallback factor and triangular inverse (overlay P1, not m32's use)
   int bytes;
@@ -120,17 +123,22 @@ __host__ __device__ inline GridSmem grid_layout(int R, int MAXR, int tbytes) {
   GridSmem L;
   L.ZP = MAXR;
   int o = 0;
-  L.G = o;     o = ga16(o + R * R * 8);
-  L.sw = o;    o = ga16(o + 2 * R * R * 4);
-  const int base = o;
+  // P1: Gram warps, contraction warps (the SIMT fiber chunks or the tensor-core stages)
   L.gids = o;  o = ga16(o + kGC * kMaxOrder * 4);
   L.Zd = o;    o = ga16(o + kGC * R * 8);
   L.cids = o;  o = ga16(o + kSC * kMaxOrder * 4);
   L.coffs = o; o = ga16(o + kSC * 8);
   L.Zf = o;    o = ga16(o + kSC * MAXR * 4);
-  L.xs = o;    o = ga16(o + 2 * kXC * kTI * tbytes);
-  const int p1 = o;
-  o = base;
+  L.xs = o;
+  const int simt_end = ga16(o + 2 * kXC * kTI * tbytes);
+  o = (o + 1023) / 1024 * 1024;          // + up to 1023 bytes of alignment of the dynamic base
+  L.stage = o;
+  const int tc_end = o + 1024 + 2 * (2 * kTM * kTK * 4 + 2 * MAXR * kTK * 4);
+  const int p1 = simt_end > tc_end ? simt_end : tc_end;
+  // after the contraction (overlays P1): G, the FP32 sweep buffers, the row solve
+  o = 0;
+  L.G = o;     o = ga16(o + R * R * 8);
+  L.sw = o;    o = ga16(o + 2 * R * R * 4);
   L.mrow = o;  o = ga16(o + kGridMaxRows * R * 8);
   L.arow = o;  o = ga16(o + kGridMaxRows * R * 8);
   const int u = o;
@@ -140,7 +148,7 @@ __host__ __device__ inline GridSmem grid_layout(int R, int MAXR, int tbytes) {
   L.fL = o;    o = ga16(o + R * R * 8);
   L.fT = o;    o = ga16(o + R * R * 8);
   L.fd = o;    o = ga16(o + R * 8);
-  int p3 = o > a ? o : a;
+  const int p3 = o > a ? o : a;
   L.bytes = p1 > p3 ? p1 : p3;
   return L;
 }
@@ -297,13 +305,14 @@ struct ModeSplit {
   int I, ntile, nsplit, spl, units, rpc;
 };
 
-__device__ __forceinline__ ModeSplit mode_split(const Prob& p, int n, int G) {
+__device__ __forceinline__ ModeSplit mode_split(const Prob& p, int n, int G, int tile_rows) {
   ModeSplit s;
   s.I = (int)p.dims[n];
-  s.ntile = (s.I + kTI - 1) / kTI;
+  s.ntile = (s.I + tile_rows - 1) / tile_rows;
   int ns = G / s.ntile;
   if (ns < 1) ns = 1;
-  const int most = (p.S + 15) / 16;   // at least 16 samples per split
+  const int mins = p.grid_min_split > 0 ? p.grid_min_split : 16;
+  const int most = (p.S + mins - 1) / mins;   // at least mins samples per split
   if (ns > most) ns = most;
   s.spl = (p.S + ns - 1) / ns;
   s.nsplit = (p.S + s.spl - 1) / s.spl;
@@ -446,16 +455,150 @@ __device__ void contract_units(const Prob& p, const GridSmem& L, unsigned char* 
   }
 }
 
+// ---- P1, contraction warps on the tensor cores: the same M_split = X_S Z_S for 128-row units.
+// Per stage of 32 samples the contraction warps write the unit's X_S tile (A: 128 rows x 32 samples)
+// and the Z_S rows (B: MAXR columns x 32 samples) into shared memory as TF32 hi / lo halves in the
+// swizzled K-major layout (each thread one row and four consecutive samples: the loads of a warp
+// read 32 consecutive fiber entries, its 16-byte stores hit distinct banks), and one thread issues
+// the MMAs hi*hi + hi*lo + lo*hi (lo*hi is exactly zero for BF16 tensors, whose values are TF32
+// values, and is skipped) into a 128 x MAXR FP32 accumulator in TMEM.  Two stages alternate; a stage
+// is rewritten once the MMAs that read it have completed (tcgen05.commit on its mbarrier).  After a
+// unit's last stage the four warps 4-7 read the accumulator (one row per TMEM lane) and store the
+// partial M column-major.  Every wait is bounded; one that runs out sets *s_tcerr, after which no
+// more MMAs are issued and the CTA waits (bounded) for the ones in flight.
+struct TcCtx {
+  uint64_t* bar;        // [0], [1]: stage MMAs complete
+  uint32_t tmem;        // accumulator base (128 lanes x MAXR columns)
+  unsigned char* st;    // stage buffers, 1024-byte aligned
+  uint32_t uses[2];     // commits made on each stage's mbarrier so far (uniform across the warps)
+  uint32_t limit;
+};
+
+template <typename T, int MAXR>
+__device__ void contract_units_tc(const Prob& p, const GridSmem& L, unsigned char* sm, const GridScratch& gs,
+                                  const GridCtx& x, int n, uint32_t t, const ModeSplit& ms, const float* scf,
+                                  TcCtx& tcx, volatile int* s_tcerr) {
+  constexpr int NT = MAXR;                       // MMA N (a multiple of 16)
+  constexpr int AH = kTM * kTK * 4;              // one A half: 16 KB
+  constexpr int BH = NT * kTK * 4;               // one B half
+  constexpr int STG = 2 * AH + 2 * BH;           // one stage
+  constexpr bool kLoA = sizeof(T) == 4;          // FP32 tensors need the A lo half
+  const int ct = threadIdx.x - kGramT;
+  const int R = p.R, ZP = L.ZP;
+  uint32_t* ids = reinterpret_cast<uint32_t*>(sm + L.cids);
+  int64_t* offs = reinterpret_cast<int64_t*>(sm + L.coffs);
+  float* Zf = reinterpret_cast<float*>(sm + L.Zf);
+  const T* __restrict__ X = reinterpret_cast<const T*>(p.Xrep[n]);
+  const int64_t stride = p.use_rep ? 1 : p.st[n];
+  const uint32_t idesc = tc::idesc_tf32(kTM, NT);
+  for (int u = x.c; u < ms.units; u += x.G) {
+    const int tile = u % ms.ntile, split = u / ms.ntile;
+    const int i0 = tile * kTM;
+    const int js = split * ms.spl;
+    const int cnt = min(ms.spl, p.S - js);
+    bool first = true;                           // the unit's first MMA overwrites the accumulator
+    for (int s0 = 0; s0 < cnt; s0 += kSC) {
+      const int scn = min(kSC, cnt - s0);
+      named_sync(2, kCT);                        // the previous super-chunk's ids and Z rows are free
+      for (int jj = ct; jj < scn; jj += kCT)
+        offs[jj] = grid_draw(p, n, t, (uint32_t)(js + s0 + jj), ids + jj * kMaxOrder);
+      named_sync(2, kCT);
+      build_rows<float>(p, n, ids, scn, scf, Zf, ZP, ct, kCT);
+      named_sync(2, kCT);
+      const int nch = (scn + kTK - 1) / kTK;
+      for (int k = 0; k < nch; ++k) {
+        const int sidx = (int)((tcx.uses[0] + tcx.uses[1]) & 1);   // alternate the stages
+        unsigned char* stg = tcx.st + sidx * STG;
+        // the stage's previous MMAs must be complete before it is rewritten
+        if (tcx.uses[sidx] > 0 && !*s_tcerr) {
+          if (!tc::mbar_wait(tcx.bar + sidx, (tcx.uses[sidx] - 1) & 1, tcx.limit) && ct == 0) *s_tcerr = 1;
+        }
+        // A: (row r, 4-sample chunk c) pairs; B: (column r, chunk c) pairs
+        for (int e = ct; e < kTM * (kTK / 4); e += kCT) {
+          const int r = e % kTM, c = e / kTM;
+          const int i = i0 + r;
+          float v[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int jj = k * kTK + 4 * c + q;
+            v[q] = (jj < scn && i < ms.I) ? gf<T>(X[offs[jj] + (int64_t)i * stride]) : 0.f;
+          }
+          float4 h, l;
+          h.x = tc::tf32_hi(v[0]); h.y = tc::tf32_hi(v[1]); h.z = tc::tf32_hi(v[2]); h.w = tc::tf32_hi(v[3]);
+          l.x = v[0] - h.x; l.y = v[1] - h.y; l.z = v[2] - h.z; l.w = v[3] - h.w;
+          const uint32_t off = tc::sw128_off(r, 4 * c);
+          *reinterpret_cast<float4*>(stg + off) = h;
+          if (kLoA) *reinterpret_cast<float4*>(stg + AH + off) = l;
+        }
+        for (int e = ct; e < NT * (kTK / 4); e += kCT) {
+          const int r = e % NT, c = e / NT;
+          float v[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int jj = k * kTK + 4 * c + q;
+            v[q] = jj < scn ? Zf[jj * ZP + r] : 0.f;
+          }
+          float4 h, l;
+          h.x = tc::tf32_hi(v[0]); h.y = tc::tf32_hi(v[1]); h.z = tc::tf32_hi(v[2]); h.w = tc::tf32_hi(v[3]);
+          l.x = v[0] - h.x; l.y = v[1] - h.y; l.z = v[2] - h.z; l.w = v[3] - h.w;
+          const uint32_t off = tc::sw128_off(r, 4 * c);
+          *reinterpret_cast<float4*>(stg + 2 * AH + off) = h;
+          *reinterpret_cast<float4*>(stg + 2 * AH + BH + off) = l;
+        }
+        tc::fence_async_smem();
+        named_sync(2, kCT);
+        if (ct == 0 && !*s_tcerr) {
+          tc::fence_after();
+          const uint32_t ah = tc::saddr(stg), al = ah + AH, bh = ah + 2 * AH, bl = bh + BH;
+#pragma unroll
+          for (int kk = 0; kk < kTK / 8; ++kk) {
+            const uint32_t o = kk * 32;
+            tc::mma_tf32(tcx.tmem, tc::sw128_desc(ah + o), tc::sw128_desc(bh + o), idesc, (first && kk == 0) ? 0u : 1u);
+            tc::mma_tf32(tcx.tmem, tc::sw128_desc(ah + o), tc::sw128_desc(bl + o), idesc, 1u);
+            if (kLoA) tc::mma_tf32(tcx.tmem, tc::sw128_desc(al + o), tc::sw128_desc(bh + o), idesc, 1u);
+          }
+          tc::commit(tcx.bar + sidx);
+        }
+        tcx.uses[sidx] += 1;                       // (every contraction thread keeps the same count)
+        first = false;
+      }
+    }
+    // the unit's MMAs are complete when the last commit's phase is
+    const int last = (int)((tcx.uses[0] + tcx.uses[1] + 1) & 1);
+    bool drained = tc::mbar_wait(tcx.bar + last, (tcx.uses[last] - 1) & 1, tcx.limit);
+    if (!drained && ct == 0) *s_tcerr = 1;
+    tc::fence_after();
+    // epilogue: warps 4-7 read TMEM lanes 32 (warp % 4) .. + 31, one row of the unit per lane
+    if (ct < 128) {
+      const int wq = (threadIdx.x >> 5) & 3;
+      const int i = i0 + 32 * wq + (threadIdx.x & 31);
+      float* dst = gs.Mpart + (int64_t)split * R * ms.I + i;
+#pragma unroll
+      for (int c0 = 0; c0 < NT; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tcx.tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)c0, v);
+        if (i < ms.I) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (c0 + q < R) dst[(int64_t)(c0 + q) * ms.I] = v[q];
+        }
+      }
+    }
+    tc::fence_before();
+    named_sync(2, kCT);                          // the accumulator is read before the next unit's MMAs
+  }
+}
+
 // Prefetch into L2 the fiber segments the contraction units of the next mode update will read.
 template <typename T>
-__device__ void prefetch_next(const Prob& p, const GridCtx& x, int n, uint32_t t, const ModeSplit& ms) {
+__device__ void prefetch_next(const Prob& p, const GridCtx& x, int n, uint32_t t, const ModeSplit& ms, int tile_rows) {
   const int ct = threadIdx.x - kGramT;
   const T* X = reinterpret_cast<const T*>(p.Xrep[n]);
   if (!(p.use_rep || n == 0)) return;   // strided fibers: nothing contiguous to prefetch
   for (int u = x.c; u < ms.units; u += x.G) {
     const int tile = u % ms.ntile, split = u / ms.ntile;
-    const int i0 = tile * kTI;
-    const int rows = min(kTI, ms.I - i0);
+    const int i0 = tile * tile_rows;
+    const int rows = min(tile_rows, ms.I - i0);
     const int js = split * ms.spl;
     const int cnt = min(ms.spl, p.S - js);
     const int lines = rows * (int)sizeof(T) / 128 + 2;   // 128-byte lines a row segment can touch
@@ -540,47 +683,48 @@ __device__ bool sweep_inverse(float* sw, int R, const unsigned char* ne_r, const
   return !bad;
 }
 
-// ---- solver warps (threads 0 .. kGramT-1), after the Gram is reduced: G from the packed triangle,
-// the Jacobi scales dsc_r = 1 / sqrt(G_rr), and the FP32 inverse X0 of the scaled Gram (G^-1 ~ D X0 D)
-// in buffer R & 1 of sw.  Returns whether the FP32 inverse is usable (identical in every CTA).
-template <int MAXR>
+// ---- after the Gram is reduced, by the NT threads of block barrier bar_id: G from the packed
+// triangle, the Jacobi scales dsc_r = 1 / sqrt(G_rr), and the FP32 inverse X0 of the scaled Gram
+// (G^-1 ~ D X0 D) in buffer R & 1 of sw.  Returns whether the FP32 inverse is usable (identical in
+// every CTA).
+template <int MAXR, int NT>
 __device__ bool solver_prepare(const Prob& p, const GridSmem& L, unsigned char* sm, const GridScratch& gs,
-                               double* dsc, const unsigned char* ne_r, const unsigned char* ne_c) {
+                               double* dsc, const unsigned char* ne_r, const unsigned char* ne_c, int bar_id) {
   const int tid = threadIdx.x, R = p.R, RR = R * R;
   const int NE = R * (R + 1) / 2;
   double* G = reinterpret_cast<double*>(sm + L.G);
   float* sw = reinterpret_cast<float*>(sm + L.sw);
-  constexpr int GPT = (MAXR * (MAXR + 1) / 2 + kGramT - 1) / kGramT;
+  constexpr int GPT = (MAXR * (MAXR + 1) / 2 + NT - 1) / NT;
   double gv[GPT];
 #pragma unroll
   for (int q = 0; q < GPT; ++q) {       // every load in flight before the stores
-    const int e = tid + q * kGramT;
+    const int e = tid + q * NT;
     gv[q] = e < NE ? __ldcg(gs.Gfull + e) : 0.0;
   }
 #pragma unroll
   for (int q = 0; q < GPT; ++q) {
-    const int e = tid + q * kGramT;
+    const int e = tid + q * NT;
     if (e < NE) {
       const int r = ne_r[e], cc = ne_c[e];
       G[r * R + cc] = gv[q];
       G[cc * R + r] = gv[q];
     }
   }
-  named_sync(1, kGramT);
+  named_sync(bar_id, NT);
   bool good = true;
-  for (int r = tid; r < R; r += kGramT) {
+  for (int r = tid; r < R; r += NT) {
     const double d = G[r * R + r];
     good = good && d > 0.0 && isfinite(d);
     dsc[r] = (d > 0.0 && isfinite(d)) ? rsqrt64(d) : 0.0;
   }
-  const bool fast = named_and(1, kGramT, good);   // the same in every solver thread
+  const bool fast = named_and(bar_id, NT, good);   // the same in every thread
   // the scaled FP32 copy (the FP32 start only needs FP32 accuracy)
-  for (int e = tid; e < RR; e += kGramT) {
+  for (int e = tid; e < RR; e += NT) {
     const int r = e / R, cc = e - r * R;
     sw[e] = (float)G[e] * (float)dsc[r] * (float)dsc[cc];
   }
-  named_sync(1, kGramT);
-  return fast && sweep_inverse<MAXR, kGramT>(sw, R, ne_r, ne_c, 1);
+  named_sync(bar_id, NT);
+  return fast && sweep_inverse<MAXR, NT>(sw, R, ne_r, ne_c, bar_id);
 }
 
 // ---- all threads, after the contraction: this CTA's rows of A^(n) = M G^-1 (Alg. 3 least-squares
@@ -704,12 +848,37 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
   __shared__ int s_flag, s_flag2, s_done, s_status, s_iter, s_stall, s_fast, s_abort;
   __shared__ unsigned s_umax[2];
   __shared__ double s_best, s_last;
+  __shared__ __align__(8) uint64_t tc_bar[2];
+  __shared__ uint32_t tc_slot;
+  __shared__ volatile int s_tcerr;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   GridCtx x;
   x.gen = 0u;
   x.G = (int)gridDim.x;
   x.c = (int)blockIdx.x;
-  for (int b = 0; b < B; ++b) {
+  // the tensor-core contraction: two stage mbarriers and a TMEM accumulator of 128 lanes x MAXR
+  // columns (allocated by warp 4, freed by it when the kernel ends)
+  const bool use_tc = gs.use_tc != 0;
+  constexpr uint32_t kTmemCols = MAXR <= 32 ? 32u : 64u;
+  TcCtx tcx;
+  tcx.uses[0] = tcx.uses[1] = 0u;
+  tcx.limit = gs.wait_limit;
+  if (use_tc) {
+    if (tid == 0) {
+      tc::mbar_init(&tc_bar[0], 1);
+      tc::mbar_init(&tc_bar[1], 1);
+      s_tcerr = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) tc::tmem_alloc(&tc_slot, kTmemCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    tcx.bar = tc_bar;
+    tcx.tmem = tc_slot;
+  }
+  bool quit = false;
+  for (int b = 0; b < B && !quit; ++b) {
     {
       const int words = (int)(sizeof(Prob) / 4);
       const uint32_t* src = reinterpret_cast<const uint32_t*>(probs + b);
@@ -720,6 +889,7 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
     const Prob& p = P;
     const int R = p.R, N = p.N;
     const GridSmem L = grid_layout(R, MAXR, (int)sizeof(T));
+    tcx.st = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(sm + L.stage) + 1023) & ~(uintptr_t)1023);
     State* st = p.state;
     if (tid == 0) {
       int e = 0;
@@ -750,7 +920,7 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
       const uint32_t t = p.t0 + (uint32_t)s_iter;
       bool singular = false;
       for (int n = 0; n < N; ++n) {
-        const ModeSplit ms = mode_split(p, n, x.G);
+        const ModeSplit ms = mode_split(p, n, x.G, use_tc ? kTM : kTI);
         // combined lazy scale of the other modes
         for (int r = tid; r < R; r += kGT) {
           double cmb = 1.0;
@@ -761,7 +931,7 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
         }
         __syncthreads();
         // ---- P1: warps 0-3 Gram partial, grid barrier among themselves (A), their slice of the
-        // reduced Gram, grid barrier (B), G and its FP32 inverse; meanwhile warps 4-15 contract
+        // reduced Gram, grid barrier (B); meanwhile warps 4-15 contract
         if (tid < kGramT) {
           gram_partial<MAXR>(p, L, sm, gs, x, n, t, scomb, ne_r, ne_c);
           bool gok = grid_sync(gs, x, &s_flag, 1, kGramT);
@@ -776,23 +946,26 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
             }
             gok = grid_sync(gs, x, &s_flag, 1, kGramT);
           }
-          if (gok) {
-            const bool f = solver_prepare<MAXR>(p, L, sm, gs, dsc, ne_r, ne_c);
-            if (tid == 0) s_fast = f ? 1 : 0;
-          } else if (tid == 0) {
-            s_abort = 1;
-          }
+          if (!gok && tid == 0) s_abort = 1;
         } else {
-          contract_units<T, MAXR>(p, L, sm, gs, x, n, t, ms, scf);
+          if (use_tc) {
+            contract_units_tc<T, MAXR>(p, L, sm, gs, x, n, t, ms, scf, tcx, &s_tcerr);
+            if (s_tcerr && threadIdx.x == kGramT) atomicExch(gs.err, 1);   // every CTA stops at a barrier
+          } else {
+            contract_units<T, MAXR>(p, L, sm, gs, x, n, t, ms, scf);
+          }
           const int nn = n + 1 < N ? n + 1 : 0;
           const uint32_t nt = n + 1 < N ? t : t + 1;
-          prefetch_next<T>(p, x, nn, nt, mode_split(p, nn, x.G));
+          prefetch_next<T>(p, x, nn, nt, mode_split(p, nn, x.G, use_tc ? kTM : kTI), use_tc ? kTM : kTI);
         }
         __syncthreads();
         if (s_abort) {
           alive = false;
           break;
         }
+        // G and its FP32 inverse by every warp (an issue-bound chain of R block barriers: it runs
+        // after the contraction, not beside it)
+        const bool fast = solver_prepare<MAXR, kGT>(p, L, sm, gs, dsc, ne_r, ne_c, 0);
         if (!(alive = grid_sync(gs, x, &s_flag))) break;   // (C) every split's partial M is stored
         // ---- P3: the split partials of this CTA's rows, then A = M G^-1
         {
@@ -820,7 +993,7 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
           }
         }
         __syncthreads();
-        const bool ok = solve_rows<MAXR>(p, L, sm, x, ms, dsc, s_fast != 0, &s_flag2, s_umax);
+        const bool ok = solve_rows<MAXR>(p, L, sm, x, ms, dsc, fast, &s_flag2, s_umax);
         {
           const double* arow = reinterpret_cast<const double*>(sm + L.arow);
           const int i0 = x.c * ms.rpc;
@@ -958,7 +1131,10 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
       }
       __syncthreads();
     }
-    if (!alive) return;   // a barrier wait ran out (the error flag is set); nothing is in flight
+    if (!alive) {         // a barrier wait ran out (the error flag is set); no copy or MMA is in flight
+      quit = true;
+      break;
+    }
     // publish the loop state, lambda and the lazy scales (CTA 0)
     if (x.c == 0) {
       for (int e = tid; e < N * R; e += kGT) p.scale[e / R][e % R] = sc[e];
@@ -973,7 +1149,19 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
       }
     }
     // the next problem reuses the scratch: every CTA leaves this one first
-    if (!grid_sync(gs, x, &s_flag)) return;
+    if (!grid_sync(gs, x, &s_flag)) quit = true;
+  }
+  if (use_tc) {
+    // every MMA has completed (each unit waited for its last commit); after a wait that ran out, wait
+    // again (bounded) for the last phase of each stage before the accumulator is freed
+    if (s_tcerr && warp >= 4) {
+      for (int sidx = 0; sidx < 2; ++sidx)
+        if (tcx.uses[sidx] > 0) tc::mbar_wait(&tc_bar[sidx], (tcx.uses[sidx] - 1) & 1, 1u << 26);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 4) tc::tmem_free(tcx.tmem, kTmemCols);
   }
 }
 

@@ -41,8 +41,16 @@ CASES = [
 ]
 
 
+@pytest.fixture(params=["tc", "fma"])
+def contract(cb, request):
+    """Runs a test with each contraction engine of the whole-GPU loop (tensor cores, FP32 FMA)."""
+    prev = cb.cpr_set_contract_engine(cb.CONTRACT_TC if request.param == "tc" else cb.CONTRACT_FMA)
+    yield request.param
+    cb.cpr_set_contract_engine(prev)
+
+
 @pytest.mark.parametrize("dims,R,S,dtype,mix", CASES)
-def test_grid_loop_matches_oracle(cb, dims, R, S, dtype, mix):
+def test_grid_loop_matches_oracle(cb, contract, dims, R, S, dtype, mix):
     prob = make_problem(dims, min(R, 8), C=0.5, eta=0.01, seed=301, dtype=dtype, device=DEV)
     T = to_oracle_array(prob.X, dims)
     iters = 3
@@ -64,7 +72,7 @@ def test_grid_loop_matches_oracle(cb, dims, R, S, dtype, mix):
     assert rel(out["lam"].cpu().numpy(), ref["lam"]) < 1e-4
 
 
-def test_grid_loop_rank_64_matches_oracle(cb):
+def test_grid_loop_rank_64_matches_oracle(cb, contract):
     # the widest column groups (R = 64): a tensor of true rank 64 with orthogonal factors and a start
     # near the truth, so that every sampled Gram is well conditioned and the 1e-4 bar measures the
     # kernel, not the amplification of FP32 rounding by an ill-conditioned least-squares problem
