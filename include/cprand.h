@@ -148,9 +148,10 @@ typedef struct {
 
 /* Contraction engine of the whole-GPU loop (loop_path 5; process-wide, applies to calls enqueued
  * afterwards): CPR_CONTRACT_AUTO and CPR_CONTRACT_TC compute M = X_S Z_S (Alg. 3) on the tensor cores
- * (tcgen05, kind::tf32, each FP32 operand split into TF32 halves: hi*hi + hi*lo + lo*hi accumulated
- * in FP32 in TMEM, about 2^-20 relative per product; BF16 tensor values are exact TF32 values, so
- * their lo*hi term is zero and is skipped); CPR_CONTRACT_FMA by FP32 FMA.  Returns the previous
+ * (tcgen05, kind::tf32, each FP32 operand split into two TF32 values rounded to nearest,
+ * hi = tf32(x) and lo = tf32(x - hi): hi*hi + hi*lo + lo*hi accumulated in FP32 in TMEM, about
+ * 3 * 2^-22 relative per product; BF16 tensor values are exact TF32 values, so their lo*hi term is
+ * zero and is skipped); CPR_CONTRACT_FMA by FP32 FMA.  Returns the previous
  * engine, or -1 (nothing changed) for an unknown value. */
 enum { CPR_CONTRACT_AUTO = 0, CPR_CONTRACT_TC = 1, CPR_CONTRACT_FMA = 2 };
 CPR_API int cpr_set_contract_engine(int engine);

@@ -299,10 +299,10 @@ Plan make_plan(int B, const ProbSpec* specs, int mix, void* ws, int als = 0, int
     int64_t imax = 1;
     for (int n = 0; n < specs[0].X->order; ++n) imax = std::max<int64_t>(imax, specs[0].X->dims[n]);
     GridScratch& g = pl.gscr;
-    g.Gpart = cv.take<double>((size_t)kGridMaxCTAs * NE);
-    g.Gfull = cv.take<double>((size_t)NE);
+    g.Gpart = cv.take<float2>((size_t)kGridMaxCTAs * NE);
+    g.Gfull = cv.take<float2>((size_t)NE);
     g.Mpart = cv.take<float>((size_t)std::max<int64_t>((int64_t)kGridMaxCTAs * kGridTileRows, imax) * R);
-    g.Npart = cv.take<double>((size_t)kGridMaxCTAs * R);
+    g.Npart = cv.take<float2>((size_t)kGridMaxCTAs * R);
     g.fitpart = cv.take<double>((size_t)kGridMaxCTAs);
     g.bar = cv.take<unsigned>(4);
     g.err = reinterpret_cast<int*>(g.bar + 2);

@@ -109,10 +109,10 @@ constexpr int kGridMaxRows = 32;   // factor rows a CTA solves per mode update (
 constexpr int kGridTileRows = 128; // most fiber rows of a contraction tile (sizes the partial M)
 constexpr uint32_t kDefaultWaitPolls = 1u << 22;   // polls of a bounded wait unless opts say otherwise
 struct GridScratch {
-  double* Gpart;     // G x NE partial Grams (packed upper triangle)
-  double* Gfull;     // NE
+  float2* Gpart;     // G x NE partial Grams (packed upper triangle; FP32 pairs hi + lo)
+  float2* Gfull;     // NE (pairs)
   float* Mpart;      // nsplit x R x I_n partial M (column-major per split)
-  double* Npart;     // G x R column sums of squares
+  float2* Npart;     // G x R column sums of squares (pairs)
   double* fitpart;   // G partial fit sums
   unsigned* bar;     // [0] arrivals, [1] generation (zeroed before each launch)
   int* err;          // set when a barrier wait ran out

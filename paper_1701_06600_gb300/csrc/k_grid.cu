@@ -64,6 +64,7 @@ constexpr int kXPT = kXC * kTI / kCT;    // fiber elements per contraction threa
 constexpr int kGC = 32;                  // Gram samples per chunk
 constexpr int kTM = 128;                 // tensor-core contraction: fiber rows per unit (MMA M)
 constexpr int kTK = 32;                  // tensor-core contraction: samples per stage (128 bytes of FP32)
+constexpr int kPPT = (kTM * (kTK / 4) + kCT - 1) / kCT;   // (row, 4-sample) pairs per contraction thread and stage
 constexpr int kNEMax = kMaxRank * (kMaxRank + 1) / 2;
 static_assert(kTI % 32 == 0 && kCT % kTI == 0 && (kXC * kTI) % kCT == 0, "tile shape");
 static_assert(kTI <= kGridTileRows && kTM <= kGridTileRows, "the workspace sizes Mpart for the tile height");
@@ -106,23 +107,28 @@ template <> __device__ __forceinline__ float gf<__nv_bfloat16>(__nv_bfloat16 v) 
 // Shared-memory layout (byte offsets), computed identically on the host and the device.  What is
 // used after the contraction (G, its FP32 inverse, the row solve) overlays the P1 region.
 struct GridSmem {
-  int G, sw;               // R x R FP64 Gram; two R x R FP32 sweep buffers (the FP64 fallback
-                           // inverse reuses them as one R x R FP64 matrix)
+  int g2, x0, piv, dp;     // S: G as pairs (the FP64 fallback's inverse reuses it), Gs then X0 in place
+                           // (FP32), the sweep's published pivot entries, the Jacobi scales D'
   int gids, Zd;            // P1, Gram warps
   int cids, coffs, Zf, xs; // P1, contraction warps (xs: SIMT fiber chunks)
   int stage;               // P1, tensor-core stages (aligned to 1024 bytes at run time)
-  int mrow, arow, m32;     // row solve (overlays P1)
-  int fL, fT, fd;          // FP64 fallback factor and triangular inverse (overlay P1, not m32's use)
+  int mrow, m32, a2;       // P3 (overlays P1): M rows as pairs, FP32 scratch, A rows as pairs
+  int G, fL, fT, fd, arow; // P3, FP64 fallback: G, Cholesky factor, triangular inverse, A rows
   int bytes;
   int ZP;                  // Zf row pitch (MAXR)
 };
-
 __host__ __device__ inline int ga16(int x) { return (x + 15) / 16 * 16; }
 
+// S is written by the Gram warps while the contraction warps use P1, and read by the row solve (P3)
 __host__ __device__ inline GridSmem grid_layout(int R, int MAXR, int tbytes) {
   GridSmem L;
   L.ZP = MAXR;
   int o = 0;
+  L.g2 = o;    o = ga16(o + R * R * 8);
+  L.x0 = o;    o = ga16(o + R * R * 4);
+  L.piv = o;   o = ga16(o + 4 * 64 * 4);
+  L.dp = o;    o = ga16(o + MAXR * 4);
+  const int s_end = o;
   // P1: Gram warps, contraction warps (the SIMT fiber chunks or the tensor-core stages)
   L.gids = o;  o = ga16(o + kGC * kMaxOrder * 4);
   L.Zd = o;    o = ga16(o + kGC * R * 8);
@@ -135,20 +141,17 @@ __host__ __device__ inline GridSmem grid_layout(int R, int MAXR, int tbytes) {
   L.stage = o;
   const int tc_end = o + 1024 + 2 * (2 * kTM * kTK * 4 + 2 * MAXR * kTK * 4);
   const int p1 = simt_end > tc_end ? simt_end : tc_end;
-  // after the contraction (overlays P1): G, the FP32 sweep buffers, the row solve
-  o = 0;
-  L.G = o;     o = ga16(o + R * R * 8);
-  L.sw = o;    o = ga16(o + 2 * R * R * 4);
+  // P3, after the contraction (overlays P1): the row solve; the FP64 fallback's scratch behind it
+  o = s_end;
   L.mrow = o;  o = ga16(o + kGridMaxRows * R * 8);
-  L.arow = o;  o = ga16(o + kGridMaxRows * R * 8);
-  const int u = o;
   L.m32 = o;   o = ga16(o + kGridMaxRows * R * 4);
-  const int a = o;
-  o = u;
+  L.a2 = o;    o = ga16(o + kGridMaxRows * R * 8);
+  L.G = o;     o = ga16(o + R * R * 8);
   L.fL = o;    o = ga16(o + R * R * 8);
   L.fT = o;    o = ga16(o + R * R * 8);
   L.fd = o;    o = ga16(o + R * 8);
-  const int p3 = o > a ? o : a;
+  L.arow = o;  o = ga16(o + kGridMaxRows * R * 8);
+  const int p3 = o;
   L.bytes = p1 > p3 ? p1 : p3;
   return L;
 }
@@ -194,6 +197,69 @@ __device__ __forceinline__ bool grid_sync(const GridScratch& gs, GridCtx& x, int
   return *s_flag != 0;
 }
 
+// ---- FP64-class quantities as unevaluated pairs of FP32 values, x = hi + lo.  On this part the FP64
+// units run at about 1/75 of the FP32 rate (conversions between FP32 and FP64 included), so the
+// Gram, M, the residual of the row solve and the column norms are carried as pairs and combined by
+// error-free transformations: Dekker's exact product (a b = p + e, e by one FMA) and Knuth's two-sum
+// (a + b = s + e).  A sum of pair products keeps about 2^-44 of the sum of the terms' magnitudes.
+// Rounding-mode intrinsics keep the compiler from contracting or reordering these steps.
+
+// x as a pair (hi = x rounded to FP32, lo = the remainder rounded: |x - hi - lo| <= 2^-48 |x|)
+__device__ __forceinline__ float2 split_pair(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+__device__ __forceinline__ double pair_value(float2 a) { return (double)a.x + (double)a.y; }
+
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+// the pair (hi, lo) renormalized so that hi = fl(hi + lo)
+__device__ __forceinline__ float2 pair_norm(float hi, float lo) {
+  float s, e;
+  two_sum(hi, lo, s, e);
+  return make_float2(s, e);
+}
+// (sh, sl) += b for an FP32 value b
+__device__ __forceinline__ void pair_acc(float b, float& sh, float& sl) {
+  float s, e;
+  two_sum(sh, b, s, e);
+  sh = s;
+  sl = __fadd_rn(sl, e);
+}
+// (sh, sl) += b for a pair b
+__device__ __forceinline__ void pair_acc2(float2 b, float& sh, float& sl) {
+  float s, e;
+  two_sum(sh, b.x, s, e);
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(e, b.y));
+}
+// a * b for a pair a and an FP32 value b
+__device__ __forceinline__ float2 pair_mul_f(float2 a, float b) {
+  const float p = __fmul_rn(a.x, b);
+  const float e = __fmaf_rn(a.x, b, -p);
+  return make_float2(p, __fmaf_rn(a.y, b, e));
+}
+// a * b for pairs (a.lo b.lo, below 2^-48 of the product, dropped)
+__device__ __forceinline__ float2 pair_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  const float e = __fmaf_rn(a.x, b.x, -p);
+  return pair_norm(p, __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, e)));
+}
+// (sh, sl) += a * g for pairs a, g: the exact product of the high parts plus the two cross terms
+__device__ __forceinline__ void pair_fma(float2 a, float2 g, float& sh, float& sl) {
+  const float p = __fmul_rn(a.x, g.x);
+  const float pe = __fmaf_rn(a.x, g.x, -p);
+  const float cr = __fmaf_rn(a.x, g.y, __fmul_rn(a.y, g.x));
+  float s, err;
+  two_sum(sh, p, s, err);
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, __fadd_rn(pe, cr)));
+}
+
 // out[j] = sum over i < rows of src[i * stride + j] for j < cols (cols <= 64), from global scratch
 // written by other CTAs: the rows are split into at most 32 chunks, each thread sums one (chunk,
 // column) pair with its loads in flight together, and the chunk partials are then added in chunk
@@ -237,6 +303,41 @@ __device__ void sum_rows(const double* src, int rows, int cols, int64_t stride, 
   named_sync(bar_id, nthr);
 }
 
+// The same fixed-order sum over rows for pair-valued entries (src: rows x cols pairs, row stride
+// `stride`); out: cols pairs; part: scratch of nthr pairs.
+__device__ void sum_pairs(const float2* src, int rows, int cols, int64_t stride, float2* out, float2* part,
+                          int bar_id = 0, int nthr = kGT) {
+  const int tid = threadIdx.x;
+  int cp = 1;
+  while (cp < cols) cp <<= 1;
+  const int nch = min(nthr / cp, 32);
+  const int j = tid % cp, q = tid / cp;
+  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+  if (j < cols && q < nch) {
+    const int per = (rows + nch - 1) / nch;
+    const int r0 = q * per, r1 = min(rows, r0 + per);
+    int i = r0;
+    for (; i + 3 < r1; i += 4) {
+      const float2 v0 = __ldcg(src + (int64_t)i * stride + j), v1 = __ldcg(src + (int64_t)(i + 1) * stride + j);
+      const float2 v2 = __ldcg(src + (int64_t)(i + 2) * stride + j), v3 = __ldcg(src + (int64_t)(i + 3) * stride + j);
+      pair_acc2(v0, h0, l0);
+      pair_acc2(v1, h1, l1);
+      pair_acc2(v2, h0, l0);
+      pair_acc2(v3, h1, l1);
+    }
+    for (; i < r1; ++i) pair_acc2(__ldcg(src + (int64_t)i * stride + j), h0, l0);
+    pair_acc2(make_float2(h1, l1), h0, l0);
+  }
+  if (q < nch) part[q * cp + j] = make_float2(h0, l0);
+  named_sync(bar_id, nthr);
+  if (tid < cols) {
+    float h = 0.f, l = 0.f;
+    for (int qq = 0; qq < nch; ++qq) pair_acc2(part[qq * cp + tid], h, l);
+    out[tid] = pair_norm(h, l);
+  }
+  named_sync(bar_id, nthr);
+}
+
 // Sample j of mode update (n, t): indices by mode (mode-n slot 0) and the fiber's storage offset
 // in the copy mode n reads (Philox stream 0, counter (j, n, t, b); the k-th mode other than n takes
 // word k%4 of block k/4; i_m = floor(w I_m / 2^32)).  With a caller sample table (test hook), the
@@ -270,30 +371,32 @@ __device__ __forceinline__ int64_t grid_draw(const Prob& p, int n, uint32_t t, u
 // by nthr threads (a multiple of 64; t = this thread's index among them): thread t takes column
 // t % 64 of every (nthr / 64)-th sample, and the factor-row loads of 8 samples of one mode are
 // issued together (L2-resident rows: the latency, not the bandwidth, is what these loads cost).
-template <typename OUT>
+template <typename OUT, int KB = 8>
 __device__ __forceinline__ void build_rows(const Prob& p, int n, const uint32_t* ids, int cnt, const OUT* pre,
                                            OUT* out, int pitch, int t, int nthr) {
+  // thread t: column r = t % 64 of samples t / 64 + k (nthr / 64), k < KB per round; every factor
+  // row entry of a round is loaded before any is used
   const int R = p.R, N = p.N;
   const int r = t & 63, lanes = nthr >> 6;
   if (r >= pitch) return;
-  for (int b = t >> 6; b < cnt; b += 8 * lanes) {
-    OUT z[8];
+  for (int b = t >> 6; b < cnt; b += KB * lanes) {
+    OUT z[KB];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) z[k] = r < R ? pre[r] : OUT(0);
+    for (int k = 0; k < KB; ++k) z[k] = r < R ? pre[r] : OUT(0);
     for (int m = 0; m < N; ++m) {
       if (m == n) continue;
       const float* Am = p.A32[m];
-      float v[8];
+      float v[KB];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < KB; ++k) {
         const int jj = b + k * lanes;
         v[k] = (jj < cnt && r < R) ? __ldcg(Am + (int64_t)ids[jj * kMaxOrder + m] * R + r) : 1.f;
       }
 #pragma unroll
-      for (int k = 0; k < 8; ++k) z[k] *= (OUT)v[k];
+      for (int k = 0; k < KB; ++k) z[k] *= (OUT)v[k];
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < KB; ++k) {
       const int jj = b + k * lanes;
       if (jj < cnt) out[jj * pitch + r] = z[k];
     }
@@ -321,51 +424,79 @@ __device__ __forceinline__ ModeSplit mode_split(const Prob& p, int n, int G, int
   return s;
 }
 
-// ---- P1, Gram warps: partial Z_S^T Z_S over this CTA's samples (packed upper triangle), FP64.
+// ---- P1, Gram warps: partial Z'^T Z' over this CTA's samples (packed upper triangle) as pairs,
+// where Z' are the sampled Khatri-Rao rows of the FP32 factor copies without the lazy column scales
+// (Z_S = Z' Sc, so Z_S^T Z_S = Sc (Z'^T Z') Sc: the scales are applied to the reduced Gram).  A Z'
+// entry is the product of N - 1 FP32 values, exact as a pair for N = 3.
+__device__ __forceinline__ void build_pairs(const Prob& p, int n, const uint32_t* ids, int cnt, float2* out, int pitch,
+                                            int t, int nthr) {
+  const int R = p.R, N = p.N;
+  const int r = t & 63, lanes = nthr >> 6;
+  if (r >= pitch) return;
+  constexpr int KB = kGC / (kGramT / 64);   // the chunk's samples in one round of loads
+  for (int b = t >> 6; b < cnt; b += KB * lanes) {
+    float2 z[KB];
+#pragma unroll
+    for (int k = 0; k < KB; ++k) z[k] = make_float2(1.f, 0.f);
+    for (int m = 0; m < N; ++m) {
+      if (m == n) continue;
+      const float* Am = p.A32[m];
+      float v[KB];
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        const int jj = b + k * lanes;
+        v[k] = (jj < cnt && r < R) ? __ldcg(Am + (int64_t)ids[jj * kMaxOrder + m] * R + r) : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < KB; ++k) z[k] = pair_mul_f(z[k], v[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      const int jj = b + k * lanes;
+      if (jj < cnt) out[jj * pitch + r] = z[k];
+    }
+  }
+}
+
 template <int MAXR>
 __device__ void gram_partial(const Prob& p, const GridSmem& L, unsigned char* sm, const GridScratch& gs,
-                             const GridCtx& x, int n, uint32_t t, const double* scomb, const unsigned char* ne_r,
-                             const unsigned char* ne_c) {
-  constexpr int EPT = (MAXR * (MAXR + 1) / 2 + kGramT - 1) / kGramT;   // packed entries per thread (at most)
-  const int tid = threadIdx.x, R = p.R, N = p.N, S = p.S;
+                             const GridCtx& x, int n, uint32_t t, const unsigned char* ne_r, const unsigned char* ne_c) {
+  const int tid = threadIdx.x, R = p.R, S = p.S;
   const int NE = R * (R + 1) / 2;
   const int gpc = (S + x.G - 1) / x.G;
   const int j0 = x.c * gpc;
   const int jn = min(S, j0 + gpc);
   uint32_t* ids = reinterpret_cast<uint32_t*>(sm + L.gids);
-  double* Zd = reinterpret_cast<double*>(sm + L.Zd);
-  double acc[EPT];
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) acc[q] = 0.0;
+  float2* Zp = reinterpret_cast<float2*>(sm + L.Zd);
+  float2* dst = gs.Gpart + (int64_t)x.c * NE;
   for (int c0 = j0; c0 < jn; c0 += kGC) {
     const int cnt = min(kGC, jn - c0);
     if (tid < cnt) grid_draw(p, n, t, (uint32_t)(c0 + tid), ids + tid * kMaxOrder);
     named_sync(1, kGramT);
-    build_rows<double>(p, n, ids, cnt, scomb, Zd, R, tid, kGramT);
+    build_pairs(p, n, ids, cnt, Zp, R, tid, kGramT);
     named_sync(1, kGramT);
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int e = tid + q * kGramT;
-      if (q * kGramT < NE && e < NE) {
-        const int r = ne_r[e], cc = ne_c[e];
-        double a0 = acc[q], a1 = 0.0;
-        int jj = 0;
-        for (; jj + 1 < cnt; jj += 2) {
-          a0 = fma(Zd[jj * R + r], Zd[jj * R + cc], a0);
-          a1 = fma(Zd[(jj + 1) * R + r], Zd[(jj + 1) * R + cc], a1);
-        }
-        if (jj < cnt) a0 = fma(Zd[jj * R + r], Zd[jj * R + cc], a0);
-        acc[q] = a0 + a1;
+    // one entry at a time, its sum over the chunk's samples in two interleaved pair accumulators
+    for (int e = tid; e < NE; e += kGramT) {
+      const int r = ne_r[e], cc = ne_c[e];
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+      if (c0 > j0) {
+        const float2 prev = dst[e];   // this thread's own earlier chunk
+        h0 = prev.x;
+        l0 = prev.y;
       }
+      int jj = 0;
+      for (; jj + 1 < cnt; jj += 2) {
+        pair_fma(Zp[jj * R + r], Zp[jj * R + cc], h0, l0);
+        pair_fma(Zp[(jj + 1) * R + r], Zp[(jj + 1) * R + cc], h1, l1);
+      }
+      if (jj < cnt) pair_fma(Zp[jj * R + r], Zp[jj * R + cc], h0, l0);
+      pair_acc2(make_float2(h1, l1), h0, l0);
+      dst[e] = pair_norm(h0, l0);
     }
     named_sync(1, kGramT);
   }
-  double* dst = gs.Gpart + (int64_t)x.c * NE;
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const int e = tid + q * kGramT;
-    if (q * kGramT < NE && e < NE) dst[e] = acc[q];
-  }
+  if (j0 >= jn)
+    for (int e = tid; e < NE; e += kGramT) dst[e] = make_float2(0.f, 0.f);
 }
 
 // ---- P1, contraction warps: M_split(tile rows, :) = X_S Z_S over the unit's samples, FP32.
@@ -503,9 +634,26 @@ __device__ void contract_units_tc(const Prob& p, const GridSmem& L, unsigned cha
       for (int jj = ct; jj < scn; jj += kCT)
         offs[jj] = grid_draw(p, n, t, (uint32_t)(js + s0 + jj), ids + jj * kMaxOrder);
       named_sync(2, kCT);
-      build_rows<float>(p, n, ids, scn, scf, Zf, ZP, ct, kCT);
+      build_rows<float, (kSC + kCT / 64 - 1) / (kCT / 64)>(p, n, ids, scn, scf, Zf, ZP, ct, kCT);
       named_sync(2, kCT);
       const int nch = (scn + kTK - 1) / kTK;
+      // the X_S values of a chunk: thread ct takes (row r, 4-sample group c) pairs e = ct + u kCT; all
+      // of a chunk's loads are issued together, as soon as the previous chunk's values are converted
+      float va[kPPT][4];
+      auto load_chunk = [&](int k, float (&v)[kPPT][4]) {
+#pragma unroll
+        for (int u = 0; u < kPPT; ++u) {
+          const int e = ct + u * kCT;
+          const int r = e % kTM, c = e / kTM;
+          const int i = i0 + r;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int jj = k * kTK + 4 * c + q;
+            v[u][q] = (e < kTM * (kTK / 4) && jj < scn && i < ms.I) ? gf<T>(X[offs[jj] + (int64_t)i * stride]) : 0.f;
+          }
+        }
+      };
+      load_chunk(0, va);
       for (int k = 0; k < nch; ++k) {
         const int sidx = (int)((tcx.uses[0] + tcx.uses[1]) & 1);   // alternate the stages
         unsigned char* stg = tcx.st + sidx * STG;
@@ -514,22 +662,22 @@ __device__ void contract_units_tc(const Prob& p, const GridSmem& L, unsigned cha
           if (!tc::mbar_wait(tcx.bar + sidx, (tcx.uses[sidx] - 1) & 1, tcx.limit) && ct == 0) *s_tcerr = 1;
         }
         // A: (row r, 4-sample chunk c) pairs; B: (column r, chunk c) pairs
-        for (int e = ct; e < kTM * (kTK / 4); e += kCT) {
-          const int r = e % kTM, c = e / kTM;
-          const int i = i0 + r;
-          float v[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int jj = k * kTK + 4 * c + q;
-            v[q] = (jj < scn && i < ms.I) ? gf<T>(X[offs[jj] + (int64_t)i * stride]) : 0.f;
+        for (int u = 0; u < kPPT; ++u) {
+          const int e = ct + u * kCT;
+          if (e < kTM * (kTK / 4)) {
+            const int r = e % kTM, c = e / kTM;
+            float4 h, l;
+            h.x = tc::tf32_round(va[u][0]); h.y = tc::tf32_round(va[u][1]);
+            h.z = tc::tf32_round(va[u][2]); h.w = tc::tf32_round(va[u][3]);
+            l.x = tc::tf32_round(va[u][0] - h.x); l.y = tc::tf32_round(va[u][1] - h.y);
+            l.z = tc::tf32_round(va[u][2] - h.z); l.w = tc::tf32_round(va[u][3] - h.w);
+            const uint32_t off = tc::sw128_off(r, 4 * c);
+            *reinterpret_cast<float4*>(stg + off) = h;
+            if (kLoA) *reinterpret_cast<float4*>(stg + AH + off) = l;
           }
-          float4 h, l;
-          h.x = tc::tf32_hi(v[0]); h.y = tc::tf32_hi(v[1]); h.z = tc::tf32_hi(v[2]); h.w = tc::tf32_hi(v[3]);
-          l.x = v[0] - h.x; l.y = v[1] - h.y; l.z = v[2] - h.z; l.w = v[3] - h.w;
-          const uint32_t off = tc::sw128_off(r, 4 * c);
-          *reinterpret_cast<float4*>(stg + off) = h;
-          if (kLoA) *reinterpret_cast<float4*>(stg + AH + off) = l;
         }
+        if (k + 1 < nch) load_chunk(k + 1, va);   // in flight through the B stores and the MMAs
         for (int e = ct; e < NT * (kTK / 4); e += kCT) {
           const int r = e % NT, c = e / NT;
           float v[4];
@@ -539,8 +687,9 @@ __device__ void contract_units_tc(const Prob& p, const GridSmem& L, unsigned cha
             v[q] = jj < scn ? Zf[jj * ZP + r] : 0.f;
           }
           float4 h, l;
-          h.x = tc::tf32_hi(v[0]); h.y = tc::tf32_hi(v[1]); h.z = tc::tf32_hi(v[2]); h.w = tc::tf32_hi(v[3]);
-          l.x = v[0] - h.x; l.y = v[1] - h.y; l.z = v[2] - h.z; l.w = v[3] - h.w;
+          h.x = tc::tf32_round(v[0]); h.y = tc::tf32_round(v[1]); h.z = tc::tf32_round(v[2]); h.w = tc::tf32_round(v[3]);
+          l.x = tc::tf32_round(v[0] - h.x); l.y = tc::tf32_round(v[1] - h.y);
+          l.z = tc::tf32_round(v[2] - h.z); l.w = tc::tf32_round(v[3] - h.w);
           const uint32_t off = tc::sw128_off(r, 4 * c);
           *reinterpret_cast<float4*>(stg + 2 * AH + off) = h;
           *reinterpret_cast<float4*>(stg + 2 * AH + BH + off) = l;
@@ -568,13 +717,14 @@ __device__ void contract_units_tc(const Prob& p, const GridSmem& L, unsigned cha
     bool drained = tc::mbar_wait(tcx.bar + last, (tcx.uses[last] - 1) & 1, tcx.limit);
     if (!drained && ct == 0) *s_tcerr = 1;
     tc::fence_after();
-    // epilogue: warps 4-7 read TMEM lanes 32 (warp % 4) .. + 31, one row of the unit per lane
-    if (ct < 128) {
-      const int wq = (threadIdx.x >> 5) & 3;
+    // epilogue: warp w (4..15) reads TMEM lanes 32 (w % 4) .. + 31 (one row of the unit per lane), the
+    // three warps of a lane quarter taking every third group of 16 columns
+    {
+      const int w = threadIdx.x >> 5;
+      const int wq = w & 3, grp = (w - 4) >> 2;
       const int i = i0 + 32 * wq + (threadIdx.x & 31);
       float* dst = gs.Mpart + (int64_t)split * R * ms.I + i;
-#pragma unroll
-      for (int c0 = 0; c0 < NT; c0 += 16) {
+      for (int c0 = 16 * grp; c0 < NT && c0 < R; c0 += 48) {   // uniform in the warp
         float v[16];
         tc::tmem_ld16(tcx.tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)c0, v);
         if (i < ms.I) {
@@ -614,164 +764,177 @@ __device__ void prefetch_next(const Prob& p, const GridCtx& x, int n, uint32_t t
   }
 }
 
-// X0 ~ Gs^-1 in FP32 for the Jacobi-scaled Gram Gs (unit diagonal) by the sweep operator: pivot k
-// maps A to A' with A'_ij = A_ij - A_ik A_kj / A_kk (i, j != k), A'_ik = A_ik / A_kk, A'_kk = -1 / A_kk;
-// after every pivot A = -Gs^-1.  A stays symmetric, so each of the NT threads updates its fixed
-// entries of the packed upper triangle (row and column looked up once; all of a step's loads are
-// issued before its stores) and writes both mirror positions
-// of the next buffer; two R x R buffers alternate (one block barrier per pivot).  A pivot below 1e-6
-// (relative to the unit diagonal) or not finite returns false in every thread.  The result (negated
-// back) is left in buffer R & 1.
-template <int EPT, int NT>
-__device__ __forceinline__ void sweep_step(const float* o, float* w, int R, int k, float inv, const int* eij, int NE) {
-  const int tid = threadIdx.x;
-  const float* ok = o + k * R;     // row k (= column k)
-  // the entries in groups of eight: every operand of a group first, then its updates, so that the
-  // stores into w do not hold back the loads from o
-  constexpr int GQ = 8;
+// X0 ~ Gs^-1 in FP32 for the Jacobi-scaled Gram Gs (unit diagonal) by the sweep operator, two pivots
+// at a time: sweeping on the index pair K = {k, k+1} with the 2 x 2 block P = A_KK maps A to A' with
+// A'_ij = A_ij - A_iK P^-1 A_Kj (i, j not in K), A'_iK = A_iK P^-1, A'_Kj = P^-1 A_Kj, A'_KK = -P^-1,
+// the same as sweeping on k and then on k+1 (P^-1 is formed from those two pivots, a and
+// p2 = A_(k+1)(k+1) - A_k(k+1)^2 / a); after every step A = -Gs^-1.  The matrix lives in the
+// registers of W warps (W = 1 for R <= 32, 2 for R <= 64): thread j (0 <= j < PAD = 32 W) holds column
+// j, padded past R with the identity (for an odd R the last step pivots on the unit entry of
+// column R, which leaves the rest unchanged).  A stays symmetric, so rows K are columns K: each
+// thread publishes its two row-K entries to shared memory for the others (one barrier per step,
+// two alternating slot sets).  The rows rotate by two positions per step so that every register
+// index is static: before step k/2, position p holds row (p + k) mod PAD, rows K are positions 0
+// and 1, and the entries of row i go to slot (i - k - 2) mod PAD, where the update of the row's next
+// position reads them.  The columns K take A'_iK = A_iK - A_iK (I - P^-1) from the same fused update
+// (their own entries are the published ones).  A pivot below 1e-6 (relative to the unit diagonal) or
+// not finite returns false in every thread.  src: Gs (R x R, FP32); dst: X0 (may be src: every read
+// precedes the first barrier); piv: 4 PAD floats of scratch (16-byte aligned); bar_id: a block
+// barrier for the PAD threads when W = 2.
+template <int W>
+__device__ __noinline__ bool sweep_regs(const float* src, float* dst, int R, float* piv, int j, int bar_id) {
+  constexpr int PAD = 32 * W;
+  float r[PAD];
 #pragma unroll
-  for (int q0 = 0; q0 < EPT; q0 += GQ) {
-    float aik[GQ], akj[GQ], aij[GQ];
-#pragma unroll
-    for (int u = 0; u < GQ; ++u) {
-      const int q = q0 + u;
-      if (q < EPT) {
-        const int i = eij[q] >> 8, j = eij[q] & 255;
-        aik[u] = ok[i];
-        akj[u] = ok[j];
-        aij[u] = o[i * R + j];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < GQ; ++u) {
-      const int q = q0 + u;
-      if (q < EPT && q * NT + tid < NE) {
-        const int i = eij[q] >> 8, j = eij[q] & 255;
-        float v;
-        if (i == k && j == k) v = -inv;
-        else if (i == k) v = akj[u] * inv;
-        else if (j == k) v = aik[u] * inv;
-        else v = fmaf(-aik[u] * inv, akj[u], aij[u]);
-        w[i * R + j] = v;
-        w[j * R + i] = v;
-      }
-    }
-  }
-}
-
-template <int MAXR, int NT>
-__device__ bool sweep_inverse(float* sw, int R, const unsigned char* ne_r, const unsigned char* ne_c, int bar_id) {
-  constexpr int EPT = (MAXR * (MAXR + 1) / 2 + NT - 1) / NT;
-  const int tid = threadIdx.x;
-  const int RR = R * R, NE = R * (R + 1) / 2;
-  int eij[EPT];   // (row << 8) | column of this thread's packed entries
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const int e = tid + q * NT;
-    eij[q] = e < NE ? ((int)ne_r[e] << 8) | ne_c[e] : 0;
-  }
+  for (int p = 0; p < PAD; ++p) r[p] = (p < R && j < R) ? src[p * R + j] : (j >= R && p == j ? 1.f : 0.f);
   bool bad = false;
-  for (int k = 0; k < R; ++k) {
-    const float d = sw[(k & 1) * RR + k * R + k];
-    bad = bad || !(d > 1e-6f) || !isfinite(d);
-    sweep_step<EPT, NT>(sw + (k & 1) * RR, sw + ((k + 1) & 1) * RR, R, k, __frcp_rn(d), eij, NE);
-    named_sync(bar_id, NT);
+  const int steps = (R + 1) >> 1;
+  for (int st = 0; st < steps; ++st) {
+    const int k = 2 * st;
+    float* u = piv + (st & 1) * 2 * PAD;      // row-k entries, then row-(k+1) entries
+    float* v = u + PAD;
+    const int slot = (j - k - 2) & (PAD - 1);
+    const float x0 = r[0], x1 = r[1];
+    u[slot] = x0;
+    v[slot] = x1;
+    if (W == 1) __syncwarp();
+    else named_sync(bar_id, PAD);
+    const float a = u[PAD - 2], b = u[PAD - 1], d = v[PAD - 1];   // P = [a b; b d]
+    const float ia = __frcp_rn(a), t = b * ia;
+    const float p2 = fmaf(-b, t, d);
+    bad = bad || !(a > 1e-6f) || !(p2 > 1e-6f) || !isfinite(a) || !isfinite(p2);
+    const float ip2 = __frcp_rn(p2);
+    const float m11 = ip2, m01 = -t * ip2, m00 = fmaf(t, t * ip2, ia);   // P^-1 = [m00 m01; m01 m11]
+    float c0, c1, n0, n1;
+    if (j == k) {
+      c0 = 1.f - m00; c1 = -m01; n0 = -m00; n1 = -m01;
+    } else if (j == k + 1) {
+      c0 = -m01; c1 = 1.f - m11; n0 = -m01; n1 = -m11;
+    } else {
+      c0 = fmaf(m00, x0, m01 * x1); c1 = fmaf(m01, x0, m11 * x1); n0 = c0; n1 = c1;
+    }
+#pragma unroll
+    for (int p = 0; p < PAD; p += 4) {
+      const float4 qu = *reinterpret_cast<const float4*>(u + p);
+      const float4 qv = *reinterpret_cast<const float4*>(v + p);
+      r[p] = fmaf(-qv.x, c1, fmaf(-qu.x, c0, r[p + 2]));
+      r[p + 1] = fmaf(-qv.y, c1, fmaf(-qu.y, c0, r[p + 3]));
+      if (p + 4 < PAD) {
+        r[p + 2] = fmaf(-qv.z, c1, fmaf(-qu.z, c0, r[p + 4]));
+        r[p + 3] = fmaf(-qv.w, c1, fmaf(-qu.w, c0, r[p + 5]));
+      }
+    }
+    r[PAD - 2] = n0;                           // the new rows K, now at the last positions
+    r[PAD - 1] = n1;
   }
-  float* res = sw + (R & 1) * RR;
-  for (int e = tid; e < RR; e += NT) res[e] = -res[e];
-  named_sync(bar_id, NT);
+  if (W == 1) __syncwarp();
+  else named_sync(bar_id, PAD);
+  if (j < R) {
+    const int rot = 2 * steps;
+#pragma unroll
+    for (int p = 0; p < PAD; ++p) {
+      const int row = (p + rot) & (PAD - 1);
+      if (row < R) dst[row * R + j] = -r[p];
+    }
+  }
   return !bad;
 }
 
-// ---- after the Gram is reduced, by the NT threads of block barrier bar_id: G from the packed
-// triangle, the Jacobi scales dsc_r = 1 / sqrt(G_rr), and the FP32 inverse X0 of the scaled Gram
-// (G^-1 ~ D X0 D) in buffer R & 1 of sw.  Returns whether the FP32 inverse is usable (identical in
-// every CTA).
+// ---- after the Gram is reduced, by the NT threads of block barrier bar_id: G = Sc G' Sc as pairs in
+// g2 (R x R; G' the reduced Gram of the unscaled rows, Sc the lazy column scales of the other modes),
+// the Jacobi-scaled FP32 copy Gs = D' G' D' (D' = diag(1 / sqrt(G'_rr)), unit diagonal) in x0, and
+// the scales of the row solve ds_r = D'_rr / Sc_rr, so that G^-1 ~ Ds X0 Ds for X0 ~ Gs^-1
+// (they only precondition the refinement, whose residual uses G itself).  Returns whether every
+// diagonal entry is positive and finite (identical in every CTA): else the FP32 start is skipped.
 template <int MAXR, int NT>
-__device__ bool solver_prepare(const Prob& p, const GridSmem& L, unsigned char* sm, const GridScratch& gs,
-                               double* dsc, const unsigned char* ne_r, const unsigned char* ne_c, int bar_id) {
+__device__ bool solver_prepare(const Prob& p, const GridSmem& L, unsigned char* sm, const GridScratch& gs, float* ds,
+                               const float2* scp, const unsigned char* ne_r, const unsigned char* ne_c, int bar_id) {
   const int tid = threadIdx.x, R = p.R, RR = R * R;
   const int NE = R * (R + 1) / 2;
-  double* G = reinterpret_cast<double*>(sm + L.G);
-  float* sw = reinterpret_cast<float*>(sm + L.sw);
+  float2* g2 = reinterpret_cast<float2*>(sm + L.g2);
+  float* sw = reinterpret_cast<float*>(sm + L.x0);
+  float* dp = reinterpret_cast<float*>(sm + L.dp);
   constexpr int GPT = (MAXR * (MAXR + 1) / 2 + NT - 1) / NT;
-  double gv[GPT];
+  float2 gv[GPT];
 #pragma unroll
   for (int q = 0; q < GPT; ++q) {       // every load in flight before the stores
     const int e = tid + q * NT;
-    gv[q] = e < NE ? __ldcg(gs.Gfull + e) : 0.0;
+    gv[q] = e < NE ? __ldcg(gs.Gfull + e) : make_float2(0.f, 0.f);
   }
 #pragma unroll
   for (int q = 0; q < GPT; ++q) {
     const int e = tid + q * NT;
     if (e < NE) {
       const int r = ne_r[e], cc = ne_c[e];
-      G[r * R + cc] = gv[q];
-      G[cc * R + r] = gv[q];
+      g2[r * R + cc] = gv[q];
+      g2[cc * R + r] = gv[q];
     }
   }
   named_sync(bar_id, NT);
   bool good = true;
   for (int r = tid; r < R; r += NT) {
-    const double d = G[r * R + r];
-    good = good && d > 0.0 && isfinite(d);
-    dsc[r] = (d > 0.0 && isfinite(d)) ? rsqrt64(d) : 0.0;
+    const float d = g2[r * R + r].x;
+    const bool ok = d > 0.f && isfinite(d);
+    good = good && ok;
+    const float y = ok ? rsqrtf(d) : 0.f;
+    dp[r] = y;
+    ds[r] = y / scp[r].x;
   }
   const bool fast = named_and(bar_id, NT, good);   // the same in every thread
-  // the scaled FP32 copy (the FP32 start only needs FP32 accuracy)
   for (int e = tid; e < RR; e += NT) {
     const int r = e / R, cc = e - r * R;
-    sw[e] = (float)G[e] * (float)dsc[r] * (float)dsc[cc];
+    const float2 g = g2[e];
+    sw[e] = g.x * dp[r] * dp[cc];
+    g2[e] = pair_mul(pair_mul(g, scp[r]), scp[cc]);
   }
   named_sync(bar_id, NT);
-  return fast && sweep_inverse<MAXR, NT>(sw, R, ne_r, ne_c, bar_id);
+  return fast;
 }
 
 // ---- all threads, after the contraction: this CTA's rows of A^(n) = M G^-1 (Alg. 3 least-squares
-// step through the FP64 normal equations) from mrow (M rows, FP64).  fast: the FP32 inverse is usable
-// (refinement path); else the FP64 Cholesky inverse, which also decides singularity.  Returns false
-// if the Gram is singular.
+// step through the normal equations) from mrow (M rows as pairs) into a2 (pairs).  fast: the FP32
+// inverse is usable: A0 = ((M Ds) X0) Ds, then refinement steps A += (M - A G) Ds X0 Ds with the
+// residual summed in pairs; else the FP64 Cholesky inverse, which also decides singularity.  Returns
+// false if the Gram is singular.
 template <int MAXR>
 __device__ bool solve_rows(const Prob& p, const GridSmem& L, unsigned char* sm, const GridCtx& x,
-                           const ModeSplit& ms, const double* dsc, bool fast, int* s_flag, unsigned* s_umax) {
+                           const ModeSplit& ms, const float* ds, bool fast, int* s_flag, unsigned* s_umax) {
   const int tid = threadIdx.x, R = p.R, RR = R * R;
-  const double* G = reinterpret_cast<const double*>(sm + L.G);
-  const double* mrow = reinterpret_cast<const double*>(sm + L.mrow);
-  double* arow = reinterpret_cast<double*>(sm + L.arow);
-  float* sw = reinterpret_cast<float*>(sm + L.sw);
+  const float2* g2 = reinterpret_cast<const float2*>(sm + L.g2);
+  const float2* mrow = reinterpret_cast<const float2*>(sm + L.mrow);
+  float2* a2 = reinterpret_cast<float2*>(sm + L.a2);
   float* m32 = reinterpret_cast<float*>(sm + L.m32);
-  const float* X0 = sw + (R & 1) * RR;   // X0(r, c), scaled: G^-1 ~ D X0 D
+  const float* X0 = reinterpret_cast<const float*>(sm + L.x0);   // X0(r, c), scaled: G^-1 ~ Ds X0 Ds
   const int i0 = x.c * ms.rpc;
   const int nrows = max(0, min(ms.I, i0 + ms.rpc) - i0);
   const int NO = nrows * R;
   if (!fast) {
-    // FP64 Cholesky inverse (also the singularity test) into the sweep buffers, then A = M G^-1
-    double* X = reinterpret_cast<double*>(sw);
+    // G in FP64, its FP64 Cholesky inverse (also the singularity test) over the pairs of G (read out
+    // first), then A = M G^-1 in FP64
+    double* G = reinterpret_cast<double*>(sm + L.G);
+    for (int e = tid; e < RR; e += kGT) G[e] = pair_value(g2[e]);
+    double* X = reinterpret_cast<double*>(sm + L.g2);
     if (tid == 0) *s_flag = 0;
     __syncthreads();
     spd_inverse_fp64(G, X, reinterpret_cast<double*>(sm + L.fL), reinterpret_cast<double*>(sm + L.fT),
                      reinterpret_cast<double*>(sm + L.fd), R, s_flag);
+    __syncthreads();
     const bool singular = *s_flag != 0;
+    double* arow = reinterpret_cast<double*>(sm + L.arow);
     for (int e = tid; e < NO; e += kGT) {
       const int li = e / R, cc = e - li * R;
-      const double* m = mrow + li * R;
-      double a0 = 0.0, a1 = 0.0;
-      int l = 0;
-      for (; l + 1 < R; l += 2) {
-        a0 = fma(m[l], X[l * R + cc], a0);
-        a1 = fma(m[l + 1], X[(l + 1) * R + cc], a1);
-      }
-      if (l < R) a0 = fma(m[l], X[l * R + cc], a0);
-      arow[e] = a0 + a1;
+      const float2* m = mrow + li * R;
+      double a0 = 0.0;
+      for (int l = 0; l < R; ++l) a0 = fma(pair_value(m[l]), X[l * R + cc], a0);
+      arow[e] = a0;
     }
+    __syncthreads();
+    for (int e = tid; e < NO; e += kGT) a2[e] = split_pair(arow[e]);
     __syncthreads();
     return !singular;
   }
-  // A0 = ((M D) X0) D in FP32
-  for (int e = tid; e < NO; e += kGT) {
-    const int r = e % R;
-    m32[e] = (float)(mrow[e] * dsc[r]);
-  }
+  // A0 = ((M Ds) X0) Ds in FP32
+  for (int e = tid; e < NO; e += kGT) m32[e] = mrow[e].x * ds[e % R];
   __syncthreads();
   for (int e = tid; e < NO; e += kGT) {
     const int li = e / R, cc = e - li * R;
@@ -783,23 +946,19 @@ __device__ bool solve_rows(const Prob& p, const GridSmem& L, unsigned char* sm, 
       a1 = fmaf(m[l + 1], X0[(l + 1) * R + cc], a1);
     }
     if (l < R) a0 = fmaf(m[l], X0[l * R + cc], a0);
-    arow[e] = (double)(a0 + a1) * dsc[cc];
+    a2[e] = make_float2((a0 + a1) * ds[cc], 0.f);
   }
   __syncthreads();
-  // refinement: residual M - A G in FP64, correction through the FP32 inverse
+  // refinement: the residual M - A G summed in pairs from -M (to about 2^-44 of its terms), the
+  // correction through the FP32 inverse, added to A as a pair
   for (int it = 0; it < 3; ++it) {
     if (tid == 0) s_umax[0] = s_umax[1] = 0u;
     for (int e = tid; e < NO; e += kGT) {
       const int li = e / R, cc = e - li * R;
-      const double* a = arow + li * R;
-      double s0 = 0.0, s1 = 0.0;
-      int l = 0;
-      for (; l + 1 < R; l += 2) {
-        s0 = fma(a[l], G[l * R + cc], s0);
-        s1 = fma(a[l + 1], G[(l + 1) * R + cc], s1);
-      }
-      if (l < R) s0 = fma(a[l], G[l * R + cc], s0);
-      m32[e] = (float)((mrow[e] - (s0 + s1)) * dsc[cc]);
+      const float2* a = a2 + li * R;
+      float sh = -mrow[e].x, sl = -mrow[e].y;
+      for (int l = 0; l < R; ++l) pair_fma(a[l], g2[l * R + cc], sh, sl);
+      m32[e] = -__fadd_rn(sh, sl) * ds[cc];
     }
     __syncthreads();
     float cm = 0.f, am = 0.f;
@@ -813,11 +972,13 @@ __device__ bool solve_rows(const Prob& p, const GridSmem& L, unsigned char* sm, 
         a1 = fmaf(m[l + 1], X0[(l + 1) * R + cc], a1);
       }
       if (l < R) a0 = fmaf(m[l], X0[l * R + cc], a0);
-      const double corr = (double)(a0 + a1) * dsc[cc];
-      const double a = arow[e] + corr;
-      arow[e] = a;
-      cm = fmaxf(cm, fabsf((float)corr));
-      am = fmaxf(am, fabsf((float)a));
+      const float corr = (a0 + a1) * ds[cc];
+      float2 a = a2[e];
+      pair_acc(corr, a.x, a.y);
+      a = pair_norm(a.x, a.y);
+      a2[e] = a;
+      cm = fmaxf(cm, fabsf(corr));
+      am = fmaxf(am, fabsf(a.x));
     }
     cm = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(cm)));
     am = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(am)));
@@ -840,12 +1001,16 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ Prob P;
   __shared__ double sc[kMaxOrder * kMaxRank];
-  __shared__ double lam[kMaxRank], scomb[kMaxRank], dsc[kMaxRank];
+  __shared__ double lam[kMaxRank];
+  __shared__ float ds[kMaxRank];
+  __shared__ float2 scp[kMaxRank];
   __shared__ float scf[kMaxRank], wrf[kMaxRank];
   __shared__ double red[kGW];
   __shared__ double red64[kMaxRank], redp[kGT];
+  float2* red2 = reinterpret_cast<float2*>(red64);   // the pair-valued sums reuse them
+  float2* redp2 = reinterpret_cast<float2*>(redp);
   __shared__ unsigned char ne_r[kNEMax], ne_c[kNEMax];
-  __shared__ int s_flag, s_flag2, s_done, s_status, s_iter, s_stall, s_fast, s_abort;
+  __shared__ int s_flag, s_flag2, s_done, s_status, s_iter, s_stall, s_fast, s_abort, s_invbad, s_gfast;
   __shared__ unsigned s_umax[2];
   __shared__ double s_best, s_last;
   __shared__ __align__(8) uint64_t tc_bar[2];
@@ -908,6 +1073,8 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
     if (tid == 0) {
       s_fast = 0;
       s_abort = 0;
+      s_invbad = 0;
+      s_gfast = 0;
     }
     for (int e = tid; e < N * R; e += kGT) sc[e] = p.scale[e / R][e % R];
     for (int r = tid; r < R; r += kGT) lam[r] = p.lambda[r];
@@ -926,14 +1093,14 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
           double cmb = 1.0;
           for (int m = 0; m < N; ++m)
             if (m != n) cmb *= sc[m * R + r];
-          scomb[r] = cmb;
+          scp[r] = split_pair(cmb);
           scf[r] = (float)cmb;
         }
         __syncthreads();
         // ---- P1: warps 0-3 Gram partial, grid barrier among themselves (A), their slice of the
         // reduced Gram, grid barrier (B); meanwhile warps 4-15 contract
         if (tid < kGramT) {
-          gram_partial<MAXR>(p, L, sm, gs, x, n, t, scomb, ne_r, ne_c);
+          gram_partial<MAXR>(p, L, sm, gs, x, n, t, ne_r, ne_c);
           bool gok = grid_sync(gs, x, &s_flag, 1, kGramT);
           if (gok) {
             const int NE = R * (R + 1) / 2;
@@ -941,8 +1108,8 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
             const int e0 = x.c * epc;
             const int ne = max(0, min(NE, e0 + epc) - e0);
             if (ne > 0) {
-              sum_rows(gs.Gpart + e0, x.G, ne, NE, red64, redp, 1, kGramT);
-              for (int e = tid; e < ne; e += kGramT) gs.Gfull[e0 + e] = red64[e];
+              sum_pairs(gs.Gpart + e0, x.G, ne, NE, red2, redp2, 1, kGramT);
+              for (int e = tid; e < ne; e += kGramT) gs.Gfull[e0 + e] = red2[e];
             }
             gok = grid_sync(gs, x, &s_flag, 1, kGramT);
           }
@@ -963,20 +1130,34 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
           alive = false;
           break;
         }
-        // G and its FP32 inverse by every warp (an issue-bound chain of R block barriers: it runs
-        // after the contraction, not beside it)
-        const bool fast = solver_prepare<MAXR, kGT>(p, L, sm, gs, dsc, ne_r, ne_c, 0);
-        if (!(alive = grid_sync(gs, x, &s_flag))) break;   // (C) every split's partial M is stored
-        // ---- P3: the split partials of this CTA's rows, then A = M G^-1
-        {
-          double* mrow = reinterpret_cast<double*>(sm + L.mrow);
+        // G and its scaled FP32 copy by every warp; then the FP32 inverse X0 by the last W warps (a
+        // chain of pivots on their registers) while the other warps pass grid barrier C and reduce
+        // this CTA's rows of M
+        const bool gfast = solver_prepare<MAXR, kGT>(p, L, sm, gs, ds, scp, ne_r, ne_c, 0);
+        const int W = (MAXR > 32 && R > 32) ? 2 : 1;
+        const int nrest = kGT - 32 * W;
+        if (tid >= nrest) {
+          if (gfast) {
+            float* x0 = reinterpret_cast<float*>(sm + L.x0);
+            float* piv = reinterpret_cast<float*>(sm + L.piv);
+            bool iok;
+            if constexpr (MAXR > 32) {
+              iok = W == 2 ? sweep_regs<2>(x0, x0, R, piv, tid - nrest, 3) : sweep_regs<1>(x0, x0, R, piv, tid - nrest, 3);
+            } else {
+              iok = sweep_regs<1>(x0, x0, R, piv, tid - nrest, 3);
+            }
+            if (tid == nrest) s_invbad = iok ? 0 : 1;
+          }
+        } else if (grid_sync(gs, x, &s_flag, 4, nrest)) {   // (C) every split's partial M is stored
+          // ---- P3: the split partials of this CTA's rows, summed exactly into pairs
+          float2* mrow = reinterpret_cast<float2*>(sm + L.mrow);
           const int i0 = x.c * ms.rpc;
           const int nrows = max(0, min(ms.I, i0 + ms.rpc) - i0);
-          for (int e = tid; e < nrows * R; e += kGT) {
+          for (int e = tid; e < nrows * R; e += nrest) {
             const int li = e / R, r = e - li * R;
             const float* src = gs.Mpart + (int64_t)r * ms.I + i0 + li;
             const int64_t sstr = (int64_t)R * ms.I;
-            double a0 = 0.0, a1 = 0.0;
+            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
             int q = 0;
             for (; q + 7 < ms.nsplit; q += 8) {   // eight loads in flight
               float v[8];
@@ -984,40 +1165,44 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
               for (int k = 0; k < 8; ++k) v[k] = __ldcg(src + (q + k) * sstr);
 #pragma unroll
               for (int k = 0; k < 8; k += 2) {
-                a0 += (double)v[k];
-                a1 += (double)v[k + 1];
+                pair_acc(v[k], h0, l0);
+                pair_acc(v[k + 1], h1, l1);
               }
             }
-            for (; q < ms.nsplit; ++q) a0 += (double)__ldcg(src + q * sstr);
-            mrow[e] = a0 + a1;
+            for (; q < ms.nsplit; ++q) pair_acc(__ldcg(src + q * sstr), h0, l0);
+            pair_acc2(make_float2(h1, l1), h0, l0);
+            mrow[e] = pair_norm(h0, l0);
           }
         }
         __syncthreads();
-        const bool ok = solve_rows<MAXR>(p, L, sm, x, ms, dsc, fast, &s_flag2, s_umax);
+        if (!(alive = s_flag != 0)) break;
+        const bool fast = gfast && s_invbad == 0;   // the same in every CTA
+        // ---- then A = M G^-1
+        const bool ok = solve_rows<MAXR>(p, L, sm, x, ms, ds, fast, &s_flag2, s_umax);
         {
-          const double* arow = reinterpret_cast<const double*>(sm + L.arow);
+          const float2* a2 = reinterpret_cast<const float2*>(sm + L.a2);
           const int i0 = x.c * ms.rpc;
           const int nrows = max(0, min(ms.I, i0 + ms.rpc) - i0);
           double* A64 = p.A64[n] + (int64_t)i0 * R;
           float* A32 = p.A32[n] + (int64_t)i0 * R;
           for (int e = tid; e < nrows * R; e += kGT) {
-            const double a = arow[e];
-            A64[e] = a;
-            A32[e] = (float)a;
+            const float2 a = a2[e];
+            A64[e] = pair_value(a);
+            A32[e] = a.x;
           }
-          for (int r = tid; r < R; r += kGT) {
-            double s0 = 0.0;
-            for (int li = 0; li < nrows; ++li) s0 = fma(arow[li * R + r], arow[li * R + r], s0);
-            gs.Npart[(int64_t)x.c * R + r] = s0;
+          for (int r = tid; r < R; r += kGT) {   // this CTA's part of the column sums of squares
+            float sh = 0.f, sl = 0.f;
+            for (int li = 0; li < nrows; ++li) pair_fma(a2[li * R + r], a2[li * R + r], sh, sl);
+            gs.Npart[(int64_t)x.c * R + r] = pair_norm(sh, sl);
           }
         }
         if (!ok) singular = true;   // identical in every CTA (same G, same arithmetic)
         if (!(alive = grid_sync(gs, x, &s_flag))) break;   // (D) every row and column partial stored
         if (singular) break;
         // ---- P4: lambda and the lazy scales of mode n
-        sum_rows(gs.Npart, x.G, R, R, red64, redp);
+        sum_pairs(gs.Npart, x.G, R, R, red2, redp2);
         for (int r = tid; r < R; r += kGT) {
-          const double a = red64[r];
+          const double a = pair_value(red2[r]);
           const double y = a > 0.0 ? rsqrt64(a) : 0.0;
           const double nrm = a * y;
           lam[r] = nrm;

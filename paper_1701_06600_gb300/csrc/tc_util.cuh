@@ -89,9 +89,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(u[q]);
 }
 
-// x = hi + lo with hi the TF32 value of x (its low 13 mantissa bits cleared) and lo = x - hi (exact);
-// hi*hi + hi*lo + lo*hi reproduces an FP32 product to about 2^-21 relative
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// x to the nearest TF32 value (10 explicit mantissa bits, ties away from zero).  Splitting
+// x = hi + lo + e with hi = tf32_rn(x) and lo = tf32_rn(x - hi) (x - hi is exact in FP32) leaves
+// |e| <= 2^-22 |x|, so hi*hi + hi*lo + lo*hi reproduces an FP32 product to about 3 * 2^-22 relative
+// (clearing the low bits instead, and letting the tensor cores drop those of lo, leaves 2^-20 per
+// operand)
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+// The same rounding of a finite x by integer arithmetic (half an ulp of TF32 added to the magnitude,
+// then the low 13 bits cleared; a carry into the exponent is the correct result): two integer
+// operations at full rate, where the conversion instruction issues at a fraction of it.
+__device__ __forceinline__ float tf32_round(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
 
 }  // namespace tc
 }  // namespace cpr

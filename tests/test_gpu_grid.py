@@ -12,6 +12,7 @@ import torch
 
 from oracle import cp, mixing
 from synth import make_problem, to_oracle_array
+from fp32_floor import fp32_product_floor
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
@@ -67,9 +68,13 @@ def test_grid_loop_matches_oracle(cb, contract, dims, R, S, dtype, mix):
     else:
         ref = cp.cprand(T, R, S, seed=17, rule=cp.StopRule(fixed_iters=iters))
     np.testing.assert_allclose(trace.cpu().numpy(), ref["fits"], rtol=0, atol=1e-4)
-    for A, Ar in zip(out["factors"], ref["factors"]):
-        assert rel(A.cpu().numpy(), Ar) < 1e-4
-    assert rel(out["lam"].cpu().numpy(), ref["lam"]) < 1e-4
+    # 1e-4, or, where the problem's conditioning makes the FP32 rounding of M alone move the factors
+    # further (R = 50 fitted to a rank-8 tensor: the extra components fit noise and the sampled Grams
+    # lose conditioning), no worse than a plain FP32 product with an exact FP64 solve
+    floor = fp32_product_floor(Th if mix else T, R, S, 17, iters, ref, ops=ops if mix else None)
+    for A, Ar, f in zip(out["factors"], ref["factors"], floor):
+        assert rel(A.cpu().numpy(), Ar) < max(1e-4, f)
+    assert rel(out["lam"].cpu().numpy(), ref["lam"]) < max(1e-4, max(floor))
 
 
 def test_grid_loop_rank_64_matches_oracle(cb, contract):
