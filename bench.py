@@ -72,6 +72,9 @@ def parse():
                     help="instead of the benchmark: time the mixing call alone on this tensor shape "
                          "(float32 or bfloat16; repeatable), as the benchmark's extras do for other workloads")
     ap.add_argument("--mix-reps", type=int, default=4)
+    ap.add_argument("--profile-grid", default=None, metavar="I1xI2x...:R:S:iters",
+                    help="run CPRAND-MIX on the whole-GPU loop twice (the second call is the one to capture) "
+                         "on a synthetic FP32 tensor of the headline's recipe and print its timings")
     ap.add_argument("--workload", choices=["1500", "400"], default="1500",
                     help="the decomposition a step runs (default: the 1500^3 headline workload)")
     return ap.parse_args()
@@ -741,6 +744,24 @@ MIX_SHAPES = [((1500, 1500, 1500), "bfloat16"), ((400, 400, 400), "float32"),
               ((100, 100, 100, 100), "bfloat16"), ((100, 100, 100, 100), "float32"), ((1500, 1500, 200), "float32")]
 
 
+def profile_grid_case(spec):
+    """A small case of the whole-GPU loop for profilers: the headline workload's recipe (congruence 0.5,
+    0.1% noise, data and Philox seeds) on the given dims, R and S, CPRAND-MIX with a fixed number of
+    outer iterations on loop_path 5, called twice with one workspace."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1701_06600_gb300 import binding as cb
+    dims_s, R, S, iters = spec.split(":")
+    w = dict(WORKLOAD, dims=[int(v) for v in dims_s.split("x")], R=int(R), S=int(S))
+    prob = make_workload(w)
+    dims = tuple(w["dims"])
+    opts = opts_for(cb, w, fixed_iters=int(iters), loop_path=cb.LOOP_GRID)
+    first = cb.cpr_cprand_mix(prob.X, dims, w["R"], w["S"], opts=opts)
+    out = cb.cpr_cprand_mix(prob.X, dims, w["R"], w["S"], opts=opts, ws=first["ws"])
+    return {"profile_grid": spec, "status": out["status"], "iters": out["iters"], "ms_setup": out["ms_setup"],
+            "us_per_iter": 1e3 * out["ms_iterate"] / max(out["iters"], 1), "fit_est": out["fit_est"]}
+
+
 def mixing_shapes(cb, reps=4, shapes=None):
     """The mixing preprocess alone (cpr_mix_tensor: the operator tables, then one factored-DCT pass per
     mode) on other tensors: device time per call by CUDA events over `reps` calls after one warm-up
@@ -1056,6 +1077,10 @@ def main():
     if args.quality_sweep:
         if rank == 0:
             print(json.dumps(run_quality_sweep(args)))
+        return
+    if args.profile_grid:
+        if rank == 0:
+            print(json.dumps(profile_grid_case(args.profile_grid)))
         return
     if args.mix_shape:
         if rank == 0:

@@ -10,7 +10,7 @@ import torch
 
 from oracle import cp, mixing, streams
 from synth import make_problem, to_oracle_array
-from fp32_floor import fp32_product_floor
+from fp32_floor import fp32_product_floor, fp32_trace_floor
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
@@ -300,11 +300,15 @@ def test_bf16_four_way_run_reaches_oracle_fit(cb):
     f_ref = cp.exact_fit(T, ref["lam"], ref["factors"])
     assert abs(f_gpu - f_ref) < 1e-3, (f_gpu, f_ref, out["iters"], ref["iters"])
     # per iteration: the oracle's CPRAND on the mixed tensor the GPU stored (BF16, so both sides see
-    # the same data and the same draws): the traces differ only by the FP32 / FP64 arithmetic
+    # the same data and the same draws): the traces differ only by the FP32 / FP64 arithmetic -- by
+    # 1e-4 at most, or, inside the swamp, where the trajectory amplifies the FP32 rounding of M, by no
+    # more than a plain FP32 product with an exact solve moves the oracle's own trace
     Th = to_oracle_array(cb.cpr_mix_tensor(prob.X, dims, seed=2002), dims)
     ref_h = cp.cprand(Th, 16, 450, seed=2002, rule=cp.StopRule(fixed_iters=50))
     err = np.abs(trace.cpu().numpy()[:50] - ref_h["fits"])
-    assert np.all(err < 1e-4), err.max()
+    floor = fp32_trace_floor(Th, 16, 450, 2002, 50, ref_h["fits"])
+    print("BF16 4-way: per-iteration |dF^| max %.2e, plain FP32 product %.2e" % (err.max(), floor))
+    assert np.all(err < max(1e-4, floor)), (err.max(), floor)
 
 
 @pytest.mark.parametrize("dims", [(24, 30, 100), (20, 12, 1500), (30, 20, 400), (16, 100, 36)])
