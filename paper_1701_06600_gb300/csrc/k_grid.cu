@@ -126,7 +126,7 @@ __host__ __device__ inline GridSmem grid_layout(int R, int MAXR, int tbytes) {
   int o = 0;
   L.g2 = o;    o = ga16(o + R * R * 8);
   L.x0 = o;    o = ga16(o + R * R * 4);
-  L.piv = o;   o = ga16(o + 4 * 64 * 4);
+  L.piv = o;   o = ga16(o + 2 * 64 * 4);
   L.dp = o;    o = ga16(o + MAXR * 4);
   const int s_end = o;
   // P1: Gram warps, contraction warps (the SIMT fiber chunks or the tensor-core stages)
@@ -764,76 +764,53 @@ __device__ void prefetch_next(const Prob& p, const GridCtx& x, int n, uint32_t t
   }
 }
 
-// X0 ~ Gs^-1 in FP32 for the Jacobi-scaled Gram Gs (unit diagonal) by the sweep operator, two pivots
-// at a time: sweeping on the index pair K = {k, k+1} with the 2 x 2 block P = A_KK maps A to A' with
-// A'_ij = A_ij - A_iK P^-1 A_Kj (i, j not in K), A'_iK = A_iK P^-1, A'_Kj = P^-1 A_Kj, A'_KK = -P^-1,
-// the same as sweeping on k and then on k+1 (P^-1 is formed from those two pivots, a and
-// p2 = A_(k+1)(k+1) - A_k(k+1)^2 / a); after every step A = -Gs^-1.  The matrix lives in the
+// X0 ~ Gs^-1 in FP32 for the Jacobi-scaled Gram Gs (unit diagonal) by the sweep operator: pivot k
+// maps A to A' with A'_ij = A_ij - A_ik A_kj / A_kk (i, j != k), A'_ik = A_ik / A_kk,
+// A'_kj = A_kj / A_kk, A'_kk = -1 / A_kk; after every pivot A = -Gs^-1.  The matrix lives in the
 // registers of W warps (W = 1 for R <= 32, 2 for R <= 64): thread j (0 <= j < PAD = 32 W) holds column
-// j, padded past R with the identity (for an odd R the last step pivots on the unit entry of
-// column R, which leaves the rest unchanged).  A stays symmetric, so rows K are columns K: each
-// thread publishes its two row-K entries to shared memory for the others (one barrier per step,
-// two alternating slot sets).  The rows rotate by two positions per step so that every register
-// index is static: before step k/2, position p holds row (p + k) mod PAD, rows K are positions 0
-// and 1, and the entries of row i go to slot (i - k - 2) mod PAD, where the update of the row's next
-// position reads them.  The columns K take A'_iK = A_iK - A_iK (I - P^-1) from the same fused update
-// (their own entries are the published ones).  A pivot below 1e-6 (relative to the unit diagonal) or
+// j, padded with zeros past R.  A stays symmetric, so row k is column k and each thread publishes its
+// row-k entry to shared memory for the others (one barrier per pivot, two alternating slot sets).  The
+// rows rotate by one position per pivot so that every register index is static: before pivot k,
+// position p holds row (p + k) mod PAD, the pivot row is position 0, and the published entry of row i
+// goes to slot (i - k - 1) mod PAD, which is where the update of the row's next position reads it.
+// The column of the pivot itself takes A'_ik = A_ik - A_ik (1 - 1 / A_kk) from the same fused update
+// (its own entries are the published ones).  A pivot below 1e-6 (relative to the unit diagonal) or
 // not finite returns false in every thread.  src: Gs (R x R, FP32); dst: X0 (may be src: every read
-// precedes the first barrier); piv: 4 PAD floats of scratch (16-byte aligned); bar_id: a block
+// precedes the first barrier); piv: 2 PAD floats of scratch (16-byte aligned); bar_id: a block
 // barrier for the PAD threads when W = 2.
 template <int W>
-__device__ __noinline__ bool sweep_regs(const float* src, float* dst, int R, float* piv, int j, int bar_id) {
+__device__ bool sweep_regs(const float* src, float* dst, int R, float* piv, int j, int bar_id) {
   constexpr int PAD = 32 * W;
   float r[PAD];
 #pragma unroll
-  for (int p = 0; p < PAD; ++p) r[p] = (p < R && j < R) ? src[p * R + j] : (j >= R && p == j ? 1.f : 0.f);
+  for (int p = 0; p < PAD; ++p) r[p] = (p < R && j < R) ? src[p * R + j] : 0.f;
   bool bad = false;
-  const int steps = (R + 1) >> 1;
-  for (int st = 0; st < steps; ++st) {
-    const int k = 2 * st;
-    float* u = piv + (st & 1) * 2 * PAD;      // row-k entries, then row-(k+1) entries
-    float* v = u + PAD;
-    const int slot = (j - k - 2) & (PAD - 1);
-    const float x0 = r[0], x1 = r[1];
-    u[slot] = x0;
-    v[slot] = x1;
+  for (int k = 0; k < R; ++k) {
+    float* pv = piv + (k & 1) * PAD;
+    pv[(j - k - 1) & (PAD - 1)] = r[0];
     if (W == 1) __syncwarp();
     else named_sync(bar_id, PAD);
-    const float a = u[PAD - 2], b = u[PAD - 1], d = v[PAD - 1];   // P = [a b; b d]
-    const float ia = __frcp_rn(a), t = b * ia;
-    const float p2 = fmaf(-b, t, d);
-    bad = bad || !(a > 1e-6f) || !(p2 > 1e-6f) || !isfinite(a) || !isfinite(p2);
-    const float ip2 = __frcp_rn(p2);
-    const float m11 = ip2, m01 = -t * ip2, m00 = fmaf(t, t * ip2, ia);   // P^-1 = [m00 m01; m01 m11]
-    float c0, c1, n0, n1;
-    if (j == k) {
-      c0 = 1.f - m00; c1 = -m01; n0 = -m00; n1 = -m01;
-    } else if (j == k + 1) {
-      c0 = -m01; c1 = 1.f - m11; n0 = -m01; n1 = -m11;
-    } else {
-      c0 = fmaf(m00, x0, m01 * x1); c1 = fmaf(m01, x0, m11 * x1); n0 = c0; n1 = c1;
-    }
+    const float d = pv[PAD - 1];                 // row k's entry of column k
+    bad = bad || !(d > 1e-6f) || !isfinite(d);
+    const float inv = __frcp_rn(d);
+    const float akj = r[0];
+    const float c = j == k ? 1.f - inv : akj * inv;
 #pragma unroll
     for (int p = 0; p < PAD; p += 4) {
-      const float4 qu = *reinterpret_cast<const float4*>(u + p);
-      const float4 qv = *reinterpret_cast<const float4*>(v + p);
-      r[p] = fmaf(-qv.x, c1, fmaf(-qu.x, c0, r[p + 2]));
-      r[p + 1] = fmaf(-qv.y, c1, fmaf(-qu.y, c0, r[p + 3]));
-      if (p + 4 < PAD) {
-        r[p + 2] = fmaf(-qv.z, c1, fmaf(-qu.z, c0, r[p + 4]));
-        r[p + 3] = fmaf(-qv.w, c1, fmaf(-qu.w, c0, r[p + 5]));
-      }
+      const float4 q = *reinterpret_cast<const float4*>(pv + p);
+      r[p] = fmaf(-q.x, c, r[p + 1]);
+      r[p + 1] = fmaf(-q.y, c, r[p + 2]);
+      r[p + 2] = fmaf(-q.z, c, r[p + 3]);
+      if (p + 4 < PAD) r[p + 3] = fmaf(-q.w, c, r[p + 4]);
     }
-    r[PAD - 2] = n0;                           // the new rows K, now at the last positions
-    r[PAD - 1] = n1;
+    r[PAD - 1] = j == k ? -inv : akj * inv;   // the new pivot row, now at the last position
   }
   if (W == 1) __syncwarp();
   else named_sync(bar_id, PAD);
   if (j < R) {
-    const int rot = 2 * steps;
 #pragma unroll
     for (int p = 0; p < PAD; ++p) {
-      const int row = (p + rot) & (PAD - 1);
+      const int row = (p + R) & (PAD - 1);
       if (row < R) dst[row * R + j] = -r[p];
     }
   }
