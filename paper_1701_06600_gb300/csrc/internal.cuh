@@ -355,6 +355,9 @@ cudaError_t launch_mix_tc16(const float* U, float* ystd, float* yunf, float* yne
 // standard layout, and its own layout into ysame when given); tab = 5 I floats (twiddles,
 // post-scales, signs) from launch_build_mix_ops
 bool mix_fft_supported(int dtype, int N, const int64_t* dims);
+// the Bluestein tables of a length with a prime factor above 7 (7 I + 4 M floats from fft_tab on,
+// after the 5 I DCT floats); nothing for a 7-smooth length
+cudaError_t launch_build_bs_tables(int I, float* fft_tab, cudaStream_t s);
 cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* tab, int dtype, int N,
                            const int64_t* dims, int n, int* err, cudaStream_t s);
 int mix_engine();   // CPR_MIX_* (process-wide, cpr_set_mix_engine)

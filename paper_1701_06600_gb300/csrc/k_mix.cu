@@ -57,7 +57,9 @@ cudaError_t launch_build_mix_ops(int I, uint64_t seed, uint32_t b, int n, double
   k_cos_table<<<(4 * I + 255) / 256, 256, 0, s>>>(I, table);
   const int64_t total = (int64_t)I * I;
   k_build_mix_ops<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(I, seed, b, n, table, W32, W64, F64, signs, fft_tab);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && fft_tab) e = launch_build_bs_tables(I, fft_tab, s);
+  return e;
 }
 
 template <typename T> struct Conv;

@@ -48,6 +48,8 @@ constexpr int kSlots = 32;          // complex values a thread holds in a stage
 constexpr int kMaxStages = 16;
 constexpr int kFftMaxSmem = 200 * 1024;
 constexpr int kMaxFftLen = 8192;    // keeps the multiply-high divisions exact
+constexpr int kBsMinLen = 24;       // Bluestein form for I >= 24: its tables (7 I + 4 M floats) fit I^2
+constexpr int kBsMaxConv = 4096;    // longest Bluestein convolution (FP64 table builder in shared memory)
 // the stage radices, in the order a plan's stages run; radix R = R1 x R2 (R2 = 1 for the plain ones)
 constexpr int kNumRadices = 14;
 constexpr int kRadR1[kNumRadices] = {5, 5, 4, 5, 4, 5, 3, 4, 7, 3, 5, 4, 3, 2};
@@ -77,6 +79,10 @@ struct FftArgs {
   int vec_v;            // the mode-v output admits 16-byte stores of 4 adjacent fibers
   int vec_in;           // BF16 input rows admit 8-byte loads of 4 entries
   int* err;
+  // Bluestein (chirp-z) form for lengths with a prime factor above 7: the length-I DFT as a cyclic
+  // convolution of length M (7-smooth, M >= 2 I - 1); st / nst then describe the length-M stages
+  int M, Mpad;
+  uint32_t mM, mI;      // ceil(2^32 / M), ceil(2^32 / I)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -436,6 +442,227 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_fft(const __grid_constan
       const float* z = Y + (f >> 1) * 2 * Ipad + (f & 1);
       for (int k = lane; k < I; k += 32) dst[k] = from_float<T>(z[2 * k]);
     }
+  }
+}
+
+// ---- the factored DCT-II for lengths I with a prime factor above 7 (Bluestein's chirp-z form) ----
+// The pass is the one of k_mix_fft (the same fiber blocks, DCT reorder and signs, separation of the
+// two real fibers of a sequence, post-rotation and stores); only the length-I DFT of the S complex
+// sequences is computed differently.  With c_n = exp(-i pi n^2 / I), the identity
+// n k = (n^2 + k^2 - (k - n)^2) / 2 gives Z_k = c_k sum_n (v_n c_n) conj(c_(k-n)): a linear
+// convolution, computed as a cyclic one of length M >= 2 I - 1 by the same Stockham stages
+// (FFT_M, times the FFT of the filter, FFT_M of the conjugate, conjugated back).  Tables behind the
+// DCT's 5 I floats: c_n (I complex), the length-M twiddles (M complex), FFT_M of the filter divided
+// by M (M complex).  Shared memory: the fiber rows (BJ x Ipad floats, the final spectra overwrite
+// them), the S length-M sequences (Mpad complex each), the tables, the mbarrier.
+template <int RIX, int TPB>
+__device__ __forceinline__ void bs_stages_of(float2* W, int M, int Mpad, int S, int nst, const StageTab* stt, int& st,
+                                             int tid, const float2* twm) {
+  for (; st < nst && stt[st].rix == RIX; ++st)
+    fft_stage<kRadR1[RIX], kRadR2[RIX], false, TPB>(W, M, Mpad, S, stt[st], tid, twm, nullptr);
+}
+
+template <int TPB>
+__device__ __forceinline__ bool bs_transform(float2* W, int M, int Mpad, int S, int nst, const StageTab* stt, int tid,
+                                             const float2* twm) {
+  int st = 0;
+  bs_stages_of<0, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  bs_stages_of<1, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  bs_stages_of<2, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  bs_stages_of<3, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  bs_stages_of<4, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  bs_stages_of<5, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  bs_stages_of<6, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  bs_stages_of<7, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  bs_stages_of<8, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  bs_stages_of<9, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  bs_stages_of<10, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  bs_stages_of<11, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  bs_stages_of<12, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  bs_stages_of<13, TPB>(W, M, Mpad, S, nst, stt, st, tid, twm);
+  return st == nst;
+}
+
+template <typename T, int TPB>
+__global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_fft_bs(const __grid_constant__ FftArgs a) {
+  extern __shared__ float4 fft_smem4[];
+  const int I = a.I, Ipad = a.Ipad, BJ = a.BJ, S = a.S, M = a.M, Mpad = a.Mpad;
+  float* Y = reinterpret_cast<float*>(fft_smem4);
+  float2* Z = reinterpret_cast<float2*>(Y);                 // sequence p at Z + p Ipad (rows 2p, 2p + 1)
+  float2* W = reinterpret_cast<float2*>(Y + BJ * Ipad);     // sequence p at W + p Mpad
+  float2* post = W + S * Mpad;                              // I complex
+  float2* chirp = post + I;                                 // I complex
+  float2* twm = chirp + I;                                  // M complex
+  float2* bf = twm + M;                                     // M complex
+  float* sg = reinterpret_cast<float*>(bf + M);             // I floats
+  uint64_t* bar = reinterpret_cast<uint64_t*>(fft_smem4) + ((BJ * Ipad + 2 * S * Mpad + 5 * I + 4 * M + 3) / 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const T* U = static_cast<const T*>(a.U);
+  __shared__ StageTab s_st[kMaxStages];
+  __shared__ longlong4 s_blk;
+  if (tid < kMaxStages) s_st[tid] = a.st[tid];
+  if (tid == 0) {
+    int64_t r0, o0;
+    const int n = fft_block(a, blockIdx.x, r0, o0);
+    s_blk = make_longlong4(r0, o0, n, 0);
+    if (a.bulk) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  __syncthreads();
+  const int64_t row0 = s_blk.x, out0 = s_blk.y;
+  const int nf = (int)s_blk.z;
+  if (a.bulk) {
+    if (tid == 0)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                   "r"((uint32_t)(nf * I * sizeof(float)))
+                   : "memory");
+    if (tid < nf)
+      fft_bulk_copy(Y + tid * Ipad, U + (row0 + (int64_t)tid * a.rs_in_v) * I, (uint32_t)(I * sizeof(float)), bar);
+  } else {
+    for (int f = warp; f < nf; f += TPB / 32) {
+      const T* src = U + (row0 + (int64_t)f * a.rs_in_v) * I;
+      for (int k = lane; k < I; k += 32) Y[f * Ipad + k] = ld_as_float<T>(src + k);
+    }
+  }
+  // the tables: post-scales and signs of the DCT, then the chirp, the length-M twiddles and the filter
+  const float* tab = a.tab;
+  for (int e = tid; e < 2 * I; e += TPB) reinterpret_cast<float*>(post)[e] = tab[2 * I + e];
+  for (int e = tid; e < I; e += TPB) sg[e] = tab[4 * I + e];
+  for (int e = tid; e < 2 * I + 4 * M; e += TPB) reinterpret_cast<float*>(chirp)[e] = tab[5 * I + e];
+  for (int e = tid; e < (BJ - nf) * Ipad; e += TPB) Y[nf * Ipad + e] = 0.f;
+  bool ok = true;
+  if (a.bulk && tid == 0) {
+    ok = false;
+    for (uint32_t it = 0; it < kFftWaitLimit && !ok; ++it) ok = fft_mbar_try(bar, 0);
+  }
+  if (__syncthreads_or(!ok)) {
+    fft_drain(bar, a.err, tid);
+    return;
+  }
+  if (a.bulk && tid != 0) (void)fft_mbar_try(bar, 0);
+  // a_p[m] = v_p[m] c_m (m < I), 0 past I: v_p[m] = d[s] (x_2p[s], x_2p+1[s]), s the DCT reorder of m
+  for (int e = tid; e < S * M; e += TPB) {
+    const int p = fdiv(e, M, a.mM), m = e - p * M;
+    float2 x = make_float2(0.f, 0.f);
+    if (m < I) {
+      const int src = 2 * m < I ? 2 * m : 2 * (I - 1 - m) + 1;
+      const float d = sg[src];
+      const float* row = Y + 2 * p * Ipad;
+      x = cmul(make_float2(row[src] * d, row[Ipad + src] * d), chirp[m]);
+    }
+    W[p * Mpad + m] = x;
+  }
+  __syncthreads();
+  bool good = bs_transform<TPB>(W, M, Mpad, S, a.nst, s_st, tid, twm);
+  for (int e = tid; e < S * M; e += TPB) {   // times FFT_M(filter) / M, conjugated
+    const int p = fdiv(e, M, a.mM), m = e - p * M;
+    const float2 y = cmul(W[p * Mpad + m], bf[m]);
+    W[p * Mpad + m] = make_float2(y.x, -y.y);
+  }
+  __syncthreads();
+  good = bs_transform<TPB>(W, M, Mpad, S, a.nst, s_st, tid, twm) && good;
+  if (!good && tid == 0) atomicExch(a.err, 1);   // a stage order the host never produces
+  // Z_p[k] = c_k conj(W_p[k]), k < I: the DFT of v_p, over the fiber rows (read in full above)
+  for (int e = tid; e < S * I; e += TPB) {
+    const int p = fdiv(e, I, a.mI), k = e - p * I;
+    const float2 w = W[p * Mpad + k];
+    Z[p * Ipad + k] = cmul(make_float2(w.x, -w.y), chirp[k]);
+  }
+  __syncthreads();
+  // separation, post-rotation and stores: as in k_mix_fft
+  {
+    const int H2 = I / 2 + 1;
+    for (int w = tid; w < S * H2; w += TPB) {
+      const int p = fdiv(w, H2, a.mH2), k = w - p * H2;
+      float2* z = Z + p * Ipad;
+      const int kk = k == 0 ? 0 : I - k;
+      const float2 A = z[k], B = z[kk];
+      const float2 pk = post[k];
+      z[k] = make_float2(pk.x * (A.x + B.x) + pk.y * (A.y - B.y), pk.x * (A.y + B.y) - pk.y * (A.x - B.x));
+      if (kk != k) {
+        const float2 pq = post[kk];
+        z[kk] = make_float2(pq.x * (B.x + A.x) + pq.y * (B.y - A.y), pq.x * (B.y + A.y) - pq.y * (B.x - A.x));
+      }
+    }
+  }
+  __syncthreads();
+  {
+    T* yv = static_cast<T*>(a.yv);
+    const int FW = BJ < 8 ? BJ : 8, KW = 32 / FW;
+    constexpr int NW = TPB / 32;
+    const int ngf = BJ / FW, G8 = ngf < NW ? ngf : NW, wpg = NW / G8;
+    const int kstep = wpg * KW;
+    for (int gf = warp % G8; gf < ngf; gf += G8) {
+      const int f = gf * FW + lane % FW;
+      int k = (warp / G8) * KW + lane / FW;
+      if (f >= nf) continue;
+      T* dst = yv + out0 + f + (int64_t)k * a.out_k;
+      const int64_t dstep = (int64_t)kstep * a.out_k;
+      const float* src = Y + (f >> 1) * 2 * Ipad + (f & 1) + 2 * k;
+      for (; k < I; k += kstep, dst += dstep, src += 2 * kstep) *dst = from_float<T>(*src);
+    }
+  }
+  if (a.ysame) {
+    T* ys = static_cast<T*>(a.ysame);
+    for (int f = warp; f < nf; f += TPB / 32) {
+      T* dst = ys + (row0 + (int64_t)f * a.rs_in_v) * I;
+      const float* z = Y + (f >> 1) * 2 * Ipad + (f & 1);
+      for (int k = lane; k < I; k += 32) dst[k] = from_float<T>(z[2 * k]);
+    }
+  }
+}
+
+// The Bluestein tables of one length I behind its 5 I DCT floats (FP64, each rounded once to FP32):
+// c_n = exp(-i pi n^2 / I) for n < I (the angle reduced exactly: n^2 mod 2 I), the length-M twiddles
+// exp(-2 pi i m / M), and B_k / M with B = FFT_M(b), b_m = conj(c_m) for m < I, conj(c_(M-m)) for
+// M - I < m < M, zero between.  Every block keeps exp(-2 pi i j / M) and conj(c_m) in FP64 shared
+// memory and forms its share of the B_k by direct sums over the 2 I - 1 nonzero b_m.
+__global__ void __launch_bounds__(256) k_build_bs_tabs(int I, int M, float* out) {
+  extern __shared__ double bs64[];
+  double2* wm = reinterpret_cast<double2*>(bs64);      // M
+  double2* dm = wm + M;                                  // I: conj(c_m)
+  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * (double)j / (double)M, &sn, &cs);
+    wm[j] = make_double2(cs, -sn);
+  }
+  for (int m = threadIdx.x; m < I; m += blockDim.x) {
+    const int64_t q = ((int64_t)m * m) % (2 * (int64_t)I);
+    double sn, cs;
+    sincospi((double)q / (double)I, &sn, &cs);
+    dm[m] = make_double2(cs, sn);
+  }
+  __syncthreads();
+  float* chirp = out + 5 * I;
+  float* twm = chirp + 2 * I;
+  float* bf = twm + 2 * M;
+  if (blockIdx.x == 0) {
+    for (int m = threadIdx.x; m < I; m += blockDim.x) {
+      chirp[2 * m] = (float)dm[m].x;
+      chirp[2 * m + 1] = (float)(-dm[m].y);
+    }
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+      twm[2 * j] = (float)wm[j].x;
+      twm[2 * j + 1] = (float)wm[j].y;
+    }
+  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int m = 0; m < I; ++m) {   // b_m = dm[m] at m and at M - m (m >= 1)
+      const double2 b = dm[m];
+      const double2 w0 = wm[(int)(((int64_t)m * k) % M)];
+      re += b.x * w0.x - b.y * w0.y;
+      im += b.x * w0.y + b.y * w0.x;
+      if (m > 0) {
+        const double2 w1 = wm[(int)(((int64_t)(M - m) * k) % M)];
+        re += b.x * w1.x - b.y * w1.y;
+        im += b.x * w1.y + b.y * w1.x;
+      }
+    }
+    bf[2 * k] = (float)(re / M);
+    bf[2 * k + 1] = (float)(im / M);
   }
 }
 
@@ -1052,6 +1279,65 @@ bool fft_plan(int I, int64_t Iv, FftPlan* pl, bool cplx = false) {
   return true;
 }
 
+// Bluestein form: the convolution length (the smallest 7-smooth M >= 2 I - 1, at most 4096), 0 when
+// there is none or I is 7-smooth itself (the direct plan applies)
+bool smooth7(int m) {
+  for (int p : {2, 3, 5, 7})
+    while (m % p == 0) m /= p;
+  return m == 1;
+}
+int bs_length(int I) {
+  if (I < kBsMinLen || smooth7(I)) return 0;
+  for (int M = 2 * I - 1; M <= kBsMaxConv; ++M)
+    if (smooth7(M)) return M;
+  return 0;
+}
+// the fiber rows, the length-M sequences, the tables (5 I + 2 I + 4 M floats), the mbarrier
+size_t bs_smem_bytes(int BJ, int Ipad, int Mpad, int I, int M) {
+  return (size_t)(BJ * Ipad + BJ * Mpad + 7 * I + 4 * M + 4) * sizeof(float) + 16;
+}
+bool fft_plan_bs(int I, int64_t Iv, FftPlan* pl, int* Mout, int* Mpad_out) {
+  const int M = bs_length(I);
+  if (M == 0) return false;
+  int Ipad = (I + 3) / 4 * 4;
+  if ((Ipad / 4) % 2 == 0) Ipad += 4;
+  int Mpad = (M + 3) / 4 * 4;
+  if ((Mpad / 4) % 2 == 0) Mpad += 4;
+  int64_t cap = 2;
+  while (cap < Iv && cap < 128) cap *= 2;
+  FftPlan best;
+  memset(&best, 0, sizeof(best));
+  const int tpbs[2] = {128, 256};
+  for (int t = 0; t < 2; ++t) {
+    const int tpb = tpbs[t];
+    const size_t smem_cap = (size_t)kFftMaxSmem / (512 / tpb);
+    // the stage plan of length M with the fewest stages, for the widest block that fits
+    for (int BJ = 128; BJ >= 2; BJ /= 2) {
+      if (BJ > cap) continue;
+      const size_t sm = bs_smem_bytes(BJ, Ipad, Mpad, I, M);
+      if (sm > (size_t)kFftMaxSmem || (BJ > 8 && sm > smem_cap)) continue;
+      FftPlan cand;
+      memset(&cand, 0, sizeof(cand));
+      int cur[kMaxStages];
+      fft_search(M, 0, cur, 0, M, (int64_t)BJ, Mpad, tpb, false, &cand);   // checks S = BJ / 2 sequences
+      if (cand.BJ < BJ) continue;
+      if (BJ > best.BJ) {
+        best = cand;
+        best.BJ = BJ;
+        best.tpb = tpb;
+        best.Ipad = Ipad;
+        best.smem = sm;
+      }
+      break;
+    }
+  }
+  if (best.BJ == 0) return false;
+  *pl = best;
+  *Mout = M;
+  *Mpad_out = Mpad;
+  return true;
+}
+
 template <typename T, int TPB>
 cudaError_t launch_fft_kernel(const FftArgs& a, size_t smem, cudaStream_t s) {
   static bool attr = false;
@@ -1063,6 +1349,20 @@ cudaError_t launch_fft_kernel(const FftArgs& a, size_t smem, cudaStream_t s) {
   }
   if (a.nblocks > INT32_MAX) return cudaErrorInvalidValue;
   k_mix_fft<T, TPB><<<(unsigned)a.nblocks, TPB, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int TPB>
+cudaError_t launch_fft_bs_kernel(const FftArgs& a, size_t smem, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_mix_fft_bs<T, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftMaxSmem + 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (a.nblocks > INT32_MAX) return cudaErrorInvalidValue;
+  k_mix_fft_bs<T, TPB><<<(unsigned)a.nblocks, TPB, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1121,9 +1421,28 @@ bool mix_fft_supported(int dtype, int N, const int64_t* dims) {
   for (int n = 0; n < N; ++n) {
     if (dims[n] < 5) return false;   // the tables live in the I x I operator buffer (5 I floats)
     FftPlan pl;
-    if (!fft_plan((int)dims[n], dims[(n + 1) % N], &pl)) return false;
+    int M, Mpad;
+    if (!fft_plan((int)dims[n], dims[(n + 1) % N], &pl) &&
+        !fft_plan_bs((int)dims[n], dims[(n + 1) % N], &pl, &M, &Mpad))
+      return false;
   }
   return true;
+}
+
+cudaError_t launch_build_bs_tables(int I, float* fft_tab, cudaStream_t s) {
+  const int M = bs_length(I);
+  if (M == 0) return cudaSuccess;   // a 7-smooth length (or none): nothing to add
+  const size_t smem = (size_t)(M + I) * sizeof(double2);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_build_bs_tabs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((kBsMaxConv + kBsMaxConv / 2 + 1) * sizeof(double2)));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int blocks = std::min(152, (M + 255) / 256 * 4);
+  k_build_bs_tabs<<<blocks, 256, smem, s>>>(I, M, fft_tab);
+  return cudaGetLastError();
 }
 
 
@@ -1136,12 +1455,13 @@ bool fft_args(FftArgs& a, FftPlan& pl, const void* U, void* yv, void* ysame, con
   const int v = (n + 1) % N;
   memset(&a, 0, sizeof(a));
   const int I = (int)dims[n];
+  int M = 0, Mpad = 0;   // Bluestein form when nonzero
   if (ct == 1 || ct == 2 || ct == 3) {
     if (ct == 1) ct_plan_of<CtPlan400>(&pl);
     if (ct == 2) ct_plan_of<CtPlan1500>(&pl);
     if (ct == 3) ct_plan_of<CtPlan100>(&pl);
   } else if (!fft_plan(I, dims[v], &pl, cplx)) {
-    return false;
+    if (cplx || !fft_plan_bs(I, dims[v], &pl, &M, &Mpad)) return false;
   }
   a.U = U;
   a.yv = yv;
@@ -1154,13 +1474,18 @@ bool fft_args(FftArgs& a, FftPlan& pl, const void* U, void* yv, void* ysame, con
   a.nst = pl.nst;
   a.mH2 = magic(I / 2 + 1);
   a.cscale = (float)(1.0 / sqrt((double)I));
+  a.M = M;
+  a.Mpad = Mpad;
+  a.mM = magic(M);
+  a.mI = magic(I);
+  const int TL = M ? M : I;   // the length the stages transform
   int Ns = 1;
   for (int st = 0; st < pl.nst; ++st) {
     const int R = kRadR1[pl.rix[st]] * kRadR2[pl.rix[st]];
     StageTab& t = a.st[st];
-    t.L = I / R;
+    t.L = TL / R;
     t.Ns = Ns;
-    t.tstep = I / (Ns * R);
+    t.tstep = TL / (Ns * R);
     t.rix = pl.rix[st];
     t.mL = magic(t.L);
     t.mNs = magic(Ns);
@@ -1215,6 +1540,15 @@ cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* ta
   if (ct == 3)
     return dtype == CPR_F32 ? launch_fft_ct_kernel<float, CtPlan100>(a, s)
                             : launch_fft_ct_kernel<__nv_bfloat16, CtPlan100>(a, s);
+  if (a.M > 0) {
+    if (dtype == CPR_F32)
+      return pl.tpb == 128 ? launch_fft_bs_kernel<float, 128>(a, pl.smem, s)
+                           : launch_fft_bs_kernel<float, 256>(a, pl.smem, s);
+    if (dtype == CPR_BF16)
+      return pl.tpb == 128 ? launch_fft_bs_kernel<__nv_bfloat16, 128>(a, pl.smem, s)
+                           : launch_fft_bs_kernel<__nv_bfloat16, 256>(a, pl.smem, s);
+    return cudaErrorInvalidValue;
+  }
   if (dtype == CPR_F32)
     return pl.tpb == 128 ? launch_fft_kernel<float, 128>(a, pl.smem, s) : launch_fft_kernel<float, 256>(a, pl.smem, s);
   if (dtype == CPR_BF16)

@@ -494,10 +494,10 @@ def test_unfolding_copies_give_identical_runs(cb, path, dims):
 # ------------------------------------------------------------------------------------------------
 # a0 on the tensor cores (dense engine): FP32 tensors whose dims are multiples of 4 take the tcgen05
 # path (FP16 halves when every dim is a multiple of 8, else 3xTF32; FP32-level accuracy); ragged
-# tiles in every direction, several column blocks
+# tiles in every direction, several column blocks; other dims the SIMT dense product (37 x 29 x 41)
 # ------------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("dims", [(64, 48, 40), (132, 20, 36), (300, 12, 8), (516, 8, 12), (16, 12, 20, 8),
-                                  (400, 400, 400)])
+                                  (400, 400, 400), (37, 29, 41)])
 def test_tensor_core_mixing_matches_oracle(cb, engine, dims):
     engine(cb.MIX_DENSE)
     X = rand_tensor(dims, torch.float32, 11)
@@ -535,6 +535,33 @@ def test_fft_mixing_matches_oracle(cb, engine, dims):
     gotd = to_oracle_array(Yd, dims)
     assert rel(gotd, ref) < 3e-5
     assert_elementwise(gotd, ref, 2.0 ** -21, 4 * len(dims) * np.sqrt(max(dims)))
+
+
+# lengths with a prime factor above 7 by Bluestein's chirp-z form (the length-I DFT as a cyclic
+# convolution of a 7-smooth length M >= 2 I - 1: 37 -> 75, 53 -> 105, 61 -> 126, 127 -> 256,
+# 331 -> 672, 26 -> 60, 34 -> 70, 38 -> 75, 29 -> 60, 31 -> 63, 509 -> 1029), alone and next to
+# 7-smooth modes, with partial blocks; FP32 to 2e-6 relative, element-wise with the depth of two
+# length-M transforms per pass
+@pytest.mark.parametrize("dims", [(61, 37, 53), (127, 12, 10), (331, 24, 9), (26, 34, 38), (29, 31, 30, 7),
+                                  (509, 40, 6), (40, 509, 6)])
+def test_bluestein_mixing_matches_oracle(cb, dims):
+    X = rand_tensor(dims, torch.float32, 13)
+    T = to_oracle_array(X, dims)
+    ref = mixing.mix_tensor(T, mixing.mixing_operators(7, 2, dims))
+    got = to_oracle_array(cb.cpr_mix_tensor(X, dims, seed=7, b=2), dims)
+    assert rel(got, ref) < 2e-6
+    assert_elementwise(got, ref, 2.0 ** -23, 16 * len(dims) * np.log2(2 * max(dims)))
+
+
+@pytest.mark.parametrize("dims", [(53, 26, 40), (37, 100, 20)])
+def test_bluestein_mixing_bf16_matches_oracle(cb, dims):
+    # BF16 in and out (rounded after every mode product), the Bluestein form in FP32 between
+    X = rand_tensor(dims, torch.bfloat16, 14)
+    T = to_oracle_array(X, dims)
+    ref = mixing.mix_tensor(T, mixing.mixing_operators(7, 2, dims))
+    got = to_oracle_array(cb.cpr_mix_tensor(X, dims, seed=7, b=2), dims)
+    assert rel(got, ref) < 1e-2
+    assert_elementwise(got, ref, 2.0 ** -8, 4 * len(dims))
 
 
 @pytest.mark.parametrize("dims", [(70, 30, 50), (100, 20, 12, 10), (400, 24, 10), (1500, 12, 9)])

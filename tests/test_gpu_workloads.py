@@ -34,6 +34,14 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
 
 
+def sampled_fit_bar(f_true, P_hat=16384):
+    """Four standard deviations of the sampled fit estimate (Sec. 3.4) around the exact fit F: the
+    estimate is 1 - sqrt(P mean(e^2)) / ||X|| over P_hat entries drawn with replacement, so with
+    near-Gaussian residuals (Var(e^2) = 2 mean(e^2)^2) its standard deviation is about
+    (1 - F) sqrt(2 / P_hat) / 2 = (1 - F) / sqrt(2 P_hat)."""
+    return 4.0 * (1.0 - f_true) / np.sqrt(2.0 * P_hat)
+
+
 def true_fit_device(X, dims, lam, factors, slab=64):
     """Exact fit 1 - ||X - X~|| / ||X|| of a 3-way CP model, FP64 on the device one slab of the last
     mode at a time (torch operations only)."""
@@ -170,7 +178,7 @@ def test_1500_cubed_mix_run_fit_estimate_matches_exact_fit(cb, big):
           % (tr[0], tr[1], f_true, out["ms_setup"], out["ms_iterate"]))
     assert np.all(np.isfinite(tr)) and tr[1] > tr[0]
     # the sampled estimate over 2^14 fixed entries tracks the exact fit (Sec. 3.4)
-    assert abs(tr[1] - f_true) < 2e-3, (tr[1], f_true)
+    assert abs(tr[1] - f_true) < sampled_fit_bar(f_true), (tr[1], f_true)
 
 
 def test_1500_cubed_cp_als_exact_fit_matches_direct_evaluation(cb, big):
@@ -246,4 +254,4 @@ def test_1500_cubed_bf16_mix_run_fit_estimate_matches_exact_fit(cb, big_bf16):
     tr = trace.cpu().numpy()
     f_true = true_fit_device(X, dims, out["lam"], out["factors"])
     print("1500^3 BF16: sampled fit %s, exact fit %.6f" % (tr, f_true))
-    assert np.all(np.isfinite(tr)) and abs(tr[-1] - f_true) < 2e-3, (tr, f_true)
+    assert np.all(np.isfinite(tr)) and abs(tr[-1] - f_true) < sampled_fit_bar(f_true), (tr, f_true)
