@@ -48,8 +48,8 @@ constexpr int kSlots = 32;          // complex values a thread holds in a stage
 constexpr int kMaxStages = 16;
 constexpr int kFftMaxSmem = 200 * 1024;
 constexpr int kMaxFftLen = 8192;    // keeps the multiply-high divisions exact
-constexpr int kBsMinLen = 24;       // Bluestein form for I >= 24: its tables (7 I + 4 M floats) fit I^2
-constexpr int kBsMaxConv = 4096;    // longest Bluestein convolution (FP64 table builder in shared memory)
+constexpr int kBsMinLen = 33;       // Bluestein form for I >= 33: its tables and FP64 scratch fit I^2 floats
+constexpr int kBsMaxConv = 4096;    // longest Bluestein convolution
 // the stage radices, in the order a plan's stages run; radix R = R1 x R2 (R2 = 1 for the plain ones)
 constexpr int kNumRadices = 14;
 constexpr int kRadR1[kNumRadices] = {5, 5, 4, 5, 4, 5, 3, 4, 7, 3, 5, 4, 3, 2};
@@ -617,50 +617,58 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_fft_bs(const __grid_cons
 // The Bluestein tables of one length I behind its 5 I DCT floats (FP64, each rounded once to FP32):
 // c_n = exp(-i pi n^2 / I) for n < I (the angle reduced exactly: n^2 mod 2 I), the length-M twiddles
 // exp(-2 pi i m / M), and B_k / M with B = FFT_M(b), b_m = conj(c_m) for m < I, conj(c_(M-m)) for
-// M - I < m < M, zero between.  Every block keeps exp(-2 pi i j / M) and conj(c_m) in FP64 shared
-// memory and forms its share of the B_k by direct sums over the 2 I - 1 nonzero b_m.
-__global__ void __launch_bounds__(256) k_build_bs_tabs(int I, int M, float* out) {
-  extern __shared__ double bs64[];
-  double2* wm = reinterpret_cast<double2*>(bs64);      // M
-  double2* dm = wm + M;                                  // I: conj(c_m)
-  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+// M - I < m < M, zero between.  First kernel: the FP64 roots exp(-2 pi i j / M) and conj(c_m) into
+// scratch behind the FP32 tables, and the FP32 c_n and twiddles.  Second kernel: one warp per B_k,
+// the lanes splitting the direct sum over the 2 I - 1 nonzero b_m (root indices stepped, no
+// divisions), a fixed-order warp reduction.
+__global__ void __launch_bounds__(256) k_build_bs_roots(int I, int M, float* out, double2* wm, double2* dm) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  float* chirp = out + 5 * I;
+  float* twm = chirp + 2 * I;
+  if (e < M) {
     double sn, cs;
-    sincospi(2.0 * (double)j / (double)M, &sn, &cs);
-    wm[j] = make_double2(cs, -sn);
-  }
-  for (int m = threadIdx.x; m < I; m += blockDim.x) {
+    sincospi(2.0 * (double)e / (double)M, &sn, &cs);
+    wm[e] = make_double2(cs, -sn);
+    twm[2 * e] = (float)cs;
+    twm[2 * e + 1] = (float)(-sn);
+  } else if (e < M + I) {
+    const int m = e - M;
     const int64_t q = ((int64_t)m * m) % (2 * (int64_t)I);
     double sn, cs;
     sincospi((double)q / (double)I, &sn, &cs);
     dm[m] = make_double2(cs, sn);
+    chirp[2 * m] = (float)cs;
+    chirp[2 * m + 1] = (float)(-sn);
   }
-  __syncthreads();
-  float* chirp = out + 5 * I;
-  float* twm = chirp + 2 * I;
-  float* bf = twm + 2 * M;
-  if (blockIdx.x == 0) {
-    for (int m = threadIdx.x; m < I; m += blockDim.x) {
-      chirp[2 * m] = (float)dm[m].x;
-      chirp[2 * m + 1] = (float)(-dm[m].y);
+}
+
+__global__ void __launch_bounds__(256) k_build_bs_tabs(int I, int M, float* out, const double2* __restrict__ wm,
+                                                       const double2* __restrict__ dm) {
+  const int k = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (k >= M) return;
+  float* bf = out + 5 * I + 2 * I + 2 * M;
+  double re = 0.0, im = 0.0;
+  int j0 = (int)(((int64_t)lane * k) % M);   // (m k) mod M for m = lane, lane + 32, ...
+  const int step = (int)(((int64_t)32 * k) % M);
+  for (int m = lane; m < I; m += 32) {   // b_m = dm[m] at m and at M - m (m >= 1)
+    const double2 b = dm[m];
+    const double2 w0 = wm[j0];
+    re += b.x * w0.x - b.y * w0.y;
+    im += b.x * w0.y + b.y * w0.x;
+    if (m > 0) {
+      const double2 w1 = wm[j0 == 0 ? 0 : M - j0];
+      re += b.x * w1.x - b.y * w1.y;
+      im += b.x * w1.y + b.y * w1.x;
     }
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-      twm[2 * j] = (float)wm[j].x;
-      twm[2 * j + 1] = (float)wm[j].y;
-    }
+    j0 += step;
+    if (j0 >= M) j0 -= M;
   }
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
-    double re = 0.0, im = 0.0;
-    for (int m = 0; m < I; ++m) {   // b_m = dm[m] at m and at M - m (m >= 1)
-      const double2 b = dm[m];
-      const double2 w0 = wm[(int)(((int64_t)m * k) % M)];
-      re += b.x * w0.x - b.y * w0.y;
-      im += b.x * w0.y + b.y * w0.x;
-      if (m > 0) {
-        const double2 w1 = wm[(int)(((int64_t)(M - m) * k) % M)];
-        re += b.x * w1.x - b.y * w1.y;
-        im += b.x * w1.y + b.y * w1.x;
-      }
-    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) {
     bf[2 * k] = (float)(re / M);
     bf[2 * k + 1] = (float)(im / M);
   }
@@ -1432,16 +1440,12 @@ bool mix_fft_supported(int dtype, int N, const int64_t* dims) {
 cudaError_t launch_build_bs_tables(int I, float* fft_tab, cudaStream_t s) {
   const int M = bs_length(I);
   if (M == 0) return cudaSuccess;   // a 7-smooth length (or none): nothing to add
-  const size_t smem = (size_t)(M + I) * sizeof(double2);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_build_bs_tabs, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((kBsMaxConv + kBsMaxConv / 2 + 1) * sizeof(double2)));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const int blocks = std::min(152, (M + 255) / 256 * 4);
-  k_build_bs_tabs<<<blocks, 256, smem, s>>>(I, M, fft_tab);
+  // FP64 scratch behind the FP32 tables (7 I + 4 M floats), inside the I x I table buffer
+  const int off = (7 * I + 4 * M + 3) / 4 * 4;
+  double2* wm = reinterpret_cast<double2*>(fft_tab + off);
+  double2* dm = wm + M;
+  k_build_bs_roots<<<(M + I + 255) / 256, 256, 0, s>>>(I, M, fft_tab, wm, dm);
+  k_build_bs_tabs<<<(M + 7) / 8, 256, 0, s>>>(I, M, fft_tab, wm, dm);
   return cudaGetLastError();
 }
 

@@ -537,12 +537,12 @@ def test_fft_mixing_matches_oracle(cb, engine, dims):
     assert_elementwise(gotd, ref, 2.0 ** -21, 4 * len(dims) * np.sqrt(max(dims)))
 
 
-# lengths with a prime factor above 7 by Bluestein's chirp-z form (the length-I DFT as a cyclic
-# convolution of a 7-smooth length M >= 2 I - 1: 37 -> 75, 53 -> 105, 61 -> 126, 127 -> 256,
-# 331 -> 672, 26 -> 60, 34 -> 70, 38 -> 75, 29 -> 60, 31 -> 63, 509 -> 1029), alone and next to
-# 7-smooth modes, with partial blocks; FP32 to 2e-6 relative, element-wise with the depth of two
-# length-M transforms per pass
-@pytest.mark.parametrize("dims", [(61, 37, 53), (127, 12, 10), (331, 24, 9), (26, 34, 38), (29, 31, 30, 7),
+# lengths of at least 33 with a prime factor above 7 by Bluestein's chirp-z form (the length-I DFT as
+# a cyclic convolution of a 7-smooth length M >= 2 I - 1: 37 -> 75, 53 -> 105, 61 -> 125,
+# 127 -> 256, 331 -> 672, 34 -> 70, 38 -> 75, 41 -> 81, 43 -> 90, 509 -> 1024), alone and next to
+# 7-smooth modes and to a short one on the dense path (26), with partial blocks; FP32 to 2e-6
+# relative, element-wise with the depth of two length-M transforms per pass
+@pytest.mark.parametrize("dims", [(61, 37, 53), (127, 12, 10), (331, 24, 9), (26, 34, 38), (41, 43, 30, 7),
                                   (509, 40, 6), (40, 509, 6)])
 def test_bluestein_mixing_matches_oracle(cb, dims):
     X = rand_tensor(dims, torch.float32, 13)
