@@ -747,8 +747,11 @@ cudaError_t launch_split_f16(const float* w, void* out16, int64_t n, cudaStream_
 }
 
 cudaError_t launch_absmax(const void* X, int dtype, int64_t P, unsigned* out, cudaStream_t s) {
-  int64_t blocks = (P + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 1;
+  int64_t blocks = (P + 255) / 256;   // grid-stride: eight blocks per SM at most
+  if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
   if (blocks < 1) blocks = 1;
   switch (dtype) {
     case CPR_F64: k_absmax<double><<<(unsigned)blocks, 256, 0, s>>>((const double*)X, P, out); break;
