@@ -317,13 +317,15 @@ __device__ void sum_pairs(const float2* src, int rows, int cols, int64_t stride,
     const int per = (rows + nch - 1) / nch;
     const int r0 = q * per, r1 = min(rows, r0 + per);
     int i = r0;
-    for (; i + 3 < r1; i += 4) {
-      const float2 v0 = __ldcg(src + (int64_t)i * stride + j), v1 = __ldcg(src + (int64_t)(i + 1) * stride + j);
-      const float2 v2 = __ldcg(src + (int64_t)(i + 2) * stride + j), v3 = __ldcg(src + (int64_t)(i + 3) * stride + j);
-      pair_acc2(v0, h0, l0);
-      pair_acc2(v1, h1, l1);
-      pair_acc2(v2, h0, l0);
-      pair_acc2(v3, h1, l1);
+    for (; i + 7 < r1; i += 8) {   // eight loads in flight
+      float2 v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = __ldcg(src + (int64_t)(i + k) * stride + j);
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        pair_acc2(v[k], h0, l0);
+        pair_acc2(v[k + 1], h1, l1);
+      }
     }
     for (; i < r1; ++i) pair_acc2(__ldcg(src + (int64_t)i * stride + j), h0, l0);
     pair_acc2(make_float2(h1, l1), h0, l0);
@@ -1130,8 +1132,8 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
           float2* mrow = reinterpret_cast<float2*>(sm + L.mrow);
           const int i0 = x.c * ms.rpc;
           const int nrows = max(0, min(ms.I, i0 + ms.rpc) - i0);
-          for (int e = tid; e < nrows * R; e += nrest) {
-            const int li = e / R, r = e - li * R;
+          for (int e = tid; e < nrows * R; e += nrest) {   // rows fastest: a column's rows are adjacent in Mpart
+            const int r = nrows > 0 ? e / nrows : 0, li = e - r * nrows;
             const float* src = gs.Mpart + (int64_t)r * ms.I + i0 + li;
             const int64_t sstr = (int64_t)R * ms.I;
             float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
@@ -1148,7 +1150,7 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
             }
             for (; q < ms.nsplit; ++q) pair_acc(__ldcg(src + q * sstr), h0, l0);
             pair_acc2(make_float2(h1, l1), h0, l0);
-            mrow[e] = pair_norm(h0, l0);
+            mrow[li * R + r] = pair_norm(h0, l0);
           }
         }
         __syncthreads();
