@@ -88,6 +88,10 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 __device__ __forceinline__ void named_sync(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
+// Arrives at block barrier id (n threads in all) without waiting; the threads that wait call named_sync.
+__device__ __forceinline__ void named_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
 
 // AND of v over the n threads of block barrier id (which all call it); also a barrier for them.
 __device__ __forceinline__ bool named_and(int id, int n, bool v) {
@@ -779,13 +783,18 @@ __device__ void prefetch_next(const Prob& p, const GridCtx& x, int n, uint32_t t
 // (its own entries are the published ones).  A pivot below 1e-6 (relative to the unit diagonal) or
 // not finite returns false in every thread.  src: Gs (R x R, FP32); dst: X0 (may be src: every read
 // precedes the first barrier); piv: 2 PAD floats of scratch (16-byte aligned); bar_id: a block
-// barrier for the PAD threads when W = 2.
+// barrier for the PAD threads when W = 2; arrive_id: a block barrier of the whole CTA at which the
+// PAD threads arrive once their columns are in registers.  Not inlined: the sweep's registers are
+// then allocated apart from the rest of the kernel's live state (the caller saves that around the
+// call), so the columns and the pivot row's loads stay in registers.
 template <int W>
-__device__ bool sweep_regs(const float* src, float* dst, int R, float* piv, int j, int bar_id) {
+__device__ __noinline__ bool sweep_regs(const float* src, float* dst, int R, float* piv, int j, int bar_id,
+                                        int arrive_id) {
   constexpr int PAD = 32 * W;
   float r[PAD];
 #pragma unroll
   for (int p = 0; p < PAD; ++p) r[p] = (p < R && j < R) ? src[p * R + j] : 0.f;
+  named_arrive(arrive_id, kGT);
   bool bad = false;
   for (int k = 0; k < R; ++k) {
     float* pv = piv + (k & 1) * PAD;
@@ -1111,7 +1120,8 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
         }
         // G and its scaled FP32 copy by every warp; then the FP32 inverse X0 by the last W warps (a
         // chain of pivots on their registers) while the other warps pass grid barrier C and reduce
-        // this CTA's rows of M
+        // this CTA's rows of M.  The M loads start once the sweep's columns are in registers (block
+        // barrier 5): shared loads issued after them queue behind the partials' L2 loads.
         const bool gfast = solver_prepare<MAXR, kGT>(p, L, sm, gs, ds, scp, ne_r, ne_c, 0);
         const int W = (MAXR > 32 && R > 32) ? 2 : 1;
         const int nrest = kGT - 32 * W;
@@ -1121,36 +1131,43 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
             float* piv = reinterpret_cast<float*>(sm + L.piv);
             bool iok;
             if constexpr (MAXR > 32) {
-              iok = W == 2 ? sweep_regs<2>(x0, x0, R, piv, tid - nrest, 3) : sweep_regs<1>(x0, x0, R, piv, tid - nrest, 3);
+              iok = W == 2 ? sweep_regs<2>(x0, x0, R, piv, tid - nrest, 3, 5)
+                           : sweep_regs<1>(x0, x0, R, piv, tid - nrest, 3, 5);
             } else {
-              iok = sweep_regs<1>(x0, x0, R, piv, tid - nrest, 3);
+              iok = sweep_regs<1>(x0, x0, R, piv, tid - nrest, 3, 5);
             }
             if (tid == nrest) s_invbad = iok ? 0 : 1;
+          } else {
+            named_arrive(5, kGT);
           }
-        } else if (grid_sync(gs, x, &s_flag, 4, nrest)) {   // (C) every split's partial M is stored
-          // ---- P3: the split partials of this CTA's rows, summed exactly into pairs
-          float2* mrow = reinterpret_cast<float2*>(sm + L.mrow);
-          const int i0 = x.c * ms.rpc;
-          const int nrows = max(0, min(ms.I, i0 + ms.rpc) - i0);
-          for (int e = tid; e < nrows * R; e += nrest) {   // rows fastest: a column's rows are adjacent in Mpart
-            const int r = nrows > 0 ? e / nrows : 0, li = e - r * nrows;
-            const float* src = gs.Mpart + (int64_t)r * ms.I + i0 + li;
-            const int64_t sstr = (int64_t)R * ms.I;
-            float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-            int q = 0;
-            for (; q + 7 < ms.nsplit; q += 8) {   // eight loads in flight
-              float v[8];
+        } else {
+          const bool cok = grid_sync(gs, x, &s_flag, 4, nrest);   // (C) every split's partial M is stored
+          named_sync(5, kGT);
+          if (cok) {
+            // ---- P3: the split partials of this CTA's rows, summed exactly into pairs
+            float2* mrow = reinterpret_cast<float2*>(sm + L.mrow);
+            const int i0 = x.c * ms.rpc;
+            const int nrows = max(0, min(ms.I, i0 + ms.rpc) - i0);
+            for (int e = tid; e < nrows * R; e += nrest) {   // rows fastest: a column's rows are adjacent in Mpart
+              const int r = nrows > 0 ? e / nrows : 0, li = e - r * nrows;
+              const float* src = gs.Mpart + (int64_t)r * ms.I + i0 + li;
+              const int64_t sstr = (int64_t)R * ms.I;
+              float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+              int q = 0;
+              for (; q + 7 < ms.nsplit; q += 8) {   // eight loads in flight
+                float v[8];
 #pragma unroll
-              for (int k = 0; k < 8; ++k) v[k] = __ldcg(src + (q + k) * sstr);
+                for (int k = 0; k < 8; ++k) v[k] = __ldcg(src + (q + k) * sstr);
 #pragma unroll
-              for (int k = 0; k < 8; k += 2) {
-                pair_acc(v[k], h0, l0);
-                pair_acc(v[k + 1], h1, l1);
+                for (int k = 0; k < 8; k += 2) {
+                  pair_acc(v[k], h0, l0);
+                  pair_acc(v[k + 1], h1, l1);
+                }
               }
+              for (; q < ms.nsplit; ++q) pair_acc(__ldcg(src + q * sstr), h0, l0);
+              pair_acc2(make_float2(h1, l1), h0, l0);
+              mrow[li * R + r] = pair_norm(h0, l0);
             }
-            for (; q < ms.nsplit; ++q) pair_acc(__ldcg(src + q * sstr), h0, l0);
-            pair_acc2(make_float2(h1, l1), h0, l0);
-            mrow[li * R + r] = pair_norm(h0, l0);
           }
         }
         __syncthreads();
@@ -1198,7 +1215,7 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
         __syncthreads();
         break;
       }
-      // ---- sampled fit (Sec. 3.4): one warp per fixed entry
+      // ---- sampled fit (Sec. 3.4) over the CTA's share of the fixed entries
       for (int r = tid; r < R; r += kGT) {
         double w = lam[r];
         for (int m = 0; m < N; ++m) w *= sc[m * R + r];
