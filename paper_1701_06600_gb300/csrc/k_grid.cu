@@ -747,8 +747,8 @@ __device__ void contract_units_tc(const Prob& p, const GridSmem& L, unsigned cha
 
 // Prefetch into L2 the fiber segments the contraction units of the next mode update will read.
 template <typename T>
-__device__ void prefetch_next(const Prob& p, const GridCtx& x, int n, uint32_t t, const ModeSplit& ms, int tile_rows) {
-  const int ct = threadIdx.x - kGramT;
+__device__ void prefetch_next(const Prob& p, const GridCtx& x, int n, uint32_t t, const ModeSplit& ms, int tile_rows,
+                              int ti, int nthr) {
   const T* X = reinterpret_cast<const T*>(p.Xrep[n]);
   if (!(p.use_rep || n == 0)) return;   // strided fibers: nothing contiguous to prefetch
   for (int u = x.c; u < ms.units; u += x.G) {
@@ -757,15 +757,12 @@ __device__ void prefetch_next(const Prob& p, const GridCtx& x, int n, uint32_t t
     const int rows = min(tile_rows, ms.I - i0);
     const int js = split * ms.spl;
     const int cnt = min(ms.spl, p.S - js);
-    const int lines = rows * (int)sizeof(T) / 128 + 2;   // 128-byte lines a row segment can touch
-    for (int e = ct; e < cnt * lines; e += kCT) {
-      const int jj = e / lines, l = e - jj * lines;
+    for (int jj = ti; jj < cnt; jj += nthr) {   // one draw per sample, then its row segment's lines
       uint32_t ids[kMaxOrder];
       const int64_t off = grid_draw(p, n, t, (uint32_t)(js + jj), ids);
-      const uintptr_t a0 = reinterpret_cast<uintptr_t>(X + off + i0) & ~(uintptr_t)127;
       const uintptr_t end = reinterpret_cast<uintptr_t>(X + off + i0 + rows);
-      const uintptr_t a = a0 + (uintptr_t)l * 128;
-      if (a < end) prefetch_l2(reinterpret_cast<const void*>(a));
+      for (uintptr_t a = reinterpret_cast<uintptr_t>(X + off + i0) & ~(uintptr_t)127; a < end; a += 128)
+        prefetch_l2(reinterpret_cast<const void*>(a));
     }
   }
 }
@@ -1109,9 +1106,6 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
           } else {
             contract_units<T, MAXR>(p, L, sm, gs, x, n, t, ms, scf);
           }
-          const int nn = n + 1 < N ? n + 1 : 0;
-          const uint32_t nt = n + 1 < N ? t : t + 1;
-          prefetch_next<T>(p, x, nn, nt, mode_split(p, nn, x.G, use_tc ? kTM : kTI), use_tc ? kTM : kTI);
         }
         __syncthreads();
         if (s_abort) {
@@ -1168,6 +1162,10 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
               pair_acc2(make_float2(h1, l1), h0, l0);
               mrow[li * R + r] = pair_norm(h0, l0);
             }
+            // the next update's sampled fibers into L2, while the last warps finish the inverse
+            const int nn = n + 1 < N ? n + 1 : 0;
+            const uint32_t nt = n + 1 < N ? t : t + 1;
+            prefetch_next<T>(p, x, nn, nt, mode_split(p, nn, x.G, use_tc ? kTM : kTI), use_tc ? kTM : kTI, tid, nrest);
           }
         }
         __syncthreads();
