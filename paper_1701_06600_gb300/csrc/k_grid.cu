@@ -88,6 +88,21 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 __device__ __forceinline__ void named_sync(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
+// Shared-memory accesses by shared-window address (a function that is not inlined cannot tell that a
+// generic pointer points to shared memory).
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ float4 lds_v4f32(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts_f32(uint32_t a, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
 // Arrives at block barrier id (n threads in all) without waiting; the threads that wait call named_sync.
 __device__ __forceinline__ void named_arrive(int id, int n) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
@@ -779,33 +794,34 @@ __device__ void prefetch_next(const Prob& p, const GridCtx& x, int n, uint32_t t
 // The column of the pivot itself takes A'_ik = A_ik - A_ik (1 - 1 / A_kk) from the same fused update
 // (its own entries are the published ones).  A pivot below 1e-6 (relative to the unit diagonal) or
 // not finite returns false in every thread.  src: Gs (R x R, FP32); dst: X0 (may be src: every read
-// precedes the first barrier); piv: 2 PAD floats of scratch (16-byte aligned); bar_id: a block
+// precedes the first barrier); piv: 2 PAD floats of scratch (16-byte aligned); src, dst and piv are
+// shared-window addresses; bar_id: a block
 // barrier for the PAD threads when W = 2; arrive_id: a block barrier of the whole CTA at which the
 // PAD threads arrive once their columns are in registers.  Not inlined: the sweep's registers are
 // then allocated apart from the rest of the kernel's live state (the caller saves that around the
 // call), so the columns and the pivot row's loads stay in registers.
 template <int W>
-__device__ __noinline__ bool sweep_regs(const float* src, float* dst, int R, float* piv, int j, int bar_id,
+__device__ __noinline__ bool sweep_regs(uint32_t src, uint32_t dst, int R, uint32_t piv, int j, int bar_id,
                                         int arrive_id) {
   constexpr int PAD = 32 * W;
   float r[PAD];
 #pragma unroll
-  for (int p = 0; p < PAD; ++p) r[p] = (p < R && j < R) ? src[p * R + j] : 0.f;
+  for (int p = 0; p < PAD; ++p) r[p] = (p < R && j < R) ? lds_f32(src + 4u * (p * R + j)) : 0.f;
   named_arrive(arrive_id, kGT);
   bool bad = false;
   for (int k = 0; k < R; ++k) {
-    float* pv = piv + (k & 1) * PAD;
-    pv[(j - k - 1) & (PAD - 1)] = r[0];
+    const uint32_t pv = piv + 4u * (k & 1) * PAD;
+    sts_f32(pv + 4u * ((j - k - 1) & (PAD - 1)), r[0]);
     if (W == 1) __syncwarp();
     else named_sync(bar_id, PAD);
-    const float d = pv[PAD - 1];                 // row k's entry of column k
+    const float d = lds_f32(pv + 4u * (PAD - 1));   // row k's entry of column k
     bad = bad || !(d > 1e-6f) || !isfinite(d);
     const float inv = __frcp_rn(d);
     const float akj = r[0];
     const float c = j == k ? 1.f - inv : akj * inv;
 #pragma unroll
     for (int p = 0; p < PAD; p += 4) {
-      const float4 q = *reinterpret_cast<const float4*>(pv + p);
+      const float4 q = lds_v4f32(pv + 4u * p);
       r[p] = fmaf(-q.x, c, r[p + 1]);
       r[p + 1] = fmaf(-q.y, c, r[p + 2]);
       r[p + 2] = fmaf(-q.z, c, r[p + 3]);
@@ -819,7 +835,7 @@ __device__ __noinline__ bool sweep_regs(const float* src, float* dst, int R, flo
 #pragma unroll
     for (int p = 0; p < PAD; ++p) {
       const int row = (p + R) & (PAD - 1);
-      if (row < R) dst[row * R + j] = -r[p];
+      if (row < R) sts_f32(dst + 4u * (row * R + j), -r[p]);
     }
   }
   return !bad;
@@ -1121,8 +1137,8 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
         const int nrest = kGT - 32 * W;
         if (tid >= nrest) {
           if (gfast) {
-            float* x0 = reinterpret_cast<float*>(sm + L.x0);
-            float* piv = reinterpret_cast<float*>(sm + L.piv);
+            const uint32_t x0 = (uint32_t)__cvta_generic_to_shared(sm + L.x0);
+            const uint32_t piv = (uint32_t)__cvta_generic_to_shared(sm + L.piv);
             bool iok;
             if constexpr (MAXR > 32) {
               iok = W == 2 ? sweep_regs<2>(x0, x0, R, piv, tid - nrest, 3, 5)
