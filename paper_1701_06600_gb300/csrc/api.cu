@@ -456,28 +456,46 @@ bool fft_mixing(int dtype, int N, const int64_t* dims) {
   return mix_engine() != CPR_MIX_DENSE && mix_fft_supported(dtype, N, dims);
 }
 
+// Whether enqueue_mixing takes the factored DCT passes for these buffers and tables.
+bool mixing_uses_fft(const void* t1, int dtype, int N, const int64_t* dims, float* const* W32, double* const* SG) {
+  bool fft = t1 != nullptr && fft_mixing(dtype, N, dims);
+  for (int n = 0; n < N && fft; ++n) fft = W32[n] != nullptr && SG[n] != nullptr;
+  return fft;
+}
+
 int enqueue_mixing(const void* src, void* final, void* t1, void* t2, void* rep_last, int dtype, int N,
                    const int64_t* dims, float* const* W32, float* const* Wlo, double* const* W64,
                    double* const* SG, int* err, unsigned* amax, bool amax0_ready, cudaStream_t s, int64_t& launches,
-                   bool* wrote_rep_last) {
+                   bool* wrote_rep_last, State* norm_state) {
   *wrote_rep_last = false;
-  bool fft = t1 != nullptr && fft_mixing(dtype, N, dims);
-  for (int n = 0; n < N && fft; ++n) fft = W32[n] != nullptr && SG[n] != nullptr;
-  if (fft) {
+  if (mixing_uses_fft(t1, dtype, N, dims, W32, SG)) {
     // factored DCT passes (the tables are in the dense operator's buffer, 5 I <= I^2 floats, built
     // with the operators); pass n writes the layout pass n + 1 reads, the outputs alternate between
-    // final and t1 so that the last pass writes final
+    // final and t1 so that the last pass writes final.  With norm_state, the first pass (which reads
+    // the caller's tensor) also leaves one sum of squares per CTA in the buffer it does not write,
+    // summed into norm_state->norm_x before the second pass overwrites that buffer.
     void* bufs[2] = {final, t1};
     const void* U = src;
     for (int n = 0; n < N; ++n) {
       void* y = bufs[(N - 1 - n) & 1];
       void* ys = (n == N - 1 && rep_last) ? rep_last : nullptr;
-      CPR_LAUNCH(CPR_KERNEL_MIX, launch_mix_fft(U, y, ys, W32[n], dtype, N, dims, n, err, s));
+      double* part = (n == 0 && norm_state) ? static_cast<double*>(bufs[N & 1]) : nullptr;
+      int64_t nblk = 0;
+      CPR_LAUNCH(CPR_KERNEL_MIX, launch_mix_fft(U, y, ys, W32[n], dtype, N, dims, n, err, s, part, &nblk));
+      if (part) {   // one partial per CTA: a first level of 4096-partial sums, then the finish
+        if (nblk <= 0) return CPR_EINVAL;
+        double* part2 = part + nblk;
+        const int64_t nb2 = sumsq_partials_blocks(nblk);
+        if (nb2 > INT32_MAX) return CPR_EINVAL;
+        CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq_partials(part, nblk, part2, s));
+        CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq_finish(part2, (int)nb2, nullptr, norm_state, 1, s));
+      }
       if (ys) *wrote_rep_last = true;
       U = y;
     }
     return CPR_OK;
   }
+  if (norm_state) return CPR_EINVAL;   // the caller reduces ||X|| itself on the other paths
   bool tc = dtype == CPR_F32 && t2 != nullptr;
   for (int n = 0; n < N && tc; ++n) tc = Wlo[n] != nullptr && mix_tc_supported(dtype, (int)dims[n]);
   bool tc16 = tc && amax != nullptr;
@@ -748,10 +766,15 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
     bool rep_last_done = false;
     // ||X|| on the caller's tensor (equal to the mixed tensor's norm, Alg. 5); for CPRAND-MIX the same
     // pass records the largest |x| (the scale of the first FP16-split mixing pass)
+    // (with the factored DCT passes, the first pass reduces ||X|| from the fibers it has loaded)
     unsigned* amax = mix ? reinterpret_cast<unsigned*>(pl.d_counter + 4) : nullptr;
-    if (amax) CPR_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned) * (size_t)(p.N + 1), s));
-    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq(Xs[b].data, p.dtype, p.P, pl.d_normpart, pl.normblk, s, amax));
-    CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq_finish(pl.d_normpart, pl.normblk, nullptr, pl.d_states + b, 1, s));
+    const bool norm_in_mix = mix && mixing_uses_fft(pl.d_tmp, p.dtype, p.N, p.dims, pl.mixb[b].W32, pl.mixb[b].sg) &&
+                             mix_fft_norm_fits(p.dtype, p.N, p.dims);
+    if (!norm_in_mix) {
+      if (amax) CPR_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned) * (size_t)(p.N + 1), s));
+      CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq(Xs[b].data, p.dtype, p.P, pl.d_normpart, pl.normblk, s, amax));
+      CPR_LAUNCH(CPR_KERNEL_OTHER, launch_sumsq_finish(pl.d_normpart, pl.normblk, nullptr, pl.d_states + b, 1, s));
+    }
     if (mix) {
       const MixBufs& mb = pl.mixb[b];
       const bool fftm = pl.d_tmp != nullptr && fft_mixing(p.dtype, p.N, p.dims) && mb.W32[0] != nullptr;
@@ -762,7 +785,7 @@ int run_batched(int B, const cpr_tensor* Xs, const int* Rs, const int64_t* Ss, c
       if (int st = enqueue_mixing(Xs[b].data, mb.xhat, pl.d_tmp, pl.d_tmp2,
                                   p.use_rep ? const_cast<void*>(p.Xrep[p.N - 1]) : nullptr, p.dtype, p.N, p.dims,
                                   mb.W32, mb.Wlo, mb.W64, mb.sg, pl.d_counter + 2, amax, true, s, launches,
-                                  &rep_last_done))
+                                  &rep_last_done, norm_in_mix ? pl.d_states + b : nullptr))
         return st;
     }
     if (p.use_rep)
@@ -1532,7 +1555,7 @@ int cpr_mix_tensor(const cpr_tensor* X, void* out_dev, uint64_t seed, uint32_t b
                                                       W64[n], F64[n], sg[n], s, fftm ? W32[n] : nullptr));
   bool unused = false;
   if (int st = enqueue_mixing(X->data, out_dev, tmp, tmp2, nullptr, dt, N, X->dims, W32, Wlo, W64, sg, derr,
-                              reinterpret_cast<unsigned*>(derr + 4), false, s, launches, &unused))
+                              reinterpret_cast<unsigned*>(derr + 4), false, s, launches, &unused, nullptr))
     return st;
   return CPR_OK;
 }

@@ -298,6 +298,10 @@ cudaError_t launch_sumsq_finish(const double* part, int nblk, double* out_norm, 
 // keeps the summation order, and so the result, the same on every device.
 constexpr int kSumsqMaxBlocks = 1216;
 int sumsq_blocks(int64_t P);
+// a first level for many sum-of-squares partials: part[0 .. nblk) into sumsq_partials_blocks(nblk)
+// sums (fixed order), for launch_sumsq_finish
+int64_t sumsq_partials_blocks(int64_t nblk);
+cudaError_t launch_sumsq_partials(const double* part, int64_t nblk, double* out, cudaStream_t s);
 
 // step hooks
 cudaError_t launch_sample_only(const void* X, int N, const int64_t* dims, int n, int64_t S,
@@ -358,8 +362,14 @@ bool mix_fft_supported(int dtype, int N, const int64_t* dims);
 // the Bluestein tables of a length with a prime factor above 7 (7 I + 4 M floats from fft_tab on,
 // after the 5 I DCT floats); nothing for a 7-smooth length
 cudaError_t launch_build_bs_tables(int I, float* fft_tab, cudaStream_t s);
+// whether the first pass's per-CTA sums of squares and their first-level sums (8 bytes each) fit
+// in one tensor-sized buffer of this dtype
+bool mix_fft_norm_fits(int dtype, int N, const int64_t* dims);
+// normpart: when given, one FP64 sum of squares of the pass's input per CTA (nblocks of them, the
+// count returned through nblocks), for launch_sumsq_finish
 cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* tab, int dtype, int N,
-                           const int64_t* dims, int n, int* err, cudaStream_t s);
+                           const int64_t* dims, int n, int* err, cudaStream_t s, double* normpart = nullptr,
+                           int64_t* nblocks = nullptr);
 int mix_engine();   // CPR_MIX_* (process-wide, cpr_set_mix_engine)
 // the unitary DFT passes of the complex form (Alg. 4): complex (float2) output; the first pass reads
 // the real FP32 tensor (real_in), later passes complex input; tab as for launch_mix_fft

@@ -235,6 +235,34 @@ cudaError_t launch_sumsq(const void* X, int dtype, int64_t P, double* part, int 
   return cudaGetLastError();
 }
 
+// First level for many partials (one per CTA of a mixing pass): CTA b sums part[4096 b ..
+// 4096 b + 4095] in a fixed order (16 loads in flight per thread) into out[b].
+constexpr int kPartChunk = 4096;
+__global__ void __launch_bounds__(256) k_sumsq_partials(const double* __restrict__ part, int64_t nblk, double* out) {
+  __shared__ double red[8];
+  const int64_t base = (int64_t)blockIdx.x * kPartChunk;
+  double v[kPartChunk / 256];
+#pragma unroll
+  for (int u = 0; u < kPartChunk / 256; ++u) {
+    const int64_t q = base + u * 256 + threadIdx.x;
+    v[u] = q < nblk ? part[q] : 0.0;
+  }
+  double a = 0.0;
+#pragma unroll
+  for (int u = 0; u < kPartChunk / 256; ++u) a += v[u];
+  const double t = block_sum(a, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = t;
+}
+
+int64_t sumsq_partials_blocks(int64_t nblk) { return (nblk + kPartChunk - 1) / kPartChunk; }
+
+cudaError_t launch_sumsq_partials(const double* part, int64_t nblk, double* out, cudaStream_t s) {
+  const int64_t nb = sumsq_partials_blocks(nblk);
+  if (nb < 1 || nb > INT32_MAX) return cudaErrorInvalidValue;
+  k_sumsq_partials<<<(unsigned)nb, 256, 0, s>>>(part, nblk, out);
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) k_sumsq_finish(const double* part, int nblk, double* out_norm, State* st,
                                                       int nstates) {
   __shared__ double red[8];

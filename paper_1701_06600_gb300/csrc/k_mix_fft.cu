@@ -83,6 +83,9 @@ struct FftArgs {
   // convolution of length M (7-smooth, M >= 2 I - 1); st / nst then describe the length-M stages
   int M, Mpad;
   uint32_t mM, mI;      // ceil(2^32 / M), ceil(2^32 / I)
+  // when given, CTA b writes the sum of squares of its input fibers to normpart[b] (FP64), so that
+  // the pass that reads the caller's tensor also yields ||X||^2 (summed by launch_sumsq_finish)
+  double* normpart;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -305,6 +308,53 @@ __device__ __forceinline__ int fft_block(const FftArgs& a, int64_t blk, int64_t&
   return (int)min((int64_t)a.BJ, a.Iv - iv0);
 }
 
+// ||fibers||^2 of the CTA's block, once its nf input rows (I FP32 entries each, rows Ipad floats
+// apart, Ipad a multiple of 4) are in shared memory and before any stage writes them: 16-byte loads,
+// four FP32 accumulators per thread, the warp's sum as an FP32 pair (error-free two-sums: the FP64
+// pipe is too slow for one reduction per CTA of every pass), converted to FP64 into part[warp].  The
+// caller adds the warps' partials in warp order after a later block barrier (fft_sumsq_store).
+// the warp's sum of the lanes' v as an FP32 pair (error-free two-sums), stored in FP64 by lane 0
+__device__ __forceinline__ void fft_sumsq_warp(float v, int lane, double* out) {
+  float h = v, l = 0.f;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    const float t = __fadd_rn(h, h2), bv = __fsub_rn(t, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bv)), __fsub_rn(h2, bv));
+    h = t;
+    l = __fadd_rn(l, __fadd_rn(l2, e));
+  }
+  if (lane == 0) *out = (double)h + (double)l;
+}
+template <int TPB>
+__device__ __forceinline__ void fft_sumsq_rows(const float* Y, int nf, int I, int Ipad, int tid, int lane,
+                                               double* part) {
+  const int I4 = I >> 2;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 4
+  for (int e = tid; e < nf * I4; e += TPB) {
+    const int f = e / I4, c = e - f * I4;
+    const float4 v = *reinterpret_cast<const float4*>(Y + f * Ipad + 4 * c);
+    s0 = fmaf(v.x, v.x, s0);
+    s1 = fmaf(v.y, v.y, s1);
+    s2 = fmaf(v.z, v.z, s2);
+    s3 = fmaf(v.w, v.w, s3);
+  }
+  for (int e = tid; e < nf * (I - 4 * I4); e += TPB) {   // the entries past the last full vector
+    const int f = e / (I - 4 * I4), c = 4 * I4 + e - f * (I - 4 * I4);
+    const float x = Y[f * Ipad + c];
+    s0 = fmaf(x, x, s0);
+  }
+  fft_sumsq_warp((s0 + s1) + (s2 + s3), lane, part + (tid >> 5));
+}
+template <int TPB>
+__device__ __forceinline__ void fft_sumsq_store(const FftArgs& a, const double* part, int tid) {
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < TPB / 32; ++w) t += part[w];
+    a.normpart[blockIdx.x] = t;
+  }
+}
+
 // the stages of radix index RIX (one loop per radix: the register arrays of different radices are
 // never live at once); the plan lists its stages in radix-index order
 template <int RIX, int TPB>
@@ -375,6 +425,8 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_fft(const __grid_constan
     return;
   }
   if (a.bulk && tid != 0) (void)fft_mbar_try(bar, 0);   // completed: returns at once
+  __shared__ double s_nrm[TPB / 32];
+  if (a.normpart) fft_sumsq_rows<TPB>(Y, nf, I, Ipad, tid, lane, s_nrm);
 
   // the DFT stages of the S = BJ / 2 complex sequences (the first also reorders the real fibers into
   // interleaved complex values)
@@ -395,6 +447,7 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_fft(const __grid_constan
   fft_stages_of<12, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
   fft_stages_of<13, TPB>(Z, I, Ipad, S, nst, s_st, st, tid, tw, sg);
   if (st != nst && tid == 0) atomicExch(a.err, 1);   // a stage order the host never produces
+  if (a.normpart) fft_sumsq_store<TPB>(a, s_nrm, tid);   // after the stages' block barriers
 
   // separate the two real fibers of each sequence and apply c_k exp(-i pi k / (2I)); the pair
   // (k, I - k) is read and written by one thread: (y_{2p}[k], y_{2p+1}[k]) replaces Z_p[k]
@@ -542,6 +595,8 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_fft_bs(const __grid_cons
     return;
   }
   if (a.bulk && tid != 0) (void)fft_mbar_try(bar, 0);
+  __shared__ double s_nrm[TPB / 32];
+  if (a.normpart) fft_sumsq_rows<TPB>(Y, nf, I, Ipad, tid, lane, s_nrm);
   // a_p[m] = v_p[m] c_m (m < I), 0 past I: v_p[m] = d[s] (x_2p[s], x_2p+1[s]), s the DCT reorder of m
   for (int e = tid; e < S * M; e += TPB) {
     const int p = fdiv(e, M, a.mM), m = e - p * M;
@@ -555,6 +610,7 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_mix_fft_bs(const __grid_cons
     W[p * Mpad + m] = x;
   }
   __syncthreads();
+  if (a.normpart) fft_sumsq_store<TPB>(a, s_nrm, tid);
   bool good = bs_transform<TPB>(W, M, Mpad, S, a.nst, s_st, tid, twm);
   for (int e = tid; e < S * M; e += TPB) {   // times FFT_M(filter) / M, conjugated
     const int p = fdiv(e, M, a.mM), m = e - p * M;
@@ -918,14 +974,17 @@ struct CtPlan {
 
 // one stage of the compiled plan (the Stockham stage of fft_stage with constant parameters).  smask:
 // for butterfly j of the first stage, bit r set when the sign of its entry r (reorder order) is -1
+// nrm (first stage only, when given): the warp's sum of squares of the entries it read, into
+// nrm[warp] before the stage's block barrier
 template <class PL, int R1, int R2, int NS, bool FIRST>
-__device__ __forceinline__ void ct_stage(float2* Z, const float2* T, const uint32_t* smask, int tid) {
+__device__ __forceinline__ void ct_stage(float2* Z, const float2* T, const uint32_t* smask, int tid, double* nrm) {
   constexpr int I = PL::I, IPAD = PL::IPAD, TPB = PL::TPB, R = R1 * R2, L = I / R, NB = PL::S * L;
   constexpr int NQ = (NB + TPB - 1) / TPB;
   constexpr bool SKW = FIRST && PL::SKEW, SKR = !FIRST && NS == PL::radix(0) && PL::SKEW;
   constexpr int R0 = PL::radix(0);
   float2 v[NQ][R];
   int dst[NQ];
+  float sqx = 0.f, sqy = 0.f;
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     const int b = tid + q * TPB;
@@ -948,6 +1007,13 @@ __device__ __forceinline__ void ct_stage(float2* Z, const float2* T, const uint3
           const uint32_t flip = (msk << (31 - r)) & 0x80000000u;   // the sign bit of d
           v[q][r] = make_float2(__uint_as_float(__float_as_uint(row[src]) ^ flip),
                                 __uint_as_float(__float_as_uint(row[IPAD + src]) ^ flip));
+        }
+        if (nrm) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            sqx = fmaf(v[q][r].x, v[q][r].x, sqx);
+            sqy = fmaf(v[q][r].y, v[q][r].y, sqy);
+          }
         }
       } else {
         const int k = j % NS;
@@ -978,6 +1044,7 @@ __device__ __forceinline__ void ct_stage(float2* Z, const float2* T, const uint3
     }
     asm volatile("" ::: "memory");
   }
+  if (FIRST && nrm) fft_sumsq_warp(sqx + sqy, tid & 31, nrm + (tid >> 5));
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < NQ; ++q)
@@ -989,10 +1056,11 @@ __device__ __forceinline__ void ct_stage(float2* Z, const float2* T, const uint3
 }
 
 template <class PL, int NS, bool FIRST, class R0, class... Rest>
-__device__ __forceinline__ void ct_stages(float2* Z, const float2* T, const uint32_t* smask, int tid) {
-  ct_stage<PL, R0::R1, R0::R2, NS, FIRST>(Z, T, smask, tid);
+__device__ __forceinline__ void ct_stages(float2* Z, const float2* T, const uint32_t* smask, int tid, double* nrm) {
+  ct_stage<PL, R0::R1, R0::R2, NS, FIRST>(Z, T, smask, tid, nrm);
   if constexpr (sizeof...(Rest) > 0)
-    ct_stages<PL, NS * R0::R, false, Rest...>(Z, FIRST ? T : T + ct_twiddle_rows(R0::R1, R0::R2) * NS, smask, tid);
+    ct_stages<PL, NS * R0::R, false, Rest...>(Z, FIRST ? T : T + ct_twiddle_rows(R0::R1, R0::R2) * NS, smask, tid,
+                                              nullptr);
 }
 
 // the stage tables from the length-I twiddles in global memory (L2-resident): row e of a stage of
@@ -1034,8 +1102,8 @@ template <class PL> struct CtStages;
 template <int I_, int TPB_, int BJ_, int MINB_, class... Rs>
 struct CtStages<CtPlan<I_, TPB_, BJ_, MINB_, Rs...>> {
   using P = CtPlan<I_, TPB_, BJ_, MINB_, Rs...>;
-  static __device__ __forceinline__ void run(float2* Z, const float2* T, const uint32_t* smask, int tid) {
-    ct_stages<P, 1, true, Rs...>(Z, T, smask, tid);
+  static __device__ __forceinline__ void run(float2* Z, const float2* T, const uint32_t* smask, int tid, double* nrm) {
+    ct_stages<P, 1, true, Rs...>(Z, T, smask, tid, nrm);
   }
   static __device__ __forceinline__ void tables(float2* T, const float2* twg, int tid) {
     ct_tables<P, 1, true, Rs...>(T, twg, tid);
@@ -1132,8 +1200,10 @@ __global__ void __launch_bounds__(PL::TPB, PL::MINB) k_mix_fft_ct(const __grid_c
     return;
   }
   if (a.bulk && tid != 0) (void)fft_mbar_try(bar, 0);
+  __shared__ double s_nrm[TPB / 32];
 
-  CtStages<PL>::run(Z, Tt, smask, tid);
+  CtStages<PL>::run(Z, Tt, smask, tid, a.normpart ? s_nrm : nullptr);   // the first stage sums the squares
+  if (a.normpart) fft_sumsq_store<TPB>(a, s_nrm, tid);   // after the stages' block barriers
 
   T* yv = static_cast<T*>(a.yv);
   constexpr int KH = I / 2;   // entries k <= KH and their partners I - k cover 0 .. I - 1
@@ -1522,13 +1592,28 @@ bool fft_args(FftArgs& a, FftPlan& pl, const void* U, void* yv, void* ysame, con
 }
 }  // namespace
 
+bool mix_fft_norm_fits(int dtype, int N, const int64_t* dims) {
+  FftArgs a;
+  FftPlan pl;
+  if (N < 2) return false;
+  if (!fft_args(a, pl, nullptr, nullptr, nullptr, nullptr, N, dims, 0, nullptr, false, ct_plan_id((int)dims[0], dims[1 % N])))
+    return false;
+  int64_t P = 1;
+  for (int m = 0; m < N; ++m) P *= dims[m];
+  const int64_t es = dtype == CPR_F32 ? 4 : 2;
+  const int64_t words = a.nblocks + sumsq_partials_blocks(a.nblocks) + 1;
+  return a.nblocks > 0 && words <= P * es / 8;
+}
+
 cudaError_t launch_mix_fft(const void* U, void* yv, void* ysame, const float* tab, int dtype, int N,
-                           const int64_t* dims, int n, int* err, cudaStream_t s) {
+                           const int64_t* dims, int n, int* err, cudaStream_t s, double* normpart, int64_t* nblocks) {
   FftArgs a;
   FftPlan pl;
   if (N < 2 || n < 0 || n >= N) return cudaErrorInvalidValue;
   const int ct = ct_plan_id((int)dims[n], dims[(n + 1) % N]);
   if (!fft_args(a, pl, U, yv, ysame, tab, N, dims, n, err, false, ct)) return cudaErrorInvalidValue;
+  a.normpart = normpart;
+  if (nblocks) *nblocks = a.nblocks;
   const int I = a.I;
   const size_t es = dtype == CPR_F32 ? 4 : 2;
   a.bulk = dtype == CPR_F32 && (I * es) % 16 == 0 && (reinterpret_cast<uintptr_t>(U) & 15) == 0;
