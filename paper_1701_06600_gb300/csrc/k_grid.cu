@@ -1128,25 +1128,27 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
           alive = false;
           break;
         }
-        // G and its scaled FP32 copy by every warp; then the FP32 inverse X0 by the last W warps (a
+        // G and its scaled FP32 copy by every warp; then the FP32 inverse X0 by W warps from warp 2 on (a
         // chain of pivots on their registers) while the other warps pass grid barrier C and reduce
         // this CTA's rows of M.  The M loads start once the sweep's columns are in registers (block
         // barrier 5): shared loads issued after them queue behind the partials' L2 loads.
         const bool gfast = solver_prepare<MAXR, kGT>(p, L, sm, gs, ds, scp, ne_r, ne_c, 0);
         const int W = (MAXR > 32 && R > 32) ? 2 : 1;
         const int nrest = kGT - 32 * W;
-        if (tid >= nrest) {
+        const bool sweeper = tid >= 64 && tid < 64 + 32 * W;   // warps 2 (and 3)
+        const int rt = tid < 64 ? tid : tid - 32 * W;          // index among the other threads
+        if (sweeper) {
           if (gfast) {
             const uint32_t x0 = (uint32_t)__cvta_generic_to_shared(sm + L.x0);
             const uint32_t piv = (uint32_t)__cvta_generic_to_shared(sm + L.piv);
             bool iok;
             if constexpr (MAXR > 32) {
-              iok = W == 2 ? sweep_regs<2>(x0, x0, R, piv, tid - nrest, 3, 5)
-                           : sweep_regs<1>(x0, x0, R, piv, tid - nrest, 3, 5);
+              iok = W == 2 ? sweep_regs<2>(x0, x0, R, piv, tid - 64, 3, 5)
+                           : sweep_regs<1>(x0, x0, R, piv, tid - 64, 3, 5);
             } else {
-              iok = sweep_regs<1>(x0, x0, R, piv, tid - nrest, 3, 5);
+              iok = sweep_regs<1>(x0, x0, R, piv, tid - 64, 3, 5);
             }
-            if (tid == nrest) s_invbad = iok ? 0 : 1;
+            if (tid == 64) s_invbad = iok ? 0 : 1;
           } else {
             named_arrive(5, kGT);
           }
@@ -1158,7 +1160,7 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
             float2* mrow = reinterpret_cast<float2*>(sm + L.mrow);
             const int i0 = x.c * ms.rpc;
             const int nrows = max(0, min(ms.I, i0 + ms.rpc) - i0);
-            for (int e = tid; e < nrows * R; e += nrest) {   // rows fastest: a column's rows are adjacent in Mpart
+            for (int e = rt; e < nrows * R; e += nrest) {   // rows fastest: a column's rows are adjacent in Mpart
               const int r = nrows > 0 ? e / nrows : 0, li = e - r * nrows;
               const float* src = gs.Mpart + (int64_t)r * ms.I + i0 + li;
               const int64_t sstr = (int64_t)R * ms.I;
@@ -1181,7 +1183,7 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
             // the next update's sampled fibers into L2, while the last warps finish the inverse
             const int nn = n + 1 < N ? n + 1 : 0;
             const uint32_t nt = n + 1 < N ? t : t + 1;
-            prefetch_next<T>(p, x, nn, nt, mode_split(p, nn, x.G, use_tc ? kTM : kTI), use_tc ? kTM : kTI, tid, nrest);
+            prefetch_next<T>(p, x, nn, nt, mode_split(p, nn, x.G, use_tc ? kTM : kTI), use_tc ? kTM : kTI, rt, nrest);
           }
         }
         __syncthreads();
