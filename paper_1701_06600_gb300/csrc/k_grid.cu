@@ -479,9 +479,12 @@ __device__ __forceinline__ void build_pairs(const Prob& p, int n, const uint32_t
   }
 }
 
+// Not inlined: its register allocation then stays apart from the rest of the kernel (1500^3: 164.6 us
+// per outer iteration, against 171.4 with the function inlined).
 template <int MAXR>
-__device__ void gram_partial(const Prob& p, const GridSmem& L, unsigned char* sm, const GridScratch& gs,
-                             const GridCtx& x, int n, uint32_t t, const unsigned char* ne_r, const unsigned char* ne_c) {
+__device__ __noinline__ void gram_partial(const Prob& p, const GridSmem& L, unsigned char* sm, const GridScratch& gs,
+                                          const GridCtx& x, int n, uint32_t t, const unsigned char* ne_r,
+                                          const unsigned char* ne_c) {
   const int tid = threadIdx.x, R = p.R, S = p.S;
   const int NE = R * (R + 1) / 2;
   const int gpc = (S + x.G - 1) / x.G;
