@@ -1183,7 +1183,7 @@ __global__ void __launch_bounds__(kGT, 1) k_grid_run(const Prob* probs, int B, G
               pair_acc2(make_float2(h1, l1), h0, l0);
               mrow[li * R + r] = pair_norm(h0, l0);
             }
-            // the next update's sampled fibers into L2, while the last warps finish the inverse
+            // the next update's sampled fibers into L2, while warps 2-3 finish the inverse
             const int nn = n + 1 < N ? n + 1 : 0;
             const uint32_t nt = n + 1 < N ? t : t + 1;
             prefetch_next<T>(p, x, nn, nt, mode_split(p, nn, x.G, use_tc ? kTM : kTI), use_tc ? kTM : kTI, rt, nrest);
