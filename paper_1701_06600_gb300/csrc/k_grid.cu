@@ -531,7 +531,7 @@ __device__ void contract_units(const Prob& p, const GridSmem& L, unsigned char* 
   static_assert(CW % 4 == 0, "float4 Z loads");
   const int ct = threadIdx.x - kGramT;     // 0 .. kCT-1
   const int ii = ct % kTI, g = ct / kTI;
-  const int R = p.R, N = p.N, ZP = L.ZP;
+  const int R = p.R, ZP = L.ZP;
   uint32_t* ids = reinterpret_cast<uint32_t*>(sm + L.cids);
   int64_t* offs = reinterpret_cast<int64_t*>(sm + L.coffs);
   float* Zf = reinterpret_cast<float*>(sm + L.Zf);
